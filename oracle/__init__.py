@@ -1,0 +1,25 @@
+"""CPU oracle for recycling BiCGSTAB (Ahuja, Benner, de Sturler, Feng).
+
+TEST INFRASTRUCTURE ONLY.  This package is a plain, slow, FP64 restatement of
+the method, written from the paper's definitions so that the CUDA path can be
+checked against it.  Only the test suite, the package's ``smoke()`` check and
+the benchmark's CPU-baseline leg may import it; the solver library never does,
+and it shares no code with the CUDA sources.
+
+Contents
+--------
+shadow     counter-based generator for the random shadow residual r~_{-1}
+           (Alg. 2 step 2): SplitMix64 from its published definition.
+bicgstab   van der Vorst's BiCGSTAB, written separately (the k = 0 baseline).
+rbicgstab  Alg. 2 (RBiCGSTAB) with eq. (3.5) ("minusXR") initial projection,
+           step-1 biorthogonalisation of C and C~, and the cycle store used by
+           the recycle-space update.
+recycle    harmonic Ritz extraction for the recycle-space update between
+           systems, and the mode-S sequence driver.
+dense      small dense helpers used by the pins (principal angles).
+
+Parity status: every function is pinned by a ``-m "not gpu"`` test against a
+closed form, an invariant, brute force (dense LU), a published test vector or
+a value the paper prints (Table 1), except where a docstring says
+"parity unpinned".
+"""
