@@ -1,0 +1,414 @@
+#!/usr/bin/env python3
+"""Benchmark: solves/sec at 1e-8 relative residual, recycled vs plain, on the
+3D 128^3 shifted convection-diffusion sequence (n = 2,097,152, 7-point CSR,
+20 shifts sigma_j in logspace(-2, 2) x 4 Gaussian right-hand sides, k = 20),
+plus the HBM roofline of the dominant fused-iteration kernel.
+
+One step = one pass of the whole hot path over the sequence: for each of the
+20 matrices set the values (Alg. 2 step 1 recycle setup included) and solve
+its 4 right-hand sides with RBiCGSTAB (Alg. 2), updating the recycle space
+during the first solve of each matrix (cycles of s = 25, harmonic Ritz).
+Each step starts from an empty recycle space, so every step does the same
+work.  Inputs (matrix values, right-hand sides) are staged in HBM before the
+timed region; they are larger than L2, so no flush is needed between steps.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
+oracle instead (see --help).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "solves/sec at 1e-8 rel. residual (recycled vs plain); fused-iter HBM GB/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--N", type=int, default=128, help="grid side (n = N^3)")
+    ap.add_argument("--shifts", type=int, default=20)
+    ap.add_argument("--rhs", type=int, default=4)
+    ap.add_argument("--k", type=int, default=20)
+    ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
+    ap.add_argument("--no-plain", action="store_true", help="skip the plain-BiCGSTAB comparison")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--quick", action="store_true", help="small grid for a smoke run (not a bench line)")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.f = None
+
+    def start(self):
+        try:
+            self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [l.strip().split(",") for l in self.f.read().splitlines() if l.strip()]
+        os.unlink(self.f.name)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+                for nm, v in zip(names, r[5:9]):
+                    if v.strip().lower() == "active":
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- roofline model
+def pass_bytes(n: int, z: int, k: int, vb: int = 8, ab: int = 8) -> list:
+    """Algorithmic HBM bytes of passes P1..P5 (CSR with int32 indices, x-gather
+    counted once, every stream touched once)."""
+    A = z * (ab + 4) + 4 * (n + 1)
+    if k > 0:
+        return [A + n * vb * (k + 3), n * vb * (k + 4), A + n * vb * (k + 2), n * vb * (k + 4), 8 * n * vb]
+    return [A + 3 * n * vb, 3 * n * vb, A + 4 * n * vb, 0, 8 * n * vb]
+
+
+def pass_flops(n: int, z: int, k: int) -> list:
+    if k > 0:
+        return [2 * z + 2 * n * (k + 1), 2 * n * (k + 2), 2 * z + 2 * n * k, 2 * n * (k + 4), 10 * n]
+    return [2 * z + 2 * n, 4 * n, 2 * z + 8 * n, 0, 10 * n]
+
+
+def measured_peaks() -> dict:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return {"hbm_gbs": float(d["hbm_gbs"]), "source": "measured"}
+    except Exception:
+        return {"hbm_gbs": 6800.0, "source": "fallback"}
+
+
+def fp64_peak_tflops(torch) -> float:
+    """FP64 dense throughput of this GPU measured with torch (cuBLAS DGEMM)."""
+    a = torch.randn(4096, 4096, dtype=torch.float64, device="cuda")
+    b = torch.randn(4096, 4096, dtype=torch.float64, device="cuda")
+    torch.mm(a, b)
+    torch.cuda.synchronize()
+    best = 1e9
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        torch.mm(a, b)
+        e1.record()
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    return 2 * 4096 ** 3 / (best * 1e-3) / 1e12
+
+
+# ---------------------------------------------------------------- CPU baseline (oracle)
+CPU_SNIPPET = r"""
+import json, os, sys, time
+sys.path.insert(0, {root!r})
+import numpy as np, scipy.sparse as sp
+from paper_1406_2831_gb300 import inputs
+from oracle import rbicgstab as orb
+spec = inputs.config_shifted_3d(N={N}, n_shifts={shifts}, n_rhs=1, k={k})
+P = spec.pattern
+S = sp.csr_matrix((spec.values[0](), P.col, P.row_ptr), shape=(P.n, P.n))
+b = spec.rhs[0][0]()
+U = inputs.random_recycle_basis(P.n, {k}, 11) if {k} else None
+t0 = time.perf_counter(); rec = orb.recycle_setup(S, U) if {k} else None; t_setup = time.perf_counter() - t0
+t0 = time.perf_counter(); orb.rbicgstab(S, b, rec, tol=1e-30, max_itn={its}, true_residual=False)
+t_it = (time.perf_counter() - t0) / {its}
+print(json.dumps({{"t_iter": t_it, "t_setup": t_setup}}))
+"""
+
+
+def cpu_oracle_timing(N, shifts, k, its=10) -> dict:
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    out = subprocess.run([sys.executable, "-c", CPU_SNIPPET.format(root=ROOT, N=N, shifts=shifts, k=k, its=its)],
+                         capture_output=True, text=True, env=env, timeout=900)
+    if out.returncode != 0:
+        raise RuntimeError(out.stderr[-2000:])
+    return json.loads(out.stdout.strip().splitlines()[-1])
+
+
+# ---------------------------------------------------------------- our arm
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_1406_2831_gb300 import inputs
+    from paper_1406_2831_gb300 import rbicgstab as rb
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    N = 48 if args.quick else args.N
+    spec = inputs.config_shifted_3d(N=N, n_shifts=args.shifts, n_rhs=args.rhs, k=args.k)
+    P = spec.pattern
+    n, z = P.n, P.nnz
+    stream = torch.cuda.current_stream(dev)
+    # stage inputs in HBM (and pinned host copies for the end-to-end leg)
+    rp = torch.from_numpy(P.row_ptr).to(dev)
+    col = torch.from_numpy(P.col).to(dev)
+    vals_h = [torch.from_numpy(f()).pin_memory() for f in spec.values]
+    vals_d = [v.to(dev) for v in vals_h]
+    rhs_h = [[torch.from_numpy(g()).pin_memory() for g in row] for row in spec.rhs]
+    rhs_d = [[b.to(dev) for b in row] for row in rhs_h]
+    xbuf = torch.zeros(n, dtype=torch.float64, device=dev)
+    xh = torch.zeros(n, dtype=torch.float64).pin_memory()
+    torch.cuda.synchronize()
+
+    def make(recycled: bool, precision: str):
+        s = rb.Solver(k_max=args.k if recycled else 0, cycle_s=spec.cycle_s,
+                      recycle=("update_first" if precision == "fp64" else "fixed") if recycled else "none",
+                      precision=precision, tol=spec.tol, stream=stream)
+        s.set_matrix(rp, col, vals_d[0])
+        return s
+
+    def sequence(s, recycled: bool, host: bool, log=None):
+        if recycled:
+            s.set_recycle(None)
+        for j in range(len(vals_d)):
+            s.set_values(vals_h[j] if host else vals_d[j])
+            for kk in range(len(rhs_d[j])):
+                if host:
+                    xh.zero_()
+                    r = s.solve(rhs_h[j][kk], xh)
+                else:
+                    xbuf.zero_()
+                    r = s.solve(rhs_d[j][kk], xbuf)
+                if log is not None:
+                    log.append(r.stats)
+                if r.stats["status"] != 0:
+                    raise RuntimeError(f"solve {j},{kk} failed: {r.stats}")
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def timed(s, recycled, host, steps, warmup, clocks=None):
+        for _ in range(warmup):
+            sequence(s, recycled, host)
+        barrier()
+        l0 = rb.kernel_launches()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        if clocks:
+            clocks.start()
+        logs = []
+        e0.record(stream)
+        for _ in range(steps):
+            sequence(s, recycled, host, logs)
+        e1.record(stream)
+        barrier()
+        ck = clocks.stop() if clocks else None
+        ms = e0.elapsed_time(e1)
+        if dist is not None:
+            t = torch.tensor([ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms, logs, rb.kernel_launches() - l0, ck
+
+    solves_per_step = sum(len(r) for r in rhs_d)
+    res = {}
+    # recycled (headline)
+    s_rec = make(True, args.precision)
+    ms, logs, launches, clk = timed(s_rec, True, False, args.steps, args.warmup, ClockSampler(local))
+    res["rec"] = dict(ms=ms, logs=logs, launches=launches, clocks=clk)
+    # roofline of the dominant pass (CUDA events around each pass on this stream)
+    s_rec.set_values(vals_d[0])
+    rb_reps = 10
+    ms_pass, code = rb.time_passes(s_rec, rhs_d[0][0], reps=rb_reps)
+    k_used = s_rec.get_recycle()[0].shape[1]
+    if args.precision == "fp64":
+        pb = pass_bytes(n, z, k_used)
+        pf = pass_flops(n, z, k_used)
+    else:
+        pb = pass_bytes(n, z, k_used, vb=4, ab=4)
+        pf = pass_flops(n, z, k_used)
+    del s_rec
+    # plain FP64 BiCGSTAB on the same sequence
+    if not args.no_plain:
+        s_pl = make(False, "fp64")
+        msp, logp, _, _ = timed(s_pl, False, False, max(1, args.steps // 2), 1)
+        res["plain"] = dict(ms=msp, logs=logp, steps=max(1, args.steps // 2))
+        ms_pass_plain, _ = rb.time_passes(s_pl, rhs_d[0][0], reps=rb_reps)
+        del s_pl
+    # end to end through the public API with pinned host buffers
+    if not args.no_e2e:
+        s_e = make(True, args.precision)
+        mse, loge, _, _ = timed(s_e, True, True, 1, 1)
+        res["e2e"] = dict(ms=mse)
+        del s_e
+    peak_fp64 = fp64_peak_tflops(torch)
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return None
+
+    peaks = measured_peaks()
+    logs = res["rec"]["logs"]
+    iters = [l["iters"] for l in logs]
+    ms_step = res["rec"]["ms"] / args.steps
+    value = solves_per_step * args.steps * world / (res["rec"]["ms"] * 1e-3)
+    dom = int(np.argmax(ms_pass))
+    gbs = pb[dom] / (ms_pass[dom] * 1e-3) / 1e9
+    gfs = pf[dom] / (ms_pass[dom] * 1e-3) / 1e9
+    hbm_frac = gbs / peaks["hbm_gbs"]
+    alu_frac = gfs / (peak_fp64 * 1e3) if args.precision == "fp64" else 0.0
+    iter_ms = float(sum(ms_pass))
+    iter_gbs = sum(pb) / (iter_ms * 1e-3) / 1e9
+    roof = {"bound": "hbm" if hbm_frac >= alu_frac else "alu", "kernel": f"P{dom + 1}",
+            "achieved": round(gbs, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": round(hbm_frac, 4), "traffic": None,
+            "peak_source": peaks["source"],
+            "fp64_alu": {"achieved_tflops": round(gfs / 1e3, 4), "peak_tflops": round(peak_fp64, 3),
+                         "frac": round(alu_frac, 4), "peak_source": "measured (torch float64 matmul)"},
+            "passes_ms": [round(v, 5) for v in ms_pass], "passes_bytes": pb,
+            "iteration": {"ms": round(iter_ms, 5), "GB/s": round(iter_gbs, 1),
+                          "frac": round(iter_gbs / peaks["hbm_gbs"], 4)}}
+    line = {
+        "metric": METRIC, "value": round(value, 3), "unit": "solves/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if args.precision == "fp64" else "f32-inner/f64-refined",
+        "data": "synthetic (seeded stencil systems and Gaussian right-hand sides)",
+        "config": {"workload": f"3d-7pt-conv-diff-{N}^3-shifted", "n": n, "nnz": z,
+                   "shifts": args.shifts, "rhs_per_shift": args.rhs, "k": args.k, "cycle_s": spec.cycle_s,
+                   "tol": spec.tol, "recycle": "update on first RHS of each matrix (harmonic Ritz)",
+                   "precision": args.precision, "parallelism": f"replicas x{world}",
+                   "l2": "inputs larger than L2 (no flush)"},
+        "recycled": {"solves_per_s": round(value, 3), "iters_mean": round(statistics.mean(iters), 2),
+                     "iters_total": int(sum(iters)), "matvecs": int(sum(l["matvecs"] for l in logs)),
+                     "matvecs_setup": int(sum(l["matvecs_setup"] for l in logs))},
+        "roofline": roof,
+        "gpu_launches": int(res["rec"]["launches"]),
+        "clocks": res["rec"]["clocks"],
+    }
+    if "plain" in res:
+        lp = res["plain"]["logs"]
+        itp = [l["iters"] for l in lp]
+        vp = solves_per_step * res["plain"]["steps"] * world / (res["plain"]["ms"] * 1e-3)
+        line["plain_fp64"] = {"solves_per_s": round(vp, 3), "iters_mean": round(statistics.mean(itp), 2),
+                              "matvecs": int(sum(l["matvecs"] for l in lp)), "steps": res["plain"]["steps"],
+                              "passes_ms": [round(v, 5) for v in ms_pass_plain]}
+        line["recycled_over_plain"] = round(value / vp, 4)
+    if "e2e" in res:
+        Bi = (len(vals_h) * z * 8 + solves_per_step * n * 8) * 1 + solves_per_step * n * 8
+        Bo = solves_per_step * n * 8
+        line["e2e"] = {"value": round(solves_per_step * world / (res["e2e"]["ms"] * 1e-3), 3), "unit": "solves/s",
+                       "h2d_bytes_per_step": int(Bi), "d2h_bytes_per_step": int(Bo)}
+    if not args.no_cpu_baseline and world >= 1:
+        try:
+            cb = cpu_oracle_timing(N, args.shifts, args.k)
+            mean_it = statistics.mean(iters)
+            v = 1.0 / (cb["t_iter"] * mean_it + cb["t_setup"] / args.rhs)
+            line["cpu_baseline"] = {"value": round(v, 5), "unit": "solves/s", "cores": 1, "kind": "oracle",
+                                    "sample": f"oracle Alg. 2 (k={args.k}, fixed recycle space) on system 1 "
+                                              f"of the sequence at full size: setup + 10 iterations timed, "
+                                              f"extrapolated to {mean_it:.1f} iterations per solve "
+                                              f"(the GPU run's mean); recycle-update cost not included"}
+        except Exception as e:  # report, do not fail the bench line
+            line["cpu_baseline"] = {"value": None, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                                    "sample": f"failed: {str(e)[:200]}"}
+    if dist is not None:
+        dist.destroy_process_group()
+    return line
+
+
+# ---------------------------------------------------------------- reference arm (the oracle)
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return None
+    N = 48 if args.quick else args.N
+    import numpy as np
+    its = 10
+    samples = []
+    t_start = time.perf_counter()
+    for step in range(args.warmup + args.steps):
+        cb = cpu_oracle_timing(N, args.shifts, args.k, its=its)
+        if step >= args.warmup:
+            samples.append(cb)
+    wall = time.perf_counter() - t_start
+    t_it = statistics.mean(s["t_iter"] for s in samples)
+    t_setup = statistics.mean(s["t_setup"] for s in samples)
+    # iterations per solve: the oracle's own count on this sequence, if stored
+    mean_it = None
+    fx = os.path.join(ROOT, "tests", "golden", f"oracle_iters_shifted3d_{N}.txt")
+    if os.path.exists(fx):
+        vals = [float(l) for l in open(fx) if l.strip() and not l.startswith("#")]
+        mean_it = statistics.mean(vals)
+    if mean_it is None:
+        mean_it = 100.0
+    value = 1.0 / (t_it * mean_it + t_setup / args.rhs)
+    return {"impl": "reference", "metric": METRIC, "value": round(value, 5), "unit": "solves/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(1e3 * (t_it * its + t_setup), 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"3d-7pt-conv-diff-{N}^3-shifted", "k": args.k, "tol": 1e-8},
+            "cpu_baseline": {"value": round(value, 5), "unit": "solves/s", "cores": 1, "kind": "oracle",
+                             "sample": f"per step: oracle Alg. 2 (k={args.k}) setup + {its} iterations on "
+                                       f"system 1 at full size, extrapolated to {mean_it:.1f} iterations/solve"},
+            "e2e": {"value": round(value, 5), "unit": "solves/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0},
+            "wall_s": round(wall, 1)}
+
+
+def main():
+    args = parse()
+    line = run_reference(args) if args.impl == "reference" else run_ours(args)
+    if line is not None:
+        print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,178 @@
+/*
+ * rbicgstab.h -- C ABI of the GB300 recycling-BiCGSTAB library (librbicgstab.so).
+ *
+ * The library solves sequences of sparse non-symmetric systems
+ *     A^(iota) x^(iota,kappa) = b^(iota,kappa)                      (Sec. 1, eq. (1.1))
+ * with Alg. 2 (RBiCGSTAB, Sec. 4) on one CUDA device, carrying a recycle space
+ * U (and U~) from one system to the next (Sec. 3, definition of C = A U,
+ * C~ = A^T U~).  Plain BiCGSTAB is the same solver with an empty recycle space.
+ *
+ * Conventions for every entry point
+ *   - Return value: RB_OK (0) on success, a warning (> 0) or an error (< 0);
+ *     rbicgstab_error_string() names it.  On an error nothing the caller owns
+ *     is modified except where stated.
+ *   - `where` says where caller pointers live: RB_HOST (pageable or pinned host
+ *     memory) or RB_DEVICE (device memory on the handle's device).
+ *   - Every setter COPIES its inputs into library-owned device memory; no
+ *     caller pointer is retained after the call returns.
+ *   - Calls are ordered on opts.cuda_stream (NULL = the legacy default stream)
+ *     and synchronise that stream before returning.
+ *   - A handle is not thread-safe; separate handles are independent.
+ *   - Matrices are CSR with int32 row pointers and column indices (0-based;
+ *     column indices need not be sorted) and float64 values; n, nnz < 2^31.
+ *   - Dense n x k blocks (U, U~) are column-major with leading dimension
+ *     ld >= n.
+ */
+#ifndef RBICGSTAB_H
+#define RBICGSTAB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------- */
+#define RB_OK                 0
+#define RB_WRECYCLE_RANK      1   /* warning: C~^T C numerically singular, k reduced */
+#define RB_EINVAL            -1   /* bad argument (NULL pointer, bad enum, k too large) */
+#define RB_EDIM              -2   /* dimension mismatch / no matrix set */
+#define RB_EBADCSR           -3   /* malformed CSR (row_ptr not monotone, column out of range) */
+#define RB_ENONFINITE        -4   /* NaN or Inf in an input */
+#define RB_ENOMEM            -5   /* device allocation failed */
+#define RB_ECUDA             -6   /* a CUDA runtime call failed */
+#define RB_ENOTCONV          -7   /* max_itn reached; x holds the last iterate */
+#define RB_EBREAKDOWN_RHO    -8   /* (r~_0, r) = 0 or (r~_0, q) = 0 after redraws (Alg. 2 step 3) */
+#define RB_EBREAKDOWN_OMEGA  -9   /* (t, t) = 0 with s != 0, or omega = 0 */
+#define RB_ETIMEOUT         -10   /* a bounded device-side wait expired */
+
+/* ---- enums --------------------------------------------------------------- */
+#define RB_HOST    0
+#define RB_DEVICE  1
+
+#define RB_FP64    0   /* FP64 storage and arithmetic throughout */
+#define RB_MIXED   1   /* FP32 inner RBiCGSTAB + FP64 iterative refinement */
+
+#define RB_RECYCLE_NONE          0  /* plain BiCGSTAB (U ignored) */
+#define RB_RECYCLE_FIXED         1  /* use U, U~ as given; never change them */
+#define RB_RECYCLE_UPDATE_FIRST  2  /* update U during the first solve after each set_matrix */
+#define RB_RECYCLE_UPDATE_ALL    3  /* update U during every solve */
+
+#define RB_KMAX  64   /* largest supported recycle dimension */
+
+typedef struct rb_ctx* rb_handle;
+
+/* Options (copied at create).  Zero fields take the stated defaults. */
+typedef struct {
+  int32_t  k_max;          /* recycle dimension k (Sec. 6.2 uses 20); 0..RB_KMAX       */
+  int32_t  cycle_s;        /* cycle length s of the recycle update (Sec. 6.2: 25); 0->25 */
+  int32_t  max_itn;        /* iteration cap (Alg. 2 step 5); 0 -> min(n, 20000)        */
+  int32_t  precision;      /* RB_FP64 or RB_MIXED                                      */
+  int32_t  recycle_mode;   /* RB_RECYCLE_*                                             */
+  int32_t  update_cycles;  /* cycles per solve that update U; 0 = every cycle          */
+  int32_t  poll;           /* iterations per host convergence check; 0 = automatic     */
+  int32_t  reserved;
+  double   tol;            /* relative residual tolerance ||r|| <= tol ||b||; 0->1e-8  */
+  uint64_t shadow_seed;    /* SplitMix64 seed of r~_{-1} (Alg. 2 step 2); 0 -> 0x5EED  */
+  void*    cuda_stream;    /* cudaStream_t the calls are ordered on (NULL = default)   */
+} rb_opts;
+
+/* Per-solve statistics. */
+typedef struct {
+  int32_t iters;           /* Alg. 2 iterations (a half step counts as one)            */
+  int32_t status;          /* same code the call returned                              */
+  int32_t k_used;          /* recycle columns in use after biorthogonalisation         */
+  int32_t seeds_used;      /* shadow draws (1 unless (r_0, r~_0) = 0 forced a redraw)  */
+  int64_t matvecs;         /* A-products inside the iteration (2 per iteration)        */
+  int64_t matvecs_setup;   /* columns of C = A U and C~ = A^T U~ formed for this solve */
+  int64_t matvecs_check;   /* true-residual products                                   */
+  int32_t cycles;          /* recycle-update cycles performed                          */
+  int32_t outer;           /* refinement steps (RB_MIXED), else 1                      */
+  double  relres_rec;      /* ||r_i|| / ||b|| of the recursive residual                */
+  double  relres_true;     /* ||b - A x|| / ||b|| recomputed in FP64 after step 8      */
+  double  ms_total;        /* wall time of the call (CUDA events)                      */
+  double  bytes_model;     /* algorithmic HBM bytes of the iterations                  */
+} rb_stats;
+
+/* Create a solver handle on the current CUDA device.  *h receives the handle.
+ * Errors: RB_EINVAL (NULL or out-of-range option), RB_ECUDA, RB_ENOMEM. */
+int rbicgstab_create(rb_handle* h, const rb_opts* opts);
+
+/* Release every device resource of the handle.  NULL is accepted. */
+int rbicgstab_destroy(rb_handle h);
+
+/* Set the system matrix A^(iota) (Sec. 1, eq. (1.1)): CSR, n rows, nnz entries.
+ * The matrix is validated on the device (monotone row_ptr, 0 <= col < n,
+ * finite values), re-laid out as SELL-32 slices, and its transpose is built
+ * (needed for C~ = A^T U~).  An existing recycle space U, U~ is kept and its
+ * C, C~, D_c are recomputed for the new matrix (Alg. 2 step 1).
+ * Errors: RB_EINVAL, RB_EBADCSR, RB_ENONFINITE, RB_ENOMEM, RB_ECUDA. */
+int rbicgstab_set_matrix(rb_handle h, int64_t n, int64_t nnz, const int32_t* row_ptr,
+                         const int32_t* col, const double* val, int where);
+
+/* Replace only the values of the current matrix (same pattern, same order as
+ * the last set_matrix call).  Cheaper than set_matrix for sequences such as
+ * A^(i) = A0 + sigma_i A1 (Sec. 6.1).  Errors: RB_EDIM (no matrix), RB_ENONFINITE. */
+int rbicgstab_set_values(rb_handle h, const double* val, int where);
+
+/* Set the recycle space (Sec. 3): U (n x k) and U~ (n x k; NULL means U~ = U,
+ * the right-only variant of Sec. 5), column-major with leading dimension ld.
+ * Forms C = A U, C~ = A^T U~, biorthogonalises them by an SVD of C~^T C
+ * (so D_c = C~^T C is diagonal and positive) and forms C-hat = C~ D_c^{-1}
+ * (Alg. 2 step 1, eq. (3.4)).  k = 0 clears the space.  Needs a matrix.
+ * Returns RB_WRECYCLE_RANK when columns were dropped (k_used < k).
+ * Errors: RB_EINVAL (k > k_max), RB_EDIM, RB_ENONFINITE. */
+int rbicgstab_set_recycle(rb_handle h, int32_t k, const double* U, const double* Ut,
+                          int64_t ld, int where);
+
+/* Copy the current (biorthogonalised) recycle space out: *k receives k_used;
+ * U and Ut (either may be NULL) receive n x k_used column-major blocks with
+ * leading dimension ld.  Errors: RB_EINVAL. */
+int rbicgstab_get_recycle(rb_handle h, int32_t* k, double* U, double* Ut, int64_t ld,
+                          int where);
+
+/* Solve A x = b with Alg. 2 using the current recycle space.  x holds the
+ * initial guess x_{-1} on entry (Alg. 2 step 2) and the solution on return
+ * (step 8: x = x - U x_c).  In the RB_RECYCLE_UPDATE_* modes the recycle
+ * space is replaced by the harmonic-Ritz update built from this solve.
+ * st may be NULL.  On RB_ENOTCONV / RB_EBREAKDOWN_* x holds the last iterate.
+ * Errors: RB_EDIM (no matrix), RB_ENONFINITE (NaN/Inf in b or x), RB_ECUDA. */
+int rbicgstab_solve(rb_handle h, const double* b, double* x, int where, rb_stats* st);
+
+/* y = A v (transpose = 0) or y = A^T v (transpose = 1) with the library's
+ * FP64 SpMV kernels; v and y have n entries.  Errors: RB_EDIM, RB_EINVAL. */
+int rbicgstab_apply(rb_handle h, const double* v, double* y, int transpose, int where);
+
+/* Harmonic-Ritz selection on the host (the small dense step of the recycle
+ * update, run between cycles of s iterations, Sec. 6.2): given G = Z^T Z and
+ * H = Z^T W (m x m, column-major) for a subspace W with Z = A W, return in Y
+ * (m x k, column-major, ld = m) the coefficients of the k harmonic Ritz
+ * vectors of smallest |theta| (G y = theta H y), a complex pair as
+ * [Re y, Im y], and their values in theta_re/theta_im (k each, may be NULL).
+ * *k_used receives the number of columns written.  Pure host code; needs no
+ * device.  Errors: RB_EINVAL. */
+int rbicgstab_harmonic_ritz(int32_t m, const double* G, const double* H, int32_t k,
+                            double* Y, double* theta_re, double* theta_im, int32_t* k_used);
+
+/* Benchmark helper: run `reps` iterations of the fused passes from a fresh
+ * start on right-hand side b (x_{-1} = 0, convergence test disabled), each
+ * pass launched on its own between CUDA events on the handle's stream, and
+ * write the average duration in milliseconds of passes P1..P5 to ms[0..4]
+ * (ms[3] = 0 when k = 0: plain BiCGSTAB has no separate P4).  The iterate is
+ * left in an unspecified state; call rbicgstab_solve afterwards as usual.
+ * Returns a breakdown code if the iteration broke down during timing.
+ * Errors: RB_EINVAL (reps outside 1..1000), RB_EDIM. */
+int rbicgstab_time_passes(rb_handle h, const double* b, int where, int32_t reps, double* ms);
+
+/* Number of CUDA kernels this library has launched in the process so far
+ * (each graph replay adds the kernels its graph holds).  Thread-safe. */
+long long rbicgstab_kernel_launches(void);
+
+/* Name of a status code (static string). */
+const char* rbicgstab_error_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RBICGSTAB_H */

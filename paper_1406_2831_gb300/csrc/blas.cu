@@ -1,0 +1,322 @@
+// Generic FP64 kernels used outside the fused iteration: the setup of a
+// solve (eq. (3.5)), the end of a solve (Alg. 2 step 8 and the true
+// residual), and the recycle-space work (Gram matrices, block updates).
+// All reductions are deterministic (fixed trees, no floating-point atomics).
+#include <algorithm>
+
+#include "device.cuh"
+#include "kernels.h"
+
+namespace rb {
+
+// ---------------------------------------------------------------- dots
+template <int KMAX>
+__global__ void __launch_bounds__(kBlock) k_dots(DotArgs d, int64_t npad, IterState* st, double* partials) {
+  constexpr int NV = KMAX + 4;
+  __shared__ ReduceSmem<NV> sm;
+  double acc[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) acc[v] = 0.0;
+  for (int64_t i = gtid(); i < npad; i += gstride()) {
+    if (d.M) {
+      const double vi = d.v[i];
+#pragma unroll
+      for (int j = 0; j < KMAX; ++j)
+        if (j < d.km) acc[j] = fma(d.M[j * d.ld + i], vi, acc[j]);
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      if (q < d.nd) acc[KMAX + q] = fma(d.a[q][i], d.b[q][i], acc[KMAX + q]);
+  }
+  if (block_reduce_last<NV>(acc, sm, partials, &st->ticket[PGEN])) {
+    if (threadIdx.x < d.km) st->red[threadIdx.x] = sm.res[threadIdx.x];
+    if (threadIdx.x < d.nd) st->red[d.km + threadIdx.x] = sm.res[KMAX + threadIdx.x];
+  }
+}
+
+cudaError_t dots(const DotArgs& d, int64_t npad, IterState* st, double* partials, int grid,
+                 cudaStream_t s) {
+  count_launches(1);
+  const int km = d.M ? d.km : 0;
+  DotArgs dd = d;
+  dd.km = km;
+  switch (kmax_bucket(km)) {
+    case 0: k_dots<0><<<grid, kBlock, 0, s>>>(dd, npad, st, partials); break;
+    case 8: k_dots<8><<<grid, kBlock, 0, s>>>(dd, npad, st, partials); break;
+    case 16: k_dots<16><<<grid, kBlock, 0, s>>>(dd, npad, st, partials); break;
+    case 32: k_dots<32><<<grid, kBlock, 0, s>>>(dd, npad, st, partials); break;
+    default: k_dots<64><<<grid, kBlock, 0, s>>>(dd, npad, st, partials); break;
+  }
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- y += sign M c
+__global__ void k_gemv_update(double* __restrict__ y, const double* __restrict__ M, int64_t ld, int k,
+                              const double* __restrict__ c, const double* __restrict__ cs,
+                              double sign, int64_t npad) {
+  __shared__ double cc[kMaxK];
+  if (threadIdx.x < k) cc[threadIdx.x] = sign * c[threadIdx.x] * (cs ? cs[threadIdx.x] : 1.0);
+  __syncthreads();
+  for (int64_t i = gtid(); i < npad; i += gstride()) {
+    double acc = 0.0;
+    for (int j = 0; j < k; ++j) acc = fma(M[j * ld + i], cc[j], acc);
+    y[i] += acc;
+  }
+}
+
+cudaError_t gemv_update(double* y, const double* M, int64_t ld, int k, const double* c,
+                        const double* c_scale, double sign, int64_t npad, int grid,
+                        cudaStream_t s) {
+  count_launches(1);
+  if (k <= 0) return cudaSuccess;
+  k_gemv_update<<<grid, kBlock, 0, s>>>(y, M, ld, k, c, c_scale, sign, npad);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- block GEMM
+// Out(:, c) = X R(:, c): each thread owns one row, reads the m entries of
+// X's row once and forms all kc outputs (kc <= kMaxK).
+__global__ void k_gemm_cols(double* const* __restrict__ out, const double* const* __restrict__ X, int m,
+                            const double* __restrict__ R, int kc, int64_t npad) {
+  extern __shared__ double sR[];   // m * kc
+  for (int e = threadIdx.x; e < m * kc; e += blockDim.x) sR[e] = R[e];
+  __syncthreads();
+  double acc[kMaxK];
+  for (int64_t i = gtid(); i < npad; i += gstride()) {
+    for (int c = 0; c < kc; ++c) acc[c] = 0.0;
+    for (int j = 0; j < m; ++j) {
+      const double xv = X[j][i];
+      for (int c = 0; c < kc; ++c) acc[c] = fma(xv, sR[j + c * m], acc[c]);
+    }
+    for (int c = 0; c < kc; ++c) out[c][i] = acc[c];
+  }
+}
+
+cudaError_t gemm_cols(double* const* out, const double* const* X, int m, const double* R,
+                      int kc, int64_t npad, int grid, cudaStream_t s) {
+  count_launches(1);
+  if (kc <= 0 || m <= 0) return cudaSuccess;
+  const size_t smem = sizeof(double) * (size_t)m * kc;
+  if (smem > 48 * 1024)
+    cudaFuncSetAttribute(k_gemm_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_gemm_cols<<<grid, kBlock, smem, s>>>(out, X, m, R, kc, npad);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- Gram X^T Y
+// Each block walks row tiles of 32 rows, stages X and Y tiles in shared
+// memory, and accumulates the (a, b) products it owns; block partials are
+// reduced in block order by a second kernel.
+constexpr int kGramRows = 32;
+
+__global__ void __launch_bounds__(kBlock) k_gram(const double* const* __restrict__ X, int mx,
+                                                const double* const* __restrict__ Y, int my,
+                                                int64_t npad, double* __restrict__ work) {
+  extern __shared__ double sm[];
+  double* sx = sm;                        // kGramRows * mx
+  double* sy = sm + kGramRows * mx;       // kGramRows * my
+  const int nout = mx * my;
+  const int per = (nout + blockDim.x - 1) / blockDim.x;   // outputs per thread (<= 32)
+  double acc[32];
+  for (int u = 0; u < per; ++u) acc[u] = 0.0;
+  const int64_t ntiles = (npad + kGramRows - 1) / kGramRows;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int64_t r0 = tile * kGramRows;
+    __syncthreads();
+    for (int e = threadIdx.x; e < kGramRows * mx; e += blockDim.x) {
+      const int a = e / kGramRows, rr = e % kGramRows;
+      sx[rr * mx + a] = (r0 + rr < npad) ? X[a][r0 + rr] : 0.0;
+    }
+    for (int e = threadIdx.x; e < kGramRows * my; e += blockDim.x) {
+      const int b = e / kGramRows, rr = e % kGramRows;
+      sy[rr * my + b] = (r0 + rr < npad) ? Y[b][r0 + rr] : 0.0;
+    }
+    __syncthreads();
+    for (int u = 0; u < per; ++u) {
+      const int o = threadIdx.x + u * blockDim.x;
+      if (o < nout) {
+        const int a = o % mx, b = o / mx;
+        double s = acc[u];
+#pragma unroll 8
+        for (int rr = 0; rr < kGramRows; ++rr) s = fma(sx[rr * mx + a], sy[rr * my + b], s);
+        acc[u] = s;
+      }
+    }
+  }
+  for (int u = 0; u < per; ++u) {
+    const int o = threadIdx.x + u * blockDim.x;
+    if (o < nout) work[(size_t)blockIdx.x * nout + o] = acc[u];
+  }
+}
+
+__global__ void k_gram_reduce(const double* __restrict__ work, int nblocks, int nout, double* out) {
+  for (int o = blockIdx.x * blockDim.x + threadIdx.x; o < nout; o += gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int b = 0; b < nblocks; ++b) s += work[(size_t)b * nout + o];
+    out[o] = s;
+  }
+}
+
+cudaError_t gram(const double* const* X, int mx, const double* const* Y, int my, int64_t npad,
+                 double* out, double* work, int grid, cudaStream_t s) {
+  count_launches(2);
+  if (mx <= 0 || my <= 0) return cudaSuccess;
+  if (mx * my > 32 * kBlock) return cudaErrorInvalidValue;
+  const size_t smem = sizeof(double) * kGramRows * (size_t)(mx + my);
+  if (smem > 48 * 1024)
+    cudaFuncSetAttribute(k_gram, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_gram<<<grid, kBlock, smem, s>>>(X, mx, Y, my, npad, work);
+  const int nout = mx * my;
+  k_gram_reduce<<<(nout + kBlock - 1) / kBlock, kBlock, 0, s>>>(work, grid, nout, out);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- shadow r~_{-1}
+// SplitMix64 (Steele, Lea, Flood 2014), output i from state `seed`:
+// z = seed + (i+1)*golden gamma; two xor-shift-multiply rounds; final xor-shift.
+__device__ __forceinline__ uint64_t splitmix64_at(uint64_t seed, uint64_t i) {
+  uint64_t z = seed + (i + 1ull) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+__global__ void k_shadow(double* rt, int64_t n, int64_t npad, uint64_t seed) {
+  for (int64_t i = gtid(); i < npad; i += gstride()) {
+    if (i < n) {
+      const uint64_t z = splitmix64_at(seed, (uint64_t)i);
+      const double u = (double)(z >> 11) * 0x1.0p-53;
+      rt[i] = 2.0 * u - 1.0;
+    } else {
+      rt[i] = 0.0;
+    }
+  }
+}
+
+cudaError_t shadow(double* rt, int64_t n, int64_t npad, uint64_t seed, cudaStream_t s) {
+  count_launches(1);
+  int g = (int)std::min<int64_t>((npad + kBlock - 1) / kBlock, 8192);
+  k_shadow<<<g, kBlock, 0, s>>>(rt, n, npad, seed);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- column scaling
+__global__ void k_scale_cols(double* M, int64_t ld, int k, const double* f, int64_t npad) {
+  for (int64_t i = gtid(); i < npad; i += gstride())
+    for (int j = 0; j < k; ++j) M[j * ld + i] *= f[j];
+}
+
+cudaError_t scale_cols(double* M, int64_t ld, int k, const double* f, int64_t npad,
+                       cudaStream_t s) {
+  count_launches(1);
+  if (k <= 0) return cudaSuccess;
+  int g = (int)std::min<int64_t>((npad + kBlock - 1) / kBlock, 8192);
+  k_scale_cols<<<g, kBlock, 0, s>>>(M, ld, k, f, npad);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- residual
+__global__ void __launch_bounds__(kBlock) k_residual(Sell<double> A, const double* __restrict__ b,
+                                                    const double* __restrict__ x, double* __restrict__ r,
+                                                    IterState* st, double* partials) {
+  __shared__ ReduceSmem<1> sm;
+  double acc[1] = {0.0};
+  const int lane = threadIdx.x & 31;
+  const int64_t w0 = gtid() >> 5, nw = gstride() >> 5;
+  for (int64_t sl = w0; sl < A.nslices; sl += nw) {
+    const int64_t row = sl * kSlice + lane;
+    const int w = A.width[sl];
+    const int64_t base = A.slice_ptr[sl] + lane;
+    double y = 0.0;
+    for (int j = 0; j < w; ++j) {
+      const int64_t e = base + (int64_t)j * kSlice;
+      y = fma(A.val[e], x[A.col[e]], y);
+    }
+    const double rv = b[row] - y;
+    r[row] = rv;
+    acc[0] = fma(rv, rv, acc[0]);
+  }
+  if (block_reduce_last<1>(acc, sm, partials, &st->ticket[PGEN]) && threadIdx.x == 0)
+    st->red[0] = sm.res[0];
+}
+
+cudaError_t residual_norm(const Sell<double>& A, const double* b, const double* x, double* r,
+                          int64_t npad, IterState* st, double* partials, int grid,
+                          cudaStream_t s) {
+  count_launches(1);
+  k_residual<<<grid, kBlock, 0, s>>>(A, b, x, r, st, partials);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- misc
+__global__ void k_finite(const double* v, int64_t n, int* flag) {
+  for (int64_t i = gtid(); i < n; i += gstride())
+    if (!isfinite(v[i])) atomicMax(flag, 1);
+}
+
+cudaError_t check_finite(const double* v, int64_t n, int* flag, cudaStream_t s) {
+  count_launches(1);
+  cudaMemsetAsync(flag, 0, sizeof(int), s);
+  if (n == 0) return cudaGetLastError();
+  int g = (int)std::min<int64_t>((n + kBlock - 1) / kBlock, 8192);
+  k_finite<<<g, kBlock, 0, s>>>(v, n, flag);
+  return cudaGetLastError();
+}
+
+__global__ void k_to_float(const double* in, float* out, int64_t n) {
+  for (int64_t i = gtid(); i < n; i += gstride()) out[i] = (float)in[i];
+}
+cudaError_t to_float(const double* in, float* out, int64_t n, cudaStream_t s) {
+  count_launches(1);
+  int g = (int)std::min<int64_t>((n + kBlock - 1) / kBlock, 8192);
+  if (n > 0) k_to_float<<<g, kBlock, 0, s>>>(in, out, n);
+  return cudaGetLastError();
+}
+
+__global__ void k_add_f2d(double* x, const float* d, int64_t n) {
+  for (int64_t i = gtid(); i < n; i += gstride()) x[i] += (double)d[i];
+}
+cudaError_t add_float_to_double(double* x, const float* d, int64_t n, cudaStream_t s) {
+  count_launches(1);
+  int g = (int)std::min<int64_t>((n + kBlock - 1) / kBlock, 8192);
+  if (n > 0) k_add_f2d<<<g, kBlock, 0, s>>>(x, d, n);
+  return cudaGetLastError();
+}
+
+// st->red holds [C^T r~_0 (k), (r~_0, r_0), (r_0, r_0)] from the last dots()
+// call; st->bnorm2 was set before.  Converged-at-start and rho_0 = 0 are
+// flagged for the host.
+__global__ void k_init_state(IterState* st, int k, double tol, int max_itn) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  for (int j = 0; j < k; ++j) {
+    st->cr[j] = st->red[j];
+    st->xc[j] = 0.0;
+  }
+  st->k = k;
+  st->rho = st->red[k];
+  st->rnorm2 = st->red[k + 1];
+  st->thresh2 = tol * tol * st->bnorm2;
+  st->alpha = st->omega = st->beta = 0.0;
+  st->iter = 0;
+  st->half = 0;
+  st->max_itn = max_itn;
+  st->status = RB_OK;
+  st->done = 0;
+  if (!isfinite(st->rnorm2) || !isfinite(st->rho)) {
+    st->status = RB_ENONFINITE;
+    st->done = 1;
+  } else if (st->rnorm2 <= st->thresh2) {
+    st->done = 1;
+  } else if (st->rho == 0.0) {
+    st->status = RB_EBREAKDOWN_RHO;
+    st->done = 1;
+  }
+}
+
+cudaError_t init_state(IterState* st, int k, double tol, int max_itn, cudaStream_t s) {
+  count_launches(1);
+  k_init_state<<<1, 32, 0, s>>>(st, k, tol, max_itn);
+  return cudaGetLastError();
+}
+
+}  // namespace rb

@@ -1,0 +1,70 @@
+// Internal definitions shared by the CUDA translation units of librbicgstab.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstdio>
+
+#include "../../include/rbicgstab.h"
+
+namespace rb {
+
+constexpr int kSlice = 32;        // SELL slice height = warp width
+constexpr int kBlock = 256;       // threads per block of the streaming kernels
+constexpr int kMaxK = RB_KMAX;
+constexpr int kMaxNV = kMaxK + 8; // values one fused reduction may carry
+
+// SELL-32 view of a sparse matrix: slice `sl` holds rows sl*32 .. sl*32+31;
+// entry j of row sl*32+lane sits at slice_ptr[sl] + j*32 + lane.  Padding
+// entries have val = 0 and col = the row itself.
+template <typename T>
+struct Sell {
+  const int64_t* slice_ptr;  // [nslices + 1]
+  const int32_t* width;      // [nslices]
+  const int32_t* col;
+  const T* val;
+  int64_t nslices;
+};
+
+// Solver state that lives on the device between kernels of one solve.  The
+// last block of each fused pass reduces the block partials in a fixed order
+// and updates these scalars (Alg. 2 step 6).
+struct IterState {
+  double rho;      // (r~_0, r_{i-1})
+  double alpha, omega, beta;
+  double rtq;      // (r~_0, q_i)
+  double snorm2, rnorm2;
+  double thresh2;  // (tol ||b||)^2
+  double st, tt, rts, rtt;
+  double bnorm2;
+  int32_t iter;     // completed iterations
+  int32_t done;     // 1 once converged / failed: every later pass returns at once
+  int32_t half;     // the current iteration ended after its half step
+  int32_t status;   // RB_* code
+  int32_t max_itn;
+  int32_t k;
+  int32_t pad0, pad1;
+  double zeta[kMaxK];
+  double gamma[kMaxK];
+  double xc[kMaxK];
+  double cr[kMaxK];    // C^T r~_0 (zero in exact arithmetic)
+  double red[kMaxNV];  // scratch for generic reductions
+  unsigned int ticket[8];
+};
+
+// Pass identifiers (index into IterState::ticket).
+enum Pass { P1 = 0, P2 = 1, P3 = 2, P4 = 3, P5 = 4, PGEN = 5 };
+
+}  // namespace rb
+
+#define RB_CUDA_TRY(expr)                                                          \
+  do {                                                                             \
+    cudaError_t _e = (expr);                                                       \
+    if (_e != cudaSuccess) {                                                       \
+      if (getenv("RB_DEBUG"))                                                      \
+        fprintf(stderr, "rbicgstab: %s failed at %s:%d: %s\n", #expr, __FILE__,    \
+                __LINE__, cudaGetErrorString(_e));                                 \
+      return (_e == cudaErrorMemoryAllocation) ? RB_ENOMEM : RB_ECUDA;             \
+    }                                                                              \
+  } while (0)

@@ -1,0 +1,135 @@
+// Internal launcher declarations (host side) for librbicgstab.
+#pragma once
+
+#include "common.cuh"
+
+namespace rb {
+
+// Pointers of one RBiCGSTAB iteration (Alg. 2 step 6).  Vectors have npad
+// entries (n rounded up to the slice height; the tail is kept at zero).
+// For k = 0, q aliases qraw and t aliases traw.
+template <typename T>
+struct IterArgs {
+  Sell<T> A;
+  const T* Chat;  // C-hat = C~ D_c^{-1}, column-major n x k, leading dim ld
+  const T* C;     // C = A U, column-major, leading dim ld
+  int64_t ld;
+  const T* rt0;   // r~_0
+  T* x;
+  T* r;
+  const T* p_in;  // p_i
+  T* p_out;       // p_{i+1} (may equal p_in)
+  T* s;
+  T* q;
+  T* qraw;        // A p_i before projection
+  T* t;
+  T* traw;        // A s_i before projection
+  IterState* st;
+  double* partials;
+  int64_t npad;
+};
+
+struct Grids {
+  int spmv;
+  int vec;
+};
+
+int kmax_bucket(int k);
+
+// Process-wide count of kernels this library has launched (graph replays add
+// the kernels their graph holds).
+void count_launches(long long n);
+
+template <typename T>
+cudaError_t launch_iteration(const IterArgs<T>& a, int k, const Grids& g, cudaStream_t s);
+
+template <typename T>
+void iteration_grids(int k, int nsm, int64_t npad, Grids* g);
+
+// One pass (P1..P5 = 0..4) of the iteration, launched on its own.
+template <typename T>
+cudaError_t launch_pass(int pass, const IterArgs<T>& a, int k, const Grids& g, cudaStream_t s);
+
+// ---------------------------------------------------------------- matrix.cu
+// Sparse matrix in SELL-32 form, owned by the library.
+template <typename T>
+struct SellBuf {
+  int64_t* slice_ptr = nullptr;
+  int32_t* width = nullptr;
+  int32_t* col = nullptr;
+  T* val = nullptr;
+  int64_t* perm = nullptr;   // SELL position -> CSR position (or -1 for padding)
+  int64_t nslices = 0;
+  int64_t cap = 0;           // entries incl. padding
+  Sell<T> view() const { return Sell<T>{slice_ptr, width, col, val, nslices}; }
+};
+
+// Validate CSR on the device; *bad receives 0 (ok), RB_EBADCSR or RB_ENONFINITE.
+int csr_validate(int64_t n, int64_t nnz, const int32_t* row_ptr, const int32_t* col,
+                 const double* val, int* d_flag, int* bad, cudaStream_t s);
+// Build SELL-32 structure from device CSR (allocates inside `out`).
+int sell_build(int64_t n, int64_t nnz, const int32_t* row_ptr, const int32_t* col,
+               SellBuf<double>* out, cudaStream_t s);
+// Refill SELL values from CSR values through out->perm.
+template <typename T>
+int sell_fill_values(const SellBuf<T>& out, const double* csr_val, cudaStream_t s);
+// Build CSR of A^T on the device (rows sorted by column index).
+int csr_transpose(int64_t n, int64_t nnz, const int32_t* row_ptr, const int32_t* col,
+                  int32_t* t_row_ptr, int32_t* t_col, int64_t* t_src, cudaStream_t s);
+// Gather values of A^T from A's values: t_val[e] = val[t_src[e]].
+int gather_values(int64_t nnz, const int64_t* t_src, const double* val, double* t_val,
+                  cudaStream_t s);
+template <typename T>
+void sell_free(SellBuf<T>* b);
+
+// y = alpha * A v + beta * y (FP64 or FP32), npad entries.
+template <typename T>
+cudaError_t spmv(const Sell<T>& A, const T* v, T* y, double alpha, double beta, int grid,
+                 cudaStream_t s);
+
+// ---------------------------------------------------------------- blas.cu
+// Generic deterministic reductions into st->red:
+//   red[j]      = sum_i M[j*ld + i] * v[i]            for j < km   (M may be null)
+//   red[km + d] = sum_i a_d[i] * b_d[i]               for d < nd  (nd <= 4)
+struct DotArgs {
+  const double* M;
+  int64_t ld;
+  int km;
+  const double* v;
+  const double* a[4];
+  const double* b[4];
+  int nd;
+};
+cudaError_t dots(const DotArgs& d, int64_t npad, IterState* st, double* partials, int grid,
+                 cudaStream_t s);
+// y[i] += sign * sum_j M[j*ld+i] * c[j], c read from device memory (c_scale[j]
+// multiplies c[j] when non-null).
+cudaError_t gemv_update(double* y, const double* M, int64_t ld, int k, const double* c,
+                        const double* c_scale, double sign, int64_t npad, int grid,
+                        cudaStream_t s);
+// Out(:, c) = sum_j X(:, j) R[j + c*m] for c < kc (column pointer lists;
+// R is m x kc column-major on the device).  Out must not alias X.
+cudaError_t gemm_cols(double* const* out, const double* const* X, int m, const double* R,
+                      int kc, int64_t npad, int grid, cudaStream_t s);
+// G[a + b*mx] = sum_i X_a[i] Y_b[i] for a < mx, b < my (column pointer lists);
+// writes mx*my doubles to `out` (device).  `work` holds grid*mx*my doubles.
+cudaError_t gram(const double* const* X, int mx, const double* const* Y, int my,
+                 int64_t npad, double* out, double* work, int grid, cudaStream_t s);
+// Shadow vector r~[i] = 2 * u53(SplitMix64(seed, i)) - 1 for i < n, 0 beyond.
+cudaError_t shadow(double* rt, int64_t n, int64_t npad, uint64_t seed, cudaStream_t s);
+// Scale column j of M (n x k, ld) by f[j] (device array); rows < npad.
+cudaError_t scale_cols(double* M, int64_t ld, int k, const double* f, int64_t npad,
+                       cudaStream_t s);
+// Residual r = b - A x and red[0] = ||r||^2 into st->red (deterministic).
+cudaError_t residual_norm(const Sell<double>& A, const double* b, const double* x, double* r,
+                          int64_t npad, IterState* st, double* partials, int grid,
+                          cudaStream_t s);
+// Non-finite check: *flag = 1 if any of v[0..n) is NaN/Inf.
+cudaError_t check_finite(const double* v, int64_t n, int* flag, cudaStream_t s);
+// Precision conversions for the mixed path.
+cudaError_t to_float(const double* in, float* out, int64_t n, cudaStream_t s);
+cudaError_t add_float_to_double(double* x, const float* d, int64_t n, cudaStream_t s);
+// Device-side solve setup: thresholds, rho_0, c_r = C^T r~_0 (from st->red).
+cudaError_t init_state(IterState* st, int k, double tol, int max_itn, cudaStream_t s);
+
+}  // namespace rb

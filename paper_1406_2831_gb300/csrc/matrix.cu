@@ -1,0 +1,274 @@
+// Sparse-matrix setup (rbicgstab_set_matrix): CSR validation, SELL-32
+// re-layout, transpose, and the generic SpMV used outside the fused passes.
+//
+// The API takes CSR (the storage the paper's problem statement implies for a
+// "large, sparse" A, Sec. 1).  On the device the matrix is kept as SELL-32:
+// 32 consecutive rows per slice, entries of a slice stored column by column
+// (entry j of every row of the slice is one 32-wide coalesced line), each
+// slice padded to its longest row with (col = row, val = 0).  Stencil rows
+// differ in length only at the boundary, so padding is small.
+#include <algorithm>
+#include <vector>
+
+#include "device.cuh"
+#include "kernels.h"
+
+namespace rb {
+
+// ---------------------------------------------------------------- validation
+__global__ void k_validate_rows(int64_t n, int64_t nnz, const int32_t* __restrict__ rp, int* flag) {
+  for (int64_t i = gtid(); i <= n; i += gstride()) {
+    const int32_t a = rp[i];
+    bool bad = (a < 0) || ((int64_t)a > nnz);
+    if (i == 0) bad |= (a != 0);
+    if (i == n) bad |= ((int64_t)a != nnz);
+    if (i < n) bad |= (rp[i + 1] < a);
+    if (bad) atomicMax(flag, 1);
+  }
+}
+
+__global__ void k_validate_entries(int64_t n, int64_t nnz, const int32_t* __restrict__ col,
+                                   const double* __restrict__ val, int* flag) {
+  for (int64_t e = gtid(); e < nnz; e += gstride()) {
+    const int32_t c = col[e];
+    if (c < 0 || (int64_t)c >= n) atomicMax(flag, 1);
+    if (val && !isfinite(val[e])) atomicMax(flag, 2);
+  }
+}
+
+int csr_validate(int64_t n, int64_t nnz, const int32_t* row_ptr, const int32_t* col,
+                 const double* val, int* d_flag, int* bad, cudaStream_t s) {
+  count_launches(2);
+  RB_CUDA_TRY(cudaMemsetAsync(d_flag, 0, sizeof(int), s));
+  int grid = (int)std::min<int64_t>((n + kBlock) / kBlock + 1, 4096);
+  k_validate_rows<<<grid, kBlock, 0, s>>>(n, nnz, row_ptr, d_flag);
+  if (nnz > 0) {
+    int g2 = (int)std::min<int64_t>((nnz + kBlock - 1) / kBlock, 8192);
+    k_validate_entries<<<g2, kBlock, 0, s>>>(n, nnz, col, val, d_flag);
+  }
+  RB_CUDA_TRY(cudaGetLastError());
+  int h = 0;
+  RB_CUDA_TRY(cudaMemcpyAsync(&h, d_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+  RB_CUDA_TRY(cudaStreamSynchronize(s));
+  *bad = (h & 1) ? RB_EBADCSR : (h & 2) ? RB_ENONFINITE : 0;
+  return RB_OK;
+}
+
+// ---------------------------------------------------------------- SELL-32
+__global__ void k_slice_width(int64_t n, int64_t nslices, const int32_t* __restrict__ rp,
+                              int32_t* __restrict__ width) {
+  for (int64_t sl = gtid(); sl < nslices; sl += gstride()) {
+    int w = 0;
+    for (int l = 0; l < kSlice; ++l) {
+      const int64_t r = sl * kSlice + l;
+      if (r < n) w = max(w, rp[r + 1] - rp[r]);
+    }
+    width[sl] = w;
+  }
+}
+
+__global__ void k_sell_fill(int64_t n, int64_t nslices, const int32_t* __restrict__ rp,
+                            const int32_t* __restrict__ col, const int64_t* __restrict__ sp,
+                            const int32_t* __restrict__ width, int32_t* __restrict__ scol,
+                            int64_t* __restrict__ perm) {
+  const int64_t total = nslices * kSlice;
+  for (int64_t r = gtid(); r < total; r += gstride()) {
+    const int64_t sl = r / kSlice;
+    const int lane = (int)(r % kSlice);
+    const int w = width[sl];
+    const int64_t b = (r < n) ? rp[r] : 0;
+    const int len = (r < n) ? (int)(rp[r + 1] - b) : 0;
+    for (int j = 0; j < w; ++j) {
+      const int64_t pos = sp[sl] + (int64_t)j * kSlice + lane;
+      if (j < len) {
+        scol[pos] = col[b + j];
+        perm[pos] = b + j;
+      } else {
+        scol[pos] = (int32_t)r;
+        perm[pos] = -1;
+      }
+    }
+  }
+}
+
+template <typename T>
+__global__ void k_sell_values(int64_t cap, const int64_t* __restrict__ perm,
+                              const double* __restrict__ v, T* __restrict__ out) {
+  for (int64_t e = gtid(); e < cap; e += gstride()) {
+    const int64_t p = perm[e];
+    out[e] = (p >= 0) ? (T)v[p] : T(0);
+  }
+}
+
+template <typename T>
+void sell_free(SellBuf<T>* b) {
+  cudaFree(b->slice_ptr);
+  cudaFree(b->width);
+  cudaFree(b->col);
+  cudaFree(b->val);
+  cudaFree(b->perm);
+  *b = SellBuf<T>();
+}
+template void sell_free<double>(SellBuf<double>*);
+template void sell_free<float>(SellBuf<float>*);
+
+int sell_build(int64_t n, int64_t nnz, const int32_t* row_ptr, const int32_t* col,
+               SellBuf<double>* out, cudaStream_t s) {
+  count_launches(2);
+  sell_free(out);
+  const int64_t nslices = (n + kSlice - 1) / kSlice;
+  out->nslices = nslices;
+  RB_CUDA_TRY(cudaMalloc(&out->width, sizeof(int32_t) * std::max<int64_t>(nslices, 1)));
+  RB_CUDA_TRY(cudaMalloc(&out->slice_ptr, sizeof(int64_t) * (nslices + 1)));
+  int grid = (int)std::min<int64_t>((nslices + kBlock - 1) / kBlock + 1, 4096);
+  k_slice_width<<<grid, kBlock, 0, s>>>(n, nslices, row_ptr, out->width);
+  RB_CUDA_TRY(cudaGetLastError());
+  std::vector<int32_t> w(nslices);
+  std::vector<int64_t> sp(nslices + 1);
+  if (nslices)
+    RB_CUDA_TRY(cudaMemcpyAsync(w.data(), out->width, sizeof(int32_t) * nslices,
+                                cudaMemcpyDeviceToHost, s));
+  RB_CUDA_TRY(cudaStreamSynchronize(s));
+  sp[0] = 0;
+  for (int64_t i = 0; i < nslices; ++i) sp[i + 1] = sp[i] + (int64_t)w[i] * kSlice;
+  out->cap = sp[nslices];
+  RB_CUDA_TRY(cudaMemcpyAsync(out->slice_ptr, sp.data(), sizeof(int64_t) * (nslices + 1),
+                              cudaMemcpyHostToDevice, s));
+  const int64_t cap = std::max<int64_t>(out->cap, 1);
+  RB_CUDA_TRY(cudaMalloc(&out->col, sizeof(int32_t) * cap));
+  RB_CUDA_TRY(cudaMalloc(&out->val, sizeof(double) * cap));
+  RB_CUDA_TRY(cudaMalloc(&out->perm, sizeof(int64_t) * cap));
+  int g2 = (int)std::min<int64_t>((nslices * kSlice + kBlock - 1) / kBlock + 1, 16384);
+  k_sell_fill<<<g2, kBlock, 0, s>>>(n, nslices, row_ptr, col, out->slice_ptr, out->width,
+                                    out->col, out->perm);
+  RB_CUDA_TRY(cudaGetLastError());
+  RB_CUDA_TRY(cudaStreamSynchronize(s));  // keeps host vectors alive until copies finish
+  return RB_OK;
+}
+
+template <typename T>
+int sell_fill_values(const SellBuf<T>& out, const double* csr_val, cudaStream_t s) {
+  count_launches(1);
+  if (out.cap == 0) return RB_OK;
+  int grid = (int)std::min<int64_t>((out.cap + kBlock - 1) / kBlock, 16384);
+  k_sell_values<T><<<grid, kBlock, 0, s>>>(out.cap, out.perm, csr_val, out.val);
+  RB_CUDA_TRY(cudaGetLastError());
+  return RB_OK;
+}
+template int sell_fill_values<double>(const SellBuf<double>&, const double*, cudaStream_t);
+template int sell_fill_values<float>(const SellBuf<float>&, const double*, cudaStream_t);
+
+// ---------------------------------------------------------------- transpose
+__global__ void k_col_count(int64_t nnz, const int32_t* __restrict__ col, int32_t* cnt) {
+  for (int64_t e = gtid(); e < nnz; e += gstride()) atomicAdd(cnt + col[e], 1);
+}
+
+__global__ void k_scatter_t(int64_t n, const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
+                            const int32_t* __restrict__ trp, int32_t* fill, int32_t* tcol,
+                            int64_t* tsrc) {
+  for (int64_t r = gtid(); r < n; r += gstride()) {
+    for (int64_t e = rp[r]; e < rp[r + 1]; ++e) {
+      const int32_t c = col[e];
+      const int64_t pos = trp[c] + atomicAdd(fill + c, 1);
+      tcol[pos] = (int32_t)r;
+      tsrc[pos] = e;
+    }
+  }
+}
+
+// Entries of one row of A^T arrive in arbitrary order; sort each row by its
+// column index (row of A) so the result is deterministic.
+__global__ void k_sort_rows(int64_t n, const int32_t* __restrict__ trp, int32_t* tcol, int64_t* tsrc) {
+  for (int64_t r = gtid(); r < n; r += gstride()) {
+    const int64_t b = trp[r], e = trp[r + 1];
+    for (int64_t i = b + 1; i < e; ++i) {
+      const int32_t c = tcol[i];
+      const int64_t s = tsrc[i];
+      int64_t j = i - 1;
+      while (j >= b && tcol[j] > c) {
+        tcol[j + 1] = tcol[j];
+        tsrc[j + 1] = tsrc[j];
+        --j;
+      }
+      tcol[j + 1] = c;
+      tsrc[j + 1] = s;
+    }
+  }
+}
+
+int csr_transpose(int64_t n, int64_t nnz, const int32_t* row_ptr, const int32_t* col,
+                  int32_t* t_row_ptr, int32_t* t_col, int64_t* t_src, cudaStream_t s) {
+  count_launches(4);
+  int32_t* cnt = nullptr;
+  RB_CUDA_TRY(cudaMalloc(&cnt, sizeof(int32_t) * (n + 1)));
+  RB_CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (n + 1), s));
+  if (nnz > 0) {
+    int g = (int)std::min<int64_t>((nnz + kBlock - 1) / kBlock, 16384);
+    k_col_count<<<g, kBlock, 0, s>>>(nnz, col, cnt);
+  }
+  std::vector<int32_t> h(n + 1);
+  RB_CUDA_TRY(cudaMemcpyAsync(h.data(), cnt, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, s));
+  RB_CUDA_TRY(cudaStreamSynchronize(s));
+  std::vector<int32_t> trp(n + 1);
+  trp[0] = 0;
+  for (int64_t i = 0; i < n; ++i) trp[i + 1] = trp[i] + h[i];
+  RB_CUDA_TRY(cudaMemcpyAsync(t_row_ptr, trp.data(), sizeof(int32_t) * (n + 1),
+                              cudaMemcpyHostToDevice, s));
+  RB_CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (n + 1), s));
+  int g = (int)std::min<int64_t>((n + kBlock - 1) / kBlock + 1, 16384);
+  k_scatter_t<<<g, kBlock, 0, s>>>(n, row_ptr, col, t_row_ptr, cnt, t_col, t_src);
+  k_sort_rows<<<g, kBlock, 0, s>>>(n, t_row_ptr, t_col, t_src);
+  RB_CUDA_TRY(cudaGetLastError());
+  RB_CUDA_TRY(cudaStreamSynchronize(s));
+  cudaFree(cnt);
+  return RB_OK;
+}
+
+__global__ void k_gather(int64_t nnz, const int64_t* __restrict__ src, const double* __restrict__ v,
+                         double* __restrict__ out) {
+  for (int64_t e = gtid(); e < nnz; e += gstride()) out[e] = v[src[e]];
+}
+
+int gather_values(int64_t nnz, const int64_t* t_src, const double* val, double* t_val,
+                  cudaStream_t s) {
+  count_launches(1);
+  if (nnz == 0) return RB_OK;
+  int g = (int)std::min<int64_t>((nnz + kBlock - 1) / kBlock, 16384);
+  k_gather<<<g, kBlock, 0, s>>>(nnz, t_src, val, t_val);
+  RB_CUDA_TRY(cudaGetLastError());
+  return RB_OK;
+}
+
+// ---------------------------------------------------------------- SpMV
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_spmv(Sell<T> A, const T* __restrict__ v, T* __restrict__ y,
+                                                double alpha, double beta) {
+  const int lane = threadIdx.x & 31;
+  const int64_t w0 = gtid() >> 5, nw = gstride() >> 5;
+  for (int64_t sl = w0; sl < A.nslices; sl += nw) {
+    const int64_t row = sl * kSlice + lane;
+    const int w = A.width[sl];
+    const int64_t base = A.slice_ptr[sl] + lane;
+    T acc = T(0);
+    for (int j = 0; j < w; ++j) {
+      const int64_t e = base + (int64_t)j * kSlice;
+      acc = fma(A.val[e], v[A.col[e]], acc);
+    }
+    const T out = (T)alpha * acc;
+    y[row] = (beta == 0.0) ? out : fma((T)beta, y[row], out);
+  }
+}
+
+template <typename T>
+cudaError_t spmv(const Sell<T>& A, const T* v, T* y, double alpha, double beta, int grid,
+                 cudaStream_t s) {
+  count_launches(1);
+  k_spmv<T><<<grid, kBlock, 0, s>>>(A, v, y, alpha, beta);
+  return cudaGetLastError();
+}
+template cudaError_t spmv<double>(const Sell<double>&, const double*, double*, double, double, int,
+                                  cudaStream_t);
+template cudaError_t spmv<float>(const Sell<float>&, const float*, float*, double, double, int,
+                                 cudaStream_t);
+
+}  // namespace rb

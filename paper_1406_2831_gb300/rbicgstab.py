@@ -1,0 +1,291 @@
+"""Python binding of librbicgstab (ctypes).  Argument marshalling only: every
+step of the solve runs in the library's CUDA kernels and host code.
+
+Arrays may be numpy arrays (host) or torch tensors (host or CUDA; CUDA
+tensors are passed by ``data_ptr()`` with ``where = RB_DEVICE``).  Torch is
+used only for device memory and streams.  If the library is missing this
+module raises at import of the first handle: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+from dataclasses import dataclass
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "librbicgstab.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "rbicgstab.h")
+
+
+def _header_constants() -> dict:
+    out = {}
+    with open(HEADER) as f:
+        for line in f:
+            m = re.match(r"#define\s+(RB_\w+)\s+(-?\d+)", line)
+            if m:
+                out[m.group(1)] = int(m.group(2))
+    return out
+
+
+C = _header_constants()
+RB_OK = C["RB_OK"]
+RB_HOST, RB_DEVICE = C["RB_HOST"], C["RB_DEVICE"]
+PRECISION = {"fp64": C["RB_FP64"], "mixed": C["RB_MIXED"]}
+RECYCLE = {"none": C["RB_RECYCLE_NONE"], "fixed": C["RB_RECYCLE_FIXED"],
+           "update_first": C["RB_RECYCLE_UPDATE_FIRST"], "update_all": C["RB_RECYCLE_UPDATE_ALL"]}
+HARD_ERRORS = {C[k] for k in ("RB_EINVAL", "RB_EDIM", "RB_EBADCSR", "RB_ENONFINITE", "RB_ENOMEM",
+                              "RB_ECUDA", "RB_ETIMEOUT")}
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("k_max", ctypes.c_int32), ("cycle_s", ctypes.c_int32), ("max_itn", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("recycle_mode", ctypes.c_int32),
+                ("update_cycles", ctypes.c_int32), ("poll", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("tol", ctypes.c_double), ("shadow_seed", ctypes.c_uint64), ("cuda_stream", ctypes.c_void_p)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int32), ("status", ctypes.c_int32), ("k_used", ctypes.c_int32),
+                ("seeds_used", ctypes.c_int32), ("matvecs", ctypes.c_int64),
+                ("matvecs_setup", ctypes.c_int64), ("matvecs_check", ctypes.c_int64),
+                ("cycles", ctypes.c_int32), ("outer", ctypes.c_int32), ("relres_rec", ctypes.c_double),
+                ("relres_true", ctypes.c_double), ("ms_total", ctypes.c_double),
+                ("bytes_model", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+class RbError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {error_string(code)} ({code})")
+
+
+_lib = None
+
+
+def lib():
+    """Load librbicgstab.so (built in-tree by ``paper_1406_2831_gb300.build``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"librbicgstab.so not built ({LIB_PATH}); run paper_1406_2831_gb300.build.build()")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, i32, i64, dp = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p
+    L.rbicgstab_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(Opts)]
+    L.rbicgstab_destroy.argtypes = [vp]
+    L.rbicgstab_set_matrix.argtypes = [vp, i64, i64, dp, dp, dp, ctypes.c_int]
+    L.rbicgstab_set_values.argtypes = [vp, dp, ctypes.c_int]
+    L.rbicgstab_set_recycle.argtypes = [vp, i32, dp, dp, i64, ctypes.c_int]
+    L.rbicgstab_get_recycle.argtypes = [vp, ctypes.POINTER(i32), dp, dp, i64, ctypes.c_int]
+    L.rbicgstab_solve.argtypes = [vp, dp, dp, ctypes.c_int, ctypes.POINTER(Stats)]
+    L.rbicgstab_apply.argtypes = [vp, dp, dp, ctypes.c_int, ctypes.c_int]
+    L.rbicgstab_harmonic_ritz.argtypes = [i32, dp, dp, i32, dp, dp, dp, ctypes.POINTER(i32)]
+    L.rbicgstab_time_passes.argtypes = [vp, dp, ctypes.c_int, i32, dp]
+    L.rbicgstab_kernel_launches.argtypes = []
+    L.rbicgstab_kernel_launches.restype = ctypes.c_longlong
+    L.rbicgstab_error_string.argtypes = [ctypes.c_int]
+    L.rbicgstab_error_string.restype = ctypes.c_char_p
+    for name in ("rbicgstab_create", "rbicgstab_destroy", "rbicgstab_set_matrix", "rbicgstab_set_values",
+                 "rbicgstab_set_recycle", "rbicgstab_get_recycle", "rbicgstab_solve", "rbicgstab_apply",
+                 "rbicgstab_harmonic_ritz", "rbicgstab_time_passes"):
+        getattr(L, name).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def error_string(code: int) -> str:
+    return lib().rbicgstab_error_string(int(code)).decode()
+
+
+def _check(code: int, where: str) -> int:
+    if code in HARD_ERRORS:
+        raise RbError(code, where)
+    return code
+
+
+# ---------------------------------------------------------------- array marshalling
+def _is_torch(a) -> bool:
+    return type(a).__module__.startswith("torch")
+
+
+def _ptr(a, dtype):
+    """(pointer, where, keepalive) for a 1-D/2-D numpy array or torch tensor."""
+    if _is_torch(a):
+        import torch
+        tdt = {np.float64: torch.float64, np.int32: torch.int32, np.float32: torch.float32}[dtype]
+        if a.dtype != tdt:
+            raise TypeError(f"expected {tdt}, got {a.dtype}")
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr(), (RB_DEVICE if a.is_cuda else RB_HOST), a
+    arr = np.ascontiguousarray(a, dtype=dtype)
+    return arr.ctypes.data, RB_HOST, arr
+
+
+def _colmajor(U, dtype=np.float64):
+    """(pointer, where, ld, keepalive) for an (n, k) block as column-major storage."""
+    if _is_torch(U):
+        Ut = U.t().contiguous()          # (k, n) row-major == (n, k) column-major
+        return Ut.data_ptr(), (RB_DEVICE if U.is_cuda else RB_HOST), U.shape[0], Ut
+    arr = np.asfortranarray(U, dtype=dtype)
+    return arr.ctypes.data, RB_HOST, arr.shape[0], arr
+
+
+@dataclass
+class SolveResult:
+    x: object
+    stats: dict
+
+
+class Solver:
+    """One solver handle (``rbicgstab_create``).  Options mirror ``rb_opts``."""
+
+    def __init__(self, k_max=0, cycle_s=25, max_itn=0, precision="fp64", recycle="none",
+                 update_cycles=0, poll=0, tol=1e-8, shadow_seed=0x5EED, stream=None):
+        L = lib()
+        o = Opts()
+        o.k_max, o.cycle_s, o.max_itn = k_max, cycle_s, max_itn
+        o.precision, o.recycle_mode = PRECISION[precision], RECYCLE[recycle]
+        o.update_cycles, o.poll, o.tol, o.shadow_seed = update_cycles, poll, tol, shadow_seed
+        if stream is not None:
+            o.cuda_stream = stream if isinstance(stream, int) else stream.cuda_stream
+        self._h = ctypes.c_void_p()
+        _check(L.rbicgstab_create(ctypes.byref(self._h), ctypes.byref(o)), "rbicgstab_create")
+        self.n = 0
+        self.opts = o
+
+    def close(self):
+        if self._h:
+            lib().rbicgstab_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def set_matrix(self, row_ptr, col, val):
+        rp, w1, k1 = _ptr(row_ptr, np.int32)
+        cp, w2, k2 = _ptr(col, np.int32)
+        vp, w3, k3 = _ptr(val, np.float64)
+        if len({w1, w2, w3}) != 1:
+            raise ValueError("row_ptr, col and val must live in the same memory space")
+        n = len(row_ptr) - 1
+        nnz = len(val)
+        _check(lib().rbicgstab_set_matrix(self._h, n, nnz, rp, cp, vp, w1), "rbicgstab_set_matrix")
+        self.n = n
+
+    def set_values(self, val):
+        vp, w, keep = _ptr(val, np.float64)
+        return _check(lib().rbicgstab_set_values(self._h, vp, w), "rbicgstab_set_values")
+
+    def set_recycle(self, U, Ut=None) -> int:
+        """Set U (n x k) and U~ (None: U~ = U).  Returns the status (RB_OK or the rank warning)."""
+        if U is None or U.shape[1] == 0:
+            return _check(lib().rbicgstab_set_recycle(self._h, 0, None, None, max(self.n, 1), RB_HOST),
+                          "rbicgstab_set_recycle")
+        up, w, ld, k1 = _colmajor(U)
+        utp = None
+        if Ut is not None:
+            utp, w2, ld2, k2 = _colmajor(Ut)
+            if w2 != w or ld2 != ld:
+                raise ValueError("U and Ut must match")
+        return _check(lib().rbicgstab_set_recycle(self._h, U.shape[1], up, utp, ld, w), "rbicgstab_set_recycle")
+
+    def get_recycle(self, device=None):
+        """Current (biorthogonalised) U, U~ as (n, k) numpy arrays, or CUDA
+        tensors when ``device`` is a torch device."""
+        k = ctypes.c_int32()
+        _check(lib().rbicgstab_get_recycle(self._h, ctypes.byref(k), None, None, max(self.n, 1), RB_HOST),
+               "rbicgstab_get_recycle")
+        kk = k.value
+        if device is not None:
+            import torch
+            U = torch.empty((kk, self.n), dtype=torch.float64, device=device)
+            Ut = torch.empty_like(U)
+            _check(lib().rbicgstab_get_recycle(self._h, ctypes.byref(k), U.data_ptr(), Ut.data_ptr(),
+                                               self.n, RB_DEVICE), "rbicgstab_get_recycle")
+            return U.t(), Ut.t()
+        U = np.zeros((self.n, kk), order="F")
+        Ut = np.zeros((self.n, kk), order="F")
+        if kk:
+            _check(lib().rbicgstab_get_recycle(self._h, ctypes.byref(k), U.ctypes.data, Ut.ctypes.data,
+                                               self.n, RB_HOST), "rbicgstab_get_recycle")
+        return U, Ut
+
+    def solve(self, b, x=None) -> SolveResult:
+        """Solve A x = b; ``x`` (updated in place when given) is x_{-1}."""
+        if x is None:
+            if _is_torch(b):
+                import torch
+                x = torch.zeros_like(b)
+            else:
+                x = np.zeros(len(b))
+        bp, wb, kb = _ptr(b, np.float64)
+        if _is_torch(x):
+            xp, wx, kx = _ptr(x, np.float64)
+        else:
+            if not (isinstance(x, np.ndarray) and x.dtype == np.float64 and x.flags.c_contiguous):
+                x = np.ascontiguousarray(x, dtype=np.float64)
+            xp, wx, kx = x.ctypes.data, RB_HOST, x
+        if wb != wx:
+            raise ValueError("b and x must live in the same memory space")
+        st = Stats()
+        _check(lib().rbicgstab_solve(self._h, bp, xp, wb, ctypes.byref(st)), "rbicgstab_solve")
+        return SolveResult(x=x, stats=st.as_dict())
+
+    def apply(self, v, transpose=False):
+        """y = A v (or A^T v) with the library's SpMV."""
+        vp, w, keep = _ptr(v, np.float64)
+        if _is_torch(v):
+            import torch
+            y = torch.empty_like(v)
+            yp = y.data_ptr()
+        else:
+            y = np.empty(len(v))
+            yp = y.ctypes.data
+        _check(lib().rbicgstab_apply(self._h, vp, yp, int(bool(transpose)), w), "rbicgstab_apply")
+        return y
+
+
+def kernel_launches() -> int:
+    """Kernels launched by the library in this process (rbicgstab_kernel_launches)."""
+    return int(lib().rbicgstab_kernel_launches())
+
+
+def time_passes(solver: "Solver", b, reps: int = 10):
+    """Average ms of passes P1..P5 (rbicgstab_time_passes); returns (ms[5], status)."""
+    bp, w, keep = _ptr(b, np.float64)
+    ms = np.zeros(5)
+    code = lib().rbicgstab_time_passes(solver._h, bp, w, int(reps), ms.ctypes.data)
+    _check(code, "rbicgstab_time_passes")
+    return ms, code
+
+
+def harmonic_ritz(G: np.ndarray, H: np.ndarray, k: int):
+    """Host harmonic-Ritz step of the library (rbicgstab_harmonic_ritz)."""
+    m = G.shape[0]
+    Gf = np.asfortranarray(G, dtype=np.float64)
+    Hf = np.asfortranarray(H, dtype=np.float64)
+    Y = np.zeros((m, k), order="F")
+    tr = np.zeros(k)
+    ti = np.zeros(k)
+    ku = ctypes.c_int32()
+    code = lib().rbicgstab_harmonic_ritz(m, Gf.ctypes.data, Hf.ctypes.data, k, Y.ctypes.data,
+                                         tr.ctypes.data, ti.ctypes.data, ctypes.byref(ku))
+    _check(code, "rbicgstab_harmonic_ritz")
+    kk = ku.value
+    return Y[:, :kk], tr[:kk] + 1j * ti[:kk]

@@ -1,0 +1,100 @@
+"""C-ABI checks that need no GPU: the library loads, exports every entry point
+declared in include/rbicgstab.h, and its host-only harmonic-Ritz step agrees
+with the oracle's (a different algorithm on the same pencil)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle.dense import principal_cosines
+from oracle.recycle import harmonic_ritz_coeffs
+from paper_1406_2831_gb300 import build as rbuild
+from paper_1406_2831_gb300 import rbicgstab as rb
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    rbuild.build()
+    return rb.lib()
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "rbicgstab.h")).read()
+    return sorted(set(re.findall(r"\b(rbicgstab_\w+)\s*\(", src)))
+
+
+def test_exports_every_declared_symbol(L):
+    names = _declared()
+    assert len(names) >= 10
+    for name in names:
+        assert hasattr(L, name), name
+        assert ctypes.cast(getattr(L, name), ctypes.c_void_p).value
+
+
+def test_error_strings(L):
+    for code in range(-10, 2):
+        s = rb.error_string(code)
+        assert s and s != "unknown status"
+    assert rb.error_string(12345) == "unknown status"
+
+
+def test_header_constants_match_binding():
+    assert rb.C["RB_KMAX"] == 64
+    assert rb.RB_HOST == 0 and rb.RB_DEVICE == 1
+
+
+def _pencil(seed, n=300, m=30, rank_drop=0):
+    rng = np.random.default_rng(seed)
+    A = rng.standard_normal((n, n)) + 5 * np.eye(n)
+    W = rng.standard_normal((n, m))
+    if rank_drop:
+        W[:, -rank_drop:] = W[:, :rank_drop] @ rng.standard_normal((rank_drop, rank_drop))
+    Z = A @ W
+    return W, Z, Z.T @ Z, Z.T @ W
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_host_harmonic_ritz_matches_oracle(L, seed):
+    W, Z, G, H = _pencil(seed)
+    k = 8
+    y1, t1 = harmonic_ritz_coeffs(G, H, k)
+    y2, t2 = rb.harmonic_ritz(G, H, k)
+    assert len(t1) == len(t2)
+    assert np.abs(np.sort_complex(t1) - np.sort_complex(t2)).max() <= 1e-9 * np.abs(t1).max()
+    c = principal_cosines(W @ y1, W @ y2)
+    assert 1.0 - c.min() <= 1e-10
+
+
+def test_host_harmonic_ritz_rank_deficient(L):
+    W, Z, G, H = _pencil(7, rank_drop=3)
+    y1, t1 = harmonic_ritz_coeffs(G, H, 6)
+    y2, t2 = rb.harmonic_ritz(G, H, 6)
+    assert len(t1) == len(t2)
+    assert np.abs(np.sort_complex(t1) - np.sort_complex(t2)).max() <= 1e-6 * np.abs(t1).max()
+
+
+def test_host_harmonic_ritz_exact_eigenvector(L):
+    """An exact eigenvector inside span W is returned with its eigenvalue."""
+    rng = np.random.default_rng(3)
+    n = 40
+    S = rng.standard_normal((n, n))
+    d = np.linspace(0.5, 9.0, n)
+    A = S @ np.diag(d) @ np.linalg.inv(S)      # non-normal, real spectrum
+    j = 0
+    v = S[:, j]
+    w = d
+    W = np.column_stack([rng.standard_normal((n, 4)), v]) @ rng.standard_normal((5, 5))
+    Z = A @ W
+    y, th = rb.harmonic_ritz(Z.T @ Z, Z.T @ W, 1)
+    u = W @ y[:, 0]
+    assert abs(abs(u @ v) / np.linalg.norm(u) / np.linalg.norm(v) - 1) <= 1e-10
+    assert abs(th[0] - w[j]) <= 1e-10 * abs(w[j])
+
+
+def test_harmonic_ritz_rejects_bad_args(L):
+    with pytest.raises(rb.RbError):
+        rb.harmonic_ritz(np.eye(3), np.eye(3), 5)

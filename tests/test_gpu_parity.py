@@ -1,0 +1,314 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 CPU oracle on
+the same seeded inputs.  Sizes span several SELL slices and a ragged tail
+(n not a multiple of 32); the full 128^3 case runs at the benchmark's size.
+
+Tolerance (stated for FP64 at a residual tolerance of 1e-8): solution
+relative difference <= 1e-7 and iteration counts within 5% (at least 1).
+"""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+from oracle import rbicgstab as orb
+from oracle import recycle as orc
+from oracle.dense import invariant_subspaces, principal_cosines
+from paper_1406_2831_gb300 import build as rbuild
+from paper_1406_2831_gb300 import inputs
+from paper_1406_2831_gb300 import rbicgstab as rb
+
+pytestmark = pytest.mark.gpu
+
+XTOL = 1e-7
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    rbuild.build()
+    rb.lib()
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def _iters_close(a, b):
+    return abs(a - b) <= max(1, int(0.05 * max(a, b)))
+
+
+def _solver(A: inputs.CSR, **kw):
+    s = rb.Solver(**kw)
+    s.set_matrix(A.row_ptr, A.col, A.val)
+    return s
+
+
+def _true_relres(A, x, b):
+    return np.linalg.norm(b - A.to_scipy() @ x) / np.linalg.norm(b)
+
+
+# ---------------------------------------------------------------- SpMV
+@pytest.mark.parametrize("N", [5, 33, 64])
+def test_apply_matches_scipy(N):
+    A = inputs.conv_diff_2d(N, 12.0)
+    v = inputs.gaussian_rhs(A.n, 1)
+    s = _solver(A)
+    y = s.apply(v)
+    yt = s.apply(v, transpose=True)
+    S = A.to_scipy()
+    assert _rel(y, S @ v) <= 1e-14
+    assert _rel(yt, S.T @ v) <= 1e-14
+
+
+def test_apply_27pt_and_torch_device():
+    import torch
+    A = inputs.stencil27_noisy(9, 7, 5, 10.0)
+    v = inputs.gaussian_rhs(A.n, 2)
+    s = _solver(A)
+    vt = torch.from_numpy(v).cuda()
+    y = s.apply(vt).cpu().numpy()
+    assert _rel(y, A.to_scipy() @ v) <= 1e-14
+
+
+# ---------------------------------------------------------------- plain BiCGSTAB
+@pytest.mark.parametrize("N,p", [(16, 10.0), (33, 13.0), (64, 17.0)])
+def test_plain_parity(N, p):
+    A = inputs.conv_diff_2d(N, p)
+    b = inputs.gaussian_rhs(A.n, 0)
+    s = _solver(A, recycle="none")
+    res = s.solve(b)
+    xo, io = orb.rbicgstab(A.to_scipy(), b, None, tol=1e-8)
+    assert res.stats["status"] == rb.RB_OK
+    assert _iters_close(res.stats["iters"], io.iters), (res.stats["iters"], io.iters)
+    assert _rel(res.x, xo) <= XTOL
+    assert _true_relres(A, res.x, b) <= 1.5e-8
+    assert abs(res.stats["relres_true"] - _true_relres(A, res.x, b)) <= 1e-12
+
+
+def test_k0_is_bitwise_plain():
+    A = inputs.conv_diff_2d(40, 11.0)
+    b = inputs.gaussian_rhs(A.n, 5)
+    x1 = _solver(A, recycle="none").solve(b).x
+    x2 = _solver(A, recycle="fixed", k_max=8).solve(b).x
+    assert np.array_equal(x1, x2)
+
+
+def test_deterministic_repeat():
+    A = inputs.conv_diff_2d(48, 14.0)
+    b = inputs.gaussian_rhs(A.n, 6)
+    U = inputs.random_recycle_basis(A.n, 6, 3)
+    s = _solver(A, recycle="fixed", k_max=8)
+    s.set_recycle(U)
+    x1 = s.solve(b).x.copy()
+    x2 = s.solve(b).x.copy()
+    assert np.array_equal(x1, x2)
+
+
+def test_nonzero_initial_guess():
+    A = inputs.conv_diff_2d(30, 12.0)
+    b = inputs.gaussian_rhs(A.n, 7)
+    x0 = inputs.gaussian_rhs(A.n, 8)
+    U = inputs.random_recycle_basis(A.n, 4, 9)
+    s = _solver(A, recycle="fixed", k_max=8)
+    s.set_recycle(U)
+    res = s.solve(b, x0.copy())
+    xo, io = orb.rbicgstab(A.to_scipy(), b, orb.recycle_setup(A.to_scipy(), U), x_m1=x0, tol=1e-8)
+    assert _iters_close(res.stats["iters"], io.iters)
+    assert _rel(res.x, xo) <= XTOL
+
+
+# ---------------------------------------------------------------- recycled, fixed space
+@pytest.mark.parametrize("N,k", [(33, 1), (33, 5), (64, 8), (45, 20), (50, 33)])
+def test_recycled_fixed_parity(N, k):
+    A = inputs.conv_diff_2d(N, 15.0)
+    b = inputs.gaussian_rhs(A.n, 1)
+    U = inputs.random_recycle_basis(A.n, k, 21)
+    Ut = inputs.random_recycle_basis(A.n, k, 22)
+    s = _solver(A, recycle="fixed", k_max=k)
+    s.set_recycle(U, Ut)
+    res = s.solve(b)
+    S = A.to_scipy()
+    rec = orb.recycle_setup(S, U, Ut)
+    xo, io = orb.rbicgstab(S, b, rec, tol=1e-8)
+    assert res.stats["k_used"] == rec.k
+    assert _iters_close(res.stats["iters"], io.iters), (res.stats["iters"], io.iters)
+    assert _rel(res.x, xo) <= XTOL
+    assert _true_relres(A, res.x, b) <= 1.5e-8
+    # the library's biorthogonalised space spans the same subspaces
+    Ug, Utg = s.get_recycle()
+    assert 1 - principal_cosines(Ug, rec.U).min() <= 1e-10
+    assert 1 - principal_cosines(Utg, rec.Ut).min() <= 1e-10
+    # C~^T C is diagonal with positive entries (Sec. 3)
+    M = (S.T @ Utg).T @ (S @ Ug)
+    off = M - np.diag(np.diag(M))
+    assert np.all(np.diag(M) > 0)
+    assert np.abs(off).max() <= 1e-10 * np.abs(np.diag(M)).max()
+
+
+def test_exact_eigenvectors_deflate():
+    N, k = 20, 6
+    A = inputs.conv_diff_2d(N, 10.0)
+    S = A.to_scipy()
+    R, L, _ = invariant_subspaces(S.toarray(), k)
+    b = inputs.gaussian_rhs(A.n, 2)
+    s = _solver(A, recycle="fixed", k_max=k)
+    s.set_recycle(R, L)
+    res = s.solve(b)
+    xo, io = orb.rbicgstab(S, b, orb.recycle_setup(S, R, L), tol=1e-8)
+    assert _iters_close(res.stats["iters"], io.iters)
+    assert _rel(res.x, xo) <= XTOL
+    plain = _solver(A).solve(b)
+    assert res.stats["iters"] <= plain.stats["iters"]
+
+
+def test_rank_deficient_recycle_space_warns():
+    A = inputs.conv_diff_2d(24, 10.0)
+    U = inputs.random_recycle_basis(A.n, 4, 1)
+    U = np.column_stack([U, U[:, 0]])       # duplicated column
+    s = _solver(A, recycle="fixed", k_max=8)
+    code = s.set_recycle(U)
+    assert code == rb.C["RB_WRECYCLE_RANK"]
+    Ug, _ = s.get_recycle()
+    assert Ug.shape[1] == 4
+
+
+# ---------------------------------------------------------------- sequences with the update
+def _seq_mats(spec):
+    P = spec.pattern
+    return [sp.csr_matrix((v() if callable(v) else v, P.col, P.row_ptr), shape=(P.n, P.n))
+            for v in spec.values]
+
+
+def test_sequence_update_first_parity():
+    spec = inputs.config_small_2d(N=32)
+    mats = _seq_mats(spec)
+    ref = orc.solve_sequence(mats, spec.rhs, k=spec.k, cycle_s=spec.cycle_s, tol=spec.tol, policy="first")
+    s = rb.Solver(k_max=spec.k, cycle_s=spec.cycle_s, recycle="update_first", tol=spec.tol)
+    P = spec.pattern
+    got_iters, xs = [], []
+    for i, (M, bs) in enumerate(zip(mats, spec.rhs)):
+        if i == 0:
+            s.set_matrix(P.row_ptr, P.col, M.data)
+        else:
+            s.set_values(M.data)
+        for b in bs:
+            r = s.solve(b)
+            got_iters.append(r.stats["iters"])
+            xs.append(r.x.copy())
+    for gi, oi in zip(got_iters, ref.iters):
+        assert _iters_close(gi, oi), (got_iters, ref.iters)
+    for xg, xo in zip(xs, ref.x):
+        assert _rel(xg, xo) <= XTOL
+    Ug, _ = s.get_recycle()
+    assert 1 - principal_cosines(Ug, ref.U_final).min() <= 1e-6
+
+
+# ---------------------------------------------------------------- mixed precision
+@pytest.mark.parametrize("k", [0, 8])
+def test_mixed_refinement(k):
+    A = inputs.conv_diff_2d(64, 12.0)
+    b = inputs.gaussian_rhs(A.n, 3)
+    S = A.to_scipy()
+    s = _solver(A, precision="mixed", recycle="fixed" if k else "none", k_max=k)
+    U = None
+    if k:
+        U = inputs.random_recycle_basis(A.n, k, 4)
+        s.set_recycle(U)
+    res = s.solve(b)
+    xo, io = orb.rbicgstab(S, b, orb.recycle_setup(S, U) if k else None, tol=1e-8)
+    assert res.stats["status"] == rb.RB_OK
+    assert _true_relres(A, res.x, b) <= 1.0e-8
+    assert res.stats["outer"] >= 2
+    err = _rel(res.x, xo)
+    assert err <= XTOL, err
+
+
+# ---------------------------------------------------------------- edge cases
+def test_zero_rhs_returns_zero():
+    A = inputs.conv_diff_2d(10, 10.0)
+    s = _solver(A)
+    res = s.solve(np.zeros(A.n))
+    assert res.stats["iters"] == 0 and np.all(res.x == 0)
+
+
+def test_single_unknown():
+    A = inputs.CSR(n=1, row_ptr=np.array([0, 1], np.int32), col=np.array([0], np.int32),
+                   val=np.array([4.0]))
+    s = _solver(A)
+    res = s.solve(np.array([2.0]))
+    assert abs(res.x[0] - 0.5) <= 1e-15
+
+
+def test_nonfinite_rhs_rejected():
+    A = inputs.conv_diff_2d(10, 10.0)
+    s = _solver(A)
+    b = inputs.gaussian_rhs(A.n, 0)
+    b[3] = np.nan
+    with pytest.raises(rb.RbError) as e:
+        s.solve(b)
+    assert e.value.code == rb.C["RB_ENONFINITE"]
+
+
+def test_bad_csr_rejected():
+    A = inputs.conv_diff_2d(6, 10.0)
+    s = rb.Solver()
+    col = A.col.copy()
+    col[5] = A.n + 3
+    with pytest.raises(rb.RbError) as e:
+        s.set_matrix(A.row_ptr, col, A.val)
+    assert e.value.code == rb.C["RB_EBADCSR"]
+    rp = A.row_ptr.copy()
+    rp[3], rp[4] = rp[4], rp[3]
+    with pytest.raises(rb.RbError):
+        s.set_matrix(rp, A.col, A.val)
+
+
+def test_max_itn_reports_notconv():
+    A = inputs.conv_diff_2d(40, 10.0)
+    b = inputs.gaussian_rhs(A.n, 0)
+    s = _solver(A, max_itn=5)
+    res = s.solve(b)
+    assert res.stats["status"] == rb.C["RB_ENOTCONV"]
+    assert res.stats["iters"] == 5
+
+
+def test_empty_rows_apply():
+    n = 70
+    rp = np.zeros(n + 1, np.int32)
+    rows = [3, 4, 40, 69]
+    cols, vals = [], []
+    for r in range(n):
+        if r in rows:
+            cols += [r, (r * 7) % n]
+            vals += [2.0, -1.0]
+        rp[r + 1] = len(cols)
+    A = inputs.CSR(n=n, row_ptr=rp, col=np.array(cols, np.int32), val=np.array(vals))
+    s = _solver(A)
+    v = inputs.gaussian_rhs(n, 1)
+    assert _rel(s.apply(v), A.to_scipy() @ v) <= 1e-15
+
+
+# ---------------------------------------------------------------- full size (128^3)
+@pytest.mark.slow
+def test_full_size_shifted_3d_plain_and_recycled():
+    """One system of the 128^3 shifted sequence at full size: GPU vs oracle."""
+    spec = inputs.config_shifted_3d(N=128, n_shifts=20, n_rhs=1)
+    P = spec.pattern
+    vals = spec.values[0]()
+    b = spec.rhs[0][0]()
+    S = sp.csr_matrix((vals, P.col, P.row_ptr), shape=(P.n, P.n))
+    s = rb.Solver(recycle="none")
+    s.set_matrix(P.row_ptr, P.col, vals)
+    res = s.solve(b)
+    xo, io = orb.rbicgstab(S, b, None, tol=1e-8)
+    assert _iters_close(res.stats["iters"], io.iters), (res.stats["iters"], io.iters)
+    assert _rel(res.x, xo) <= XTOL
+    assert np.linalg.norm(b - S @ res.x) / np.linalg.norm(b) <= 1.5e-8
+    # SpMV sampled rows, computed one by one by the oracle's CSR definition
+    v = inputs.gaussian_rhs(P.n, 77)
+    y = s.apply(v)
+    rows = np.random.default_rng(0).integers(0, P.n, 2000)
+    for i in rows[:200]:
+        lo, hi = P.row_ptr[i], P.row_ptr[i + 1]
+        ref = float(np.dot(vals[lo:hi], v[P.col[lo:hi]]))
+        assert abs(y[i] - ref) <= 1e-13 * (abs(ref) + 1.0)
