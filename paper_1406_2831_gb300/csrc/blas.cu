@@ -28,7 +28,7 @@ __global__ void __launch_bounds__(kBlock) k_dots(DotArgs d, int64_t npad, IterSt
     for (int q = 0; q < 4; ++q)
       if (q < d.nd) acc[KMAX + q] = fma(d.a[q][i], d.b[q][i], acc[KMAX + q]);
   }
-  if (block_reduce_last<NV>(acc, sm, partials, &st->ticket[PGEN])) {
+  if (block_reduce_last<NV>(acc, KMAX + 4, sm, partials, &st->ticket[PGEN])) {
     if (threadIdx.x < d.km) st->red[threadIdx.x] = sm.res[threadIdx.x];
     if (threadIdx.x < d.nd) st->red[d.km + threadIdx.x] = sm.res[KMAX + threadIdx.x];
   }
@@ -44,7 +44,9 @@ cudaError_t dots(const DotArgs& d, int64_t npad, IterState* st, double* partials
     case 0: k_dots<0><<<grid, kBlock, 0, s>>>(dd, npad, st, partials); break;
     case 8: k_dots<8><<<grid, kBlock, 0, s>>>(dd, npad, st, partials); break;
     case 16: k_dots<16><<<grid, kBlock, 0, s>>>(dd, npad, st, partials); break;
+    case 24: k_dots<24><<<grid, kBlock, 0, s>>>(dd, npad, st, partials); break;
     case 32: k_dots<32><<<grid, kBlock, 0, s>>>(dd, npad, st, partials); break;
+    case 48: k_dots<48><<<grid, kBlock, 0, s>>>(dd, npad, st, partials); break;
     default: k_dots<64><<<grid, kBlock, 0, s>>>(dd, npad, st, partials); break;
   }
   return cudaGetLastError();
@@ -236,7 +238,7 @@ __global__ void __launch_bounds__(kBlock) k_residual(Sell<double> A, const doubl
     r[row] = rv;
     acc[0] = fma(rv, rv, acc[0]);
   }
-  if (block_reduce_last<1>(acc, sm, partials, &st->ticket[PGEN]) && threadIdx.x == 0)
+  if (block_reduce_last<1>(acc, 1, sm, partials, &st->ticket[PGEN]) && threadIdx.x == 0)
     st->red[0] = sm.res[0];
 }
 

@@ -29,11 +29,15 @@ struct ReduceSmem {
   int last;
 };
 
-// Reduce acc[0..NV) over the grid.  Returns true in every thread of the last
-// block, with sm.res[0..NV) holding the grid totals.  `partials` has
-// gridDim.x * NV doubles; `ticket` is reset to 0 by the last block.
+// Reduce acc[0..nv) (nv <= NV, runtime) over the grid.  Returns true in
+// every thread of the last block, with sm.res[0..nv) holding the grid totals.
+// `partials` holds gridDim.x * nv doubles (block-major); `ticket` is reset to
+// 0 by the last block.  The last block sums the partials with every thread
+// (thread t takes blocks t, t + blockDim, ... in order), then reuses the
+// fixed warp/cross-warp tree, so the result does not depend on which block
+// finished last.
 template <int NV>
-__device__ bool block_reduce_last(double (&acc)[NV], ReduceSmem<NV>& sm, double* partials,
+__device__ bool block_reduce_last(double (&acc)[NV], int nv, ReduceSmem<NV>& sm, double* partials,
                                   unsigned int* ticket) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   constexpr int NW = kBlock / 32;
@@ -43,11 +47,11 @@ __device__ bool block_reduce_last(double (&acc)[NV], ReduceSmem<NV>& sm, double*
     for (int v = 0; v < NV; ++v) sm.w[warp][v] = acc[v];
   }
   __syncthreads();
-  for (int v = threadIdx.x; v < NV; v += blockDim.x) {
+  for (int v = threadIdx.x; v < nv; v += blockDim.x) {
     double s = 0.0;
 #pragma unroll
     for (int w = 0; w < NW; ++w) s += sm.w[w][v];
-    partials[(size_t)blockIdx.x * NV + v] = s;
+    partials[(size_t)blockIdx.x * nv + v] = s;
   }
   __threadfence();
   __syncthreads();
@@ -58,13 +62,26 @@ __device__ bool block_reduce_last(double (&acc)[NV], ReduceSmem<NV>& sm, double*
   __syncthreads();
   if (!sm.last) return false;
   __threadfence();
-  // value v is reduced by warp (v % NW): lanes take blocks lane, lane+32, ...
-  for (int v = warp; v < NV; v += NW) {
-    double s = 0.0;
-    for (int b = lane; b < (int)gridDim.x; b += 32) s += __ldcg(partials + (size_t)b * NV + v);
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-    if (lane == 0) sm.res[v] = s;
+  for (int v = 0; v < NV; ++v) acc[v] = 0.0;
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
+    const double* pb = partials + (size_t)b * nv;
+#pragma unroll
+    for (int v = 0; v < NV; ++v)
+      if (v < nv) acc[v] += __ldcg(pb + v);
+  }
+  warp_sum<NV>(acc);
+  __syncthreads();
+  if (lane == 0) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) sm.w[warp][v] = acc[v];
+  }
+  __syncthreads();
+  for (int v = threadIdx.x; v < nv; v += blockDim.x) {
+    double s = 0.0;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) s += sm.w[w][v];
+    sm.res[v] = s;
   }
   __syncthreads();
   if (threadIdx.x == 0) *ticket = 0u;

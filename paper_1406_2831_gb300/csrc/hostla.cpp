@@ -3,7 +3,8 @@
 //   * svd_small: the biorthogonalisation of C and C~ (Alg. 2 step 1 requires
 //     C~^T C diagonal and positive, Sec. 3): one-sided Jacobi SVD (Hestenes).
 //   * harmonic_ritz: the eigenproblem of the recycle update between cycles
-//     (Sec. 6.2): column scaling, pivoted Cholesky of G = Z^T Z, reduction to
+//     (Sec. 6.2): column scaling, restriction to the numerical range of W by
+//     a cyclic Jacobi eigendecomposition of the scaled G = Z^T Z, reduction to
 //     a standard problem, Householder-Hessenberg + Francis double-shift QR for
 //     the eigenvalues (Golub & Van Loan, Matrix Computations, Sec. 7.4-7.5),
 //     and complex inverse iteration for the selected eigenvectors.
@@ -294,6 +295,55 @@ static std::vector<cd> inverse_iteration(int n, const std::vector<double>& M, cd
   return v;
 }
 
+// ---------------------------------------------------------------- symmetric eig
+// Cyclic Jacobi eigenvalue algorithm (Golub & Van Loan, Sec. 8.5) for a
+// symmetric m x m matrix (column-major): S = V diag(lam) V^T.
+static void jacobi_eig(int m, const std::vector<double>& S, std::vector<double>& lam,
+                       std::vector<double>& V) {
+  std::vector<double> A = S;
+  V.assign((size_t)m * m, 0.0);
+  for (int i = 0; i < m; ++i) V[i + (size_t)i * m] = 1.0;
+  auto a = [&](int i, int j) -> double& { return A[i + (size_t)j * m]; };
+  const double eps = 2.220446049250313e-16;
+  for (int sweep = 0; sweep < 100; ++sweep) {
+    double off = 0.0, diag = 0.0;
+    for (int j = 0; j < m; ++j) {
+      diag += a(j, j) * a(j, j);
+      for (int i = 0; i < j; ++i) off += 2.0 * a(i, j) * a(i, j);
+    }
+    if (off <= eps * eps * diag || off == 0.0) break;
+    for (int p = 0; p < m - 1; ++p)
+      for (int q = p + 1; q < m; ++q) {
+        const double apq = a(p, q);
+        if (std::fabs(apq) <= 1e-300) continue;
+        if (std::fabs(apq) <= eps * 1e-3 * std::sqrt(std::fabs(a(p, p) * a(q, q)))) {
+          a(p, q) = a(q, p) = 0.0;
+          continue;
+        }
+        const double theta = (a(q, q) - a(p, p)) / (2.0 * apq);
+        const double t = (theta >= 0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(1.0 + theta * theta));
+        const double c = 1.0 / std::sqrt(1.0 + t * t), s = t * c;
+        for (int k = 0; k < m; ++k) {
+          const double akp = a(k, p), akq = a(k, q);
+          a(k, p) = c * akp - s * akq;
+          a(k, q) = s * akp + c * akq;
+        }
+        for (int k = 0; k < m; ++k) {
+          const double apk = a(p, k), aqk = a(q, k);
+          a(p, k) = c * apk - s * aqk;
+          a(q, k) = s * apk + c * aqk;
+        }
+        for (int k = 0; k < m; ++k) {
+          const double vkp = V[k + (size_t)p * m], vkq = V[k + (size_t)q * m];
+          V[k + (size_t)p * m] = c * vkp - s * vkq;
+          V[k + (size_t)q * m] = s * vkp + c * vkq;
+        }
+      }
+  }
+  lam.resize(m);
+  for (int i = 0; i < m; ++i) lam[i] = a(i, i);
+}
+
 // ---------------------------------------------------------------- harmonic Ritz
 int harmonic_ritz(int m, const double* G, const double* Hm, int k, double tol_rank, double* Y,
                   double* th_re, double* th_im) {
@@ -310,52 +360,38 @@ int harmonic_ritz(int m, const double* G, const double* Hm, int k, double tol_ra
       Gs[i + (size_t)j * m] = d[i] * G[i + (size_t)j * m] * d[j];
       Hs[i + (size_t)j * m] = d[i] * Hm[i + (size_t)j * m] * d[j];
     }
-  // pivoted Cholesky of Gs (symmetric, unit diagonal): Gs[piv,piv] = L L^T
-  std::vector<int> piv(m);
-  std::iota(piv.begin(), piv.end(), 0);
-  std::vector<double> A = Gs;   // working copy, column-major
-  auto at = [&](int i, int j) -> double& { return A[i + (size_t)j * m]; };
-  double dmax = 0.0;
-  for (int j = 0; j < m; ++j) dmax = std::max(dmax, at(j, j));
-  if (!(dmax > 0)) return 0;
-  int r = 0;
-  for (; r < m; ++r) {
-    int best = r;
-    for (int j = r + 1; j < m; ++j)
-      if (at(j, j) > at(best, best)) best = j;
-    if (!(at(best, best) > tol_rank * dmax)) break;
-    if (best != r) {
-      std::swap(piv[r], piv[best]);
-      for (int i = 0; i < m; ++i) std::swap(at(i, r), at(i, best));
-      for (int j = 0; j < m; ++j) std::swap(at(r, j), at(best, j));
-    }
-    const double l = std::sqrt(at(r, r));
-    at(r, r) = l;
-    for (int i = r + 1; i < m; ++i) at(i, r) /= l;
-    // update the whole trailing block (both triangles) so later symmetric
-    // pivots read consistent entries
-    for (int j = r + 1; j < m; ++j)
-      for (int i = r + 1; i < m; ++i) at(i, j) -= at(i, r) * at(j, r);
-    for (int j = r + 1; j < m; ++j) at(r, j) = 0.0;
-  }
+  // Restrict the pencil to the dominant eigenspace of Gs: Gs = V L V^T by
+  // cyclic Jacobi rotations; keep eigenvalues > tol_rank * max (numerical
+  // rank of W); with T = V_r L_r^{-1/2}, M = T^T Hs T and M z = (1/theta) z.
+  std::vector<double> lam, V;
+  jacobi_eig(m, Gs, lam, V);
+  double lmax = 0.0;
+  for (double v : lam) lmax = std::max(lmax, v);
+  if (!(lmax > 0)) return 0;
+  std::vector<int> keep;
+  for (int j = 0; j < m; ++j)
+    if (lam[j] > tol_rank * lmax) keep.push_back(j);
+  const int r = (int)keep.size();
   if (r == 0) return 0;
-  // M = L^{-1} Hs[piv,piv] L^{-T}   (r x r, row-major for the QR routines)
-  std::vector<double> B((size_t)r * r);
-  for (int i = 0; i < r; ++i)
-    for (int j = 0; j < r; ++j) B[(size_t)i * r + j] = Hs[piv[i] + (size_t)piv[j] * m];
-  // B <- L^{-1} B  (forward substitution on columns)
-  for (int j = 0; j < r; ++j)
-    for (int i = 0; i < r; ++i) {
-      double s = B[(size_t)i * r + j];
-      for (int q = 0; q < i; ++q) s -= at(i, q) * B[(size_t)q * r + j];
-      B[(size_t)i * r + j] = s / at(i, i);
+  std::vector<double> T((size_t)m * r);   // column-major m x r
+  for (int c = 0; c < r; ++c) {
+    const double f = 1.0 / std::sqrt(lam[keep[c]]);
+    for (int i = 0; i < m; ++i) T[i + (size_t)c * m] = V[i + (size_t)keep[c] * m] * f;
+  }
+  // HT = Hs T (m x r), then B = T^T HT (r x r, row-major)
+  std::vector<double> HT((size_t)m * r, 0.0);
+  for (int c = 0; c < r; ++c)
+    for (int j = 0; j < m; ++j) {
+      const double t = T[j + (size_t)c * m];
+      if (t == 0.0) continue;
+      for (int i = 0; i < m; ++i) HT[i + (size_t)c * m] += Hs[i + (size_t)j * m] * t;
     }
-  // B <- B L^{-T}  (solve X L^T = B row by row)
-  for (int i = 0; i < r; ++i)
-    for (int j = 0; j < r; ++j) {
-      double s = B[(size_t)i * r + j];
-      for (int q = 0; q < j; ++q) s -= B[(size_t)i * r + q] * at(j, q);
-      B[(size_t)i * r + j] = s / at(j, j);
+  std::vector<double> B((size_t)r * r, 0.0);
+  for (int a = 0; a < r; ++a)
+    for (int c = 0; c < r; ++c) {
+      double acc = 0.0;
+      for (int i = 0; i < m; ++i) acc += T[i + (size_t)a * m] * HT[i + (size_t)c * m];
+      B[(size_t)a * r + c] = acc;
     }
   std::vector<double> Hh = B, wr(r), wi(r);
   hessenberg(r, Hh);
@@ -383,15 +419,11 @@ int harmonic_ritz(int m, const double* G, const double* Hm, int k, double tol_ra
     const int need = u.cplx ? 2 : 1;
     if (used + need > k) break;
     std::vector<cd> z = inverse_iteration(r, B, u.mu);
-    // w = L^{-T} z (back substitution with L^T), then y = d .* scatter(piv, w)
-    std::vector<cd> w(z);
-    for (int i = r - 1; i >= 0; --i) {
-      cd s = w[i];
-      for (int q = i + 1; q < r; ++q) s -= at(q, i) * w[q];
-      w[i] = s / at(i, i);
-    }
+    // y = d .* (T z)
     std::vector<cd> y(m, cd(0.0));
-    for (int i = 0; i < r; ++i) y[piv[i]] = d[piv[i]] * w[i];
+    for (int c = 0; c < r; ++c)
+      for (int i = 0; i < m; ++i) y[i] += T[i + (size_t)c * m] * z[c];
+    for (int i = 0; i < m; ++i) y[i] *= d[i];
     const cd th = 1.0 / u.mu;
     for (int i = 0; i < m; ++i) Y[i + (size_t)used * m] = y[i].real();
     if (th_re) th_re[used] = th.real();

@@ -142,7 +142,7 @@ __global__ void __launch_bounds__(kBlock) k_p1(IterArgs<T> a) {
 #pragma unroll
   for (int v = 0; v < NV; ++v) acc[v] = 0.0;
   spmv_project<T, KMAX, true, false>(a, a.p_in, a.qraw, acc, k);
-  if (block_reduce_last<NV>(acc, sm, a.partials, &st->ticket[P1]) && threadIdx.x == 0)
+  if (block_reduce_last<NV>(acc, 1 + k, sm, a.partials, &st->ticket[P1]) && threadIdx.x == 0)
     finish_p1(st, sm.res, k);
 }
 
@@ -158,7 +158,7 @@ __global__ void __launch_bounds__(kBlock) k_p3(IterArgs<T> a) {
 #pragma unroll
   for (int v = 0; v < NV; ++v) acc[v] = 0.0;
   spmv_project<T, KMAX, false, DOTS>(a, a.s, a.traw, acc, k);
-  if (block_reduce_last<NV>(acc, sm, a.partials, &st->ticket[P3]) && threadIdx.x == 0) {
+  if (block_reduce_last<NV>(acc, DOTS ? 4 : k, sm, a.partials, &st->ticket[P3]) && threadIdx.x == 0) {
     if (DOTS) finish_p4(st, sm.res, 0);
     else finish_p3(st, sm.res, k);
   }
@@ -190,7 +190,7 @@ __global__ void __launch_bounds__(kBlock) k_p2(IterArgs<T> a) {
     a.s[i] = sv;
     acc[0] = fma((double)sv, (double)sv, acc[0]);
   }
-  if (block_reduce_last<1>(acc, sm, a.partials, &st->ticket[P2]) && threadIdx.x == 0)
+  if (block_reduce_last<1>(acc, 1, sm, a.partials, &st->ticket[P2]) && threadIdx.x == 0)
     finish_p2(st, sm.res);
 }
 
@@ -218,7 +218,7 @@ __global__ void __launch_bounds__(kBlock) k_p4(IterArgs<T> a) {
     acc[2] = fma(rv, td, acc[2]);
     acc[3] = fma(rv, sv, acc[3]);
   }
-  if (block_reduce_last<4>(acc, sm, a.partials, &st->ticket[P4]) && threadIdx.x == 0)
+  if (block_reduce_last<4>(acc, 4, sm, a.partials, &st->ticket[P4]) && threadIdx.x == 0)
     finish_p4(st, sm.res, k);
 }
 
@@ -247,7 +247,7 @@ __global__ void __launch_bounds__(kBlock) k_p5(IterArgs<T> a) {
       acc[0] = fma((double)rv, (double)rv, acc[0]);
     }
   }
-  if (block_reduce_last<1>(acc, sm, a.partials, &st->ticket[P5]) && threadIdx.x == 0)
+  if (block_reduce_last<1>(acc, 1, sm, a.partials, &st->ticket[P5]) && threadIdx.x == 0)
     finish_p5(st, sm.res, k);
 }
 
@@ -278,7 +278,9 @@ int kmax_bucket(int k) {
   if (k <= 0) return 0;
   if (k <= 8) return 8;
   if (k <= 16) return 16;
+  if (k <= 24) return 24;
   if (k <= 32) return 32;
+  if (k <= 48) return 48;
   return 64;
 }
 
@@ -288,7 +290,9 @@ cudaError_t launch_iteration(const IterArgs<T>& a, int k, const Grids& g, cudaSt
     case 0: return launch_iter_k<T, 0>(a, g, s);
     case 8: return launch_iter_k<T, 8>(a, g, s);
     case 16: return launch_iter_k<T, 16>(a, g, s);
+    case 24: return launch_iter_k<T, 24>(a, g, s);
     case 32: return launch_iter_k<T, 32>(a, g, s);
+    case 48: return launch_iter_k<T, 48>(a, g, s);
     default: return launch_iter_k<T, 64>(a, g, s);
   }
 }
@@ -300,7 +304,9 @@ cudaError_t launch_pass(int pass, const IterArgs<T>& a, int k, const Grids& g, c
     case 0: return launch_pass_k<T, 0>(pass, a, g, s);
     case 8: return launch_pass_k<T, 8>(pass, a, g, s);
     case 16: return launch_pass_k<T, 16>(pass, a, g, s);
+    case 24: return launch_pass_k<T, 24>(pass, a, g, s);
     case 32: return launch_pass_k<T, 32>(pass, a, g, s);
+    case 48: return launch_pass_k<T, 48>(pass, a, g, s);
     default: return launch_pass_k<T, 64>(pass, a, g, s);
   }
 }
@@ -327,7 +333,9 @@ void iteration_grids(int k, int nsm, int64_t npad, Grids* g) {
     case 0: f1 = (const void*)k_p1<T, 0>; f2 = (const void*)k_p5<T, 0>; break;
     case 8: f1 = (const void*)k_p1<T, 8>; f2 = (const void*)k_p2<T, 8>; break;
     case 16: f1 = (const void*)k_p1<T, 16>; f2 = (const void*)k_p2<T, 16>; break;
+    case 24: f1 = (const void*)k_p1<T, 24>; f2 = (const void*)k_p2<T, 24>; break;
     case 32: f1 = (const void*)k_p1<T, 32>; f2 = (const void*)k_p2<T, 32>; break;
+    case 48: f1 = (const void*)k_p1<T, 48>; f2 = (const void*)k_p2<T, 48>; break;
     default: f1 = (const void*)k_p1<T, 64>; f2 = (const void*)k_p2<T, 64>; break;
   }
   const int64_t work_blocks = (npad + kBlock - 1) / kBlock;

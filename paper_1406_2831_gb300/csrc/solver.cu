@@ -900,8 +900,13 @@ static int solve_fp64(rb_ctx* h, SolveOut* so, bool x_nonzero) {
   const bool upd = (h->o.recycle_mode == RB_RECYCLE_UPDATE_ALL) ||
                    (h->o.recycle_mode == RB_RECYCLE_UPDATE_FIRST && h->update_epoch != h->matrix_epoch);
   if (!h->hst->done) {
-    if (upd) rc = iterate_cycles(h, so);
-    else rc = iterate_plain<double>(h);
+    if (upd) {
+      rc = iterate_cycles(h, so);
+    } else {
+      // p_1 = r_0 (Alg. 2 step 4 with beta_0 = 0)
+      RB_CUDA_TRY(cudaMemcpyAsync(h->p, h->r, sizeof(double) * h->npad, cudaMemcpyDeviceToDevice, h->us));
+      rc = iterate_plain<double>(h);
+    }
     if (rc) return rc;
   }
   rc = finish_solve(h, so, true);
@@ -936,7 +941,9 @@ static int solve_mixed(rb_ctx* h, SolveOut* so, bool x_nonzero) {
   const int64_t ld = h->npad;
   (void)x_nonzero;
   const double bn2 = h->hst->red[0];
-  const double target = h->o.tol * std::sqrt(bn2);
+  // refine to a tenth of the tolerance: the last FP32 correction then leaves
+  // a forward error comparable to the FP64 solver's at the tolerance itself
+  const double target = 0.1 * h->o.tol * std::sqrt(bn2);
   const int max_outer = 12;
   int outer = 0, total_it = 0, last_status = RB_OK;
   double rn = 0.0;
