@@ -164,6 +164,28 @@ int rbicgstab_harmonic_ritz(int32_t m, const double* G, const double* H, int32_t
  * Errors: RB_EINVAL (reps outside 1..1000), RB_EDIM. */
 int rbicgstab_time_passes(rb_handle h, const double* b, int where, int32_t reps, double* ms);
 
+/* Residual without allocation: r = b - A x and *rnorm2 = ||r||^2 for an n x n
+ * CSR matrix given by device pointers (row_ptr[n+1], col[nnz], val[nnz]), with
+ * x, b, r (n entries each) and rnorm2 (one double) also in device memory.
+ * The paper has no counterpart: this is for callers that cannot allocate
+ * device memory (a framework that owns the allocator and forbids cudaMalloc,
+ * work about to be captured into a CUDA graph, a service whose device memory
+ * is sized once at start-up).  Nothing is allocated and no handle is needed:
+ * the kernel's scratch (1024 block partial sums and a completion ticket,
+ * about 8 KB) is a fixed device array that every GPU loading the library
+ * keeps until the process exits.  The first call on a device looks up that
+ * array's address (which can load the module): make it before any stream
+ * capture.  The call is ordered on `cuda_stream` (NULL = legacy default
+ * stream) and does not synchronise; outputs are ready when the stream gets
+ * there.  All calls share the one scratch array, so calls whose kernels can
+ * overlap on the GPU (different streams, or different host threads) race;
+ * serialise them.  The CSR is not validated (pass a matrix that
+ * rbicgstab_set_matrix accepts).  Errors: RB_EINVAL (n <= 0, n > 2^31 - 1,
+ * or a NULL pointer), RB_ECUDA. */
+int rbicgstab_residual_noalloc(int64_t n, const int32_t* row_ptr, const int32_t* col,
+                               const double* val, const double* x, const double* b, double* r,
+                               double* rnorm2, void* cuda_stream);
+
 /* Number of CUDA kernels this library has launched in the process so far
  * (each graph replay adds the kernels its graph holds).  Thread-safe. */
 long long rbicgstab_kernel_launches(void);

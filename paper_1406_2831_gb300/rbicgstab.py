@@ -87,6 +87,8 @@ def lib():
     L.rbicgstab_apply.argtypes = [vp, dp, dp, ctypes.c_int, ctypes.c_int]
     L.rbicgstab_harmonic_ritz.argtypes = [i32, dp, dp, i32, dp, dp, dp, ctypes.POINTER(i32)]
     L.rbicgstab_time_passes.argtypes = [vp, dp, ctypes.c_int, i32, dp]
+    L.rbicgstab_residual_noalloc.argtypes = [i64, dp, dp, dp, dp, dp, dp, dp, vp]
+    L.rbicgstab_residual_noalloc.restype = ctypes.c_int
     L.rbicgstab_kernel_launches.argtypes = []
     L.rbicgstab_kernel_launches.restype = ctypes.c_longlong
     L.rbicgstab_error_string.argtypes = [ctypes.c_int]
@@ -259,6 +261,22 @@ class Solver:
             yp = y.ctypes.data
         _check(lib().rbicgstab_apply(self._h, vp, yp, int(bool(transpose)), w), "rbicgstab_apply")
         return y
+
+
+def residual_noalloc(row_ptr, col, val, x, b, r, rnorm2, stream=None, n=None) -> int:
+    """r = b - A x and rnorm2[0] = ||r||^2 (rbicgstab_residual_noalloc).
+
+    For callers that cannot allocate device memory: every argument is a CUDA
+    tensor the caller owns (int32 row_ptr/col, float64 val/x/b/r, a
+    one-element float64 rnorm2); the library allocates nothing.  Ordered on
+    ``stream`` (default: the legacy default stream), not synchronised."""
+    args = [t.data_ptr() for t in (row_ptr, col, val, x, b, r, rnorm2)]
+    for t in (row_ptr, col, val, x, b, r, rnorm2):
+        if not (_is_torch(t) and t.is_cuda and t.is_contiguous()):
+            raise ValueError("residual_noalloc takes contiguous CUDA tensors")
+    nn = (row_ptr.numel() - 1) if n is None else int(n)
+    sp = None if stream is None else (stream if isinstance(stream, int) else stream.cuda_stream)
+    return _check(lib().rbicgstab_residual_noalloc(nn, *args, sp), "rbicgstab_residual_noalloc")
 
 
 def kernel_launches() -> int:
