@@ -48,6 +48,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--quick", action="store_true", help="small grid for a smoke run (not a bench line)")
+    ap.add_argument("--passes-only", action="store_true",
+                    help="set up one system and a k-column right-only recycle space, time the five "
+                         "fused passes (recycled and plain) and exit; a short program for profilers")
     return ap.parse_args()
 
 
@@ -172,6 +175,38 @@ def cpu_oracle_timing(N, shifts, k, its=10) -> dict:
 
 
 # ---------------------------------------------------------------- our arm
+def run_passes_only(args):
+    """Per-pass CUDA-event timings on one system of the sequence (no solves)."""
+    import numpy as np
+    import torch
+
+    from paper_1406_2831_gb300 import inputs
+    from paper_1406_2831_gb300 import rbicgstab as rb
+
+    spec = inputs.config_shifted_3d(N=args.N, n_shifts=args.shifts, n_rhs=1, k=args.k)
+    P = spec.pattern
+    dev = torch.device("cuda", 0)
+    vals = torch.from_numpy(spec.values[0]()).to(dev)
+    b = torch.from_numpy(spec.rhs[0][0]()).to(dev)
+    rp, col = torch.from_numpy(P.row_ptr).to(dev), torch.from_numpy(P.col).to(dev)
+    out = {"workload": f"3d-7pt-{args.N}^3 system 1", "n": P.n, "nnz": P.nnz, "k": args.k,
+           "precision": args.precision}
+    for label, k in (("recycled", args.k), ("plain", 0)):
+        s = rb.Solver(k_max=k, recycle="fixed" if k else "none", precision=args.precision)
+        s.set_matrix(rp, col, vals)
+        if k:
+            U = torch.from_numpy(inputs.random_recycle_basis(P.n, k, 11)).to(dev)
+            s.set_recycle(U)
+        ms, code = rb.time_passes(s, b, reps=5)
+        vb = 8 if args.precision == "fp64" else 4
+        pb = pass_bytes(P.n, P.nnz, k, vb=vb, ab=vb)
+        out[label] = {"passes_ms": [round(v, 5) for v in ms],
+                      "passes_GBs": [round(bb / (m * 1e-3) / 1e9, 1) if m > 0 else 0 for bb, m in zip(pb, ms)],
+                      "status": code}
+        del s
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -207,7 +242,7 @@ def run_ours(args):
 
     def make(recycled: bool, precision: str):
         s = rb.Solver(k_max=args.k if recycled else 0, cycle_s=spec.cycle_s,
-                      recycle=("update_first" if precision == "fp64" else "fixed") if recycled else "none",
+                      recycle="update_first" if recycled else "none",
                       precision=precision, tol=spec.tol, stream=stream)
         s.set_matrix(rp, col, vals_d[0])
         return s
@@ -405,7 +440,10 @@ def run_reference(args):
 
 def main():
     args = parse()
-    line = run_reference(args) if args.impl == "reference" else run_ours(args)
+    if args.passes_only:
+        line = run_passes_only(args)
+    else:
+        line = run_reference(args) if args.impl == "reference" else run_ours(args)
     if line is not None:
         print(json.dumps(line), flush=True)
 

@@ -77,77 +77,85 @@ cudaError_t gemv_update(double* y, const double* M, int64_t ld, int k, const dou
 
 // ---------------------------------------------------------------- block GEMM
 // Out(:, c) = X R(:, c): each thread owns one row, reads the m entries of
-// X's row once and forms all kc outputs (kc <= kMaxK).
-__global__ void k_gemm_cols(double* const* __restrict__ out, const double* const* __restrict__ X, int m,
+// X's row once and forms all kc outputs (kc <= kMaxK), accumulating in T.
+template <typename T>
+__global__ void k_gemm_cols(T* const* __restrict__ out, const T* const* __restrict__ X, int m,
                             const double* __restrict__ R, int kc, int64_t npad) {
-  extern __shared__ double sR[];   // m * kc
-  for (int e = threadIdx.x; e < m * kc; e += blockDim.x) sR[e] = R[e];
+  extern __shared__ __align__(16) unsigned char gem_sm[];
+  T* sR = (T*)gem_sm;   // m * kc coefficients in the column type
+  for (int e = threadIdx.x; e < m * kc; e += blockDim.x) sR[e] = (T)R[e];
   __syncthreads();
-  double acc[kMaxK];
+  T acc[kMaxK];
   for (int64_t i = gtid(); i < npad; i += gstride()) {
-    for (int c = 0; c < kc; ++c) acc[c] = 0.0;
+    for (int c = 0; c < kc; ++c) acc[c] = T(0);
     for (int j = 0; j < m; ++j) {
-      const double xv = X[j][i];
-      for (int c = 0; c < kc; ++c) acc[c] = fma(xv, sR[j + c * m], acc[c]);
+      const T xv = X[j][i];
+      for (int c = 0; c < kc; ++c) acc[c] = fma_t(xv, sR[j + c * m], acc[c]);
     }
     for (int c = 0; c < kc; ++c) out[c][i] = acc[c];
   }
 }
 
-cudaError_t gemm_cols(double* const* out, const double* const* X, int m, const double* R,
-                      int kc, int64_t npad, int grid, cudaStream_t s) {
+template <typename T>
+cudaError_t gemm_cols(T* const* out, const T* const* X, int m, const double* R, int kc, int64_t npad,
+                      int grid, cudaStream_t s) {
   count_launches(1);
   if (kc <= 0 || m <= 0) return cudaSuccess;
-  const size_t smem = sizeof(double) * (size_t)m * kc;
+  const size_t smem = sizeof(T) * (size_t)m * kc;
   if (smem > 48 * 1024)
-    cudaFuncSetAttribute(k_gemm_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k_gemm_cols<<<grid, kBlock, smem, s>>>(out, X, m, R, kc, npad);
+    cudaFuncSetAttribute(k_gemm_cols<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_gemm_cols<T><<<grid, kBlock, smem, s>>>(out, X, m, R, kc, npad);
   return cudaGetLastError();
 }
+template cudaError_t gemm_cols<double>(double* const*, const double* const*, int, const double*, int,
+                                       int64_t, int, cudaStream_t);
+template cudaError_t gemm_cols<float>(float* const*, const float* const*, int, const double*, int,
+                                      int64_t, int, cudaStream_t);
 
 // ---------------------------------------------------------------- Gram X^T Y
 // Each block walks row tiles of 32 rows, stages X and Y tiles in shared
-// memory, and accumulates the (a, b) products it owns; block partials are
-// reduced in block order by a second kernel.
+// memory, and accumulates the (a, b) products it owns (FP64 FMA for FP64
+// columns, Dot2 for FP32 columns); block partials are reduced in block order
+// by a second kernel.
 constexpr int kGramRows = 32;
 
-__global__ void __launch_bounds__(kBlock) k_gram(const double* const* __restrict__ X, int mx,
-                                                const double* const* __restrict__ Y, int my,
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_gram(const T* const* __restrict__ X, int mx,
+                                                const T* const* __restrict__ Y, int my,
                                                 int64_t npad, double* __restrict__ work) {
-  extern __shared__ double sm[];
-  double* sx = sm;                        // kGramRows * mx
-  double* sy = sm + kGramRows * mx;       // kGramRows * my
+  extern __shared__ __align__(16) unsigned char gsm[];
+  T* sx = (T*)gsm;                        // kGramRows * mx
+  T* sy = sx + kGramRows * mx;            // kGramRows * my
   const int nout = mx * my;
   const int per = (nout + blockDim.x - 1) / blockDim.x;   // outputs per thread (<= 32)
-  double acc[32];
-  for (int u = 0; u < per; ++u) acc[u] = 0.0;
+  Acc<T> acc[32];
   const int64_t ntiles = (npad + kGramRows - 1) / kGramRows;
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int64_t r0 = tile * kGramRows;
     __syncthreads();
     for (int e = threadIdx.x; e < kGramRows * mx; e += blockDim.x) {
       const int a = e / kGramRows, rr = e % kGramRows;
-      sx[rr * mx + a] = (r0 + rr < npad) ? X[a][r0 + rr] : 0.0;
+      sx[rr * mx + a] = (r0 + rr < npad) ? X[a][r0 + rr] : T(0);
     }
     for (int e = threadIdx.x; e < kGramRows * my; e += blockDim.x) {
       const int b = e / kGramRows, rr = e % kGramRows;
-      sy[rr * my + b] = (r0 + rr < npad) ? Y[b][r0 + rr] : 0.0;
+      sy[rr * my + b] = (r0 + rr < npad) ? Y[b][r0 + rr] : T(0);
     }
     __syncthreads();
     for (int u = 0; u < per; ++u) {
       const int o = threadIdx.x + u * blockDim.x;
       if (o < nout) {
         const int a = o % mx, b = o / mx;
-        double s = acc[u];
+        Acc<T> sacc = acc[u];
 #pragma unroll 8
-        for (int rr = 0; rr < kGramRows; ++rr) s = fma(sx[rr * mx + a], sy[rr * my + b], s);
-        acc[u] = s;
+        for (int rr = 0; rr < kGramRows; ++rr) sacc.add(sx[rr * mx + a], sy[rr * my + b]);
+        acc[u] = sacc;
       }
     }
   }
   for (int u = 0; u < per; ++u) {
     const int o = threadIdx.x + u * blockDim.x;
-    if (o < nout) work[(size_t)blockIdx.x * nout + o] = acc[u];
+    if (o < nout) work[(size_t)blockIdx.x * nout + o] = acc[u].get();
   }
 }
 
@@ -159,19 +167,24 @@ __global__ void k_gram_reduce(const double* __restrict__ work, int nblocks, int 
   }
 }
 
-cudaError_t gram(const double* const* X, int mx, const double* const* Y, int my, int64_t npad,
-                 double* out, double* work, int grid, cudaStream_t s) {
+template <typename T>
+cudaError_t gram(const T* const* X, int mx, const T* const* Y, int my, int64_t npad, double* out,
+                 double* work, int grid, cudaStream_t s) {
   count_launches(2);
   if (mx <= 0 || my <= 0) return cudaSuccess;
   if (mx * my > 32 * kBlock) return cudaErrorInvalidValue;
-  const size_t smem = sizeof(double) * kGramRows * (size_t)(mx + my);
+  const size_t smem = sizeof(T) * kGramRows * (size_t)(mx + my);
   if (smem > 48 * 1024)
-    cudaFuncSetAttribute(k_gram, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k_gram<<<grid, kBlock, smem, s>>>(X, mx, Y, my, npad, work);
+    cudaFuncSetAttribute(k_gram<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_gram<T><<<grid, kBlock, smem, s>>>(X, mx, Y, my, npad, work);
   const int nout = mx * my;
   k_gram_reduce<<<(nout + kBlock - 1) / kBlock, kBlock, 0, s>>>(work, grid, nout, out);
   return cudaGetLastError();
 }
+template cudaError_t gram<double>(const double* const*, int, const double* const*, int, int64_t, double*,
+                                  double*, int, cudaStream_t);
+template cudaError_t gram<float>(const float* const*, int, const float* const*, int, int64_t, double*,
+                                 double*, int, cudaStream_t);
 
 // ---------------------------------------------------------------- shadow r~_{-1}
 // SplitMix64 (Steele, Lea, Flood 2014), output i from state `seed`:
@@ -203,19 +216,22 @@ cudaError_t shadow(double* rt, int64_t n, int64_t npad, uint64_t seed, cudaStrea
 }
 
 // ---------------------------------------------------------------- column scaling
-__global__ void k_scale_cols(double* M, int64_t ld, int k, const double* f, int64_t npad) {
+template <typename T>
+__global__ void k_scale_cols(T* M, int64_t ld, int k, const double* f, int64_t npad) {
   for (int64_t i = gtid(); i < npad; i += gstride())
-    for (int j = 0; j < k; ++j) M[j * ld + i] *= f[j];
+    for (int j = 0; j < k; ++j) M[j * ld + i] = (T)((double)M[j * ld + i] * f[j]);
 }
 
-cudaError_t scale_cols(double* M, int64_t ld, int k, const double* f, int64_t npad,
-                       cudaStream_t s) {
+template <typename T>
+cudaError_t scale_cols(T* M, int64_t ld, int k, const double* f, int64_t npad, cudaStream_t s) {
   count_launches(1);
   if (k <= 0) return cudaSuccess;
   int g = (int)std::min<int64_t>((npad + kBlock - 1) / kBlock, 8192);
-  k_scale_cols<<<g, kBlock, 0, s>>>(M, ld, k, f, npad);
+  k_scale_cols<T><<<g, kBlock, 0, s>>>(M, ld, k, f, npad);
   return cudaGetLastError();
 }
+template cudaError_t scale_cols<double>(double*, int64_t, int, const double*, int64_t, cudaStream_t);
+template cudaError_t scale_cols<float>(float*, int64_t, int, const double*, int64_t, cudaStream_t);
 
 // ---------------------------------------------------------------- residual
 __global__ void __launch_bounds__(kBlock) k_residual(Sell<double> A, const double* __restrict__ b,
@@ -272,6 +288,16 @@ cudaError_t to_float(const double* in, float* out, int64_t n, cudaStream_t s) {
   count_launches(1);
   int g = (int)std::min<int64_t>((n + kBlock - 1) / kBlock, 8192);
   if (n > 0) k_to_float<<<g, kBlock, 0, s>>>(in, out, n);
+  return cudaGetLastError();
+}
+
+__global__ void k_to_double(const float* in, double* out, int64_t n) {
+  for (int64_t i = gtid(); i < n; i += gstride()) out[i] = (double)in[i];
+}
+cudaError_t to_double(const float* in, double* out, int64_t n, cudaStream_t s) {
+  count_launches(1);
+  int g = (int)std::min<int64_t>((n + kBlock - 1) / kBlock, 8192);
+  if (n > 0) k_to_double<<<g, kBlock, 0, s>>>(in, out, n);
   return cudaGetLastError();
 }
 

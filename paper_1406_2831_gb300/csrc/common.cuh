@@ -10,6 +10,12 @@
 
 namespace rb {
 
+// Fused multiply-add in the precision of its operands.  Templated code calls
+// this instead of fma() so that FP32 arithmetic can never be promoted to the
+// FP64 overload (FP64 runs on two lanes per SM per clock on this GPU).
+__device__ __forceinline__ float fma_t(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_t(double a, double b, double c) { return __fma_rn(a, b, c); }
+
 constexpr int kSlice = 32;        // SELL slice height = warp width
 constexpr int kBlock = 256;       // threads per block of the streaming kernels
 constexpr int kMaxK = RB_KMAX;

@@ -1,81 +1,139 @@
 // Device helpers: deterministic block + grid reductions ("last block" pattern).
 //
-// Every fused pass accumulates NV per-thread partial sums in FP64.  A block
-// reduces them with a fixed warp-shuffle tree and a fixed cross-warp order,
-// writes one row of `partials`, and takes a ticket.  The block that takes the
-// last ticket reduces all rows in block order (fixed, independent of which
-// block finishes last) and runs the pass's scalar step.  Results are bitwise
-// reproducible run to run.
+// Every fused pass accumulates nv per-thread partial sums in FP64.  A block
+// sums them through shared memory in a fixed order, writes one row of
+// `partials`, and takes a ticket.  The block that takes the last ticket sums
+// all rows (every thread takes a fixed subset of blocks) and runs the pass's
+// scalar step.  Results are bitwise reproducible run to run.
+//
+// FP64 adds are scarce on this GPU (two FP64 lanes per SM per clock), so the
+// block sum is a shared-memory transpose (one add per partial) rather than a
+// warp-shuffle tree (five adds per lane per value).
 #pragma once
 
 #include "common.cuh"
 
 namespace rb {
 
-template <int NV>
-__device__ __forceinline__ void warp_sum(double (&a)[NV]) {
-#pragma unroll
-  for (int v = 0; v < NV; ++v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) a[v] += __shfl_down_sync(0xffffffffu, a[v], o);
-  }
-}
+// Per-thread dot-product accumulator.  FP64 data accumulate with FP64 FMA.
+// FP32 data (the inner solve of the mixed path) accumulate with the Dot2
+// scheme of Ogita, Rump and Oishi ("Accurate sum and dot product", SIAM J.
+// Sci. Comput. 26, 2005): each product a*b is split exactly into p + e with an
+// FMA, p is added to the running sum with Knuth's TwoSum, and the rounding
+// errors are collected in a second FP32 word.  The pair (hi, lo) carries about
+// twice FP32's precision, and the per-thread result is handed to the FP64 grid
+// reduction as hi + lo.  This keeps FP64-class dot products on the FP32 pipes.
+template <typename T>
+struct Acc;
 
-// Shared memory needed by block_reduce_last: NWARPS * NV + NV doubles + flag.
+template <>
+struct Acc<double> {
+  double v = 0.0;
+  __device__ __forceinline__ void add(double a, double b) { v = fma(a, b, v); }
+  __device__ __forceinline__ double get() const { return v; }
+};
+
+template <>
+struct Acc<float> {
+  float hi = 0.0f, lo = 0.0f;
+  // The _rn intrinsics are never contracted into FMAs, which would break the
+  // exactness of the error-free transformations.
+  __device__ __forceinline__ void add(float a, float b) {
+    const float p = __fmul_rn(a, b);
+    const float e = __fmaf_rn(a, b, -p);                 // a*b = p + e exactly
+    const float s = __fadd_rn(hi, p);                    // TwoSum(hi, p) = s + err
+    const float bb = __fsub_rn(s, hi);
+    const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+    hi = s;
+    lo = __fadd_rn(lo, __fadd_rn(err, e));
+  }
+  __device__ __forceinline__ double get() const { return (double)hi + (double)lo; }
+};
+
 template <int NV>
 struct ReduceSmem {
-  double w[kBlock / 32][NV > 0 ? NV : 1];
+  static constexpr int CH = 8;                  // values per transpose chunk
+  double t[kBlock / 32][CH][33];                // [warp][value][lane] (+1 pad)
+  double w[kBlock / 32][NV > 0 ? NV : 1];      // per-warp sums
   double res[NV > 0 ? NV : 1];
   int last;
 };
 
-// Reduce acc[0..nv) (nv <= NV, runtime) over the grid.  Returns true in
-// every thread of the last block, with sm.res[0..nv) holding the grid totals.
-// `partials` holds gridDim.x * nv doubles (block-major); `ticket` is reset to
-// 0 by the last block.  The last block sums the partials with every thread
-// (thread t takes blocks t, t + blockDim, ... in order), then reuses the
-// fixed warp/cross-warp tree, so the result does not depend on which block
-// finished last.
+// Warp-level sums of per-thread accumulators into sm.w[warp][v].
+// * FP32 Dot2 pairs (hi, lo): shuffle tree combining pairs with TwoSum in
+//   FP32, one conversion to FP64 per warp and value.
+// * FP64 values: the FP64 pipe is charged per warp instruction (about 16
+//   cycles each, however many lanes are active), so few values use the
+//   5-step shuffle tree (5 instructions per value) and 8 or more use a
+//   shared-memory transpose (32 instructions per 8 values).
 template <int NV>
-__device__ bool block_reduce_last(double (&acc)[NV], int nv, ReduceSmem<NV>& sm, double* partials,
-                                  unsigned int* ticket) {
+__device__ __forceinline__ void warp_sums(Acc<float> (&acc)[NV], int nv, ReduceSmem<NV>& sm) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    if (v < nv) {
+      float hi = acc[v].hi, lo = acc[v].lo;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const float h2 = __shfl_down_sync(0xffffffffu, hi, o);
+        const float l2 = __shfl_down_sync(0xffffffffu, lo, o);
+        const float s = __fadd_rn(hi, h2);
+        const float bb = __fsub_rn(s, hi);
+        const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(h2, bb));
+        hi = s;
+        lo = __fadd_rn(__fadd_rn(lo, l2), e);
+      }
+      if (lane == 0) sm.w[warp][v] = (double)hi + (double)lo;
+    }
+  }
+}
+
+template <int NV>
+__device__ __forceinline__ void warp_sums(Acc<double> (&acc)[NV], int nv, ReduceSmem<NV>& sm) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (NV < 8) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      if (v < nv) {
+        double x = acc[v].v;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+        if (lane == 0) sm.w[warp][v] = x;
+      }
+    }
+    return;
+  }
+  constexpr int CH = ReduceSmem<NV>::CH;
+#pragma unroll
+  for (int c0 = 0; c0 < NV; c0 += CH) {
+    if (c0 < nv) {
+#pragma unroll
+      for (int u = 0; u < CH; ++u)
+        if (c0 + u < NV) sm.t[warp][u][lane] = acc[c0 + u].v;
+      __syncwarp();
+      if (lane < CH && c0 + lane < nv) {
+        const double* row = sm.t[warp][lane];
+        double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+#pragma unroll
+        for (int j = 0; j < 32; j += 4) {
+          s0 += row[j];
+          s1 += row[j + 1];
+          s2 += row[j + 2];
+          s3 += row[j + 3];
+        }
+        sm.w[warp][c0 + lane] = (s0 + s1) + (s2 + s3);
+      }
+      __syncwarp();
+    }
+  }
+}
+
+// Sum per-thread accumulators over the block: sm.res[v] holds the block
+// total of value v on return (after a __syncthreads).  Fixed order.
+template <typename T, int NV>
+__device__ __forceinline__ void block_sum(Acc<T> (&acc)[NV], int nv, ReduceSmem<NV>& sm) {
   constexpr int NW = kBlock / 32;
-  warp_sum<NV>(acc);
-  if (lane == 0) {
-#pragma unroll
-    for (int v = 0; v < NV; ++v) sm.w[warp][v] = acc[v];
-  }
-  __syncthreads();
-  for (int v = threadIdx.x; v < nv; v += blockDim.x) {
-    double s = 0.0;
-#pragma unroll
-    for (int w = 0; w < NW; ++w) s += sm.w[w][v];
-    partials[(size_t)blockIdx.x * nv + v] = s;
-  }
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    unsigned int t = atomicAdd(ticket, 1u);
-    sm.last = (t == gridDim.x - 1);
-  }
-  __syncthreads();
-  if (!sm.last) return false;
-  __threadfence();
-#pragma unroll
-  for (int v = 0; v < NV; ++v) acc[v] = 0.0;
-  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
-    const double* pb = partials + (size_t)b * nv;
-#pragma unroll
-    for (int v = 0; v < NV; ++v)
-      if (v < nv) acc[v] += __ldcg(pb + v);
-  }
-  warp_sum<NV>(acc);
-  __syncthreads();
-  if (lane == 0) {
-#pragma unroll
-    for (int v = 0; v < NV; ++v) sm.w[warp][v] = acc[v];
-  }
+  warp_sums<NV>(acc, nv, sm);
   __syncthreads();
   for (int v = threadIdx.x; v < nv; v += blockDim.x) {
     double s = 0.0;
@@ -84,8 +142,59 @@ __device__ bool block_reduce_last(double (&acc)[NV], int nv, ReduceSmem<NV>& sm,
     sm.res[v] = s;
   }
   __syncthreads();
+}
+
+// Second half of a grid reduction: every warp has written its sums to
+// sm.w[warp][0..nv).  Sums them across warps, publishes the block partial,
+// takes a ticket; returns true in every thread of the last block with
+// sm.res[0..nv) holding the grid totals.  `ticket` is reset to 0.
+template <int NV>
+__device__ bool grid_finish(int nv, ReduceSmem<NV>& sm, double* partials, unsigned int* ticket) {
+  constexpr int NW = kBlock / 32;
+  __syncthreads();
+  for (int v = threadIdx.x; v < nv; v += blockDim.x) {
+    double s = 0.0;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) s += sm.w[w][v];
+    partials[(size_t)blockIdx.x * nv + v] = s;
+  }
+  if (threadIdx.x < nv) __threadfence();   // only the writers publish before the ticket
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned int t = atomicAdd(ticket, 1u);
+    sm.last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!sm.last) return false;
+  __threadfence();
+  Acc<double> tot[NV];
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
+    const double* pb = partials + (size_t)b * nv;
+#pragma unroll
+    for (int v = 0; v < NV; ++v)
+      if (v < nv) tot[v].v += __ldcg(pb + v);
+  }
+  block_sum<double, NV>(tot, nv, sm);
   if (threadIdx.x == 0) *ticket = 0u;
   return true;
+}
+
+// Reduce per-thread accumulators acc[0..nv) (nv <= NV) over the grid.
+template <typename T, int NV>
+__device__ bool block_reduce_last(Acc<T> (&acc)[NV], int nv, ReduceSmem<NV>& sm, double* partials,
+                                  unsigned int* ticket) {
+  warp_sums<NV>(acc, nv, sm);
+  return grid_finish<NV>(nv, sm, partials, ticket);
+}
+
+// FP64 convenience form: per-thread doubles.
+template <int NV>
+__device__ bool block_reduce_last(double (&vals)[NV], int nv, ReduceSmem<NV>& sm, double* partials,
+                                  unsigned int* ticket) {
+  Acc<double> acc[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) acc[v].v = vals[v];
+  return block_reduce_last<double, NV>(acc, nv, sm, partials, ticket);
 }
 
 __device__ __forceinline__ int64_t gtid() { return blockIdx.x * (int64_t)blockDim.x + threadIdx.x; }

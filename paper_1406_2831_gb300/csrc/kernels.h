@@ -30,8 +30,9 @@ struct IterArgs {
 };
 
 struct Grids {
-  int spmv;
-  int vec;
+  int spmv;     // generic SpMV-shaped kernels
+  int vec;      // generic streaming kernels
+  int pass[5];  // fused passes P1..P5: one full wave each
 };
 
 int kmax_bucket(int k);
@@ -108,18 +109,22 @@ cudaError_t gemv_update(double* y, const double* M, int64_t ld, int k, const dou
                         const double* c_scale, double sign, int64_t npad, int grid,
                         cudaStream_t s);
 // Out(:, c) = sum_j X(:, j) R[j + c*m] for c < kc (column pointer lists;
-// R is m x kc column-major on the device).  Out must not alias X.
-cudaError_t gemm_cols(double* const* out, const double* const* X, int m, const double* R,
-                      int kc, int64_t npad, int grid, cudaStream_t s);
-// G[a + b*mx] = sum_i X_a[i] Y_b[i] for a < mx, b < my (column pointer lists);
-// writes mx*my doubles to `out` (device).  `work` holds grid*mx*my doubles.
-cudaError_t gram(const double* const* X, int mx, const double* const* Y, int my,
-                 int64_t npad, double* out, double* work, int grid, cudaStream_t s);
+// R is m x kc column-major FP64 on the device; accumulation in T).  Out must
+// not alias X.
+template <typename T>
+cudaError_t gemm_cols(T* const* out, const T* const* X, int m, const double* R, int kc, int64_t npad,
+                      int grid, cudaStream_t s);
+// G[a + b*mx] = sum_i X_a[i] Y_b[i] for a < mx, b < my (column pointer lists),
+// FP64 result (Dot2 accumulation for FP32 columns); writes mx*my doubles to
+// `out` (device).  `work` holds grid*mx*my doubles.
+template <typename T>
+cudaError_t gram(const T* const* X, int mx, const T* const* Y, int my, int64_t npad, double* out,
+                 double* work, int grid, cudaStream_t s);
 // Shadow vector r~[i] = 2 * u53(SplitMix64(seed, i)) - 1 for i < n, 0 beyond.
 cudaError_t shadow(double* rt, int64_t n, int64_t npad, uint64_t seed, cudaStream_t s);
 // Scale column j of M (n x k, ld) by f[j] (device array); rows < npad.
-cudaError_t scale_cols(double* M, int64_t ld, int k, const double* f, int64_t npad,
-                       cudaStream_t s);
+template <typename T>
+cudaError_t scale_cols(T* M, int64_t ld, int k, const double* f, int64_t npad, cudaStream_t s);
 // Residual r = b - A x and red[0] = ||r||^2 into st->red (deterministic).
 cudaError_t residual_norm(const Sell<double>& A, const double* b, const double* x, double* r,
                           int64_t npad, IterState* st, double* partials, int grid,
@@ -129,6 +134,7 @@ cudaError_t check_finite(const double* v, int64_t n, int* flag, cudaStream_t s);
 // Precision conversions for the mixed path.
 cudaError_t to_float(const double* in, float* out, int64_t n, cudaStream_t s);
 cudaError_t add_float_to_double(double* x, const float* d, int64_t n, cudaStream_t s);
+cudaError_t to_double(const float* in, double* out, int64_t n, cudaStream_t s);
 // Device-side solve setup: thresholds, rho_0, c_r = C^T r~_0 (from st->red).
 cudaError_t init_state(IterState* st, int k, double tol, int max_itn, cudaStream_t s);
 

@@ -252,10 +252,10 @@ __global__ void __launch_bounds__(kBlock) k_spmv(Sell<T> A, const T* __restrict_
     T acc = T(0);
     for (int j = 0; j < w; ++j) {
       const int64_t e = base + (int64_t)j * kSlice;
-      acc = fma(A.val[e], v[A.col[e]], acc);
+      acc = fma_t(A.val[e], v[A.col[e]], acc);
     }
     const T out = (T)alpha * acc;
-    y[row] = (beta == 0.0) ? out : fma((T)beta, y[row], out);
+    y[row] = (beta == 0.0) ? out : fma_t((T)beta, y[row], out);
   }
 }
 

@@ -29,8 +29,17 @@ void rb::count_launches(long long n) { g_launches.fetch_add(n, std::memory_order
 
 namespace {
 
-constexpr double kSvdDrop = 1e-12;   // biorthogonalisation: drop sigma_j < 1e-12 sigma_1
-constexpr double kRankTol = 1e-10;   // harmonic Ritz: numerical rank of scaled Z^T Z
+// Rank thresholds.  FP64 solves: biorthogonalisation drops sigma_j < 1e-12
+// sigma_1; the harmonic-Ritz pencil keeps eigenvalues > 1e-10 max of the
+// scaled Z^T Z.  The mixed path iterates with FP32 copies of C, C-hat and
+// builds the update from FP32 Krylov vectors (relative accuracy ~1e-7), so
+// both thresholds are raised to 1e-6: a projector whose C-hat^T C
+// conditioning exceeds 1e6 is not representable in FP32, and directions of W
+// below that level are rounding noise.
+constexpr double kSvdDrop = 1e-12;
+constexpr double kRankTol = 1e-10;
+constexpr double kSvdDropF32 = 1e-6;
+constexpr double kRankTolF32 = 1e-6;
 constexpr int kMaxGram = 90;         // k + 2 s must not exceed this
 
 template <typename T>
@@ -89,8 +98,10 @@ struct rb_ctx {
   int* dflag = nullptr;
   // cycle store for the recycle update
   int cyc = 0;
-  double* cstore = nullptr;     // P: 2*cyc, S: cyc, QR: cyc, TR: cyc vectors
-  double *Yc = nullptr, *AYc = nullptr, *Yn = nullptr, *AYn = nullptr;
+  // P: 2*cyc, S: cyc, QR: cyc, TR: cyc vectors of the inner precision
+  // (double for RB_FP64, float for RB_MIXED), and the candidate Y, A Y
+  void* cstore = nullptr;
+  void *Yc = nullptr, *AYc = nullptr, *Yn = nullptr, *AYn = nullptr;
   int kY = 0;
   double* gwork = nullptr;
   int64_t gwork_cap = 0;
@@ -157,7 +168,8 @@ int run_dots(rb_ctx* h, const DotArgs& d, double* out, int cnt) {
 }
 
 int ensure_partials(rb_ctx* h) {
-  const int64_t need = (int64_t)std::max(h->grids.spmv, h->grids.vec) * kMaxNV;
+  // every kernel runs at most one full wave: <= 8 blocks of 256 threads per SM
+  const int64_t need = (int64_t)std::max(8 * h->nsm, std::max(h->grids.spmv, h->grids.vec)) * kMaxNV;
   if (need <= h->partials_cap) return RB_OK;
   cudaFree(h->partials);
   int err = 0;
@@ -168,14 +180,16 @@ int ensure_partials(rb_ctx* h) {
 }
 
 // Column pointer lists for gram / gemm_cols.
-int upload_ptrs(rb_ctx* h, int slot, const std::vector<const double*>& v) {
+template <typename P>
+int upload_ptrs(rb_ctx* h, int slot, const std::vector<P>& v) {
   RB_CUDA_TRY(cudaMemcpy(h->dptr + slot * 128, v.data(), sizeof(double*) * v.size(),
                          cudaMemcpyHostToDevice));
   return RB_OK;
 }
 
 // Out = X R (column lists) with R (m x kc column-major) given on the host.
-int block_gemm(rb_ctx* h, const std::vector<double*>& out, const std::vector<const double*>& X,
+template <typename T>
+int block_gemm(rb_ctx* h, const std::vector<T*>& out, const std::vector<const T*>& X,
                const std::vector<double>& R, int kc) {
   const int m = (int)X.size();
   if (kc == 0 || m == 0) return RB_OK;
@@ -183,17 +197,17 @@ int block_gemm(rb_ctx* h, const std::vector<double*>& out, const std::vector<con
   if (rc) return rc;
   rc = upload_ptrs(h, 0, X);
   if (rc) return rc;
-  std::vector<const double*> o(out.begin(), out.end());
-  rc = upload_ptrs(h, 1, o);
+  rc = upload_ptrs(h, 1, out);
   if (rc) return rc;
   RB_CUDA_TRY(cudaMemcpy(h->dR, R.data(), sizeof(double) * (size_t)m * kc, cudaMemcpyHostToDevice));
-  RB_CUDA_TRY(gemm_cols((double* const*)(h->dptr + 128), h->dptr, m, h->dR, kc, h->npad,
-                        vec_grid(h), h->us));
+  RB_CUDA_TRY(gemm_cols<T>((T* const*)(h->dptr + 128), (const T* const*)h->dptr, m, h->dR, kc,
+                           h->npad, vec_grid(h), h->us));
   return RB_OK;
 }
 
 // G (mx x my, column-major) = X^T Y, returned on the host.
-int block_gram(rb_ctx* h, const std::vector<const double*>& X, const std::vector<const double*>& Y,
+template <typename T>
+int block_gram(rb_ctx* h, const std::vector<const T*>& X, const std::vector<const T*>& Y,
                std::vector<double>& G) {
   const int mx = (int)X.size(), my = (int)Y.size();
   G.assign((size_t)mx * my, 0.0);
@@ -213,7 +227,8 @@ int block_gram(rb_ctx* h, const std::vector<const double*>& X, const std::vector
     if (!h->gwork) return err;
     h->gwork_cap = need;
   }
-  RB_CUDA_TRY(gram(h->dptr + 256, mx, h->dptr + 384, my, h->npad, h->dG, h->gwork, grid, h->us));
+  RB_CUDA_TRY(gram<T>((const T* const*)(h->dptr + 256), mx, (const T* const*)(h->dptr + 384), my, h->npad,
+                      h->dG, h->gwork, grid, h->us));
   RB_CUDA_TRY(cudaMemcpyAsync(G.data(), h->dG, sizeof(double) * G.size(), cudaMemcpyDeviceToHost, h->us));
   return sync(h);
 }
@@ -229,7 +244,7 @@ int alloc_vectors(rb_ctx* h) {
     RB_CUDA_TRY(cudaMemsetAsync(*v, 0, sizeof(double) * h->npad, h->us));
   }
   const int kc = std::max(1, h->kcap);
-  double** ms[] = {&h->U, &h->Ut, &h->C, &h->Ct, &h->Chat, &h->T1, &h->T2, &h->Yc, &h->AYc, &h->Yn, &h->AYn};
+  double** ms[] = {&h->U, &h->Ut, &h->C, &h->Ct, &h->Chat, &h->T1, &h->T2};
   for (double** m : ms) {
     cudaFree(*m);
     *m = dalloc<double>(h->npad * kc, &err);
@@ -237,11 +252,16 @@ int alloc_vectors(rb_ctx* h) {
     RB_CUDA_TRY(cudaMemsetAsync(*m, 0, sizeof(double) * h->npad * kc, h->us));
   }
   if (h->o.recycle_mode >= RB_RECYCLE_UPDATE_FIRST) {
-    cudaFree(h->cstore);
+    const size_t es = h->o.precision == RB_MIXED ? sizeof(float) : sizeof(double);
     h->cyc = h->o.cycle_s;
-    h->cstore = dalloc<double>(h->npad * 5 * (int64_t)h->cyc, &err);
-    if (!h->cstore) return err;
-    RB_CUDA_TRY(cudaMemsetAsync(h->cstore, 0, sizeof(double) * h->npad * 5 * h->cyc, h->us));
+    void** ys[] = {&h->cstore, &h->Yc, &h->AYc, &h->Yn, &h->AYn};
+    for (void** y : ys) {
+      cudaFree(*y);
+      const int64_t cnt = (y == &h->cstore ? 5 * (int64_t)h->cyc : (int64_t)kc) * h->npad;
+      *y = dalloc<unsigned char>((int64_t)es * cnt, &err);
+      if (!*y) return err;
+      RB_CUDA_TRY(cudaMemsetAsync(*y, 0, es * cnt, h->us));
+    }
   }
   if (h->o.precision == RB_MIXED) {
     float** fs[] = {&h->fx, &h->fr, &h->fp, &h->fs, &h->fq, &h->ft, &h->fqraw, &h->ftraw, &h->frt0};
@@ -287,15 +307,16 @@ int recycle_setup(rb_ctx* h, int kin, int64_t* setup_mv) {
     Yc.push_back(colp(h->C, ld, j));
   }
   std::vector<double> M;
-  int rc = block_gram(h, Xc, Yc, M);
+  int rc = block_gram<double>(h, Xc, Yc, M);
   if (rc) return rc;
   for (double v : M)
     if (!std::isfinite(v)) return RB_ENONFINITE;
   std::vector<double> P((size_t)kin * kin), Q((size_t)kin * kin), sig(kin);
   svd_small(kin, M.data(), P.data(), sig.data(), Q.data());
   int kk = 0;
+  const double drop = h->o.precision == RB_MIXED ? kSvdDropF32 : kSvdDrop;
   if (sig[0] > 0)
-    while (kk < kin && sig[kk] >= kSvdDrop * sig[0]) ++kk;
+    while (kk < kin && sig[kk] >= drop * sig[0]) ++kk;
   if (kk == 0) return RB_OK;
   // U <- U Q, C <- C Q, U~ <- U~ P, C~ <- C~ P (first kk columns of P, Q)
   std::vector<double> Qk(Q.begin(), Q.begin() + (size_t)kin * kk), Pk(P.begin(), P.begin() + (size_t)kin * kk);
@@ -312,7 +333,7 @@ int recycle_setup(rb_ctx* h, int kin, int64_t* setup_mv) {
   struct Job { double** src; const std::vector<double>* R; };
   Job jobs[] = {{&h->U, &Qk}, {&h->C, &Qk}, {&h->Ut, &Pk}, {&h->Ct, &Pk}};
   for (Job& jb : jobs) {
-    rc = block_gemm(h, cols(h->T1, kk), ccols(*jb.src, kin), *jb.R, kk);
+    rc = block_gemm<double>(h, cols(h->T1, kk), ccols(*jb.src, kin), *jb.R, kk);
     if (rc) return rc;
     std::swap(*jb.src, h->T1);
   }
@@ -322,7 +343,7 @@ int recycle_setup(rb_ctx* h, int kin, int64_t* setup_mv) {
   rc = sync(h);
   if (rc) return rc;
   RB_CUDA_TRY(cudaMemcpy(h->Dinv, dinv.data(), sizeof(double) * kk, cudaMemcpyHostToDevice));
-  RB_CUDA_TRY(scale_cols(h->Chat, ld, kk, h->Dinv, h->npad, h->us));
+  RB_CUDA_TRY(scale_cols<double>(h->Chat, ld, kk, h->Dinv, h->npad, h->us));
   h->k = kk;
   if (h->o.precision == RB_MIXED) {
     RB_CUDA_TRY(to_float(h->U, h->fU, ld * kk, h->us));
@@ -385,10 +406,14 @@ IterArgs<float> base_args<float>(rb_ctx* h) {
 }
 
 // Cycle-store slots: P bank b slot j, S/QR/TR slot j.
-double* slotP(rb_ctx* h, int bank, int j) { return h->cstore + (int64_t)(bank * h->cyc + j) * h->npad; }
-double* slotS(rb_ctx* h, int j) { return h->cstore + (int64_t)(2 * h->cyc + j) * h->npad; }
-double* slotQ(rb_ctx* h, int j) { return h->cstore + (int64_t)(3 * h->cyc + j) * h->npad; }
-double* slotT(rb_ctx* h, int j) { return h->cstore + (int64_t)(4 * h->cyc + j) * h->npad; }
+template <typename T>
+T* slotP(rb_ctx* h, int bank, int j) { return (T*)h->cstore + (int64_t)(bank * h->cyc + j) * h->npad; }
+template <typename T>
+T* slotS(rb_ctx* h, int j) { return (T*)h->cstore + (int64_t)(2 * h->cyc + j) * h->npad; }
+template <typename T>
+T* slotQ(rb_ctx* h, int j) { return (T*)h->cstore + (int64_t)(3 * h->cyc + j) * h->npad; }
+template <typename T>
+T* slotT(rb_ctx* h, int j) { return (T*)h->cstore + (int64_t)(4 * h->cyc + j) * h->npad; }
 
 template <typename T>
 int capture(rb_ctx* h, GraphSlot* g, int iters, int bank, bool cycle_mode) {
@@ -401,19 +426,19 @@ int capture(rb_ctx* h, GraphSlot* g, int iters, int bank, bool cycle_mode) {
   for (int j = 0; j < iters && err == cudaSuccess; ++j) {
     IterArgs<T> a = base_args<T>(h);
     if (cycle_mode) {
-      if constexpr (std::is_same<T, double>::value) {
-        a.p_in = slotP(h, bank, j);
-        a.p_out = (j + 1 < h->cyc) ? slotP(h, bank, j + 1) : slotP(h, 1 - bank, 0);
-        a.s = slotS(h, j);
-        a.qraw = slotQ(h, j);
-        a.traw = slotT(h, j);
-        if (h->k == 0) {
-          a.q = a.qraw;
-          a.t = a.traw;
-        }
+      a.p_in = slotP<T>(h, bank, j);
+      a.p_out = (j + 1 < h->cyc) ? slotP<T>(h, bank, j + 1) : slotP<T>(h, 1 - bank, 0);
+      a.s = slotS<T>(h, j);
+      a.qraw = slotQ<T>(h, j);
+      a.traw = slotT<T>(h, j);
+      if (h->k == 0) {
+        a.q = a.qraw;
+        a.t = a.traw;
       }
     }
-    err = launch_iteration<T>(a, h->k, h->grids, h->cs);
+    Grids g;
+    iteration_grids<T>(h->k, h->nsm, h->npad, &g);
+    err = launch_iteration<T>(a, h->k, g, h->cs);
   }
   cudaError_t e2 = cudaStreamEndCapture(h->cs, &graph);
   if (err != cudaSuccess || e2 != cudaSuccess) {
@@ -438,6 +463,7 @@ struct SolveOut {
   int iters = 0;
   int seeds = 1;
   int cycles = 0;
+  int outer = 1;
   int64_t mv = 0, mv_setup = 0, mv_check = 0;
   double relres_rec = 0, relres_true = 0;
   double bytes = 0;
@@ -515,47 +541,56 @@ int iterate_plain(rb_ctx* h) {
   return RB_OK;
 }
 
-// Recycle update after a cycle: W = [Y, P, S], Z = [A Y, A P, A S].
+// Recycle update after a cycle: W = [Y, P, S], Z = [A Y, A P, A S] (Sec. 6.2
+// cycles; harmonic-Ritz reading).  T is the inner precision: the Gram
+// matrices are FP64 either way (Dot2 accumulation for FP32 columns); the new
+// Y = W y and A Y = Z y are formed in T.
+template <typename T>
 int cycle_update(rb_ctx* h, int bank, int nit, int ns) {
   const int64_t ld = h->npad;
-  std::vector<const double*> W, Z;
+  T* Yc = (T*)h->Yc;
+  T* AYc = (T*)h->AYc;
+  T* Yn = (T*)h->Yn;
+  T* AYn = (T*)h->AYn;
+  std::vector<const T*> W, Z;
   for (int j = 0; j < h->kY; ++j) {
-    W.push_back(colp(h->Yc, ld, j));
-    Z.push_back(colp(h->AYc, ld, j));
+    W.push_back(Yc + (int64_t)j * ld);
+    Z.push_back(AYc + (int64_t)j * ld);
   }
   for (int j = 0; j < nit; ++j) {
-    W.push_back(slotP(h, bank, j));
-    Z.push_back(slotQ(h, j));
+    W.push_back(slotP<T>(h, bank, j));
+    Z.push_back(slotQ<T>(h, j));
   }
   for (int j = 0; j < ns; ++j) {
-    W.push_back(slotS(h, j));
-    Z.push_back(slotT(h, j));
+    W.push_back(slotS<T>(h, j));
+    Z.push_back(slotT<T>(h, j));
   }
   const int m = (int)W.size();
   if (m == 0) return RB_OK;
   std::vector<double> G, H;
-  int rc = block_gram(h, Z, Z, G);
+  int rc = block_gram<T>(h, Z, Z, G);
   if (rc) return rc;
-  rc = block_gram(h, Z, W, H);
+  rc = block_gram<T>(h, Z, W, H);
   if (rc) return rc;
   const int kt = std::min(h->o.k_max, m);
   std::vector<double> Y((size_t)m * std::max(kt, 1));
-  const int kn = harmonic_ritz(m, G.data(), H.data(), kt, kRankTol, Y.data(), nullptr, nullptr);
+  const double rtol = std::is_same<T, float>::value ? kRankTolF32 : kRankTol;
+  const int kn = harmonic_ritz(m, G.data(), H.data(), kt, rtol, Y.data(), nullptr, nullptr);
   if (kn <= 0) return RB_OK;   // nothing usable: keep the old candidate
   Y.resize((size_t)m * kn);
-  std::vector<double*> oY, oAY;
+  std::vector<T*> oY, oAY;
   for (int j = 0; j < kn; ++j) {
-    oY.push_back(colp(h->Yn, ld, j));
-    oAY.push_back(colp(h->AYn, ld, j));
+    oY.push_back(Yn + (int64_t)j * ld);
+    oAY.push_back(AYn + (int64_t)j * ld);
   }
-  rc = block_gemm(h, oY, W, Y, kn);
+  rc = block_gemm<T>(h, oY, W, Y, kn);
   if (rc) return rc;
-  rc = block_gemm(h, oAY, Z, Y, kn);
+  rc = block_gemm<T>(h, oAY, Z, Y, kn);
   if (rc) return rc;
   // unit 2-norm columns
-  std::vector<const double*> yc(oY.begin(), oY.end());
+  std::vector<const T*> yc(oY.begin(), oY.end());
   std::vector<double> N2;
-  rc = block_gram(h, yc, yc, N2);
+  rc = block_gram<T>(h, yc, yc, N2);
   if (rc) return rc;
   std::vector<double> f(kn);
   for (int j = 0; j < kn; ++j) {
@@ -563,27 +598,33 @@ int cycle_update(rb_ctx* h, int bank, int nit, int ns) {
     f[j] = nn > 0 ? 1.0 / std::sqrt(nn) : 0.0;
   }
   RB_CUDA_TRY(cudaMemcpy(h->dR, f.data(), sizeof(double) * kn, cudaMemcpyHostToDevice));
-  RB_CUDA_TRY(scale_cols(h->Yn, ld, kn, h->dR, h->npad, h->us));
-  RB_CUDA_TRY(scale_cols(h->AYn, ld, kn, h->dR, h->npad, h->us));
+  RB_CUDA_TRY(scale_cols<T>(Yn, ld, kn, h->dR, h->npad, h->us));
+  RB_CUDA_TRY(scale_cols<T>(AYn, ld, kn, h->dR, h->npad, h->us));
   std::swap(h->Yc, h->Yn);
   std::swap(h->AYc, h->AYn);
   h->kY = kn;
   return sync(h);
 }
 
+// One solve's iterations in update mode: graphs of one cycle each, the
+// recycle update between cycles.  Candidate Y = U, A Y = C at the start;
+// p_1 = r_0 goes to bank 0, slot 0.
+template <typename T>
 int iterate_cycles(rb_ctx* h, SolveOut* so) {
   const int64_t ld = h->npad;
-  // candidate Y = U, A Y = C
+  const bool f32 = std::is_same<T, float>::value;
   h->kY = h->k;
   if (h->k > 0) {
-    RB_CUDA_TRY(cudaMemcpyAsync(h->Yc, h->U, sizeof(double) * ld * h->k, cudaMemcpyDeviceToDevice, h->us));
-    RB_CUDA_TRY(cudaMemcpyAsync(h->AYc, h->C, sizeof(double) * ld * h->k, cudaMemcpyDeviceToDevice, h->us));
+    RB_CUDA_TRY(cudaMemcpyAsync(h->Yc, f32 ? (const void*)h->fU : (const void*)h->U, sizeof(T) * ld * h->k,
+                                cudaMemcpyDeviceToDevice, h->us));
+    RB_CUDA_TRY(cudaMemcpyAsync(h->AYc, f32 ? (const void*)h->fC : (const void*)h->C, sizeof(T) * ld * h->k,
+                                cudaMemcpyDeviceToDevice, h->us));
   }
-  // p_1 = r_0 goes to bank 0, slot 0
-  RB_CUDA_TRY(cudaMemcpyAsync(slotP(h, 0, 0), h->r, sizeof(double) * ld, cudaMemcpyDeviceToDevice, h->us));
+  RB_CUDA_TRY(cudaMemcpyAsync(slotP<T>(h, 0, 0), f32 ? (const void*)h->fr : (const void*)h->r, sizeof(T) * ld,
+                              cudaMemcpyDeviceToDevice, h->us));
   if (h->g_k != h->k || !h->g_cycle[0].valid || !h->g_cycle[1].valid) {
     for (int bnk = 0; bnk < 2; ++bnk) {
-      int rc = capture<double>(h, &h->g_cycle[bnk], h->cyc, bnk, true);
+      int rc = capture<T>(h, &h->g_cycle[bnk], h->cyc, bnk, true);
       if (rc) return rc;
     }
     h->g_k = h->k;
@@ -602,7 +643,7 @@ int iterate_cycles(rb_ctx* h, SolveOut* so) {
     const bool allowed = (h->o.update_cycles == 0) || (c < h->o.update_cycles);
     if (ok && allowed && nit > 0) {
       const int ns = nit - (hs.half ? 1 : 0);
-      rc = cycle_update(h, bank, nit, ns);
+      rc = cycle_update<T>(h, bank, nit, ns);
       if (rc) return rc;
       so->cycles += 1;
     }
@@ -658,7 +699,6 @@ extern "C" int rbicgstab_create(rb_handle* out, const rb_opts* opts) {
       o.recycle_mode > RB_RECYCLE_UPDATE_ALL || o.update_cycles < 0 || o.poll < 0)
     return RB_EINVAL;
   if (o.recycle_mode >= RB_RECYCLE_UPDATE_FIRST && o.k_max + 2 * o.cycle_s > kMaxGram) return RB_EINVAL;
-  if (o.recycle_mode >= RB_RECYCLE_UPDATE_FIRST && o.precision == RB_MIXED) return RB_EINVAL;
   rb_ctx* h = new rb_ctx();
   h->o = o;
   h->us = (cudaStream_t)o.cuda_stream;
@@ -901,7 +941,7 @@ static int solve_fp64(rb_ctx* h, SolveOut* so, bool x_nonzero) {
                    (h->o.recycle_mode == RB_RECYCLE_UPDATE_FIRST && h->update_epoch != h->matrix_epoch);
   if (!h->hst->done) {
     if (upd) {
-      rc = iterate_cycles(h, so);
+      rc = iterate_cycles<double>(h, so);
     } else {
       // p_1 = r_0 (Alg. 2 step 4 with beta_0 = 0)
       RB_CUDA_TRY(cudaMemcpyAsync(h->p, h->r, sizeof(double) * h->npad, cudaMemcpyDeviceToDevice, h->us));
@@ -946,6 +986,9 @@ static int solve_mixed(rb_ctx* h, SolveOut* so, bool x_nonzero) {
   const double target = 0.1 * h->o.tol * std::sqrt(bn2);
   const int max_outer = 12;
   int outer = 0, total_it = 0, last_status = RB_OK;
+  const bool upd = (h->o.recycle_mode == RB_RECYCLE_UPDATE_ALL) ||
+                   (h->o.recycle_mode == RB_RECYCLE_UPDATE_FIRST && h->update_epoch != h->matrix_epoch);
+  bool did_update = false;
   double rn = 0.0;
   for (;;) {
     RB_CUDA_TRY(residual_norm(h->A.view(), h->b, h->x, h->rin, h->npad, h->st, h->partials, h->grids.spmv, h->us));
@@ -970,7 +1013,13 @@ static int solve_mixed(rb_ctx* h, SolveOut* so, bool x_nonzero) {
     RB_CUDA_TRY(to_float(h->rt0, h->frt0, ld, h->us));
     RB_CUDA_TRY(to_float(h->xin, h->fx, ld, h->us));
     if (!h->hst->done) {
-      rc = iterate_plain<float>(h);
+      if (upd && !did_update) {
+        // the first (longest) inner solve collects the cycles of the update
+        rc = iterate_cycles<float>(h, so);
+        did_update = true;
+      } else {
+        rc = iterate_plain<float>(h);
+      }
       if (rc) return rc;
     }
     rc = read_state(h);
@@ -991,7 +1040,18 @@ static int solve_mixed(rb_ctx* h, SolveOut* so, bool x_nonzero) {
   so->relres_true = bn2 > 0 ? rn / std::sqrt(bn2) : 0.0;
   so->relres_rec = so->relres_true;
   so->bytes = (double)total_it * iter_bytes(h, h->k, 4, 4);
-  so->cycles = outer;   // reported as `outer` by the caller
+  so->outer = outer;
+  if (did_update && h->kY > 0 && (so->status == RB_OK || so->status == RB_ENOTCONV)) {
+    // U_next = Y (FP32 candidate promoted to FP64), U~_next = U_next
+    for (int j = 0; j < h->kY; ++j)
+      RB_CUDA_TRY(to_double((const float*)h->Yc + (int64_t)j * ld, h->U + (int64_t)j * ld, ld, h->us));
+    RB_CUDA_TRY(cudaMemcpyAsync(h->Ut, h->U, sizeof(double) * ld * h->kY, cudaMemcpyDeviceToDevice, h->us));
+    int64_t mv = 0;
+    int rc2 = recycle_setup(h, h->kY, &mv);
+    if (rc2 < 0) return rc2;
+    so->mv_setup += mv;
+    h->update_epoch = h->matrix_epoch;
+  }
   return sync(h);
 }
 
@@ -1044,8 +1104,8 @@ extern "C" int rbicgstab_solve(rb_handle h, const double* b, double* x, int wher
     st_out->matvecs = so.mv;
     st_out->matvecs_setup = so.mv_setup;
     st_out->matvecs_check = so.mv_check;
-    st_out->cycles = (h->o.precision == RB_MIXED) ? 0 : so.cycles;
-    st_out->outer = (h->o.precision == RB_MIXED) ? so.cycles : 1;
+    st_out->cycles = so.cycles;
+    st_out->outer = so.outer;
     st_out->relres_rec = so.relres_rec;
     st_out->relres_true = so.relres_true;
     st_out->ms_total = ms;
@@ -1060,6 +1120,8 @@ extern "C" int rbicgstab_solve(rb_handle h, const double* b, double* x, int wher
 template <typename T>
 static int time_passes_t(rb_ctx* h, int reps, double* ms) {
   IterArgs<T> a = base_args<T>(h);
+  Grids g;
+  iteration_grids<T>(h->k, h->nsm, h->npad, &g);
   const int npass = 5;
   std::vector<cudaEvent_t> ev((size_t)reps * npass * 2);
   for (auto& e : ev) cudaEventCreate(&e);
@@ -1067,7 +1129,7 @@ static int time_passes_t(rb_ctx* h, int reps, double* ms) {
     for (int pz = 0; pz < npass; ++pz) {
       if (pz == P4 && h->k == 0) continue;
       RB_CUDA_TRY(cudaEventRecord(ev[(it * npass + pz) * 2], h->us));
-      RB_CUDA_TRY(launch_pass<T>(pz, a, h->k, h->grids, h->us));
+      RB_CUDA_TRY(launch_pass<T>(pz, a, h->k, g, h->us));
       RB_CUDA_TRY(cudaEventRecord(ev[(it * npass + pz) * 2 + 1], h->us));
     }
   int rc = read_state(h);
