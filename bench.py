@@ -363,7 +363,10 @@ def run_ours(args):
                    "l2": "inputs larger than L2 (no flush)"},
         "recycled": {"solves_per_s": round(value, 3), "iters_mean": round(statistics.mean(iters), 2),
                      "iters_total": int(sum(iters)), "matvecs": int(sum(l["matvecs"] for l in logs)),
-                     "matvecs_setup": int(sum(l["matvecs_setup"] for l in logs))},
+                     "matvecs_setup": int(sum(l["matvecs_setup"] for l in logs)),
+                     "ms_update_per_step": round(sum(l["ms_update"] for l in logs) / args.steps, 1),
+                     "cycles_per_step": round(sum(l["cycles"] for l in logs) / args.steps, 1),
+                     "outer_mean": round(statistics.mean(l["outer"] for l in logs), 2)},
         "roofline": roof,
         "gpu_launches": int(res["rec"]["launches"]),
         "clocks": res["rec"]["clocks"],

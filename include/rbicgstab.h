@@ -92,6 +92,8 @@ typedef struct {
   double  relres_true;     /* ||b - A x|| / ||b|| recomputed in FP64 after step 8      */
   double  ms_total;        /* wall time of the call (CUDA events)                      */
   double  bytes_model;     /* algorithmic HBM bytes of the iterations                  */
+  double  ms_update;       /* host wall time spent in recycle-space updates (cycle
+                              Gram/eig/rebuild and the new space's Alg. 2 step 1)     */
 } rb_stats;
 
 /* Create a solver handle on the current CUDA device.  *h receives the handle.

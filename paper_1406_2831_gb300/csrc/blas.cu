@@ -77,23 +77,44 @@ cudaError_t gemv_update(double* y, const double* M, int64_t ld, int k, const dou
 
 // ---------------------------------------------------------------- block GEMM
 // Out(:, c) = X R(:, c): each thread owns one row, reads the m entries of
-// X's row once and forms all kc outputs (kc <= kMaxK), accumulating in T.
-template <typename T>
-__global__ void k_gemm_cols(T* const* __restrict__ out, const T* const* __restrict__ X, int m,
-                            const double* __restrict__ R, int kc, int64_t npad) {
+// X's row once and forms all kc <= KC outputs in registers (KC is a
+// compile-time bucket so the accumulators never spill to local memory).
+template <typename T, int KC>
+__global__ void __launch_bounds__(kBlock) k_gemm_cols(T* const* __restrict__ out, const T* const* __restrict__ X,
+                                                     int m, const double* __restrict__ R, int kc, int64_t npad) {
   extern __shared__ __align__(16) unsigned char gem_sm[];
-  T* sR = (T*)gem_sm;   // m * kc coefficients in the column type
-  for (int e = threadIdx.x; e < m * kc; e += blockDim.x) sR[e] = (T)R[e];
-  __syncthreads();
-  T acc[kMaxK];
-  for (int64_t i = gtid(); i < npad; i += gstride()) {
-    for (int c = 0; c < kc; ++c) acc[c] = T(0);
-    for (int j = 0; j < m; ++j) {
-      const T xv = X[j][i];
-      for (int c = 0; c < kc; ++c) acc[c] = fma_t(xv, sR[j + c * m], acc[c]);
-    }
-    for (int c = 0; c < kc; ++c) out[c][i] = acc[c];
+  T* sR = (T*)gem_sm;                              // m * KC coefficients (zero-padded)
+  const T** sX = (const T**)(sR + (size_t)m * KC);  // m column pointers
+  for (int e = threadIdx.x; e < m * KC; e += blockDim.x) {
+    const int j = e / KC, c = e % KC;
+    sR[e] = c < kc ? (T)R[j + (size_t)c * m] : T(0);
   }
+  for (int j = threadIdx.x; j < m; j += blockDim.x) sX[j] = X[j];
+  __syncthreads();
+  for (int64_t i = gtid(); i < npad; i += gstride()) {
+    T acc[KC];
+#pragma unroll
+    for (int c = 0; c < KC; ++c) acc[c] = T(0);
+    for (int j = 0; j < m; ++j) {
+      const T xv = sX[j][i];
+      const T* rj = sR + (size_t)j * KC;
+#pragma unroll
+      for (int c = 0; c < KC; ++c) acc[c] = fma_t(xv, rj[c], acc[c]);
+    }
+#pragma unroll
+    for (int c = 0; c < KC; ++c)
+      if (c < kc) out[c][i] = acc[c];
+  }
+}
+
+template <typename T, int KC>
+static cudaError_t gemm_cols_k(T* const* out, const T* const* X, int m, const double* R, int kc, int64_t npad,
+                               int grid, cudaStream_t s) {
+  const size_t smem = sizeof(T) * (size_t)m * KC + sizeof(void*) * (size_t)m;
+  if (smem > 48 * 1024)
+    cudaFuncSetAttribute(k_gemm_cols<T, KC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_gemm_cols<T, KC><<<grid, kBlock, smem, s>>>(out, X, m, R, kc, npad);
+  return cudaGetLastError();
 }
 
 template <typename T>
@@ -101,11 +122,12 @@ cudaError_t gemm_cols(T* const* out, const T* const* X, int m, const double* R, 
                       int grid, cudaStream_t s) {
   count_launches(1);
   if (kc <= 0 || m <= 0) return cudaSuccess;
-  const size_t smem = sizeof(T) * (size_t)m * kc;
-  if (smem > 48 * 1024)
-    cudaFuncSetAttribute(k_gemm_cols<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k_gemm_cols<T><<<grid, kBlock, smem, s>>>(out, X, m, R, kc, npad);
-  return cudaGetLastError();
+  if (kc <= 8) return gemm_cols_k<T, 8>(out, X, m, R, kc, npad, grid, s);
+  if (kc <= 16) return gemm_cols_k<T, 16>(out, X, m, R, kc, npad, grid, s);
+  if (kc <= 24) return gemm_cols_k<T, 24>(out, X, m, R, kc, npad, grid, s);
+  if (kc <= 32) return gemm_cols_k<T, 32>(out, X, m, R, kc, npad, grid, s);
+  if (kc <= 48) return gemm_cols_k<T, 48>(out, X, m, R, kc, npad, grid, s);
+  return gemm_cols_k<T, 64>(out, X, m, R, kc, npad, grid, s);
 }
 template cudaError_t gemm_cols<double>(double* const*, const double* const*, int, const double*, int,
                                        int64_t, int, cudaStream_t);
@@ -185,6 +207,179 @@ template cudaError_t gram<double>(const double* const*, int, const double* const
                                   double*, int, cudaStream_t);
 template cudaError_t gram<float>(const float* const*, int, const float* const*, int, int64_t, double*,
                                  double*, int, cudaStream_t);
+
+// ---------------------------------------------------------------- fused Gram
+// One pass over the m columns of Z and W forms G = Z^T Z (upper triangle,
+// a <= b) and H = Z^T W, the two matrices of the harmonic-Ritz step.  Rows
+// are staged in shared memory 64 at a time; each thread owns up to two 4x4
+// output tiles and reads 4 + 4 staged values per row for 16 products.
+// Accumulation: FP64 FMA for FP64 columns, Dot2 for FP32 columns.  Block
+// partials (block-major) are summed in block order by k_gram_reduce.
+constexpr int kGR = 64;      // rows per shared-memory chunk
+constexpr int kGT = 4;       // output tile edge
+
+template <typename T, int TPT>
+__global__ void __launch_bounds__(kBlock) k_gram_gh(const T* const* __restrict__ Z,
+                                                   const T* const* __restrict__ W, int m, int mp,
+                                                   int ntile_g, int ntile_h, int64_t npad,
+                                                   double* __restrict__ work) {
+  extern __shared__ __align__(16) unsigned char ghsm[];
+  T* sz = (T*)ghsm;               // kGR x mp
+  T* sw = sz + kGR * mp;          // kGR x mp
+  const int nt = mp / kGT;        // tiles per edge
+  const int ntot = ntile_g + ntile_h;
+  // this thread's tiles: t = threadIdx.x + q * blockDim.x, q < TPT
+  int ta[TPT], tb[TPT], isg[TPT];
+  int ntl = 0;
+  for (int t = threadIdx.x; t < ntot && ntl < TPT; t += blockDim.x, ++ntl) {
+    if (t < ntile_g) {   // upper-triangle tile index -> (row tile, col tile)
+      int r = 0, rem = t;
+      while (rem >= nt - r) { rem -= nt - r; ++r; }
+      ta[ntl] = r; tb[ntl] = r + rem; isg[ntl] = 1;
+    } else {
+      const int u = t - ntile_g;
+      ta[ntl] = u / nt; tb[ntl] = u % nt; isg[ntl] = 0;
+    }
+  }
+  Acc<T> acc[TPT][kGT][kGT];
+  const int64_t nch = (npad + kGR - 1) / kGR;
+  for (int64_t ch = blockIdx.x; ch < nch; ch += gridDim.x) {
+    const int64_t r0 = ch * kGR;
+    __syncthreads();
+    for (int e = threadIdx.x; e < kGR * mp; e += blockDim.x) {
+      const int c = e / kGR, rr = e % kGR;
+      const bool in = (c < m) && (r0 + rr < npad);
+      sz[rr * mp + c] = in ? Z[c][r0 + rr] : T(0);
+      sw[rr * mp + c] = in ? W[c][r0 + rr] : T(0);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < TPT; ++q) {
+      if (q < ntl) {
+        const T* za = sz + ta[q] * kGT;
+        const T* yb = (isg[q] ? sz : sw) + tb[q] * kGT;
+#pragma unroll 1
+        for (int rr = 0; rr < kGR; ++rr) {
+          T a[kGT], b[kGT];
+#pragma unroll
+          for (int u = 0; u < kGT; ++u) {
+            a[u] = za[rr * mp + u];
+            b[u] = yb[rr * mp + u];
+          }
+#pragma unroll
+          for (int i = 0; i < kGT; ++i)
+#pragma unroll
+            for (int j = 0; j < kGT; ++j) acc[q][i][j].add(a[i], b[j]);
+        }
+      }
+    }
+  }
+  // block partials: G tiles then H tiles, 16 values per tile
+  double* wb = work + (size_t)blockIdx.x * ntot * kGT * kGT;
+  for (int q = 0; q < ntl; ++q) {
+    const int t = threadIdx.x + q * blockDim.x;
+#pragma unroll
+    for (int i = 0; i < kGT; ++i)
+#pragma unroll
+      for (int j = 0; j < kGT; ++j) wb[(size_t)t * kGT * kGT + i * kGT + j] = acc[q][i][j].get();
+  }
+}
+
+// Sum block partials in block order and scatter into G (m x m, both
+// triangles) and H (m x m), column-major.
+__global__ void k_gram_gh_reduce(const double* __restrict__ work, int nblocks, int m, int mp, int ntile_g,
+                                 int ntile_h, double* __restrict__ G, double* __restrict__ H) {
+  const int nt = mp / kGT, ntot = ntile_g + ntile_h;
+  const int nval = ntot * kGT * kGT;
+  for (int o = blockIdx.x * blockDim.x + threadIdx.x; o < nval; o += gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int b = 0; b < nblocks; ++b) s += work[(size_t)b * nval + o];
+    const int t = o / (kGT * kGT), ij = o % (kGT * kGT), i = ij / kGT, j = ij % kGT;
+    int a0, b0;
+    bool g;
+    if (t < ntile_g) {
+      int r = 0, rem = t;
+      while (rem >= nt - r) { rem -= nt - r; ++r; }
+      a0 = r; b0 = r + rem; g = true;
+    } else {
+      a0 = (t - ntile_g) / nt; b0 = (t - ntile_g) % nt; g = false;
+    }
+    const int a = a0 * kGT + i, b = b0 * kGT + j;
+    if (a >= m || b >= m) continue;
+    if (g) {
+      if (a <= b) {
+        G[a + (size_t)b * m] = s;
+        G[b + (size_t)a * m] = s;
+      }
+    } else {
+      H[a + (size_t)b * m] = s;
+    }
+  }
+}
+
+int gram_gh_work(int m) {
+  const int mp = (m + kGT - 1) / kGT * kGT, nt = mp / kGT;
+  return (nt * (nt + 1) / 2 + nt * nt) * kGT * kGT;
+}
+
+template <typename T>
+cudaError_t gram_gh(const T* const* Z, const T* const* W, int m, int64_t npad, double* G, double* H,
+                    double* work, int grid, cudaStream_t s) {
+  count_launches(2);
+  if (m <= 0) return cudaSuccess;
+  const int mp = (m + kGT - 1) / kGT * kGT, nt = mp / kGT;
+  const int ntile_g = nt * (nt + 1) / 2, ntile_h = nt * nt;
+  if (ntile_g + ntile_h > 4 * kBlock) return cudaErrorInvalidValue;
+  const size_t smem = sizeof(T) * 2 * kGR * (size_t)mp;
+  if (ntile_g + ntile_h <= 2 * kBlock) {
+    if (smem > 48 * 1024)
+      cudaFuncSetAttribute(k_gram_gh<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_gram_gh<T, 2><<<grid, kBlock, smem, s>>>(Z, W, m, mp, ntile_g, ntile_h, npad, work);
+  } else {
+    if (smem > 48 * 1024)
+      cudaFuncSetAttribute(k_gram_gh<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_gram_gh<T, 4><<<grid, kBlock, smem, s>>>(Z, W, m, mp, ntile_g, ntile_h, npad, work);
+  }
+  const int nval = (ntile_g + ntile_h) * kGT * kGT;
+  k_gram_gh_reduce<<<(nval + kBlock - 1) / kBlock, kBlock, 0, s>>>(work, grid, m, mp, ntile_g, ntile_h, G, H);
+  return cudaGetLastError();
+}
+template cudaError_t gram_gh<double>(const double* const*, const double* const*, int, int64_t, double*,
+                                     double*, double*, int, cudaStream_t);
+template cudaError_t gram_gh<float>(const float* const*, const float* const*, int, int64_t, double*, double*,
+                                    double*, int, cudaStream_t);
+
+// ---------------------------------------------------------------- column norms
+// out[j] = ||M(:, j)||^2 for column pointers M[0..k), deterministic.
+template <typename T, int KMAX>
+__global__ void __launch_bounds__(kBlock) k_colnorm2(const T* const* __restrict__ M, int k, int64_t npad,
+                                                    IterState* st, double* partials) {
+  __shared__ ReduceSmem<KMAX> sm;
+  Acc<T> acc[KMAX];
+  for (int64_t i = gtid(); i < npad; i += gstride()) {
+#pragma unroll
+    for (int j = 0; j < KMAX; ++j)
+      if (j < k) {
+        const T v = M[j][i];
+        acc[j].add(v, v);
+      }
+  }
+  if (block_reduce_last<T, KMAX>(acc, k, sm, partials, &st->ticket[PGEN])) {
+    for (int j = threadIdx.x; j < k; j += blockDim.x) st->red[j] = sm.res[j];
+  }
+}
+
+template <typename T>
+cudaError_t colnorm2(const T* const* M, int k, int64_t npad, IterState* st, double* partials, int grid,
+                     cudaStream_t s) {
+  count_launches(1);
+  if (k <= 0) return cudaSuccess;
+  if (k <= 32) k_colnorm2<T, 32><<<grid, kBlock, 0, s>>>(M, k, npad, st, partials);
+  else k_colnorm2<T, 64><<<grid, kBlock, 0, s>>>(M, k, npad, st, partials);
+  return cudaGetLastError();
+}
+template cudaError_t colnorm2<double>(const double* const*, int, int64_t, IterState*, double*, int, cudaStream_t);
+template cudaError_t colnorm2<float>(const float* const*, int, int64_t, IterState*, double*, int, cudaStream_t);
 
 // ---------------------------------------------------------------- shadow r~_{-1}
 // SplitMix64 (Steele, Lea, Flood 2014), output i from state `seed`:

@@ -4,10 +4,11 @@
 //     C~^T C diagonal and positive, Sec. 3): one-sided Jacobi SVD (Hestenes).
 //   * harmonic_ritz: the eigenproblem of the recycle update between cycles
 //     (Sec. 6.2): column scaling, restriction to the numerical range of W by
-//     a cyclic Jacobi eigendecomposition of the scaled G = Z^T Z, reduction to
-//     a standard problem, Householder-Hessenberg + Francis double-shift QR for
-//     the eigenvalues (Golub & Van Loan, Matrix Computations, Sec. 7.4-7.5),
-//     and complex inverse iteration for the selected eigenvectors.
+//     a symmetric eigendecomposition of the scaled G = Z^T Z (Householder
+//     tridiagonalisation + implicit QL), reduction to a standard problem,
+//     Householder-Hessenberg + Francis double-shift QR for the eigenvalues
+//     (Golub & Van Loan, Matrix Computations, Sec. 7.4-7.5), and complex
+//     inverse iteration on the Hessenberg form for the selected eigenvectors.
 // These are deliberately different algorithms from the LAPACK routines the
 // CPU oracle calls, so agreement between the two is evidence for both.
 #include "hostla.h"
@@ -79,8 +80,11 @@ void svd_small(int k, const double* M, double* P, double* sigma, double* Q) {
 
 // ---------------------------------------------------------------- Hessenberg + QR
 // Reduce a (n x n, row-major h[i*n+j]) to upper Hessenberg form by Householder
-// reflections (eigenvalues only, no accumulation).
-static void hessenberg(int n, std::vector<double>& h) {
+// reflections P_c = I - 2 v v^T / (v^T v), H = P_{n-3} .. P_0 A P_0 .. P_{n-3};
+// the reflectors are returned in refl (row c holds v for column c, zero if
+// the step was skipped) so eigenvectors of H can be mapped back to A.
+static void hessenberg(int n, std::vector<double>& h, std::vector<double>* refl = nullptr) {
+  if (refl) refl->assign((size_t)n * n, 0.0);
   for (int c = 0; c < n - 2; ++c) {
     double alpha = 0.0;
     for (int i = c + 1; i < n; ++i) alpha += h[i * n + c] * h[i * n + c];
@@ -94,6 +98,8 @@ static void hessenberg(int n, std::vector<double>& h) {
     double vv = 0.0;
     for (int i = c + 1; i < n; ++i) vv += v[i] * v[i];
     if (vv == 0.0) continue;
+    if (refl)
+      for (int i = 0; i < n; ++i) (*refl)[(size_t)c * n + i] = v[i];
     // H <- (I - 2 v v^T / vv) H (I - 2 v v^T / vv)
     for (int j = 0; j < n; ++j) {
       double s = 0.0;
@@ -242,106 +248,171 @@ static bool hqr(int n, std::vector<double>& a, std::vector<double>& wr, std::vec
   return true;
 }
 
-// Eigenvector of M (n x n row-major) for eigenvalue lam by inverse iteration
-// with complex LU (partial pivoting); zero pivots are replaced by eps*||M||.
-static std::vector<cd> inverse_iteration(int n, const std::vector<double>& M, cd lam) {
+// Eigenvector of M (n x n) for eigenvalue lam by inverse iteration on its
+// upper Hessenberg form Hs = P^T M P (row-major): Gaussian elimination with
+// partial pivoting needs only adjacent-row swaps on a Hessenberg matrix
+// (O(n^2) per solve); zero pivots are replaced by eps*||Hs||.  The result is
+// mapped back to M's basis with the reflectors of the reduction.
+static std::vector<cd> inverse_iteration(int n, const std::vector<double>& Hs, const std::vector<double>& refl,
+                                         cd lam) {
   double mnorm = 0.0;
-  for (double v : M) mnorm = std::max(mnorm, std::fabs(v));
+  for (double v : Hs) mnorm = std::max(mnorm, std::fabs(v));
   mnorm = std::max(mnorm, std::abs(lam));
   const double tiny = 2.220446049250313e-16 * (mnorm > 0 ? mnorm : 1.0);
   std::vector<cd> a((size_t)n * n);
   for (int i = 0; i < n; ++i)
-    for (int j = 0; j < n; ++j) a[(size_t)i * n + j] = cd(M[(size_t)i * n + j], 0.0) - (i == j ? lam : cd(0));
-  std::vector<int> piv(n);
-  for (int c = 0; c < n; ++c) {
-    int pr = c;
-    double best = std::abs(a[(size_t)c * n + c]);
-    for (int i = c + 1; i < n; ++i)
-      if (std::abs(a[(size_t)i * n + c]) > best) {
-        best = std::abs(a[(size_t)i * n + c]);
-        pr = i;
-      }
-    piv[c] = pr;
-    if (pr != c)
-      for (int j = 0; j < n; ++j) std::swap(a[(size_t)c * n + j], a[(size_t)pr * n + j]);
-    if (std::abs(a[(size_t)c * n + c]) < tiny) a[(size_t)c * n + c] = tiny;
-    for (int i = c + 1; i < n; ++i) {
-      const cd f = a[(size_t)i * n + c] / a[(size_t)c * n + c];
-      a[(size_t)i * n + c] = f;
-      for (int j = c + 1; j < n; ++j) a[(size_t)i * n + j] -= f * a[(size_t)c * n + j];
+    for (int j = 0; j < n; ++j) a[(size_t)i * n + j] = cd(Hs[(size_t)i * n + j], 0.0) - (i == j ? lam : cd(0));
+  std::vector<cd> mult(n, cd(0));
+  std::vector<char> swp(n, 0);
+  for (int c = 0; c < n - 1; ++c) {
+    const int lo = std::max(c - 1, 0);   // row c and c+1 are nonzero from column c-1 on
+    if (std::abs(a[(size_t)(c + 1) * n + c]) > std::abs(a[(size_t)c * n + c])) {
+      swp[c] = 1;
+      for (int j = lo; j < n; ++j) std::swap(a[(size_t)c * n + j], a[(size_t)(c + 1) * n + j]);
     }
+    if (std::abs(a[(size_t)c * n + c]) < tiny) a[(size_t)c * n + c] = tiny;
+    const cd f = a[(size_t)(c + 1) * n + c] / a[(size_t)c * n + c];
+    mult[c] = f;
+    a[(size_t)(c + 1) * n + c] = 0.0;
+    for (int j = c + 1; j < n; ++j) a[(size_t)(c + 1) * n + j] -= f * a[(size_t)c * n + j];
   }
+  if (std::abs(a[(size_t)(n - 1) * n + n - 1]) < tiny) a[(size_t)(n - 1) * n + n - 1] = tiny;
   std::vector<cd> v(n);
   for (int i = 0; i < n; ++i) v[i] = cd(1.0 + 0.01 * i, 0.0);
   for (int it = 0; it < 3; ++it) {
-    for (int c = 0; c < n; ++c) std::swap(v[c], v[piv[c]]);
-    for (int i = 0; i < n; ++i)
-      for (int j = 0; j < i; ++j) v[i] -= a[(size_t)i * n + j] * v[j];
+    for (int c = 0; c < n - 1; ++c) {
+      if (swp[c]) std::swap(v[c], v[c + 1]);
+      v[c + 1] -= mult[c] * v[c];
+    }
     for (int i = n - 1; i >= 0; --i) {
-      for (int j = i + 1; j < n; ++j) v[i] -= a[(size_t)i * n + j] * v[j];
-      v[i] /= a[(size_t)i * n + i];
+      cd s = v[i];
+      for (int j = i + 1; j < n; ++j) s -= a[(size_t)i * n + j] * v[j];
+      v[i] = s / a[(size_t)i * n + i];
     }
     double nrm = 0.0;
     for (auto& z : v) nrm += std::norm(z);
     nrm = std::sqrt(nrm);
     if (!(nrm > 0) || !std::isfinite(nrm)) break;
-    // phase-fix: largest component real positive
     int im = 0;
     for (int i = 1; i < n; ++i)
       if (std::abs(v[i]) > std::abs(v[im])) im = i;
     const cd ph = std::conj(v[im]) / std::abs(v[im]);
     for (auto& z : v) z = z * ph / nrm;
   }
+  // z = P_0 P_1 ... P_{n-3} v
+  for (int c = n - 3; c >= 0; --c) {
+    const double* u = &refl[(size_t)c * n];
+    double uu = 0.0;
+    for (int i = c + 1; i < n; ++i) uu += u[i] * u[i];
+    if (uu == 0.0) continue;
+    cd s(0.0);
+    for (int i = c + 1; i < n; ++i) s += u[i] * v[i];
+    s *= 2.0 / uu;
+    for (int i = c + 1; i < n; ++i) v[i] -= s * u[i];
+  }
   return v;
 }
 
 // ---------------------------------------------------------------- symmetric eig
-// Cyclic Jacobi eigenvalue algorithm (Golub & Van Loan, Sec. 8.5) for a
-// symmetric m x m matrix (column-major): S = V diag(lam) V^T.
-static void jacobi_eig(int m, const std::vector<double>& S, std::vector<double>& lam,
-                       std::vector<double>& V) {
-  std::vector<double> A = S;
-  V.assign((size_t)m * m, 0.0);
-  for (int i = 0; i < m; ++i) V[i + (size_t)i * m] = 1.0;
-  auto a = [&](int i, int j) -> double& { return A[i + (size_t)j * m]; };
-  const double eps = 2.220446049250313e-16;
-  for (int sweep = 0; sweep < 100; ++sweep) {
-    double off = 0.0, diag = 0.0;
-    for (int j = 0; j < m; ++j) {
-      diag += a(j, j) * a(j, j);
-      for (int i = 0; i < j; ++i) off += 2.0 * a(i, j) * a(i, j);
+// Symmetric S (m x m, column-major) = V diag(lam) V^T: Householder reduction
+// to tridiagonal form with the transformation accumulated (Golub & Van Loan,
+// Sec. 8.3.1), then the implicit symmetric QL iteration with Wilkinson-type
+// shifts on the tridiagonal matrix, rotating V along (Sec. 8.3.3).
+static void sym_eig(int m, const std::vector<double>& S, std::vector<double>& lam, std::vector<double>& V) {
+  // A row-major working copy; Q accumulates the reflections (A = Q T Q^T).
+  std::vector<double> A(S);   // symmetric: row- and column-major coincide
+  std::vector<double> Q((size_t)m * m, 0.0);
+  for (int i = 0; i < m; ++i) Q[(size_t)i * m + i] = 1.0;
+  auto a = [&](int i, int j) -> double& { return A[(size_t)i * m + j]; };
+  std::vector<double> v(m), p(m), w(m);
+  for (int k = 0; k < m - 2; ++k) {
+    double alpha = 0.0;
+    for (int i = k + 1; i < m; ++i) alpha += a(i, k) * a(i, k);
+    alpha = std::sqrt(alpha);
+    if (alpha == 0.0) continue;
+    const double x0 = a(k + 1, k);
+    const double beta0 = x0 >= 0 ? -alpha : alpha;
+    std::fill(v.begin(), v.end(), 0.0);
+    v[k + 1] = x0 - beta0;
+    for (int i = k + 2; i < m; ++i) v[i] = a(i, k);
+    double vv = 0.0;
+    for (int i = k + 1; i < m; ++i) vv += v[i] * v[i];
+    if (vv == 0.0) continue;
+    const double beta = 2.0 / vv;
+    // p = beta A22 v, w = p - (beta p^T v / 2) v, A22 -= v w^T + w v^T
+    double pv = 0.0;
+    for (int i = k + 1; i < m; ++i) {
+      double s = 0.0;
+      for (int j = k + 1; j < m; ++j) s += a(i, j) * v[j];
+      p[i] = beta * s;
+      pv += p[i] * v[i];
     }
-    if (off <= eps * eps * diag || off == 0.0) break;
-    for (int p = 0; p < m - 1; ++p)
-      for (int q = p + 1; q < m; ++q) {
-        const double apq = a(p, q);
-        if (std::fabs(apq) <= 1e-300) continue;
-        if (std::fabs(apq) <= eps * 1e-3 * std::sqrt(std::fabs(a(p, p) * a(q, q)))) {
-          a(p, q) = a(q, p) = 0.0;
-          continue;
+    const double c = 0.5 * beta * pv;
+    for (int i = k + 1; i < m; ++i) w[i] = p[i] - c * v[i];
+    for (int i = k + 1; i < m; ++i)
+      for (int j = k + 1; j < m; ++j) a(i, j) -= v[i] * w[j] + w[i] * v[j];
+    a(k + 1, k) = a(k, k + 1) = beta0;
+    for (int i = k + 2; i < m; ++i) a(i, k) = a(k, i) = 0.0;
+    // Q <- Q (I - beta v v^T)
+    for (int r = 0; r < m; ++r) {
+      double s = 0.0;
+      for (int j = k + 1; j < m; ++j) s += Q[(size_t)r * m + j] * v[j];
+      s *= beta;
+      for (int j = k + 1; j < m; ++j) Q[(size_t)r * m + j] -= s * v[j];
+    }
+  }
+  std::vector<double> d(m), e(m, 0.0);
+  for (int i = 0; i < m; ++i) d[i] = a(i, i);
+  for (int i = 0; i + 1 < m; ++i) e[i] = a(i + 1, i);   // e[i] couples i and i+1
+  const double eps = 2.220446049250313e-16;
+  for (int l = 0; l < m; ++l) {
+    for (int iter = 0; iter < 100; ++iter) {
+      int mm = l;
+      for (; mm < m - 1; ++mm) {
+        const double dd = std::fabs(d[mm]) + std::fabs(d[mm + 1]);
+        if (std::fabs(e[mm]) <= eps * dd) break;
+      }
+      if (mm == l) break;
+      // shift from the leading 2x2 block, chase the bulge from mm up to l
+      double g = (d[l + 1] - d[l]) / (2.0 * e[l]);
+      double r = std::hypot(g, 1.0);
+      g = d[mm] - d[l] + e[l] / (g + (g >= 0 ? r : -r));
+      double s = 1.0, c = 1.0, pp = 0.0;
+      int i = mm - 1;
+      bool early = false;
+      for (; i >= l; --i) {
+        const double f = s * e[i], b = c * e[i];
+        r = std::hypot(f, g);
+        e[i + 1] = r;
+        if (r == 0.0) {
+          d[i + 1] -= pp;
+          e[mm] = 0.0;
+          early = true;
+          break;
         }
-        const double theta = (a(q, q) - a(p, p)) / (2.0 * apq);
-        const double t = (theta >= 0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(1.0 + theta * theta));
-        const double c = 1.0 / std::sqrt(1.0 + t * t), s = t * c;
+        s = f / r;
+        c = g / r;
+        g = d[i + 1] - pp;
+        r = (d[i] - g) * s + 2.0 * c * b;
+        pp = s * r;
+        d[i + 1] = g + pp;
+        g = c * r - b;
         for (int k = 0; k < m; ++k) {
-          const double akp = a(k, p), akq = a(k, q);
-          a(k, p) = c * akp - s * akq;
-          a(k, q) = s * akp + c * akq;
-        }
-        for (int k = 0; k < m; ++k) {
-          const double apk = a(p, k), aqk = a(q, k);
-          a(p, k) = c * apk - s * aqk;
-          a(q, k) = s * apk + c * aqk;
-        }
-        for (int k = 0; k < m; ++k) {
-          const double vkp = V[k + (size_t)p * m], vkq = V[k + (size_t)q * m];
-          V[k + (size_t)p * m] = c * vkp - s * vkq;
-          V[k + (size_t)q * m] = s * vkp + c * vkq;
+          const double qf = Q[(size_t)k * m + i + 1];
+          Q[(size_t)k * m + i + 1] = s * Q[(size_t)k * m + i] + c * qf;
+          Q[(size_t)k * m + i] = c * Q[(size_t)k * m + i] - s * qf;
         }
       }
+      if (early) continue;
+      d[l] -= pp;
+      e[l] = g;
+      e[mm] = 0.0;
+    }
   }
-  lam.resize(m);
-  for (int i = 0; i < m; ++i) lam[i] = a(i, i);
+  lam = d;
+  V.assign((size_t)m * m, 0.0);
+  for (int i = 0; i < m; ++i)
+    for (int j = 0; j < m; ++j) V[i + (size_t)j * m] = Q[(size_t)i * m + j];   // column j = eigenvector j
 }
 
 // ---------------------------------------------------------------- harmonic Ritz
@@ -364,7 +435,7 @@ int harmonic_ritz(int m, const double* G, const double* Hm, int k, double tol_ra
   // cyclic Jacobi rotations; keep eigenvalues > tol_rank * max (numerical
   // rank of W); with T = V_r L_r^{-1/2}, M = T^T Hs T and M z = (1/theta) z.
   std::vector<double> lam, V;
-  jacobi_eig(m, Gs, lam, V);
+  sym_eig(m, Gs, lam, V);
   double lmax = 0.0;
   for (double v : lam) lmax = std::max(lmax, v);
   if (!(lmax > 0)) return 0;
@@ -393,8 +464,9 @@ int harmonic_ritz(int m, const double* G, const double* Hm, int k, double tol_ra
       for (int i = 0; i < m; ++i) acc += T[i + (size_t)a * m] * HT[i + (size_t)c * m];
       B[(size_t)a * r + c] = acc;
     }
-  std::vector<double> Hh = B, wr(r), wi(r);
-  hessenberg(r, Hh);
+  std::vector<double> Hh = B, wr(r), wi(r), refl;
+  hessenberg(r, Hh, &refl);
+  const std::vector<double> Hhess = Hh;   // hqr works in place
   if (!hqr(r, Hh, wr, wi)) return -1;
   // theta = 1 / mu; units: real values, or pairs represented by Im(theta) > 0
   struct Unit {
@@ -418,7 +490,7 @@ int harmonic_ritz(int m, const double* G, const double* Hm, int k, double tol_ra
   for (const Unit& u : units) {
     const int need = u.cplx ? 2 : 1;
     if (used + need > k) break;
-    std::vector<cd> z = inverse_iteration(r, B, u.mu);
+    std::vector<cd> z = inverse_iteration(r, Hhess, refl, u.mu);
     // y = d .* (T z)
     std::vector<cd> y(m, cd(0.0));
     for (int c = 0; c < r; ++c)

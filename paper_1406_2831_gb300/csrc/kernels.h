@@ -120,6 +120,17 @@ cudaError_t gemm_cols(T* const* out, const T* const* X, int m, const double* R, 
 template <typename T>
 cudaError_t gram(const T* const* X, int mx, const T* const* Y, int my, int64_t npad, double* out,
                  double* work, int grid, cudaStream_t s);
+// G = Z^T Z and H = Z^T W (m x m each, column-major, FP64) in one pass over
+// the column pointer lists Z[0..m), W[0..m); `work` holds grid *
+// gram_gh_work(m) doubles.  m <= 90.
+int gram_gh_work(int m);
+template <typename T>
+cudaError_t gram_gh(const T* const* Z, const T* const* W, int m, int64_t npad, double* G, double* H,
+                    double* work, int grid, cudaStream_t s);
+// st->red[j] = ||M_j||^2 for column pointers M[0..k) (deterministic).
+template <typename T>
+cudaError_t colnorm2(const T* const* M, int k, int64_t npad, IterState* st, double* partials, int grid,
+                     cudaStream_t s);
 // Shadow vector r~[i] = 2 * u53(SplitMix64(seed, i)) - 1 for i < n, 0 beyond.
 cudaError_t shadow(double* rt, int64_t n, int64_t npad, uint64_t seed, cudaStream_t s);
 // Scale column j of M (n x k, ld) by f[j] (device array); rows < npad.

@@ -115,6 +115,18 @@ struct rb_ctx {
 // ============================================================ helpers
 namespace {
 
+// Optional phase timing of the recycle update (RB_TIMING=1 prints to stderr).
+struct PhaseClock {
+  bool on = getenv("RB_TIMING") != nullptr;
+  std::chrono::steady_clock::time_point t = std::chrono::steady_clock::now();
+  void lap(const char* what) {
+    if (!on) return;
+    const auto now = std::chrono::steady_clock::now();
+    fprintf(stderr, "rb_timing %-14s %8.3f ms\n", what, std::chrono::duration<double, std::milli>(now - t).count());
+    t = now;
+  }
+};
+
 int sync(rb_ctx* h) {
   RB_CUDA_TRY(cudaStreamSynchronize(h->us));
   return RB_OK;
@@ -233,6 +245,55 @@ int block_gram(rb_ctx* h, const std::vector<const T*>& X, const std::vector<cons
   return sync(h);
 }
 
+// G = Z^T Z and H = Z^T W in one pass (both m x m, column-major, on the host).
+template <typename T>
+int block_gram_gh(rb_ctx* h, const std::vector<const T*>& Z, const std::vector<const T*>& W,
+                  std::vector<double>& G, std::vector<double>& H) {
+  const int m = (int)Z.size();
+  G.assign((size_t)m * m, 0.0);
+  H.assign((size_t)m * m, 0.0);
+  if (!m) return RB_OK;
+  int rc = sync(h);
+  if (rc) return rc;
+  rc = upload_ptrs(h, 2, Z);
+  if (rc) return rc;
+  rc = upload_ptrs(h, 3, W);
+  if (rc) return rc;
+  const int grid = 2 * h->nsm;
+  const int64_t need = (int64_t)grid * gram_gh_work(m);
+  if (need > h->gwork_cap) {
+    cudaFree(h->gwork);
+    int err = 0;
+    h->gwork = dalloc<double>(need, &err);
+    if (!h->gwork) return err;
+    h->gwork_cap = need;
+  }
+  RB_CUDA_TRY(gram_gh<T>((const T* const*)(h->dptr + 256), (const T* const*)(h->dptr + 384), m, h->npad, h->dG,
+                         h->dG + (size_t)kMaxGram * kMaxGram, h->gwork, grid, h->us));
+  RB_CUDA_TRY(cudaMemcpyAsync(G.data(), h->dG, sizeof(double) * G.size(), cudaMemcpyDeviceToHost, h->us));
+  RB_CUDA_TRY(cudaMemcpyAsync(H.data(), h->dG + (size_t)kMaxGram * kMaxGram, sizeof(double) * H.size(),
+                              cudaMemcpyDeviceToHost, h->us));
+  return sync(h);
+}
+
+// Squared 2-norms of the given columns.
+template <typename T>
+int block_colnorm2(rb_ctx* h, const std::vector<const T*>& M, std::vector<double>& out) {
+  const int k = (int)M.size();
+  out.assign(k, 0.0);
+  if (!k) return RB_OK;
+  int rc = sync(h);
+  if (rc) return rc;
+  rc = upload_ptrs(h, 2, M);
+  if (rc) return rc;
+  RB_CUDA_TRY(colnorm2<T>((const T* const*)(h->dptr + 256), k, h->npad, h->st, h->partials, h->grids.vec, h->us));
+  RB_CUDA_TRY(cudaMemcpyAsync(h->hst->red, h->st->red, sizeof(double) * k, cudaMemcpyDeviceToHost, h->us));
+  rc = sync(h);
+  if (rc) return rc;
+  std::memcpy(out.data(), h->hst->red, sizeof(double) * k);
+  return RB_OK;
+}
+
 int alloc_vectors(rb_ctx* h) {
   int err = 0;
   double** vs[] = {&h->b, &h->x, &h->r, &h->p, &h->s, &h->q, &h->t, &h->qraw, &h->traw, &h->rt0, &h->tmp,
@@ -291,6 +352,7 @@ int alloc_vectors(rb_ctx* h) {
 // Alg. 2 step 1 for the columns currently in U, Ut (kin of them):
 // C = A U, C~ = A^T U~, SVD biorthogonalisation, C-hat = C~ D_c^{-1}.
 int recycle_setup(rb_ctx* h, int kin, int64_t* setup_mv) {
+  PhaseClock pc;
   h->k = 0;
   reset_graphs(h);
   if (kin == 0) return RB_OK;
@@ -309,6 +371,7 @@ int recycle_setup(rb_ctx* h, int kin, int64_t* setup_mv) {
   std::vector<double> M;
   int rc = block_gram<double>(h, Xc, Yc, M);
   if (rc) return rc;
+  pc.lap("setup_spmm+gram");
   for (double v : M)
     if (!std::isfinite(v)) return RB_ENONFINITE;
   std::vector<double> P((size_t)kin * kin), Q((size_t)kin * kin), sig(kin);
@@ -337,6 +400,8 @@ int recycle_setup(rb_ctx* h, int kin, int64_t* setup_mv) {
     if (rc) return rc;
     std::swap(*jb.src, h->T1);
   }
+  rc = sync(h);
+  pc.lap("setup_gemm");
   std::vector<double> dinv(kk);
   for (int j = 0; j < kk; ++j) dinv[j] = 1.0 / sig[j];
   RB_CUDA_TRY(cudaMemcpyAsync(h->Chat, h->Ct, sizeof(double) * ld * kk, cudaMemcpyDeviceToDevice, h->us));
@@ -464,6 +529,7 @@ struct SolveOut {
   int seeds = 1;
   int cycles = 0;
   int outer = 1;
+  double ms_update = 0;
   int64_t mv = 0, mv_setup = 0, mv_check = 0;
   double relres_rec = 0, relres_true = 0;
   double bytes = 0;
@@ -547,6 +613,7 @@ int iterate_plain(rb_ctx* h) {
 // Y = W y and A Y = Z y are formed in T.
 template <typename T>
 int cycle_update(rb_ctx* h, int bank, int nit, int ns) {
+  PhaseClock pc;
   const int64_t ld = h->npad;
   T* Yc = (T*)h->Yc;
   T* AYc = (T*)h->AYc;
@@ -568,14 +635,14 @@ int cycle_update(rb_ctx* h, int bank, int nit, int ns) {
   const int m = (int)W.size();
   if (m == 0) return RB_OK;
   std::vector<double> G, H;
-  int rc = block_gram<T>(h, Z, Z, G);
+  int rc = block_gram_gh<T>(h, Z, W, G, H);
   if (rc) return rc;
-  rc = block_gram<T>(h, Z, W, H);
-  if (rc) return rc;
+  pc.lap("gram");
   const int kt = std::min(h->o.k_max, m);
   std::vector<double> Y((size_t)m * std::max(kt, 1));
   const double rtol = std::is_same<T, float>::value ? kRankTolF32 : kRankTol;
   const int kn = harmonic_ritz(m, G.data(), H.data(), kt, rtol, Y.data(), nullptr, nullptr);
+  pc.lap("harmonic_ritz");
   if (kn <= 0) return RB_OK;   // nothing usable: keep the old candidate
   Y.resize((size_t)m * kn);
   std::vector<T*> oY, oAY;
@@ -587,14 +654,16 @@ int cycle_update(rb_ctx* h, int bank, int nit, int ns) {
   if (rc) return rc;
   rc = block_gemm<T>(h, oAY, Z, Y, kn);
   if (rc) return rc;
+  rc = sync(h);
+  pc.lap("gemm");
   // unit 2-norm columns
   std::vector<const T*> yc(oY.begin(), oY.end());
   std::vector<double> N2;
-  rc = block_gram<T>(h, yc, yc, N2);
+  rc = block_colnorm2<T>(h, yc, N2);
   if (rc) return rc;
   std::vector<double> f(kn);
   for (int j = 0; j < kn; ++j) {
-    const double nn = N2[j + (size_t)j * kn];
+    const double nn = N2[j];
     f[j] = nn > 0 ? 1.0 / std::sqrt(nn) : 0.0;
   }
   RB_CUDA_TRY(cudaMemcpy(h->dR, f.data(), sizeof(double) * kn, cudaMemcpyHostToDevice));
@@ -603,7 +672,9 @@ int cycle_update(rb_ctx* h, int bank, int nit, int ns) {
   std::swap(h->Yc, h->Yn);
   std::swap(h->AYc, h->AYn);
   h->kY = kn;
-  return sync(h);
+  rc = sync(h);
+  pc.lap("normalise");
+  return rc;
 }
 
 // One solve's iterations in update mode: graphs of one cycle each, the
@@ -643,7 +714,9 @@ int iterate_cycles(rb_ctx* h, SolveOut* so) {
     const bool allowed = (h->o.update_cycles == 0) || (c < h->o.update_cycles);
     if (ok && allowed && nit > 0) {
       const int ns = nit - (hs.half ? 1 : 0);
+      const auto t0 = std::chrono::steady_clock::now();
       rc = cycle_update<T>(h, bank, nit, ns);
+      so->ms_update += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
       if (rc) return rc;
       so->cycles += 1;
     }
@@ -723,7 +796,7 @@ extern "C" int rbicgstab_create(rb_handle* out, const rb_opts* opts) {
   if (!h->Dinv) return fail(err);
   h->dptr = (const double**)dalloc<double*>(4 * 128, &err);
   if (!h->dptr) return fail(err);
-  h->dG = dalloc<double>(kMaxGram * kMaxGram, &err);
+  h->dG = dalloc<double>(2 * kMaxGram * kMaxGram, &err);
   h->dR = dalloc<double>(kMaxGram * std::max(RB_KMAX, kMaxGram), &err);
   if (!h->dG || !h->dR) return fail(err ? err : RB_ENOMEM);
   *out = h;
@@ -965,7 +1038,9 @@ static int solve_fp64(rb_ctx* h, SolveOut* so, bool x_nonzero) {
     RB_CUDA_TRY(cudaMemcpyAsync(h->U, h->Yc, sizeof(double) * ld * h->kY, cudaMemcpyDeviceToDevice, h->us));
     RB_CUDA_TRY(cudaMemcpyAsync(h->Ut, h->Yc, sizeof(double) * ld * h->kY, cudaMemcpyDeviceToDevice, h->us));
     int64_t mv = 0;
+    const auto t0 = std::chrono::steady_clock::now();
     rc = recycle_setup(h, h->kY, &mv);
+    so->ms_update += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     if (rc < 0) return rc;
     so->mv_setup += mv;
     h->update_epoch = h->matrix_epoch;
@@ -1047,7 +1122,9 @@ static int solve_mixed(rb_ctx* h, SolveOut* so, bool x_nonzero) {
       RB_CUDA_TRY(to_double((const float*)h->Yc + (int64_t)j * ld, h->U + (int64_t)j * ld, ld, h->us));
     RB_CUDA_TRY(cudaMemcpyAsync(h->Ut, h->U, sizeof(double) * ld * h->kY, cudaMemcpyDeviceToDevice, h->us));
     int64_t mv = 0;
+    const auto t0 = std::chrono::steady_clock::now();
     int rc2 = recycle_setup(h, h->kY, &mv);
+    so->ms_update += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     if (rc2 < 0) return rc2;
     so->mv_setup += mv;
     h->update_epoch = h->matrix_epoch;
@@ -1110,6 +1187,7 @@ extern "C" int rbicgstab_solve(rb_handle h, const double* b, double* x, int wher
     st_out->relres_true = so.relres_true;
     st_out->ms_total = ms;
     st_out->bytes_model = so.bytes;
+    st_out->ms_update = so.ms_update;
   }
   return so.status;
 }

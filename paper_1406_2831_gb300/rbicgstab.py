@@ -53,7 +53,7 @@ class Stats(ctypes.Structure):
                 ("matvecs_setup", ctypes.c_int64), ("matvecs_check", ctypes.c_int64),
                 ("cycles", ctypes.c_int32), ("outer", ctypes.c_int32), ("relres_rec", ctypes.c_double),
                 ("relres_true", ctypes.c_double), ("ms_total", ctypes.c_double),
-                ("bytes_model", ctypes.c_double)]
+                ("bytes_model", ctypes.c_double), ("ms_update", ctypes.c_double)]
 
     def as_dict(self) -> dict:
         return {name: getattr(self, name) for name, _ in self._fields_}
