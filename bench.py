@@ -120,6 +120,14 @@ def pass_flops(n: int, z: int, k: int) -> list:
     return [2 * z + 2 * n, 4 * n, 2 * z + 8 * n, 0, 10 * n]
 
 
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of the dominant
+# pass per launch, from ncu captures summarised in profiles/; keyed by
+# (precision, pass, grid side, k).  Set to None when the kernel changes.
+TRAFFIC = {
+    ("mixed", "P1", 128, 20): 312_008_448,   # profiles/mixed_passes_3d7pt_128cubed_k20.md
+}
+
+
 def measured_peaks() -> dict:
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -343,7 +351,7 @@ def run_ours(args):
     iter_gbs = sum(pb) / (iter_ms * 1e-3) / 1e9
     roof = {"bound": "hbm" if hbm_frac >= alu_frac else "alu", "kernel": f"P{dom + 1}",
             "achieved": round(gbs, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
-            "frac": round(hbm_frac, 4), "traffic": None,
+            "frac": round(hbm_frac, 4), "traffic": TRAFFIC.get((args.precision, f"P{dom + 1}", N, args.k)),
             "peak_source": peaks["source"],
             "fp64_alu": {"achieved_tflops": round(gfs / 1e3, 4), "peak_tflops": round(peak_fp64, 3),
                          "frac": round(alu_frac, 4), "peak_source": "measured (torch float64 matmul)"},
