@@ -6,8 +6,12 @@ plus the HBM roofline of the dominant fused-iteration kernel.
 
 One step = one pass of the whole hot path over the sequence: for each of the
 20 matrices set the values (Alg. 2 step 1 recycle setup included) and solve
-its 4 right-hand sides with RBiCGSTAB (Alg. 2), updating the recycle space
-during the first solve of each matrix (cycles of s = 25, harmonic Ritz).
+its 4 right-hand sides with RBiCGSTAB (Alg. 2) as one block (the four
+systems iterate together and share each pass over A, C and C-hat), updating
+the recycle space from the block's first system (cycles of s = 25, harmonic
+Ritz); the update takes effect from the next matrix.  The default headline
+runs the FP32 inner solve with FP64 refinement; plain FP64 BiCGSTAB on the
+same sequence (one system at a time, and blocked) is timed beside it.
 Each step starts from an empty recycle space, so every step does the same
 work.  Inputs (matrix values, right-hand sides) are staged in HBM before the
 timed region; they are larger than L2, so no flush is needed between steps.
@@ -43,7 +47,8 @@ def parse():
     ap.add_argument("--shifts", type=int, default=20)
     ap.add_argument("--rhs", type=int, default=4)
     ap.add_argument("--k", type=int, default=20)
-    ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
+    ap.add_argument("--precision", choices=["fp64", "mixed"], default="mixed")
+    ap.add_argument("--block", type=int, default=4, help="right-hand sides per blocked solve (1..4)")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain-BiCGSTAB comparison")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -105,26 +110,30 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------- roofline model
-def pass_bytes(n: int, z: int, k: int, vb: int = 8, ab: int = 8) -> list:
-    """Algorithmic HBM bytes of passes P1..P5 (CSR with int32 indices, x-gather
-    counted once, every stream touched once)."""
+def pass_bytes(n: int, z: int, k: int, vb: int = 8, ab: int = 8, R: int = 1) -> list:
+    """Algorithmic HBM bytes of passes P1..P5 for a block of R right-hand
+    sides (CSR with int32 indices, x-gather counted once, every stream touched
+    once; A, C, C-hat and r~_0 are read once per pass for the whole block)."""
     A = z * (ab + 4) + 4 * (n + 1)
     if k > 0:
-        return [A + n * vb * (k + 3), n * vb * (k + 4), A + n * vb * (k + 2), n * vb * (k + 4), 8 * n * vb]
-    return [A + 3 * n * vb, 3 * n * vb, A + 4 * n * vb, 0, 8 * n * vb]
+        return [A + n * vb * (k + 1 + 2 * R), n * vb * (k + 4 * R), A + n * vb * (k + 2 * R),
+                n * vb * (k + 1 + 3 * R), 8 * R * n * vb]
+    return [A + n * vb * (1 + 2 * R), 3 * R * n * vb, A + n * vb * (1 + 3 * R), 0, 8 * R * n * vb]
 
 
-def pass_flops(n: int, z: int, k: int) -> list:
+def pass_flops(n: int, z: int, k: int, R: int = 1) -> list:
     if k > 0:
-        return [2 * z + 2 * n * (k + 1), 2 * n * (k + 2), 2 * z + 2 * n * k, 2 * n * (k + 4), 10 * n]
-    return [2 * z + 2 * n, 4 * n, 2 * z + 8 * n, 0, 10 * n]
+        f = [2 * z + 2 * n * (k + 1), 2 * n * (k + 2), 2 * z + 2 * n * k, 2 * n * (k + 4), 10 * n]
+    else:
+        f = [2 * z + 2 * n, 4 * n, 2 * z + 8 * n, 0, 10 * n]
+    return [R * v for v in f]
 
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of the dominant
 # pass per launch, from ncu captures summarised in profiles/; keyed by
-# (precision, pass, grid side, k).  Set to None when the kernel changes.
+# (precision, pass, grid side, k, right-hand sides per block).  An entry is
+# removed when its kernel changes.
 TRAFFIC = {
-    ("mixed", "P1", 128, 20): 312_008_448,   # profiles/mixed_passes_3d7pt_128cubed_k20.md
 }
 
 
@@ -198,16 +207,17 @@ def run_passes_only(args):
     b = torch.from_numpy(spec.rhs[0][0]()).to(dev)
     rp, col = torch.from_numpy(P.row_ptr).to(dev), torch.from_numpy(P.col).to(dev)
     out = {"workload": f"3d-7pt-{args.N}^3 system 1", "n": P.n, "nnz": P.nnz, "k": args.k,
-           "precision": args.precision}
+           "precision": args.precision, "rhs_block": args.block}
     for label, k in (("recycled", args.k), ("plain", 0)):
         s = rb.Solver(k_max=k, recycle="fixed" if k else "none", precision=args.precision)
         s.set_matrix(rp, col, vals)
         if k:
             U = torch.from_numpy(inputs.random_recycle_basis(P.n, k, 11)).to(dev)
             s.set_recycle(U)
-        ms, code = rb.time_passes(s, b, reps=5)
+        B = torch.stack([b] * args.block) if args.block > 1 else b
+        ms, code = rb.time_passes(s, B, reps=5)
         vb = 8 if args.precision == "fp64" else 4
-        pb = pass_bytes(P.n, P.nnz, k, vb=vb, ab=vb)
+        pb = pass_bytes(P.n, P.nnz, k, vb=vb, ab=vb, R=args.block)
         out[label] = {"passes_ms": [round(v, 5) for v in ms],
                       "passes_GBs": [round(bb / (m * 1e-3) / 1e9, 1) if m > 0 else 0 for bb, m in zip(pb, ms)],
                       "status": code}
@@ -246,6 +256,13 @@ def run_ours(args):
     rhs_d = [[b.to(dev) for b in row] for row in rhs_h]
     xbuf = torch.zeros(n, dtype=torch.float64, device=dev)
     xh = torch.zeros(n, dtype=torch.float64).pin_memory()
+    blk = max(1, min(args.block, 4))
+    # right-hand sides of each shift as (blk, n) blocks
+    chunks = [[(c, min(c + blk, len(row))) for c in range(0, len(row), blk)] for row in rhs_h]
+    rhs_hb = [[torch.stack(row[a:b]).pin_memory() for a, b in ch] for row, ch in zip(rhs_h, chunks)]
+    rhs_db = [[B.to(dev) for B in row] for row in rhs_hb]
+    xbufb = torch.zeros((blk, n), dtype=torch.float64, device=dev)
+    xhb = torch.zeros((blk, n), dtype=torch.float64).pin_memory()
     torch.cuda.synchronize()
 
     def make(recycled: bool, precision: str):
@@ -255,11 +272,24 @@ def run_ours(args):
         s.set_matrix(rp, col, vals_d[0])
         return s
 
-    def sequence(s, recycled: bool, host: bool, log=None):
+    def sequence(s, recycled: bool, host: bool, log=None, block=1):
         if recycled:
             s.set_recycle(None)
         for j in range(len(vals_d)):
             s.set_values(vals_h[j] if host else vals_d[j])
+            if block > 1:
+                for kk, B in enumerate(rhs_hb[j] if host else rhs_db[j]):
+                    X = (xhb if host else xbufb)[: B.shape[0]]
+                    X.zero_()
+                    r = s.solve_block(B, X)
+                    for ib, st in enumerate(r.stats):
+                        if st["status"] != 0:
+                            raise RuntimeError(f"block {j},{kk} failed: {st}")
+                        if log is not None:
+                            # update cost, cycles and setup products describe the
+                            # whole blocked call: count them once
+                            log.append(st if ib == 0 else dict(st, ms_update=0.0, cycles=0, matvecs_setup=0))
+                continue
             for kk in range(len(rhs_d[j])):
                 if host:
                     xh.zero_()
@@ -277,9 +307,9 @@ def run_ours(args):
             dist.barrier()
         torch.cuda.synchronize()
 
-    def timed(s, recycled, host, steps, warmup, clocks=None):
+    def timed(s, recycled, host, steps, warmup, clocks=None, block=1):
         for _ in range(warmup):
-            sequence(s, recycled, host)
+            sequence(s, recycled, host, block=block)
         barrier()
         l0 = rb.kernel_launches()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -288,7 +318,7 @@ def run_ours(args):
         logs = []
         e0.record(stream)
         for _ in range(steps):
-            sequence(s, recycled, host, logs)
+            sequence(s, recycled, host, logs, block=block)
         e1.record(stream)
         barrier()
         ck = clocks.stop() if clocks else None
@@ -303,31 +333,34 @@ def run_ours(args):
     res = {}
     # recycled (headline)
     s_rec = make(True, args.precision)
-    ms, logs, launches, clk = timed(s_rec, True, False, args.steps, args.warmup, ClockSampler(local))
+    ms, logs, launches, clk = timed(s_rec, True, False, args.steps, args.warmup, ClockSampler(local), block=blk)
     res["rec"] = dict(ms=ms, logs=logs, launches=launches, clocks=clk)
     # roofline of the dominant pass (CUDA events around each pass on this stream)
     s_rec.set_values(vals_d[0])
     rb_reps = 10
-    ms_pass, code = rb.time_passes(s_rec, rhs_d[0][0], reps=rb_reps)
+    B0 = rhs_db[0][0] if blk > 1 else rhs_d[0][0]
+    R0 = B0.shape[0] if blk > 1 else 1
+    ms_pass, code = rb.time_passes(s_rec, B0, reps=rb_reps)
     k_used = s_rec.get_recycle()[0].shape[1]
-    if args.precision == "fp64":
-        pb = pass_bytes(n, z, k_used)
-        pf = pass_flops(n, z, k_used)
-    else:
-        pb = pass_bytes(n, z, k_used, vb=4, ab=4)
-        pf = pass_flops(n, z, k_used)
+    vb = 8 if args.precision == "fp64" else 4
+    pb = pass_bytes(n, z, k_used, vb=vb, ab=vb, R=R0)
+    pf = pass_flops(n, z, k_used, R=R0)
     del s_rec
-    # plain FP64 BiCGSTAB on the same sequence
+    # plain FP64 BiCGSTAB on the same sequence: one system at a time, and blocked
     if not args.no_plain:
+        ps = max(1, args.steps // 2)
         s_pl = make(False, "fp64")
-        msp, logp, _, _ = timed(s_pl, False, False, max(1, args.steps // 2), 1)
-        res["plain"] = dict(ms=msp, logs=logp, steps=max(1, args.steps // 2))
+        msp, logp, _, _ = timed(s_pl, False, False, ps, 1)
+        res["plain"] = dict(ms=msp, logs=logp, steps=ps)
         ms_pass_plain, _ = rb.time_passes(s_pl, rhs_d[0][0], reps=rb_reps)
+        if blk > 1:
+            msb, logb, _, _ = timed(s_pl, False, False, ps, 1, block=blk)
+            res["plain_block"] = dict(ms=msb, logs=logb, steps=ps)
         del s_pl
     # end to end through the public API with pinned host buffers
     if not args.no_e2e:
         s_e = make(True, args.precision)
-        mse, loge, _, _ = timed(s_e, True, True, 1, 1)
+        mse, loge, _, _ = timed(s_e, True, True, 1, 1, block=blk)
         res["e2e"] = dict(ms=mse)
         del s_e
     peak_fp64 = fp64_peak_tflops(torch)
@@ -351,7 +384,7 @@ def run_ours(args):
     iter_gbs = sum(pb) / (iter_ms * 1e-3) / 1e9
     roof = {"bound": "hbm" if hbm_frac >= alu_frac else "alu", "kernel": f"P{dom + 1}",
             "achieved": round(gbs, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
-            "frac": round(hbm_frac, 4), "traffic": TRAFFIC.get((args.precision, f"P{dom + 1}", N, args.k)),
+            "frac": round(hbm_frac, 4), "traffic": TRAFFIC.get((args.precision, f"P{dom + 1}", N, args.k, R0)),
             "peak_source": peaks["source"],
             "fp64_alu": {"achieved_tflops": round(gfs / 1e3, 4), "peak_tflops": round(peak_fp64, 3),
                          "frac": round(alu_frac, 4), "peak_source": "measured (torch float64 matmul)"},
@@ -366,8 +399,8 @@ def run_ours(args):
         "data": "synthetic (seeded stencil systems and Gaussian right-hand sides)",
         "config": {"workload": f"3d-7pt-conv-diff-{N}^3-shifted", "n": n, "nnz": z,
                    "shifts": args.shifts, "rhs_per_shift": args.rhs, "k": args.k, "cycle_s": spec.cycle_s,
-                   "tol": spec.tol, "recycle": "update on first RHS of each matrix (harmonic Ritz)",
-                   "precision": args.precision, "parallelism": f"replicas x{world}",
+                   "tol": spec.tol, "recycle": "update from the first RHS of each matrix (harmonic Ritz), in force from the next matrix",
+                   "precision": args.precision, "rhs_block": blk, "parallelism": f"replicas x{world}",
                    "l2": "inputs larger than L2 (no flush)"},
         "recycled": {"solves_per_s": round(value, 3), "iters_mean": round(statistics.mean(iters), 2),
                      "iters_total": int(sum(iters)), "matvecs": int(sum(l["matvecs"] for l in logs)),
@@ -387,6 +420,12 @@ def run_ours(args):
                               "matvecs": int(sum(l["matvecs"] for l in lp)), "steps": res["plain"]["steps"],
                               "passes_ms": [round(v, 5) for v in ms_pass_plain]}
         line["recycled_over_plain"] = round(value / vp, 4)
+        if "plain_block" in res:
+            lb = res["plain_block"]["logs"]
+            vpb = solves_per_step * res["plain_block"]["steps"] * world / (res["plain_block"]["ms"] * 1e-3)
+            line["plain_fp64_blocked"] = {"solves_per_s": round(vpb, 3), "rhs_block": blk,
+                                          "iters_mean": round(statistics.mean(l["iters"] for l in lb), 2)}
+            line["recycled_over_plain_blocked"] = round(value / vpb, 4)
     if "e2e" in res:
         Bi = (len(vals_h) * z * 8 + solves_per_step * n * 8) * 1 + solves_per_step * n * 8
         Bo = solves_per_step * n * 8

@@ -141,6 +141,28 @@ int rbicgstab_get_recycle(rb_handle h, int32_t* k, double* U, double* Ut, int64_
  * Errors: RB_EDIM (no matrix), RB_ENONFINITE (NaN/Inf in b or x), RB_ECUDA. */
 int rbicgstab_solve(rb_handle h, const double* b, double* x, int where, rb_stats* st);
 
+/* Maximum number of right-hand sides of one blocked solve. */
+#define RB_MAX_RHS 4
+
+/* Blocked solve of A X = B for 1 <= nrhs <= RB_MAX_RHS right-hand sides of
+ * the same matrix (a practical extension: the paper solves one system at a
+ * time).  Column i of B and X (column-major, leading dimension ld >= n when
+ * nrhs > 1) is one system; X holds the initial guesses on entry and the
+ * solutions on return.  Every system runs Alg. 2 with its own iterates and
+ * scalars, the same recycle space and the same shadow vector r~_0; their
+ * iterations share each pass over A, C and C-hat, and a system that has
+ * converged stops updating while the others go on.  Each system's iterates
+ * are those rbicgstab_solve would compute for it alone, up to the rounding
+ * of the dot products and of a reseeded shadow (when (r~_0, r_0) = 0 for one
+ * system, all take the next seed).  In the RB_RECYCLE_UPDATE_* modes the
+ * update is built from the first system's Krylov vectors.  st, if not NULL,
+ * receives nrhs records (cycles, matvecs_setup and ms_update describe the
+ * whole call; ms_total is the call's duration).  Returns RB_OK when every
+ * system converged, else the first system's non-OK status.  Errors as
+ * rbicgstab_solve, plus RB_EINVAL for nrhs outside 1..RB_MAX_RHS or ld < n. */
+int rbicgstab_solve_block(rb_handle h, int32_t nrhs, const double* B, double* X, int64_t ld,
+                          int where, rb_stats* st);
+
 /* y = A v (transpose = 0) or y = A^T v (transpose = 1) with the library's
  * FP64 SpMV kernels; v and y have n entries.  Errors: RB_EDIM, RB_EINVAL. */
 int rbicgstab_apply(rb_handle h, const double* v, double* y, int transpose, int where);
@@ -157,14 +179,16 @@ int rbicgstab_harmonic_ritz(int32_t m, const double* G, const double* H, int32_t
                             double* Y, double* theta_re, double* theta_im, int32_t* k_used);
 
 /* Benchmark helper: run `reps` iterations of the fused passes from a fresh
- * start on right-hand side b (x_{-1} = 0, convergence test disabled), each
- * pass launched on its own between CUDA events on the handle's stream, and
- * write the average duration in milliseconds of passes P1..P5 to ms[0..4]
- * (ms[3] = 0 when k = 0: plain BiCGSTAB has no separate P4).  The iterate is
- * left in an unspecified state; call rbicgstab_solve afterwards as usual.
- * Returns a breakdown code if the iteration broke down during timing.
- * Errors: RB_EINVAL (reps outside 1..1000), RB_EDIM. */
-int rbicgstab_time_passes(rb_handle h, const double* b, int where, int32_t reps, double* ms);
+ * start on the nrhs right-hand sides in B (column-major, leading dimension
+ * ld; x_{-1} = 0, convergence test disabled), each pass launched on its own
+ * between CUDA events on the handle's stream, and write the average duration
+ * in milliseconds of passes P1..P5 to ms[0..4] (ms[3] = 0 when k = 0: plain
+ * BiCGSTAB has no separate P4).  The iterates are left in an unspecified
+ * state; call rbicgstab_solve afterwards as usual.  Returns a breakdown code
+ * if the iteration broke down during timing.  Errors: RB_EINVAL (reps
+ * outside 1..1000, nrhs outside 1..RB_MAX_RHS, ld < n), RB_EDIM. */
+int rbicgstab_time_passes(rb_handle h, int32_t nrhs, const double* B, int64_t ld, int where,
+                          int32_t reps, double* ms);
 
 /* Residual without allocation: r = b - A x and *rnorm2 = ||r||^2 for an n x n
  * CSR matrix given by device pointers (row_ptr[n+1], col[nnz], val[nnz]), with

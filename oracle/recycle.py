@@ -132,13 +132,19 @@ def solve_sequence(matrices, rhs, k, cycle_s=25, tol=1e-8, policy="first", recyc
     vectors during the solves selected by ``policy`` ("first": the first RHS
     of every matrix, "all", "none").  ``recycle=False`` runs plain BiCGSTAB
     (Alg. 2 with k = 0) on every system.  Setup (C, C~, D_c) is recomputed
-    only when the matrix or U changes (the note under Alg. 2)."""
+    only when the matrix or U changes (the note under Alg. 2).
+
+    ``policy="first_block"`` is the order of a blocked solve, in which all
+    right-hand sides of one matrix iterate together: every RHS of A^(i) uses
+    the space in force when A^(i) arrives, and the update built during the
+    first RHS's solve takes effect from A^(i+1) on."""
     from .shadow import DEFAULT_SEED
     seed = DEFAULT_SEED if shadow_seed is None else shadow_seed
     res = SequenceResult()
     U = U0
     for A, bs in zip(matrices, rhs):
         rec = None
+        pending = None
         for ib, b in enumerate(bs):
             b = b() if callable(b) else b
             if recycle and (rec is None or rec_U_changed):
@@ -147,7 +153,7 @@ def solve_sequence(matrices, rhs, k, cycle_s=25, tol=1e-8, policy="first", recyc
             elif not recycle:
                 rec = empty_space(A.shape[0])
             rec_U_changed = False
-            upd = recycle and (policy == "all" or (policy == "first" and ib == 0))
+            upd = recycle and (policy == "all" or (policy in ("first", "first_block") and ib == 0))
             cand = None
             if upd:
                 cand = Candidate(Y=rec.U.copy(), AY=rec.C.copy(), k=k, max_cycles=max_cycles)
@@ -160,7 +166,12 @@ def solve_sequence(matrices, rhs, k, cycle_s=25, tol=1e-8, policy="first", recyc
             res.matvecs_iter += info.matvecs
             res.k_used.append(rec.k)
             if upd and cand.Y.shape[1] > 0:
-                U = cand.Y
-                rec_U_changed = True
+                if policy == "first_block":
+                    pending = cand.Y
+                else:
+                    U = cand.Y
+                    rec_U_changed = True
+        if pending is not None:
+            U = pending
     res.U_final = U
     return res

@@ -19,7 +19,8 @@ __device__ __forceinline__ double fma_t(double a, double b, double c) { return _
 constexpr int kSlice = 32;        // SELL slice height = warp width
 constexpr int kBlock = 256;       // threads per block of the streaming kernels
 constexpr int kMaxK = RB_KMAX;
-constexpr int kMaxNV = kMaxK + 8; // values one fused reduction may carry
+constexpr int kMaxNV = kMaxK + 8; // values one fused reduction may carry per RHS
+constexpr int kMaxRhs = RB_MAX_RHS; // right-hand sides one blocked solve iterates together
 
 // SELL-32 view of a sparse matrix: slice `sl` holds rows sl*32 .. sl*32+31;
 // entry j of row sl*32+lane sits at slice_ptr[sl] + j*32 + lane.  Padding

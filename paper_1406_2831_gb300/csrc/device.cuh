@@ -30,6 +30,7 @@ template <>
 struct Acc<double> {
   double v = 0.0;
   __device__ __forceinline__ void add(double a, double b) { v = fma(a, b, v); }
+  __device__ __forceinline__ void add1(double x) { v += x; }
   __device__ __forceinline__ double get() const { return v; }
 };
 
@@ -47,16 +48,34 @@ struct Acc<float> {
     hi = s;
     lo = __fadd_rn(lo, __fadd_rn(err, e));
   }
+  // Compensated add of one FP32 value (TwoSum, error into lo).
+  __device__ __forceinline__ void add1(float x) {
+    const float s = __fadd_rn(hi, x);
+    const float bb = __fsub_rn(s, hi);
+    const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(x, bb));
+    hi = s;
+    lo = __fadd_rn(lo, err);
+  }
   __device__ __forceinline__ double get() const { return (double)hi + (double)lo; }
 };
 
+constexpr int kRedCH = 8;   // values per transpose chunk
+
+// Transpose buffer of the FP64 block sums: [warp][value][lane] (+1 pad).
+typedef double RedT[kBlock / 32][kRedCH][33];
+
+// Per-warp sums, the block/grid totals and the last-block flag.
 template <int NV>
-struct ReduceSmem {
-  static constexpr int CH = 8;                  // values per transpose chunk
-  double t[kBlock / 32][CH][33];                // [warp][value][lane] (+1 pad)
-  double w[kBlock / 32][NV > 0 ? NV : 1];      // per-warp sums
+struct ReduceCore {
+  double w[kBlock / 32][NV > 0 ? NV : 1];
   double res[NV > 0 ? NV : 1];
   int last;
+};
+
+template <int NV>
+struct ReduceSmem : ReduceCore<NV> {
+  static constexpr int CH = kRedCH;
+  RedT t;
 };
 
 // Warp-level sums of per-thread accumulators into sm.w[warp][v].
@@ -148,9 +167,16 @@ __device__ __forceinline__ void block_sum(Acc<T> (&acc)[NV], int nv, ReduceSmem<
 // sm.w[warp][0..nv).  Sums them across warps, publishes the block partial,
 // takes a ticket; returns true in every thread of the last block with
 // sm.res[0..nv) holding the grid totals.  `ticket` is reset to 0.
+//
+// The last block sums the partial rows in chunks of FCH values (each thread
+// takes a fixed subset of rows, then a per-warp transpose and a cross-warp
+// sum), so the registers this tail needs do not grow with nv and do not
+// limit the occupancy of the kernel's main loop.
 template <int NV>
-__device__ bool grid_finish(int nv, ReduceSmem<NV>& sm, double* partials, unsigned int* ticket) {
+__device__ bool grid_finish(int nv, ReduceCore<NV>& sm, RedT& tbuf, double* partials, unsigned int* ticket) {
   constexpr int NW = kBlock / 32;
+  constexpr int CH = kRedCH;
+  constexpr int FCH = 2 * CH;
   __syncthreads();
   for (int v = threadIdx.x; v < nv; v += blockDim.x) {
     double s = 0.0;
@@ -167,16 +193,53 @@ __device__ bool grid_finish(int nv, ReduceSmem<NV>& sm, double* partials, unsign
   __syncthreads();
   if (!sm.last) return false;
   __threadfence();
-  Acc<double> tot[NV];
-  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
-    const double* pb = partials + (size_t)b * nv;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll 1
+  for (int c0 = 0; c0 < nv; c0 += FCH) {
+    double tot[FCH];
 #pragma unroll
-    for (int v = 0; v < NV; ++v)
-      if (v < nv) tot[v].v += __ldcg(pb + v);
+    for (int u = 0; u < FCH; ++u) tot[u] = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
+      const double* pb = partials + (size_t)b * nv + c0;
+#pragma unroll
+      for (int u = 0; u < FCH; ++u)
+        if (c0 + u < nv) tot[u] += __ldcg(pb + u);
+    }
+#pragma unroll
+    for (int h = 0; h < FCH; h += CH) {
+#pragma unroll
+      for (int u = 0; u < CH; ++u) tbuf[warp][u][lane] = tot[h + u];
+      __syncwarp();
+      if (lane < CH && c0 + h + lane < nv) {
+        const double* row = tbuf[warp][lane];
+        double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+#pragma unroll
+        for (int j = 0; j < 32; j += 4) {
+          s0 += row[j];
+          s1 += row[j + 1];
+          s2 += row[j + 2];
+          s3 += row[j + 3];
+        }
+        sm.w[warp][c0 + h + lane] = (s0 + s1) + (s2 + s3);
+      }
+      __syncwarp();
+    }
   }
-  block_sum<double, NV>(tot, nv, sm);
+  __syncthreads();
+  for (int v = threadIdx.x; v < nv; v += blockDim.x) {
+    double s = 0.0;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) s += sm.w[w][v];
+    sm.res[v] = s;
+  }
+  __syncthreads();
   if (threadIdx.x == 0) *ticket = 0u;
   return true;
+}
+
+template <int NV>
+__device__ __forceinline__ bool grid_finish(int nv, ReduceSmem<NV>& sm, double* partials, unsigned int* ticket) {
+  return grid_finish<NV>(nv, static_cast<ReduceCore<NV>&>(sm), sm.t, partials, ticket);
 }
 
 // Reduce per-thread accumulators acc[0..nv) (nv <= NV) over the grid.

@@ -17,8 +17,17 @@
 // equal forms above instead of fresh dots with q and r_i; they differ from
 // the literal ones only by rounding.
 //
+// Blocked solves: every pass handles R right-hand sides of the same matrix
+// and recycle space at once (R = 1, 2 or 4; per-RHS vectors and device
+// state, one grid reduction), so A, C, C-hat and r~_0 are read once per pass
+// for all R.  A right-hand side whose solve has ended is masked out.
+//
 // T is the storage and SpMV type (double for RB_FP64, float for the inner
-// solve of RB_MIXED); all dot products and projections accumulate in FP64.
+// solve of RB_MIXED).  Dot products of the scalar recurrences accumulate in
+// FP64 (FP64 data) or Dot2-compensated FP32 (FP32 data).  The projection
+// coefficients zeta, gamma of FP32 data are summed in FP32 within each
+// 32-row slice and compensated across slices: accuracy at the level of the
+// FP32 vectors they project.
 #include <algorithm>
 #include <cstdlib>
 #include <type_traits>
@@ -93,9 +102,96 @@ __device__ void finish_p5(IterState* st, const double* res, int k) {
   else if (st->iter >= st->max_itn) fail(st, RB_ENOTCONV);
 }
 
+
+// ---------------------------------------------------------------- helpers
+template <typename T, int KMAX, int R>
+struct ColProj {   // projections column-per-lane (FP32 data, or several RHS)
+  static constexpr bool value = KMAX > 0 && (std::is_same<T, float>::value || R > 1);
+};
+
+// Warp sum of one per-thread accumulator; lane 0 stores it to sm.w[warp][slot].
+template <int NV>
+__device__ __forceinline__ void warp_slot(const Acc<float>& a, int slot, ReduceCore<NV>& sm) {
+  float hi = a.hi, lo = a.lo;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float h2 = __shfl_down_sync(0xffffffffu, hi, o);
+    const float l2 = __shfl_down_sync(0xffffffffu, lo, o);
+    const float s = __fadd_rn(hi, h2);
+    const float bb = __fsub_rn(s, hi);
+    const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(h2, bb));
+    hi = s;
+    lo = __fadd_rn(__fadd_rn(lo, l2), e);
+  }
+  if ((threadIdx.x & 31) == 0) sm.w[threadIdx.x >> 5][slot] = (double)hi + (double)lo;
+}
+
+template <int NV>
+__device__ __forceinline__ void warp_slot(const Acc<double>& a, int slot, ReduceCore<NV>& sm) {
+  double x = a.v;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+  if ((threadIdx.x & 31) == 0) sm.w[threadIdx.x >> 5][slot] = x;
+}
+
+template <int NV>
+__device__ __forceinline__ void zero_slot(int slot, ReduceCore<NV>& sm) {
+  if ((threadIdx.x & 31) == 0) sm.w[threadIdx.x >> 5][slot] = 0.0;
+}
+
+// 16-byte vector of T.
+template <typename T>
+struct Vec;
+template <>
+struct Vec<float> {
+  using type = float4;
+  static constexpr int W = 4;
+};
+template <>
+struct Vec<double> {
+  using type = double2;
+  static constexpr int W = 2;
+};
+
+// Dot products of one 32-row column (shared memory) with the R slice
+// vectors ys[r] (shared memory, read as broadcasts), each summed in T in row
+// order: part[r] = sum_i col[i] * ys[r][i].
+template <int R>
+__device__ __forceinline__ void col_dot(const float* col, const float (*ys)[32], const bool (&act)[R],
+                                        float (&part)[R]) {
+#pragma unroll
+  for (int u = 0; u < 8; ++u) {
+    const float4 c = *reinterpret_cast<const float4*>(col + 4 * u);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      if (!act[r]) continue;
+      const float4 y = *reinterpret_cast<const float4*>(ys[r] + 4 * u);
+      part[r] = __fmaf_rn(c.x, y.x, part[r]);
+      part[r] = __fmaf_rn(c.y, y.y, part[r]);
+      part[r] = __fmaf_rn(c.z, y.z, part[r]);
+      part[r] = __fmaf_rn(c.w, y.w, part[r]);
+    }
+  }
+}
+template <int R>
+__device__ __forceinline__ void col_dot(const double* col, const double (*ys)[32], const bool (&act)[R],
+                                        double (&part)[R]) {
+#pragma unroll
+  for (int u = 0; u < 16; ++u) {
+    const double2 c = *reinterpret_cast<const double2*>(col + 2 * u);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      if (!act[r]) continue;
+      const double2 y = *reinterpret_cast<const double2*>(ys[r] + 2 * u);
+      part[r] = __fma_rn(c.x, y.x, part[r]);
+      part[r] = __fma_rn(c.y, y.y, part[r]);
+    }
+  }
+}
+
 // ---------------------------------------------------------------- SpMV core
 // Rows sl*32+lane of two slices at once (sl1 < 0: only the first), so each
-// warp keeps two independent gather chains in flight.
+// warp keeps two independent gather chains in flight (single RHS, FP64).
 template <typename T>
 __device__ __forceinline__ void sell_rows2(const Sell<T>& A, int64_t sl0, int64_t sl1, int lane,
                                            const T* __restrict__ v, T& y0, T& y1) {
@@ -128,10 +224,9 @@ __device__ __forceinline__ void sell_rows2(const Sell<T>& A, int64_t sl0, int64_
 }
 
 // ---------------------------------------------------------------- P1 / P3
-// y = A v stored to `out`; acc[OFF + j] += Chat_j^T y (j < k); RTQ adds
-// acc[0] += (r~0, y); DOTS (k = 0 only) accumulates
-// [(s,t), (t,t), (r~0,t), (r~0,s)] with s = v, t = y.
-template <typename T, int KMAX, bool RTQ, bool DOTS>
+// Single RHS, FP64, row-per-lane projection: y = A v stored to `out`;
+// acc[OFF + j] += Chat_j^T y (j < k); RTQ adds acc[0] += (r~0, y).
+template <typename T, int KMAX, bool RTQ>
 __device__ __forceinline__ void spmv_project(const IterArgs<T>& a, const T* __restrict__ v,
                                              T* __restrict__ out, Acc<T>* acc, int k) {
   const int lane = threadIdx.x & 31;
@@ -151,13 +246,6 @@ __device__ __forceinline__ void spmv_project(const IterArgs<T>& a, const T* __re
       out[row] = y[h];
       const T yd = y[h];
       if (RTQ) acc[0].add(__ldg(rt0 + row), yd);
-      if (DOTS) {
-        const T sv = __ldg(v + row), rv = __ldg(rt0 + row);
-        acc[0].add(sv, yd);
-        acc[1].add(yd, yd);
-        acc[2].add(rv, yd);
-        acc[3].add(rv, sv);
-      }
 #pragma unroll
       for (int j = 0; j < KMAX; ++j)
         if (j < k) acc[OFF + j].add(__ldg(Chat + j * ld + row), yd);
@@ -165,294 +253,728 @@ __device__ __forceinline__ void spmv_project(const IterArgs<T>& a, const T* __re
   }
 }
 
-// FP32 projection, column per lane (KMAX <= 32): after the SpMV of a slice,
-// lane j accumulates sum over the slice's 32 rows of Chat[j*ld + row] * y[row]
-// with Dot2: the column's 32 consecutive values arrive as eight 16-byte loads
-// and y is broadcast by warp shuffles.  One accumulator per lane instead of k
-// per thread keeps registers low and occupancy high.  RTQ adds (r~0, y) per
-// row.  Warp sums land in sm.w[warp][*] (value 0 = (r~0, y) when RTQ).
-template <int KMAX, bool RTQ>
-__device__ __forceinline__ void spmv_project_f32(const IterArgs<float>& a, const float* __restrict__ v,
-                                                 float* __restrict__ out, int k, ReduceSmem<KMAX + 1>& sm) {
+// ---------------------------------------------------------------- cp.async
+// Asynchronous 16-byte global -> shared copies (L2 only), grouped per thread.
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+// Bring bytes [p, p + bytes) into L2 (no register or shared-memory cost);
+// p 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void prefetch_l2(const void* p, unsigned bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(p), "r"(bytes) : "memory");
+}
+
+// Per-warp shared staging of the multi-RHS / FP32 SpMV + projection passes.
+// Each stage holds one slice's first NE matrix entries per row (columns and
+// values, as stored in SELL-32) and its C-hat tile transposed: column j's 32
+// rows contiguous with a row stride of 32 elements plus 16 bytes, which keeps
+// the 16-byte column reads of the projection free of bank conflicts.  Two
+// stages (one when they do not fit) let the next slice stream in while the
+// current one is gathered.  y holds the slice products y_r.  After the main
+// loop the storage serves the last block's reduction.
+template <typename T, int KMAX, int R>
+struct PipeSmem {
+  static constexpr int KT = KMAX > 0 ? KMAX : 1;
+  static constexpr int PAD = 32 + 16 / (int)sizeof(T);
+  static constexpr int NE = 8;   // matrix entries per row staged
+  static constexpr size_t kStage = sizeof(T) * KT * PAD + 4 * NE * 32 + sizeof(T) * NE * 32;
+  static constexpr int NST = (kBlock / 32) * (2 * kStage + sizeof(T) * R * 32) <= 190 * 1024 ? 2 : 1;
+  struct Warp {
+    T tile[NST][KT][PAD];
+    int32_t col[NST][NE][32];
+    T val[NST][NE][32];
+    T y[R][32];
+  };
+  union {
+    Warp w[kBlock / 32];
+    RedT t;
+  };
+};
+
+// Issue the copies of slice sl (width w, first entry e0) into stage stg.
+template <typename T, int KMAX, int R>
+__device__ __forceinline__ void stage_slice(const IterArgs<T>& a, typename PipeSmem<T, KMAX, R>::Warp& ws, int stg,
+                                            int64_t sl, int w, int64_t e0, int k) {
+  constexpr int NE = PipeSmem<T, KMAX, R>::NE;
+  constexpr int VC = 16 / (int)sizeof(T);   // values per 16-byte chunk
+  constexpr int VPR = 32 / VC;              // chunks per 32-entry row
+  const int lane = threadIdx.x & 31;
+  const int we = w < NE ? w : NE;
+  for (int q = lane; q < we * 8; q += 32)
+    cp_async16(&ws.col[stg][q >> 3][(q & 7) * 4], a.A.col + e0 + (int64_t)(q >> 3) * kSlice + (q & 7) * 4);
+  for (int q = lane; q < we * VPR; q += 32)
+    cp_async16(&ws.val[stg][q / VPR][(q % VPR) * VC], a.A.val + e0 + (int64_t)(q / VPR) * kSlice + (q % VPR) * VC);
+  if (KMAX > 0) {
+    const int64_t base = sl * kSlice;
+    for (int q = lane; q < k * VPR; q += 32) {
+      const int j = q / VPR, c = q % VPR;
+      cp_async16(&ws.tile[stg][j][c * VC], a.Chat + (int64_t)j * a.ld + base + c * VC);
+    }
+  }
+}
+
+// L2 prefetch of slice sl (width w, first entry e0): its matrix entries
+// (columns and values, each one contiguous segment) and the 32 rows of each
+// C-hat column, one bulk prefetch per lane.
+template <typename T, int KMAX, int R>
+__device__ __forceinline__ void prefetch_slice(const IterArgs<T>& a, int64_t sl, int w, int64_t e0, int k) {
+  const int lane = threadIdx.x & 31;
+  const int kk = KMAX > 0 ? k : 0;
+  for (int q = lane; q < kk + 2; q += 32) {
+    if (q < kk) prefetch_l2(a.Chat + (int64_t)q * a.ld + sl * kSlice, 32 * sizeof(T));
+    else if (w > 0 && q == kk) prefetch_l2(a.A.col + e0, (unsigned)w * kSlice * 4);
+    else if (w > 0) prefetch_l2(a.A.val + e0, (unsigned)w * kSlice * sizeof(T));
+  }
+}
+
+// R right-hand sides (or FP32 data), one slice per step: y_r = A v_r stored
+// to out_r.  Per RHS r the block values live at sm.w[.][r*nvr + ...]:
+// RTQ -> slot 0 = (r~0, y_r), projections -> slots OFF + j = Chat_j^T y_r,
+// DOTS (k = 0) -> slots 0..3 = (s,t), (t,t), (r~0,t), (r~0,s) with s = v_r.
+// Software pipeline per warp: while slice i is gathered and projected, the
+// matrix entries and C-hat tile of slice i + 1 stream into the other stage
+// (cp.async), those of slice i + 2 are prefetched into L2, and the width /
+// start of slice i + 3 are loaded.  Lane j owns
+// column j of the projection (no cross-lane reduction); each slice's 32
+// products are summed in T and the total is carried across slices in the
+// accumulator (Dot2 for FP32).
+template <typename T, int KMAX, int R, bool RTQ, bool DOTS, int NVT>
+__device__ __forceinline__ void spmv_multi(const IterArgs<T>& a, const T* const* v, T* const* out,
+                                           const bool (&act)[R], int k, int nvr, ReduceCore<NVT>& sm,
+                                           PipeSmem<T, KMAX, R>& ps) {
+  using PS = PipeSmem<T, KMAX, R>;
+  constexpr int NE = PS::NE;
+  constexpr int NST = PS::NST;
+  constexpr int CPL = KMAX > 0 ? (KMAX + 31) / 32 : 1;
+  constexpr int OFF = RTQ ? 1 : 0;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t w0 = gtid() >> 5, nw = gstride() >> 5;
-  const float* __restrict__ rt0 = a.rt0;
-  const float* __restrict__ col = a.Chat + (int64_t)(lane < k ? lane : 0) * a.ld;
   const int64_t ns = a.A.nslices;
-  Acc<float> accr, accc;
-  for (int64_t sl = w0; sl < ns; sl += 2 * nw) {
-    const int64_t sl1 = (sl + nw < ns) ? sl + nw : -1;
-    float y[2];
-    sell_rows2<float>(a.A, sl, sl1, lane, v, y[0], y[1]);
+  const int32_t* __restrict__ colp = a.A.col;
+  const T* __restrict__ valp = a.A.val;
+  typename PS::Warp& ws = ps.w[warp];
+  Acc<T> accr[R], accd[R][4], accp[R][CPL];
+  // slice metadata: current (wc, ec), next (wn, en), the one after (wn2, en2)
+  int wc = 0, wn = 0, wn2 = 0;
+  int64_t ec = 0, en = 0, en2 = 0;
+  if (w0 < ns) {
+    wc = __ldg(a.A.width + w0);
+    ec = __ldg(a.A.slice_ptr + w0);
+    stage_slice<T, KMAX, R>(a, ws, 0, w0, wc, ec, k);
+  }
+  cp_async_commit();
+  if (w0 + nw < ns) {
+    wn = __ldg(a.A.width + w0 + nw);
+    en = __ldg(a.A.slice_ptr + w0 + nw);
+  }
+  if (w0 + 2 * nw < ns) {
+    wn2 = __ldg(a.A.width + w0 + 2 * nw);
+    en2 = __ldg(a.A.slice_ptr + w0 + 2 * nw);
+  }
+  int stg = 0;
+  for (int64_t sl = w0; sl < ns; sl += nw) {
+    const int64_t nx = sl + nw, nx2 = sl + 2 * nw, nx3 = sl + 3 * nw;
+    int wn3 = 0;
+    int64_t en3 = 0;
+    if (nx3 < ns) {
+      wn3 = __ldg(a.A.width + nx3);
+      en3 = __ldg(a.A.slice_ptr + nx3);
+    }
+    if (nx2 < ns) prefetch_slice<T, KMAX, R>(a, nx2, wn2, en2, k);
+    const int64_t row = sl * kSlice + lane;
+    const T rv = (RTQ || DOTS) ? __ldg(a.rt0 + row) : T(0);
+    if (NST == 2) {
+      __syncwarp();   // every lane is done with the stage about to be refilled
+      if (nx < ns) stage_slice<T, KMAX, R>(a, ws, stg ^ 1, nx, wn, en, k);
+      cp_async_commit();
+      cp_async_wait<1>();   // this thread's copies of the current stage landed
+    } else {
+      cp_async_wait<0>();
+    }
+    __syncwarp();   // ... and every lane's
+    T y[R];
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      if (h == 1 && sl1 < 0) break;
-      const int64_t base = (h == 0 ? sl : sl1) * kSlice;
-      out[base + lane] = y[h];
-      if (RTQ) accr.add(__ldg(rt0 + base + lane), y[h]);
-      float4 cv[8];
-      if (lane < k) {
-        const float4* cp = reinterpret_cast<const float4*>(col + base);
+    for (int r = 0; r < R; ++r) y[r] = T(0);
 #pragma unroll
-        for (int u = 0; u < 8; ++u) cv[u] = __ldg(cp + u);
+    for (int u = 0; u < NE; ++u) {
+      if (u < wc) {
+        const int c = ws.col[stg][u][lane];
+        const T av = ws.val[stg][u][lane];
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+          if (act[r]) y[r] = fma_t(av, __ldg(v[r] + c), y[r]);
       }
+    }
+    for (int j = NE; j < wc; ++j) {   // rows wider than NE entries
+      const int64_t e = ec + (int64_t)j * kSlice + lane;
+      const int cc = __ldg(colp + e);
+      const T vv = __ldg(valp + e);
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        const float y0 = __shfl_sync(0xffffffffu, y[h], 4 * u);
-        const float y1 = __shfl_sync(0xffffffffu, y[h], 4 * u + 1);
-        const float y2 = __shfl_sync(0xffffffffu, y[h], 4 * u + 2);
-        const float y3 = __shfl_sync(0xffffffffu, y[h], 4 * u + 3);
-        if (lane < k) {
-          accc.add(cv[u].x, y0);
-          accc.add(cv[u].y, y1);
-          accc.add(cv[u].z, y2);
-          accc.add(cv[u].w, y3);
+      for (int r = 0; r < R; ++r)
+        if (act[r]) y[r] = fma_t(vv, __ldg(v[r] + cc), y[r]);
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      if (!act[r]) continue;
+      out[r][row] = y[r];
+      if (RTQ) accr[r].add(rv, y[r]);
+      if (DOTS) {
+        const T sv = __ldg(v[r] + row);
+        accd[r][0].add(sv, y[r]);
+        accd[r][1].add(y[r], y[r]);
+        accd[r][2].add(rv, y[r]);
+        accd[r][3].add(rv, sv);
+      }
+    }
+    if (KMAX > 0) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) ws.y[r][lane] = act[r] ? y[r] : T(0);
+      __syncwarp();
+#pragma unroll
+      for (int cc = 0; cc < CPL; ++cc) {
+        const int j = lane + 32 * cc;
+        if (j < k) {
+          T part[R];
+#pragma unroll
+          for (int r = 0; r < R; ++r) part[r] = T(0);
+          col_dot<R>(ws.tile[stg][j], ws.y, act, part);
+#pragma unroll
+          for (int r = 0; r < R; ++r)
+            if (act[r]) accp[r][cc].add1(part[r]);
         }
       }
     }
-  }
-  constexpr int OFF = RTQ ? 1 : 0;
-  if (RTQ) {
-    Acc<float> r1[1] = {accr};
-    float hi = r1[0].hi, lo = r1[0].lo;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const float h2 = __shfl_down_sync(0xffffffffu, hi, o);
-      const float l2 = __shfl_down_sync(0xffffffffu, lo, o);
-      const float s = __fadd_rn(hi, h2);
-      const float bb = __fsub_rn(s, hi);
-      const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(h2, bb));
-      hi = s;
-      lo = __fadd_rn(__fadd_rn(lo, l2), e);
+    if (NST == 1) {
+      __syncwarp();   // the single stage is refilled for the next slice
+      if (nx < ns) stage_slice<T, KMAX, R>(a, ws, 0, nx, wn, en, k);
+      cp_async_commit();
+    } else {
+      stg ^= 1;
     }
-    if (lane == 0) sm.w[warp][0] = (double)hi + (double)lo;
+    wc = wn;
+    ec = en;
+    wn = wn2;
+    en = en2;
+    wn2 = wn3;
+    en2 = en3;
   }
-  if (lane < k) sm.w[warp][OFF + lane] = accc.get();
+  cp_async_wait<0>();
+  // warp sums into sm.w (inactive right-hand sides contribute zeros)
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    if (RTQ) {
+      if (act[r]) warp_slot(accr[r], r * nvr, sm);
+      else zero_slot(r * nvr, sm);
+    }
+    if (DOTS) {
+#pragma unroll
+      for (int d = 0; d < 4; ++d) {
+        if (act[r]) warp_slot(accd[r][d], r * nvr + d, sm);
+        else zero_slot(r * nvr + d, sm);
+      }
+    }
+    if (KMAX > 0) {
+#pragma unroll
+      for (int cc = 0; cc < CPL; ++cc) {
+        const int j = lane + 32 * cc;
+        if (j < k) sm.w[warp][r * nvr + OFF + j] = act[r] ? accp[r][cc].get() : 0.0;
+      }
+    }
+  }
+  __syncthreads();   // the staging storage is reused by the reduction
 }
 
-template <typename T, int KMAX>
-__global__ void __launch_bounds__(kBlock) k_p1(IterArgs<T> a) {
+// Dynamic shared memory of P1 / P3: the staging of the pipelined path.
+template <typename T, int KMAX, int R>
+struct P13Smem {
+  static constexpr bool multi = ColProj<T, KMAX, R>::value || R > 1 || KMAX == 0;
+  static constexpr size_t bytes = multi ? sizeof(PipeSmem<T, KMAX, R>) : 0;
+};
+
+template <typename T, int KMAX, int R>
+__global__ void __launch_bounds__(kBlock, 2) k_p1(IterArgs<T> a) {
   IterState* st = a.st;
-  if (st->done) return;
-  constexpr int NV = KMAX + 1;
-  __shared__ ReduceSmem<NV> sm;
-  const int k = KMAX > 0 ? st->k : 0;
+  bool act[R];
+  bool any = false;
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    act[r] = (r < a.nrhs) && !st[r].done;
+    any |= act[r];
+  }
+  if (!any) return;
+  constexpr int NVR = KMAX + 1;
+  const int k = KMAX > 0 ? st[0].k : 0;
+  const int nvr = 1 + k;
   bool last;
-  if constexpr (std::is_same<T, float>::value && KMAX > 0 && KMAX <= 32) {
-    spmv_project_f32<KMAX, true>(a, a.p_in, a.qraw, k, sm);
-    last = grid_finish<NV>(1 + k, sm, a.partials, &st->ticket[P1]);
+  double* res;
+  if constexpr (!P13Smem<T, KMAX, R>::multi) {
+    __shared__ ReduceSmem<NVR> sm;
+    Acc<T> acc[NVR];
+    spmv_project<T, KMAX, true>(a, a.p_in[0], a.qraw[0], acc, k);
+    last = block_reduce_last<T, NVR>(acc, nvr, sm, a.partials, &st[0].ticket[P1]);
+    res = sm.res;
   } else {
-    Acc<T> acc[NV];
-    spmv_project<T, KMAX, true, false>(a, a.p_in, a.qraw, acc, k);
-    last = block_reduce_last<T, NV>(acc, 1 + k, sm, a.partials, &st->ticket[P1]);
+    __shared__ ReduceCore<R * NVR> sm;
+    extern __shared__ __align__(16) unsigned char dsm[];
+    auto& ps = *reinterpret_cast<PipeSmem<T, KMAX, R>*>(dsm);
+    spmv_multi<T, KMAX, R, true, false, R * NVR>(a, a.p_in, a.qraw, act, k, nvr, sm, ps);
+    last = grid_finish<R * NVR>(R * nvr, sm, ps.t, a.partials, &st[0].ticket[P1]);
+    res = sm.res;
   }
-  if (last && threadIdx.x == 0) finish_p1(st, sm.res, k);
+  if (last && threadIdx.x == 0) {
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+      if (act[r]) finish_p1(&st[r], res + r * nvr, k);
+  }
 }
 
-template <typename T, int KMAX>
-__global__ void __launch_bounds__(kBlock) k_p3(IterArgs<T> a) {
+template <typename T, int KMAX, int R>
+__global__ void __launch_bounds__(kBlock, 2) k_p3(IterArgs<T> a) {
   IterState* st = a.st;
-  if (st->done || st->half) return;
+  bool act[R];
+  bool any = false;
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    act[r] = (r < a.nrhs) && !st[r].done && !st[r].half;
+    any |= act[r];
+  }
+  if (!any) return;
   constexpr bool DOTS = (KMAX == 0);
-  constexpr int NV = DOTS ? 4 : KMAX;
-  const int k = KMAX > 0 ? st->k : 0;
+  constexpr int NVR = DOTS ? 4 : KMAX;
+  const int k = KMAX > 0 ? st[0].k : 0;
+  const int nvr = DOTS ? 4 : k;
   bool last;
-  if constexpr (std::is_same<T, float>::value && KMAX > 0 && KMAX <= 32) {
-    __shared__ ReduceSmem<KMAX + 1> sm;
-    spmv_project_f32<KMAX, false>(a, a.s, a.traw, k, sm);
-    last = grid_finish<KMAX + 1>(k, sm, a.partials, &st->ticket[P3]);
-    if (last && threadIdx.x == 0) finish_p3(st, sm.res, k);
+  double* res;
+  if constexpr (!P13Smem<T, KMAX, R>::multi) {
+    __shared__ ReduceSmem<NVR> sm;
+    Acc<T> acc[NVR];
+    spmv_project<T, KMAX, false>(a, a.s[0], a.traw[0], acc, k);
+    last = block_reduce_last<T, NVR>(acc, nvr, sm, a.partials, &st[0].ticket[P3]);
+    res = sm.res;
   } else {
-    __shared__ ReduceSmem<NV> sm;
-    Acc<T> acc[NV];
-    spmv_project<T, KMAX, false, DOTS>(a, a.s, a.traw, acc, k);
-    last = block_reduce_last<T, NV>(acc, DOTS ? 4 : k, sm, a.partials, &st->ticket[P3]);
-    if (last && threadIdx.x == 0) {
-      if (DOTS) finish_p4(st, sm.res, 0);
-      else finish_p3(st, sm.res, k);
+    __shared__ ReduceCore<R * NVR> sm;
+    extern __shared__ __align__(16) unsigned char dsm[];
+    auto& ps = *reinterpret_cast<PipeSmem<T, KMAX, R>*>(dsm);
+    spmv_multi<T, KMAX, R, false, DOTS, R * NVR>(a, a.s, a.traw, act, k, nvr, sm, ps);
+    last = grid_finish<R * NVR>(R * nvr, sm, ps.t, a.partials, &st[0].ticket[P3]);
+    res = sm.res;
+  }
+  if (last && threadIdx.x == 0) {
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      if (!act[r]) continue;
+      if (DOTS) finish_p4(&st[r], res + r * nvr, 0);
+      else finish_p3(&st[r], res + r * nvr, k);
     }
   }
 }
 
-// y_i - sum_j M[j*ld + i] c_j for two rows at once.  Loads are issued in
-// batches of 8 columns (16 loads in flight per thread) before their FMAs.
-template <typename T, int KMAX>
-__device__ __forceinline__ void correct2(const T* __restrict__ M, int64_t ld, const T* c, int k,
-                                         int64_t i0, int64_t i1, bool two, T& y0, T& y1) {
-  constexpr int B = 8;
-  T a0 = T(0), a1 = T(0);
+// L2 prefetch, by one warp, of rows [row0, row0 + nrows) of the first ncols
+// columns of the column-major block M (leading dimension ld) and of the
+// vectors vs[0..nvs): one bulk prefetch per lane and segment.
+template <typename T>
+__device__ __forceinline__ void prefetch_rows(const T* M, int64_t ld, int ncols, const T* const* vs, int nvs,
+                                              int64_t row0, int nrows) {
+  const int lane = threadIdx.x & 31;
+  const unsigned bytes = (unsigned)nrows * sizeof(T);
+  for (int q = lane; q < ncols + nvs; q += 32) {
+    const T* p = q < ncols ? M + (int64_t)q * ld + row0 : vs[q - ncols] + row0;
+    prefetch_l2(p, bytes);
+  }
+}
+
+// ---------------------------------------------------------------- streaming passes
+// P2, P4 and P5 stream n-vectors and the n x k block C.  With one RHS each
+// thread takes VW consecutive rows per step (one 16-byte vector of each
+// stream), the C columns of a step are loaded up front (predicated, no
+// branches) so that they are all in flight together, and the warp's rows two
+// steps ahead are prefetched into L2.  A block of several RHS already has
+// R times the streams in flight per row: one row per thread.
+template <typename T, int W>
+struct Pack;
+template <typename T>
+struct Pack<T, 1> {
+  using type = T;
+};
+template <>
+struct Pack<float, 4> {
+  using type = float4;
+};
+template <>
+struct Pack<double, 2> {
+  using type = double2;
+};
+
+template <typename T, int R>
+struct StreamVW {
+  static constexpr int value = R == 1 ? Vec<T>::W : 1;
+};
+
+template <typename T, int W>
+__device__ __forceinline__ typename Pack<T, W>::type ldv(const T* p) {
+  return __ldg(reinterpret_cast<const typename Pack<T, W>::type*>(p));
+}
+template <typename T, int W>
+__device__ __forceinline__ typename Pack<T, W>::type ldv_coherent(const T* p) {
+  return *reinterpret_cast<const typename Pack<T, W>::type*>(p);
+}
+template <typename T, int W>
+__device__ __forceinline__ void stv(T* p, const T (&v)[W]) {
+  typename Pack<T, W>::type x;
+  T* xs = reinterpret_cast<T*>(&x);
 #pragma unroll
-  for (int j0 = 0; j0 < KMAX; j0 += B) {
-    if (j0 < k) {
-      T m0[B], m1[B];
+  for (int e = 0; e < W; ++e) xs[e] = v[e];
+  *reinterpret_cast<typename Pack<T, W>::type*>(p) = x;
+}
+template <typename T, int W>
+__device__ __forceinline__ void unpack(const typename Pack<T, W>::type& x, T (&v)[W]) {
+  const T* xs = reinterpret_cast<const T*>(&x);
 #pragma unroll
-      for (int u = 0; u < B; ++u) {
-        const bool ok = (j0 + u < KMAX) && (j0 + u < k);
-        m0[u] = ok ? __ldg(M + (j0 + u) * ld + i0) : T(0);
-        m1[u] = (ok && two) ? __ldg(M + (j0 + u) * ld + i1) : T(0);
-      }
+  for (int e = 0; e < W; ++e) v[e] = xs[e];
+}
+
+// corr[r][e] = sum_{j < KMAX} C[j*ld + i + e] cs[r][j] for the VW rows at i
+// (cs zero beyond k, so the predicated-off columns add nothing).  Columns go
+// in chunks (24 vectors for one RHS, fewer for several, whose loaded vectors
+// and accumulators need the registers), each chunk's loads issued together.
+template <typename T, int KMAX, int R, int W>
+__device__ __forceinline__ void correct_vec(const T* __restrict__ C, int64_t ld, int k, int64_t i,
+                                            const T (*cs)[KMAX > 0 ? KMAX : 1], const bool (&act)[R],
+                                            T (&corr)[R][W]) {
+  constexpr int CHR = W > 1 ? 24 : (KMAX > 0 ? KMAX : 1);
+  constexpr int CH = KMAX < CHR ? (KMAX > 0 ? KMAX : 1) : CHR;
+  using V = typename Pack<T, W>::type;
 #pragma unroll
-      for (int u = 0; u < B; ++u) {
-        if (j0 + u < KMAX) {
-          const T cu = (j0 + u < k) ? c[j0 + u] : T(0);
-          a0 = fma_t(m0[u], cu, a0);
-          a1 = fma_t(m1[u], cu, a1);
-        }
+  for (int r = 0; r < R; ++r)
+#pragma unroll
+    for (int e = 0; e < W; ++e) corr[r][e] = T(0);
+#pragma unroll
+  for (int j0 = 0; j0 < KMAX; j0 += CH) {
+    V m[CH];
+#pragma unroll
+    for (int u = 0; u < CH; ++u) {
+      const int j = j0 + u;
+      if (j < KMAX && j < k) m[u] = ldv<T, W>(C + (int64_t)j * ld + i);
+      else m[u] = V{};
+    }
+#pragma unroll
+    for (int u = 0; u < CH; ++u) {
+      const int j = j0 + u;
+      if (j >= KMAX) break;
+      T mv[W];
+      unpack<T, W>(m[u], mv);
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        if (!act[r]) continue;
+        const T z = cs[r][j];
+#pragma unroll
+        for (int e = 0; e < W; ++e) corr[r][e] = fma_t(mv[e], z, corr[r][e]);
       }
     }
   }
-  y0 -= a0;
-  y1 -= a1;
 }
 
 // ---------------------------------------------------------------- P2
-template <typename T, int KMAX>
-__global__ void __launch_bounds__(kBlock) k_p2(IterArgs<T> a) {
+template <typename T, int KMAX, int R>
+__global__ void __launch_bounds__(kBlock, 2) k_p2(IterArgs<T> a) {
   IterState* st = a.st;
-  if (st->done) return;
-  __shared__ ReduceSmem<1> sm;
-  __shared__ T zs[KMAX > 0 ? KMAX : 1];
-  const int k = KMAX > 0 ? st->k : 0;
-  if (KMAX > 0 && threadIdx.x < k) zs[threadIdx.x] = (T)st->zeta[threadIdx.x];
-  const T al = (T)st->alpha;
+  bool act[R];
+  bool any = false;
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    act[r] = (r < a.nrhs) && !st[r].done;
+    any |= act[r];
+  }
+  if (!any) return;
+  constexpr int KK = KMAX > 0 ? KMAX : 1;
+  constexpr int W = StreamVW<T, R>::value;
+  using V = typename Pack<T, W>::type;
+  __shared__ ReduceSmem<R> sm;
+  __shared__ __align__(16) T zs[R][KK];
+  __shared__ const T* pvs[2 * R];
+  __shared__ int npvs;
+  if (threadIdx.x == 0) {
+    int n = 0;
+    for (int r = 0; r < R; ++r)
+      if (act[r]) {
+        pvs[n++] = a.qraw[r];
+        pvs[n++] = a.r[r];
+      }
+    npvs = n;
+  }
+  const int k = KMAX > 0 ? st[0].k : 0;
+  for (int e = threadIdx.x; e < R * KK; e += blockDim.x) {
+    const int r = e / KK, j = e % KK;
+    zs[r][j] = (act[r] && j < k) ? (T)st[r].zeta[j] : T(0);
+  }
+  T al[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) al[r] = (T)st[r].alpha;
   __syncthreads();
-  const T* __restrict__ qraw = a.qraw;
-  const T* __restrict__ r = a.r;
-  T* __restrict__ q = a.q;
-  T* __restrict__ s = a.s;
-  const int64_t npad = a.npad, stride = gstride();
-  Acc<T> acc[1];
-  for (int64_t i = gtid(); i < npad; i += 2 * stride) {
-    const int64_t i1 = i + stride;
-    const bool two = i1 < npad;
-    T q0 = qraw[i], q1 = two ? qraw[i1] : T(0);
-    const T r0 = r[i], r1 = two ? r[i1] : T(0);
-    if (KMAX > 0) {
-      correct2<T, KMAX>(a.C, a.ld, zs, k, i, i1, two, q0, q1);
-      q[i] = q0;
-      if (two) q[i1] = q1;
+  const int npv = npvs;
+  const int64_t npad = a.npad, nvec = npad / W, stride = gstride(), ld = a.ld;
+  const int lane = threadIdx.x & 31;
+  Acc<T> acc[R];
+  for (int64_t i0 = gtid(); i0 < nvec; i0 += stride) {
+    const int64_t i = i0 * W;
+    if (W > 1) {   // the warp's rows two steps ahead go to L2
+      const int64_t row0 = (i0 - lane + 2 * stride) * W;
+      if (row0 < npad)
+        prefetch_rows<T>(a.C, ld, KMAX > 0 ? k : 0, pvs, npv, row0, (int)(npad - row0 < 32 * W ? npad - row0 : 32 * W));
     }
-    const T s0 = r0 - al * q0;
-    s[i] = s0;
-    acc[0].add(s0, s0);
-    if (two) {
-      const T s1 = r1 - al * q1;
-      s[i1] = s1;
-      acc[0].add(s1, s1);
+    V qr[R], rr[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      qr[r] = act[r] ? ldv<T, W>(a.qraw[r] + i) : V{};
+      rr[r] = act[r] ? ldv<T, W>(a.r[r] + i) : V{};
+    }
+    T corr[R][W];
+    if (KMAX > 0) correct_vec<T, KMAX, R, W>(a.C, ld, k, i, zs, act, corr);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      if (!act[r]) continue;
+      T q[W], rv[W], sv[W];
+      unpack<T, W>(qr[r], q);
+      unpack<T, W>(rr[r], rv);
+#pragma unroll
+      for (int e = 0; e < W; ++e) {
+        if (KMAX > 0) q[e] -= corr[r][e];
+        sv[e] = rv[e] - al[r] * q[e];
+        acc[r].add(sv[e], sv[e]);
+      }
+      if (KMAX > 0) stv<T, W>(a.q[r] + i, q);
+      stv<T, W>(a.s[r] + i, sv);
     }
   }
-  if (block_reduce_last<T, 1>(acc, 1, sm, a.partials, &st->ticket[P2]) && threadIdx.x == 0)
-    finish_p2(st, sm.res);
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    if (act[r]) warp_slot(acc[r], r, sm);
+    else zero_slot(r, sm);
+  }
+  if (grid_finish<R>(R, sm, a.partials, &st[0].ticket[P2]) && threadIdx.x == 0) {
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+      if (act[r]) finish_p2(&st[r], sm.res + r);
+  }
 }
 
 // ---------------------------------------------------------------- P4 (k > 0)
-template <typename T, int KMAX>
-__global__ void __launch_bounds__(kBlock) k_p4(IterArgs<T> a) {
+template <typename T, int KMAX, int R>
+__global__ void __launch_bounds__(kBlock, 2) k_p4(IterArgs<T> a) {
   IterState* st = a.st;
-  if (st->done || st->half) return;
-  __shared__ ReduceSmem<4> sm;
-  __shared__ T gs[KMAX];
-  const int k = st->k;
-  if (threadIdx.x < k) gs[threadIdx.x] = (T)st->gamma[threadIdx.x];
-  __syncthreads();
-  const T* __restrict__ traw = a.traw;
-  const T* __restrict__ s = a.s;
-  const T* __restrict__ rt0 = a.rt0;
-  T* __restrict__ t = a.t;
-  const int64_t npad = a.npad, stride = gstride();
-  Acc<T> acc[4];
-  for (int64_t i = gtid(); i < npad; i += 2 * stride) {
-    const int64_t i1 = i + stride;
-    const bool two = i1 < npad;
-    T t0 = traw[i], t1 = two ? traw[i1] : T(0);
-    const T s0 = s[i], s1 = two ? s[i1] : T(0);
-    const T r0 = __ldg(rt0 + i), r1 = two ? __ldg(rt0 + i1) : T(0);
-    correct2<T, KMAX>(a.C, a.ld, gs, k, i, i1, two, t0, t1);
-    t[i] = t0;
-    if (two) t[i1] = t1;
+  bool act[R];
+  bool any = false;
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      if (h == 1 && !two) break;
-      const T td = h ? t1 : t0, sv = h ? s1 : s0, rv = h ? r1 : r0;
-      acc[0].add(sv, td);
-      acc[1].add(td, td);
-      acc[2].add(rv, td);
-      acc[3].add(rv, sv);
+  for (int r = 0; r < R; ++r) {
+    act[r] = (r < a.nrhs) && !st[r].done && !st[r].half;
+    any |= act[r];
+  }
+  if (!any) return;
+  constexpr int W = StreamVW<T, R>::value;
+  using V = typename Pack<T, W>::type;
+  __shared__ ReduceSmem<4 * R> sm;
+  __shared__ __align__(16) T gs[R][KMAX];
+  __shared__ const T* pvs[2 * R + 1];
+  __shared__ int npvs;
+  if (threadIdx.x == 0) {
+    int n = 0;
+    pvs[n++] = a.rt0;
+    for (int r = 0; r < R; ++r)
+      if (act[r]) {
+        pvs[n++] = a.traw[r];
+        pvs[n++] = a.s[r];
+      }
+    npvs = n;
+  }
+  const int k = st[0].k;
+  for (int e = threadIdx.x; e < R * KMAX; e += blockDim.x) {
+    const int r = e / KMAX, j = e % KMAX;
+    gs[r][j] = (act[r] && j < k) ? (T)st[r].gamma[j] : T(0);
+  }
+  __syncthreads();
+  const int npv = npvs;
+  const T* __restrict__ rt0 = a.rt0;
+  const int64_t npad = a.npad, nvec = npad / W, stride = gstride(), ld = a.ld;
+  const int lane = threadIdx.x & 31;
+  Acc<T> acc[R][4];
+  for (int64_t i0 = gtid(); i0 < nvec; i0 += stride) {
+    const int64_t i = i0 * W;
+    if (W > 1) {
+      const int64_t row0 = (i0 - lane + 2 * stride) * W;
+      if (row0 < npad) prefetch_rows<T>(a.C, ld, k, pvs, npv, row0, (int)(npad - row0 < 32 * W ? npad - row0 : 32 * W));
+    }
+    V tr[R], sr[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      tr[r] = act[r] ? ldv<T, W>(a.traw[r] + i) : V{};
+      sr[r] = act[r] ? ldv<T, W>(a.s[r] + i) : V{};
+    }
+    T rv[W];
+    unpack<T, W>(ldv<T, W>(rt0 + i), rv);
+    T corr[R][W];
+    correct_vec<T, KMAX, R, W>(a.C, ld, k, i, gs, act, corr);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      if (!act[r]) continue;
+      T t[W], sv[W];
+      unpack<T, W>(tr[r], t);
+      unpack<T, W>(sr[r], sv);
+#pragma unroll
+      for (int e = 0; e < W; ++e) {
+        t[e] -= corr[r][e];
+        acc[r][0].add(sv[e], t[e]);
+        acc[r][1].add(t[e], t[e]);
+        acc[r][2].add(rv[e], t[e]);
+        acc[r][3].add(rv[e], sv[e]);
+      }
+      stv<T, W>(a.t[r] + i, t);
     }
   }
-  if (block_reduce_last<T, 4>(acc, 4, sm, a.partials, &st->ticket[P4]) && threadIdx.x == 0)
-    finish_p4(st, sm.res, k);
+#pragma unroll
+  for (int r = 0; r < R; ++r)
+#pragma unroll
+    for (int d = 0; d < 4; ++d) {
+      if (act[r]) warp_slot(acc[r][d], 4 * r + d, sm);
+      else zero_slot(4 * r + d, sm);
+    }
+  if (grid_finish<4 * R>(4 * R, sm, a.partials, &st[0].ticket[P4]) && threadIdx.x == 0) {
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+      if (act[r]) finish_p4(&st[r], sm.res + 4 * r, k);
+  }
 }
 
 // ---------------------------------------------------------------- P5
-template <typename T, int KMAX>
-__global__ void __launch_bounds__(kBlock) k_p5(IterArgs<T> a) {
+template <typename T, int KMAX, int R>
+__global__ void __launch_bounds__(kBlock, 3) k_p5(IterArgs<T> a) {
   IterState* st = a.st;
-  if (st->done) return;
-  __shared__ ReduceSmem<1> sm;
-  const int k = KMAX > 0 ? st->k : 0;
-  Acc<T> acc[1];
-  T* __restrict__ x = a.x;
-  T* __restrict__ r = a.r;
-  const T* __restrict__ p = a.p_in;
-  const T* __restrict__ s = a.s;
-  const int64_t npad = a.npad, stride = gstride();
-  if (st->half) {
-    const T al = (T)st->alpha;
-    for (int64_t i = gtid(); i < npad; i += stride) {
-      x[i] = fma_t(al, p[i], x[i]);
-      r[i] = s[i];
+  bool act[R], half[R];
+  bool any = false;
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    act[r] = (r < a.nrhs) && !st[r].done;
+    half[r] = act[r] && st[r].half;
+    any |= act[r];
+  }
+  if (!any) return;
+  constexpr int W = StreamVW<T, R>::value;
+  using V = typename Pack<T, W>::type;
+  __shared__ ReduceSmem<R> sm;
+  // vectors read by this pass (x and p are also written here, so they use
+  // coherent loads; s, t, q use the read-only path)
+  __shared__ const T* pvs[5 * R];
+  __shared__ int npvs;
+  if (threadIdx.x == 0) {
+    int n = 0;
+    for (int r = 0; r < R; ++r)
+      if (act[r]) {
+        pvs[n++] = a.p_in[r];
+        pvs[n++] = a.s[r];
+        pvs[n++] = a.x[r];
+        if (!half[r]) {
+          pvs[n++] = a.t[r];
+          pvs[n++] = a.q[r];
+        }
+      }
+    npvs = n;
+  }
+  __syncthreads();
+  const int npv = npvs;
+  const int k = KMAX > 0 ? st[0].k : 0;
+  T al[R], om[R], be[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    al[r] = (T)st[r].alpha;
+    om[r] = (T)st[r].omega;
+    be[r] = (T)st[r].beta;
+  }
+  const int64_t npad = a.npad, nvec = npad / W, stride = gstride();
+  const int lane = threadIdx.x & 31;
+  Acc<T> acc[R];
+  for (int64_t i0 = gtid(); i0 < nvec; i0 += stride) {
+    const int64_t i = i0 * W;
+    {
+      const int64_t row0 = (i0 - lane + 2 * stride) * W;
+      if (row0 < npad)
+        prefetch_rows<T>(nullptr, 0, 0, pvs, npv, row0, (int)(npad - row0 < 32 * W ? npad - row0 : 32 * W));
     }
-  } else {
-    const T al = (T)st->alpha, om = (T)st->omega, be = (T)st->beta;
-    const T* __restrict__ t = a.t;
-    const T* __restrict__ q = a.q;
-    T* __restrict__ po = a.p_out;
-    for (int64_t i = gtid(); i < npad; i += 2 * stride) {
-      const int64_t i1 = i + stride;
-      const bool two = i1 < npad;
-      const T p0 = p[i], s0 = s[i], t0 = t[i], q0 = q[i], x0 = x[i];
-      T p1 = T(0), s1 = T(0), t1 = T(0), q1 = T(0), x1 = T(0);
-      if (two) {
-        p1 = p[i1]; s1 = s[i1]; t1 = t[i1]; q1 = q[i1]; x1 = x[i1];
+    V P[R], S[R], X[R], Tt[R], Q[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      P[r] = act[r] ? ldv_coherent<T, W>(a.p_in[r] + i) : V{};
+      S[r] = act[r] ? ldv<T, W>(a.s[r] + i) : V{};
+      X[r] = act[r] ? ldv_coherent<T, W>(a.x[r] + i) : V{};
+      Tt[r] = (act[r] && !half[r]) ? ldv<T, W>(a.t[r] + i) : V{};
+      Q[r] = (act[r] && !half[r]) ? ldv<T, W>(a.q[r] + i) : V{};
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      if (!act[r]) continue;
+      T p[W], s_[W], x[W], t[W], q[W];
+      unpack<T, W>(P[r], p);
+      unpack<T, W>(S[r], s_);
+      unpack<T, W>(X[r], x);
+      unpack<T, W>(Tt[r], t);
+      unpack<T, W>(Q[r], q);
+      if (half[r]) {
+#pragma unroll
+        for (int e = 0; e < W; ++e) x[e] = fma_t(al[r], p[e], x[e]);
+        stv<T, W>(a.x[r] + i, x);
+        stv<T, W>(a.r[r] + i, s_);
+        continue;
       }
-      const T r0 = s0 - om * t0;
-      x[i] = fma_t(om, s0, fma_t(al, p0, x0));
-      r[i] = r0;
-      po[i] = fma_t(be, p0 - om * q0, r0);
-      acc[0].add(r0, r0);
-      if (two) {
-        const T r1 = s1 - om * t1;
-        x[i1] = fma_t(om, s1, fma_t(al, p1, x1));
-        r[i1] = r1;
-        po[i1] = fma_t(be, p1 - om * q1, r1);
-        acc[0].add(r1, r1);
+      T rr[W], pn[W];
+#pragma unroll
+      for (int e = 0; e < W; ++e) {
+        rr[e] = s_[e] - om[r] * t[e];
+        x[e] = fma_t(om[r], s_[e], fma_t(al[r], p[e], x[e]));
+        pn[e] = fma_t(be[r], p[e] - om[r] * q[e], rr[e]);
+        acc[r].add(rr[e], rr[e]);
       }
+      stv<T, W>(a.x[r] + i, x);
+      stv<T, W>(a.r[r] + i, rr);
+      stv<T, W>(a.p_out[r] + i, pn);
     }
   }
-  if (block_reduce_last<T, 1>(acc, 1, sm, a.partials, &st->ticket[P5]) && threadIdx.x == 0)
-    finish_p5(st, sm.res, k);
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    if (act[r]) warp_slot(acc[r], r, sm);
+    else zero_slot(r, sm);
+  }
+  if (grid_finish<R>(R, sm, a.partials, &st[0].ticket[P5]) && threadIdx.x == 0) {
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+      if (act[r]) finish_p5(&st[r], sm.res + r, k);
+  }
 }
 
 // ---------------------------------------------------------------- launchers
-template <typename T, int KMAX>
-static cudaError_t launch_iter_k(const IterArgs<T>& a, const Grids& g, cudaStream_t s) {
-  k_p1<T, KMAX><<<g.pass[P1], kBlock, 0, s>>>(a);
-  k_p2<T, KMAX><<<g.pass[P2], kBlock, 0, s>>>(a);
-  k_p3<T, KMAX><<<g.pass[P3], kBlock, 0, s>>>(a);
-  if (KMAX > 0) k_p4<T, (KMAX > 0 ? KMAX : 1)><<<g.pass[P4], kBlock, 0, s>>>(a);
-  k_p5<T, KMAX><<<g.pass[P5], kBlock, 0, s>>>(a);
+template <typename T, int KMAX, int R>
+static cudaError_t launch_iter_kr(const IterArgs<T>& a, const Grids& g, cudaStream_t s) {
+  constexpr size_t dsm = P13Smem<T, KMAX, R>::bytes;
+  k_p1<T, KMAX, R><<<g.pass[P1], kBlock, dsm, s>>>(a);
+  k_p2<T, KMAX, R><<<g.pass[P2], kBlock, 0, s>>>(a);
+  k_p3<T, KMAX, R><<<g.pass[P3], kBlock, dsm, s>>>(a);
+  if (KMAX > 0) k_p4<T, (KMAX > 0 ? KMAX : 1), R><<<g.pass[P4], kBlock, 0, s>>>(a);
+  k_p5<T, KMAX, R><<<g.pass[P5], kBlock, 0, s>>>(a);
   return cudaGetLastError();
 }
 
-template <typename T, int KMAX>
-static cudaError_t launch_pass_k(int pass, const IterArgs<T>& a, const Grids& g, cudaStream_t s) {
+template <typename T, int KMAX, int R>
+static cudaError_t launch_pass_kr(int pass, const IterArgs<T>& a, const Grids& g, cudaStream_t s) {
+  constexpr size_t dsm = P13Smem<T, KMAX, R>::bytes;
   switch (pass) {
-    case P1: k_p1<T, KMAX><<<g.pass[P1], kBlock, 0, s>>>(a); break;
-    case P2: k_p2<T, KMAX><<<g.pass[P2], kBlock, 0, s>>>(a); break;
-    case P3: k_p3<T, KMAX><<<g.pass[P3], kBlock, 0, s>>>(a); break;
-    case P4: if (KMAX > 0) k_p4<T, (KMAX > 0 ? KMAX : 1)><<<g.pass[P4], kBlock, 0, s>>>(a); break;
-    default: k_p5<T, KMAX><<<g.pass[P5], kBlock, 0, s>>>(a); break;
+    case P1: k_p1<T, KMAX, R><<<g.pass[P1], kBlock, dsm, s>>>(a); break;
+    case P2: k_p2<T, KMAX, R><<<g.pass[P2], kBlock, 0, s>>>(a); break;
+    case P3: k_p3<T, KMAX, R><<<g.pass[P3], kBlock, dsm, s>>>(a); break;
+    case P4: if (KMAX > 0) k_p4<T, (KMAX > 0 ? KMAX : 1), R><<<g.pass[P4], kBlock, 0, s>>>(a); break;
+    default: k_p5<T, KMAX, R><<<g.pass[P5], kBlock, 0, s>>>(a); break;
   }
   return cudaGetLastError();
 }
@@ -467,31 +989,35 @@ int kmax_bucket(int k) {
   return 64;
 }
 
+int rhs_bucket(int nrhs) { return nrhs <= 1 ? 1 : (nrhs <= 2 ? 2 : 4); }
+
+// Dispatch (k bucket, RHS bucket) to a compile-time instantiation.
+#define RB_DISPATCH(KB, RB, CALL)                                   \
+  switch (KB) {                                                     \
+    case 0: { constexpr int KM = 0; RB_DISPATCH_R(RB, CALL) }        \
+    case 8: { constexpr int KM = 8; RB_DISPATCH_R(RB, CALL) }        \
+    case 16: { constexpr int KM = 16; RB_DISPATCH_R(RB, CALL) }      \
+    case 24: { constexpr int KM = 24; RB_DISPATCH_R(RB, CALL) }      \
+    case 32: { constexpr int KM = 32; RB_DISPATCH_R(RB, CALL) }      \
+    case 48: { constexpr int KM = 48; RB_DISPATCH_R(RB, CALL) }      \
+    default: { constexpr int KM = 64; RB_DISPATCH_R(RB, CALL) }      \
+  }
+#define RB_DISPATCH_R(RB, CALL)                                     \
+  switch (RB) {                                                     \
+    case 1: { constexpr int RR = 1; return CALL; }                  \
+    case 2: { constexpr int RR = 2; return CALL; }                  \
+    default: { constexpr int RR = 4; return CALL; }                 \
+  }
+
 template <typename T>
 cudaError_t launch_iteration(const IterArgs<T>& a, int k, const Grids& g, cudaStream_t s) {
-  switch (kmax_bucket(k)) {
-    case 0: return launch_iter_k<T, 0>(a, g, s);
-    case 8: return launch_iter_k<T, 8>(a, g, s);
-    case 16: return launch_iter_k<T, 16>(a, g, s);
-    case 24: return launch_iter_k<T, 24>(a, g, s);
-    case 32: return launch_iter_k<T, 32>(a, g, s);
-    case 48: return launch_iter_k<T, 48>(a, g, s);
-    default: return launch_iter_k<T, 64>(a, g, s);
-  }
+  RB_DISPATCH(kmax_bucket(k), rhs_bucket(a.nrhs), (launch_iter_kr<T, KM, RR>(a, g, s)))
 }
 
 template <typename T>
 cudaError_t launch_pass(int pass, const IterArgs<T>& a, int k, const Grids& g, cudaStream_t s) {
   count_launches(1);
-  switch (kmax_bucket(k)) {
-    case 0: return launch_pass_k<T, 0>(pass, a, g, s);
-    case 8: return launch_pass_k<T, 8>(pass, a, g, s);
-    case 16: return launch_pass_k<T, 16>(pass, a, g, s);
-    case 24: return launch_pass_k<T, 24>(pass, a, g, s);
-    case 32: return launch_pass_k<T, 32>(pass, a, g, s);
-    case 48: return launch_pass_k<T, 48>(pass, a, g, s);
-    default: return launch_pass_k<T, 64>(pass, a, g, s);
-  }
+  RB_DISPATCH(kmax_bucket(k), rhs_bucket(a.nrhs), (launch_pass_kr<T, KM, RR>(pass, a, g, s)))
 }
 
 template cudaError_t launch_pass<double>(int, const IterArgs<double>&, int, const Grids&, cudaStream_t);
@@ -502,39 +1028,48 @@ template cudaError_t launch_iteration<float>(const IterArgs<float>&, int, const 
 // Grid sizes: one full wave of resident blocks per kernel configuration (a
 // second partial wave would leave SMs idle at the end of every pass), capped
 // by the work.
-template <typename T>
-static int occ(const void* f, int nsm) {
+static int occ(const void* f, int nsm, size_t dsm = 0) {
+  if (dsm > 0) cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm);
   int b = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, f, kBlock, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, f, kBlock, dsm);
   return (b > 0 ? b : 1) * nsm;
 }
 
-template <typename T, int KMAX>
-static void grids_k(int nsm, int64_t npad, Grids* g) {
-  const int64_t work = (npad + kBlock - 1) / kBlock;
-  const int o[5] = {occ<T>((const void*)k_p1<T, KMAX>, nsm), occ<T>((const void*)k_p2<T, KMAX>, nsm),
-                    occ<T>((const void*)k_p3<T, KMAX>, nsm),
-                    occ<T>((const void*)k_p4<T, (KMAX > 0 ? KMAX : 1)>, nsm),
-                    occ<T>((const void*)k_p5<T, KMAX>, nsm)};
-  for (int p = 0; p < 5; ++p) g->pass[p] = (int)std::max<int64_t>(1, std::min<int64_t>(work, o[p]));
+template <typename T, int KMAX, int R>
+static void grids_kr(int nsm, int64_t npad, Grids* g) {
+  // P1/P3: one warp per slice; P2/P4/P5: one thread per 16-byte row vector
+  const int64_t work13 = (npad + kBlock - 1) / kBlock;
+  const int64_t workv = (npad / StreamVW<T, R>::value + kBlock - 1) / kBlock;
+  constexpr size_t dsm = P13Smem<T, KMAX, R>::bytes;
+  const int o[5] = {occ((const void*)k_p1<T, KMAX, R>, nsm, dsm), occ((const void*)k_p2<T, KMAX, R>, nsm),
+                    occ((const void*)k_p3<T, KMAX, R>, nsm, dsm),
+                    occ((const void*)k_p4<T, (KMAX > 0 ? KMAX : 1), R>, nsm),
+                    occ((const void*)k_p5<T, KMAX, R>, nsm)};
+  for (int p = 0; p < 5; ++p)
+    g->pass[p] = (int)std::max<int64_t>(1, std::min<int64_t>((p == P1 || p == P3) ? work13 : workv, o[p]));
   g->spmv = std::max(g->pass[P1], g->pass[P3]);
   g->vec = std::max(g->pass[P2], g->pass[P5]);
 }
 
 template <typename T>
-void iteration_grids(int k, int nsm, int64_t npad, Grids* g) {
-  switch (kmax_bucket(k)) {
-    case 0: grids_k<T, 0>(nsm, npad, g); break;
-    case 8: grids_k<T, 8>(nsm, npad, g); break;
-    case 16: grids_k<T, 16>(nsm, npad, g); break;
-    case 24: grids_k<T, 24>(nsm, npad, g); break;
-    case 32: grids_k<T, 32>(nsm, npad, g); break;
-    case 48: grids_k<T, 48>(nsm, npad, g); break;
-    default: grids_k<T, 64>(nsm, npad, g); break;
+static void grids_dispatch(int kb, int rb, int nsm, int64_t npad, Grids* g) {
+  switch (kb) {
+    case 0: { constexpr int KM = 0; switch (rb) { case 1: grids_kr<T, KM, 1>(nsm, npad, g); return; case 2: grids_kr<T, KM, 2>(nsm, npad, g); return; default: grids_kr<T, KM, 4>(nsm, npad, g); return; } }
+    case 8: { constexpr int KM = 8; switch (rb) { case 1: grids_kr<T, KM, 1>(nsm, npad, g); return; case 2: grids_kr<T, KM, 2>(nsm, npad, g); return; default: grids_kr<T, KM, 4>(nsm, npad, g); return; } }
+    case 16: { constexpr int KM = 16; switch (rb) { case 1: grids_kr<T, KM, 1>(nsm, npad, g); return; case 2: grids_kr<T, KM, 2>(nsm, npad, g); return; default: grids_kr<T, KM, 4>(nsm, npad, g); return; } }
+    case 24: { constexpr int KM = 24; switch (rb) { case 1: grids_kr<T, KM, 1>(nsm, npad, g); return; case 2: grids_kr<T, KM, 2>(nsm, npad, g); return; default: grids_kr<T, KM, 4>(nsm, npad, g); return; } }
+    case 32: { constexpr int KM = 32; switch (rb) { case 1: grids_kr<T, KM, 1>(nsm, npad, g); return; case 2: grids_kr<T, KM, 2>(nsm, npad, g); return; default: grids_kr<T, KM, 4>(nsm, npad, g); return; } }
+    case 48: { constexpr int KM = 48; switch (rb) { case 1: grids_kr<T, KM, 1>(nsm, npad, g); return; case 2: grids_kr<T, KM, 2>(nsm, npad, g); return; default: grids_kr<T, KM, 4>(nsm, npad, g); return; } }
+    default: { constexpr int KM = 64; switch (rb) { case 1: grids_kr<T, KM, 1>(nsm, npad, g); return; case 2: grids_kr<T, KM, 2>(nsm, npad, g); return; default: grids_kr<T, KM, 4>(nsm, npad, g); return; } }
   }
 }
 
-template void iteration_grids<double>(int, int, int64_t, Grids*);
-template void iteration_grids<float>(int, int, int64_t, Grids*);
+template <typename T>
+void iteration_grids(int k, int nsm, int64_t npad, Grids* g, int nrhs) {
+  grids_dispatch<T>(kmax_bucket(k), rhs_bucket(nrhs), nsm, npad, g);
+}
+
+template void iteration_grids<double>(int, int, int64_t, Grids*, int);
+template void iteration_grids<float>(int, int, int64_t, Grids*, int);
 
 }  // namespace rb

@@ -5,28 +5,31 @@
 
 namespace rb {
 
-// Pointers of one RBiCGSTAB iteration (Alg. 2 step 6).  Vectors have npad
-// entries (n rounded up to the slice height; the tail is kept at zero).
-// For k = 0, q aliases qraw and t aliases traw.
+// Pointers of one RBiCGSTAB iteration (Alg. 2 step 6) over nrhs <= kMaxRhs
+// right-hand sides of the same matrix and recycle space.  Vectors have npad
+// entries (n rounded up to the slice height; the tail is kept at zero).  For
+// k = 0, q aliases qraw and t aliases traw.  st points to nrhs consecutive
+// states; the grid-reduction tickets of st[0] serve all of them.
 template <typename T>
 struct IterArgs {
   Sell<T> A;
   const T* Chat;  // C-hat = C~ D_c^{-1}, column-major n x k, leading dim ld
   const T* C;     // C = A U, column-major, leading dim ld
   int64_t ld;
-  const T* rt0;   // r~_0
-  T* x;
-  T* r;
-  const T* p_in;  // p_i
-  T* p_out;       // p_{i+1} (may equal p_in)
-  T* s;
-  T* q;
-  T* qraw;        // A p_i before projection
-  T* t;
-  T* traw;        // A s_i before projection
+  const T* rt0;   // r~_0 (shared)
+  T* x[kMaxRhs];
+  T* r[kMaxRhs];
+  T* p_in[kMaxRhs];   // p_i
+  T* p_out[kMaxRhs];  // p_{i+1} (may equal p_in)
+  T* s[kMaxRhs];
+  T* q[kMaxRhs];
+  T* qraw[kMaxRhs];   // A p_i before projection
+  T* t[kMaxRhs];
+  T* traw[kMaxRhs];   // A s_i before projection
   IterState* st;
   double* partials;
   int64_t npad;
+  int nrhs;
 };
 
 struct Grids {
@@ -36,6 +39,8 @@ struct Grids {
 };
 
 int kmax_bucket(int k);
+// Compiled right-hand-side block sizes: 1, 2 or 4 (unused slots are masked).
+int rhs_bucket(int nrhs);
 
 // Process-wide count of kernels this library has launched (graph replays add
 // the kernels their graph holds).
@@ -45,7 +50,7 @@ template <typename T>
 cudaError_t launch_iteration(const IterArgs<T>& a, int k, const Grids& g, cudaStream_t s);
 
 template <typename T>
-void iteration_grids(int k, int nsm, int64_t npad, Grids* g);
+void iteration_grids(int k, int nsm, int64_t npad, Grids* g, int nrhs);
 
 // One pass (P1..P5 = 0..4) of the iteration, launched on its own.
 template <typename T>

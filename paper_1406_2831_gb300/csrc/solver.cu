@@ -3,18 +3,26 @@
 // A solve (Alg. 2) runs as: setup of x_0, r_0, r~_0 (eq. (3.5)) with a few
 // generic kernels; then the fused five-pass iteration, captured once per
 // handle as a CUDA graph of `poll` iterations and replayed until the device
-// convergence flag is set (every pass returns at once after it is set, so
-// the overshoot of the last replay costs only empty launches); then step 8
+// convergence flags are set (every pass returns at once after they are set,
+// so the overshoot of the last replay costs only empty launches); then step 8
 // (x = x - U x_c) and a true-residual check.  In the recycle-update modes the
 // graph spans one cycle of s iterations whose p, s, A p, A s vectors land in
 // a cycle store; between cycles the Gram matrices G = Z^T Z, H = Z^T W are
 // formed on the device, the small harmonic-Ritz problem is solved on the
 // host, and the candidate space Y, A Y is rebuilt on the device (Sec. 6.2).
+//
+// Blocked solves: up to four right-hand sides of the same matrix iterate
+// together ("slots"), each with its own vectors and device state, so every
+// pass reads A, C, C-hat and r~_0 once for all of them.  In update mode the
+// cycle store takes slot 0's vectors, so the recycle update is built from the
+// Krylov space of the first right-hand side of the block.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <type_traits>
 #include <vector>
 
 #include "device.cuh"
@@ -23,7 +31,6 @@
 
 using namespace rb;
 
-#include <atomic>
 static std::atomic<long long> g_launches{0};
 void rb::count_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
@@ -59,6 +66,18 @@ struct GraphSlot {
   bool valid = false;
 };
 
+// Vectors of one right-hand side.  FP64: b, x and the iteration vectors;
+// rin, xin are the inner right-hand side and correction of the mixed path,
+// whose FP32 iteration vectors are the f* fields.
+struct Slot {
+  double *b = nullptr, *x = nullptr, *r = nullptr, *p = nullptr, *s = nullptr, *q = nullptr, *t = nullptr,
+         *qraw = nullptr, *traw = nullptr, *rin = nullptr, *xin = nullptr;
+  float *fx = nullptr, *fr = nullptr, *fp = nullptr, *fs = nullptr, *fq = nullptr, *ft = nullptr,
+        *fqraw = nullptr, *ftraw = nullptr;
+};
+
+const int kOne = 1;   // source of the "done" flag written for masked slots
+
 }  // namespace
 
 struct rb_ctx {
@@ -82,34 +101,32 @@ struct rb_ctx {
   double *U = nullptr, *Ut = nullptr, *C = nullptr, *Ct = nullptr, *Chat = nullptr;
   double *T1 = nullptr, *T2 = nullptr;   // scratch blocks (kcap columns each)
   double* Dinv = nullptr;                // 1 / D_c (device)
-  // vectors
-  double *b = nullptr, *x = nullptr, *r = nullptr, *p = nullptr, *s = nullptr, *q = nullptr,
-         *t = nullptr, *qraw = nullptr, *traw = nullptr, *rt0 = nullptr, *tmp = nullptr,
-         *rin = nullptr, *xin = nullptr;
-  // mixed path (FP32 inner solve)
-  float *fx = nullptr, *fr = nullptr, *fp = nullptr, *fs = nullptr, *fq = nullptr, *ft = nullptr,
-        *fqraw = nullptr, *ftraw = nullptr, *frt0 = nullptr, *fU = nullptr, *fC = nullptr,
-        *fChat = nullptr;
-  // device state
+  float *fU = nullptr, *fC = nullptr, *fChat = nullptr;
+  // per right-hand-side vectors; shared r~_0 and scratch
+  Slot sl[kMaxRhs];
+  int nslots = 0;
+  double *rt0 = nullptr, *tmp = nullptr, *tmp2 = nullptr;
+  float* frt0 = nullptr;
+  // device states, one per slot (contiguous), and their pinned host mirror
   IterState* st = nullptr;
-  IterState* hst = nullptr;     // pinned host mirror
+  IterState* hst = nullptr;
   double* partials = nullptr;
   int64_t partials_cap = 0;
   int* dflag = nullptr;
-  // cycle store for the recycle update
+  // cycle store for the recycle update: P: 2*cyc, S: cyc, QR: cyc, TR: cyc
+  // vectors of the inner precision (double for RB_FP64, float for RB_MIXED),
+  // and the candidate Y, A Y
   int cyc = 0;
-  // P: 2*cyc, S: cyc, QR: cyc, TR: cyc vectors of the inner precision
-  // (double for RB_FP64, float for RB_MIXED), and the candidate Y, A Y
   void* cstore = nullptr;
   void *Yc = nullptr, *AYc = nullptr, *Yn = nullptr, *AYn = nullptr;
   int kY = 0;
   double* gwork = nullptr;
   int64_t gwork_cap = 0;
-  double *dG = nullptr, *dH = nullptr, *dR = nullptr;
+  double *dG = nullptr, *dR = nullptr;
   const double** dptr = nullptr;   // device pointer lists (4 * 128)
-  Grids grids{1, 1};
+  Grids grids{};
   GraphSlot g_plain, g_cycle[2];
-  int g_k = -1;
+  int g_k = -1, g_nrhs = -1;
 };
 
 // ============================================================ helpers
@@ -139,6 +156,7 @@ void reset_graphs(rb_ctx* h) {
     g->valid = false;
   }
   h->g_k = -1;
+  h->g_nrhs = -1;
 }
 
 int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
@@ -159,29 +177,32 @@ int copy_out(void* dst, const void* src, size_t bytes, int where, cudaStream_t s
   return RB_OK;
 }
 
-int read_state(rb_ctx* h) {
-  RB_CUDA_TRY(cudaMemcpyAsync(h->hst, h->st, sizeof(IterState), cudaMemcpyDeviceToHost, h->us));
+// Copy the device states of slots [0, nrhs) to the pinned mirror and wait.
+int read_state(rb_ctx* h, int nrhs = 1) {
+  RB_CUDA_TRY(cudaMemcpyAsync(h->hst, h->st, sizeof(IterState) * nrhs, cudaMemcpyDeviceToHost, h->us));
   return sync(h);
 }
 
 int vec_grid(rb_ctx* h) { return h->grids.vec; }
 
-// Deterministic dot products / projections into st->red, then read back `cnt` values.
-int run_dots(rb_ctx* h, const DotArgs& d, double* out, int cnt) {
-  RB_CUDA_TRY(dots(d, h->npad, h->st, h->partials, vec_grid(h), h->us));
+// Deterministic dot products / projections into st[slot].red, then read
+// back `cnt` values.
+int run_dots(rb_ctx* h, const DotArgs& d, double* out, int cnt, int slot = 0) {
+  RB_CUDA_TRY(dots(d, h->npad, h->st + slot, h->partials, vec_grid(h), h->us));
   if (out) {
-    RB_CUDA_TRY(cudaMemcpyAsync(h->hst->red, h->st->red, sizeof(double) * cnt,
+    RB_CUDA_TRY(cudaMemcpyAsync(h->hst[slot].red, h->st[slot].red, sizeof(double) * cnt,
                                 cudaMemcpyDeviceToHost, h->us));
     int rc = sync(h);
     if (rc) return rc;
-    std::memcpy(out, h->hst->red, sizeof(double) * cnt);
+    std::memcpy(out, h->hst[slot].red, sizeof(double) * cnt);
   }
   return RB_OK;
 }
 
 int ensure_partials(rb_ctx* h) {
-  // every kernel runs at most one full wave: <= 8 blocks of 256 threads per SM
-  const int64_t need = (int64_t)std::max(8 * h->nsm, std::max(h->grids.spmv, h->grids.vec)) * kMaxNV;
+  // every kernel runs at most one full wave (<= 8 blocks of 256 threads per
+  // SM) and reduces at most kMaxRhs * kMaxNV values per block
+  const int64_t need = (int64_t)std::max(8 * h->nsm, std::max(h->grids.spmv, h->grids.vec)) * kMaxRhs * kMaxNV;
   if (need <= h->partials_cap) return RB_OK;
   cudaFree(h->partials);
   int err = 0;
@@ -217,6 +238,16 @@ int block_gemm(rb_ctx* h, const std::vector<T*>& out, const std::vector<const T*
   return RB_OK;
 }
 
+int ensure_gwork(rb_ctx* h, int64_t need) {
+  if (need <= h->gwork_cap) return RB_OK;
+  cudaFree(h->gwork);
+  int err = 0;
+  h->gwork = dalloc<double>(need, &err);
+  if (!h->gwork) return err;
+  h->gwork_cap = need;
+  return RB_OK;
+}
+
 // G (mx x my, column-major) = X^T Y, returned on the host.
 template <typename T>
 int block_gram(rb_ctx* h, const std::vector<const T*>& X, const std::vector<const T*>& Y,
@@ -231,14 +262,8 @@ int block_gram(rb_ctx* h, const std::vector<const T*>& X, const std::vector<cons
   rc = upload_ptrs(h, 3, Y);
   if (rc) return rc;
   const int grid = vec_grid(h);
-  const int64_t need = (int64_t)grid * mx * my;
-  if (need > h->gwork_cap) {
-    cudaFree(h->gwork);
-    int err = 0;
-    h->gwork = dalloc<double>(need, &err);
-    if (!h->gwork) return err;
-    h->gwork_cap = need;
-  }
+  rc = ensure_gwork(h, (int64_t)grid * mx * my);
+  if (rc) return rc;
   RB_CUDA_TRY(gram<T>((const T* const*)(h->dptr + 256), mx, (const T* const*)(h->dptr + 384), my, h->npad,
                       h->dG, h->gwork, grid, h->us));
   RB_CUDA_TRY(cudaMemcpyAsync(G.data(), h->dG, sizeof(double) * G.size(), cudaMemcpyDeviceToHost, h->us));
@@ -260,14 +285,8 @@ int block_gram_gh(rb_ctx* h, const std::vector<const T*>& Z, const std::vector<c
   rc = upload_ptrs(h, 3, W);
   if (rc) return rc;
   const int grid = 2 * h->nsm;
-  const int64_t need = (int64_t)grid * gram_gh_work(m);
-  if (need > h->gwork_cap) {
-    cudaFree(h->gwork);
-    int err = 0;
-    h->gwork = dalloc<double>(need, &err);
-    if (!h->gwork) return err;
-    h->gwork_cap = need;
-  }
+  rc = ensure_gwork(h, (int64_t)grid * gram_gh_work(m));
+  if (rc) return rc;
   RB_CUDA_TRY(gram_gh<T>((const T* const*)(h->dptr + 256), (const T* const*)(h->dptr + 384), m, h->npad, h->dG,
                          h->dG + (size_t)kMaxGram * kMaxGram, h->gwork, grid, h->us));
   RB_CUDA_TRY(cudaMemcpyAsync(G.data(), h->dG, sizeof(double) * G.size(), cudaMemcpyDeviceToHost, h->us));
@@ -294,57 +313,84 @@ int block_colnorm2(rb_ctx* h, const std::vector<const T*>& M, std::vector<double
   return RB_OK;
 }
 
-int alloc_vectors(rb_ctx* h) {
+template <typename T>
+int zero_alloc(T** p, int64_t cnt, rb_ctx* h) {
+  cudaFree(*p);
   int err = 0;
-  double** vs[] = {&h->b, &h->x, &h->r, &h->p, &h->s, &h->q, &h->t, &h->qraw, &h->traw, &h->rt0, &h->tmp,
-                    &h->rin, &h->xin};
-  for (double** v : vs) {
-    cudaFree(*v);
-    *v = dalloc<double>(h->npad, &err);
-    if (!*v) return err;
-    RB_CUDA_TRY(cudaMemsetAsync(*v, 0, sizeof(double) * h->npad, h->us));
+  *p = dalloc<T>(cnt, &err);
+  if (!*p) return err;
+  RB_CUDA_TRY(cudaMemsetAsync(*p, 0, sizeof(T) * (size_t)cnt, h->us));
+  return RB_OK;
+}
+
+void free_slot(Slot& s) {
+  void* ptrs[] = {s.b, s.x, s.r, s.p, s.s, s.q, s.t, s.qraw, s.traw, s.rin, s.xin,
+                  s.fx, s.fr, s.fp, s.fs, s.fq, s.ft, s.fqraw, s.ftraw};
+  for (void* p : ptrs) cudaFree(p);
+  s = Slot();
+}
+
+// Vectors of slots [0, nrhs) (npad entries; the tail beyond n stays zero).
+int ensure_slots(rb_ctx* h, int nrhs) {
+  for (int i = h->nslots; i < nrhs; ++i) {
+    Slot& s = h->sl[i];
+    double** vs[] = {&s.b, &s.x, &s.r, &s.p, &s.s, &s.q, &s.t, &s.qraw, &s.traw, &s.rin, &s.xin};
+    for (double** v : vs) {
+      int rc = zero_alloc(v, h->npad, h);
+      if (rc) return rc;
+    }
+    if (h->o.precision == RB_MIXED) {
+      float** fs[] = {&s.fx, &s.fr, &s.fp, &s.fs, &s.fq, &s.ft, &s.fqraw, &s.ftraw};
+      for (float** v : fs) {
+        int rc = zero_alloc(v, h->npad, h);
+        if (rc) return rc;
+      }
+    }
+    h->nslots = i + 1;
+    reset_graphs(h);
   }
+  return RB_OK;
+}
+
+int alloc_vectors(rb_ctx* h) {
+  for (int i = 0; i < h->nslots; ++i) free_slot(h->sl[i]);
+  h->nslots = 0;
+  int rc = ensure_slots(h, 1);
+  if (rc) return rc;
+  double** vs[] = {&h->rt0, &h->tmp, &h->tmp2};
+  for (double** v : vs)
+    if ((rc = zero_alloc(v, h->npad, h))) return rc;
   const int kc = std::max(1, h->kcap);
   double** ms[] = {&h->U, &h->Ut, &h->C, &h->Ct, &h->Chat, &h->T1, &h->T2};
-  for (double** m : ms) {
-    cudaFree(*m);
-    *m = dalloc<double>(h->npad * kc, &err);
-    if (!*m) return err;
-    RB_CUDA_TRY(cudaMemsetAsync(*m, 0, sizeof(double) * h->npad * kc, h->us));
-  }
+  for (double** m : ms)
+    if ((rc = zero_alloc(m, h->npad * kc, h))) return rc;
   if (h->o.recycle_mode >= RB_RECYCLE_UPDATE_FIRST) {
-    const size_t es = h->o.precision == RB_MIXED ? sizeof(float) : sizeof(double);
+    const int64_t es = h->o.precision == RB_MIXED ? sizeof(float) : sizeof(double);
     h->cyc = h->o.cycle_s;
     void** ys[] = {&h->cstore, &h->Yc, &h->AYc, &h->Yn, &h->AYn};
     for (void** y : ys) {
-      cudaFree(*y);
       const int64_t cnt = (y == &h->cstore ? 5 * (int64_t)h->cyc : (int64_t)kc) * h->npad;
-      *y = dalloc<unsigned char>((int64_t)es * cnt, &err);
-      if (!*y) return err;
-      RB_CUDA_TRY(cudaMemsetAsync(*y, 0, es * cnt, h->us));
+      unsigned char* p = (unsigned char*)*y;
+      rc = zero_alloc(&p, es * cnt, h);
+      *y = p;
+      if (rc) return rc;
     }
   }
   if (h->o.precision == RB_MIXED) {
-    float** fs[] = {&h->fx, &h->fr, &h->fp, &h->fs, &h->fq, &h->ft, &h->fqraw, &h->ftraw, &h->frt0};
-    for (float** v : fs) {
-      cudaFree(*v);
-      *v = dalloc<float>(h->npad, &err);
-      if (!*v) return err;
-      RB_CUDA_TRY(cudaMemsetAsync(*v, 0, sizeof(float) * h->npad, h->us));
-    }
+    if ((rc = zero_alloc(&h->frt0, h->npad, h))) return rc;
     float** fm[] = {&h->fU, &h->fC, &h->fChat};
-    for (float** m : fm) {
-      cudaFree(*m);
-      *m = dalloc<float>(h->npad * kc, &err);
-      if (!*m) return err;
-      RB_CUDA_TRY(cudaMemsetAsync(*m, 0, sizeof(float) * h->npad * kc, h->us));
-    }
+    for (float** m : fm)
+      if ((rc = zero_alloc(m, h->npad * kc, h))) return rc;
   }
-  iteration_grids<double>(h->kcap, h->nsm, h->npad, &h->grids);
-  Grids g0;
-  iteration_grids<double>(0, h->nsm, h->npad, &g0);
-  h->grids.spmv = std::max(h->grids.spmv, g0.spmv);
-  h->grids.vec = std::max(h->grids.vec, g0.vec);
+  // generic grids: the largest over k in {0, kcap} and every block size
+  h->grids = Grids{};
+  for (int kk : {0, h->kcap})
+    for (int nr : {1, 2, kMaxRhs}) {
+      Grids g;
+      iteration_grids<double>(kk, h->nsm, h->npad, &g, nr);
+      h->grids.spmv = std::max(h->grids.spmv, g.spmv);
+      h->grids.vec = std::max(h->grids.vec, g.vec);
+    }
   return ensure_partials(h);
 }
 
@@ -393,7 +439,10 @@ int recycle_setup(rb_ctx* h, int kin, int64_t* setup_mv) {
     for (int j = 0; j < cnt; ++j) v.push_back(colp(base, ld, j));
     return v;
   };
-  struct Job { double** src; const std::vector<double>* R; };
+  struct Job {
+    double** src;
+    const std::vector<double>* R;
+  };
   Job jobs[] = {{&h->U, &Qk}, {&h->C, &Qk}, {&h->Ut, &Pk}, {&h->Ct, &Pk}};
   for (Job& jb : jobs) {
     rc = block_gemm<double>(h, cols(h->T1, kk), ccols(*jb.src, kin), *jb.R, kk);
@@ -401,6 +450,7 @@ int recycle_setup(rb_ctx* h, int kin, int64_t* setup_mv) {
     std::swap(*jb.src, h->T1);
   }
   rc = sync(h);
+  if (rc) return rc;
   pc.lap("setup_gemm");
   std::vector<double> dinv(kk);
   for (int j = 0; j < kk; ++j) dinv[j] = 1.0 / sig[j];
@@ -422,51 +472,59 @@ int recycle_setup(rb_ctx* h, int kin, int64_t* setup_mv) {
 
 // ------------------------------------------------------------ iteration args
 template <typename T>
-IterArgs<T> base_args(rb_ctx* h);
+IterArgs<T> base_args(rb_ctx* h, int nrhs);
 
 template <>
-IterArgs<double> base_args<double>(rb_ctx* h) {
+IterArgs<double> base_args<double>(rb_ctx* h, int nrhs) {
   IterArgs<double> a{};
   a.A = h->A.view();
   a.Chat = h->Chat;
   a.C = h->C;
   a.ld = h->npad;
   a.rt0 = h->rt0;
-  a.x = h->x;
-  a.r = h->r;
-  a.p_in = h->p;
-  a.p_out = h->p;
-  a.s = h->s;
-  a.qraw = h->qraw;
-  a.traw = h->traw;
-  a.q = h->k > 0 ? h->q : h->qraw;
-  a.t = h->k > 0 ? h->t : h->traw;
+  for (int i = 0; i < nrhs; ++i) {
+    Slot& s = h->sl[i];
+    a.x[i] = s.x;
+    a.r[i] = s.r;
+    a.p_in[i] = s.p;
+    a.p_out[i] = s.p;
+    a.s[i] = s.s;
+    a.qraw[i] = s.qraw;
+    a.traw[i] = s.traw;
+    a.q[i] = h->k > 0 ? s.q : s.qraw;
+    a.t[i] = h->k > 0 ? s.t : s.traw;
+  }
   a.st = h->st;
   a.partials = h->partials;
   a.npad = h->npad;
+  a.nrhs = nrhs;
   return a;
 }
 
 template <>
-IterArgs<float> base_args<float>(rb_ctx* h) {
+IterArgs<float> base_args<float>(rb_ctx* h, int nrhs) {
   IterArgs<float> a{};
   a.A = h->A32.view();
   a.Chat = h->fChat;
   a.C = h->fC;
   a.ld = h->npad;
   a.rt0 = h->frt0;
-  a.x = h->fx;
-  a.r = h->fr;
-  a.p_in = h->fp;
-  a.p_out = h->fp;
-  a.s = h->fs;
-  a.qraw = h->fqraw;
-  a.traw = h->ftraw;
-  a.q = h->k > 0 ? h->fq : h->fqraw;
-  a.t = h->k > 0 ? h->ft : h->ftraw;
+  for (int i = 0; i < nrhs; ++i) {
+    Slot& s = h->sl[i];
+    a.x[i] = s.fx;
+    a.r[i] = s.fr;
+    a.p_in[i] = s.fp;
+    a.p_out[i] = s.fp;
+    a.s[i] = s.fs;
+    a.qraw[i] = s.fqraw;
+    a.traw[i] = s.ftraw;
+    a.q[i] = h->k > 0 ? s.fq : s.fqraw;
+    a.t[i] = h->k > 0 ? s.ft : s.ftraw;
+  }
   a.st = h->st;
   a.partials = h->partials;
   a.npad = h->npad;
+  a.nrhs = nrhs;
   return a;
 }
 
@@ -481,29 +539,29 @@ template <typename T>
 T* slotT(rb_ctx* h, int j) { return (T*)h->cstore + (int64_t)(4 * h->cyc + j) * h->npad; }
 
 template <typename T>
-int capture(rb_ctx* h, GraphSlot* g, int iters, int bank, bool cycle_mode) {
+int capture(rb_ctx* h, GraphSlot* g, int iters, int bank, bool cycle_mode, int nrhs) {
   if (g->exec) cudaGraphExecDestroy(g->exec);
   g->exec = nullptr;
   g->valid = false;
   cudaGraph_t graph = nullptr;
+  Grids gr;
+  iteration_grids<T>(h->k, h->nsm, h->npad, &gr, nrhs);
   RB_CUDA_TRY(cudaStreamBeginCapture(h->cs, cudaStreamCaptureModeThreadLocal));
   cudaError_t err = cudaSuccess;
   for (int j = 0; j < iters && err == cudaSuccess; ++j) {
-    IterArgs<T> a = base_args<T>(h);
-    if (cycle_mode) {
-      a.p_in = slotP<T>(h, bank, j);
-      a.p_out = (j + 1 < h->cyc) ? slotP<T>(h, bank, j + 1) : slotP<T>(h, 1 - bank, 0);
-      a.s = slotS<T>(h, j);
-      a.qraw = slotQ<T>(h, j);
-      a.traw = slotT<T>(h, j);
+    IterArgs<T> a = base_args<T>(h, nrhs);
+    if (cycle_mode) {   // slot 0's vectors go to the cycle store
+      a.p_in[0] = slotP<T>(h, bank, j);
+      a.p_out[0] = (j + 1 < h->cyc) ? slotP<T>(h, bank, j + 1) : slotP<T>(h, 1 - bank, 0);
+      a.s[0] = slotS<T>(h, j);
+      a.qraw[0] = slotQ<T>(h, j);
+      a.traw[0] = slotT<T>(h, j);
       if (h->k == 0) {
-        a.q = a.qraw;
-        a.t = a.traw;
+        a.q[0] = a.qraw[0];
+        a.t[0] = a.traw[0];
       }
     }
-    Grids g;
-    iteration_grids<T>(h->k, h->nsm, h->npad, &g);
-    err = launch_iteration<T>(a, h->k, g, h->cs);
+    err = launch_iteration<T>(a, h->k, gr, h->cs);
   }
   cudaError_t e2 = cudaStreamEndCapture(h->cs, &graph);
   if (err != cudaSuccess || e2 != cudaSuccess) {
@@ -522,6 +580,8 @@ int poll_iters(rb_ctx* h) {
   return h->npad >= (1 << 20) ? 8 : 16;
 }
 
+int passes_per_iter(rb_ctx* h) { return h->k > 0 ? 5 : 4; }
+
 // ------------------------------------------------------------ solve core
 struct SolveOut {
   int status = RB_OK;
@@ -535,35 +595,46 @@ struct SolveOut {
   double bytes = 0;
 };
 
-double iter_bytes(rb_ctx* h, int k, size_t vb, size_t ab) {
-  // per iteration: 2 SpMVs (values + int32 cols + slice padding ignored)
-  // + 4 n*k reads (C-hat twice, C twice) + vector streams.
+// Modelled HBM bytes of one iteration attributed to one of nrhs slots: two
+// SpMVs (values + int32 columns + row pointers) and four n x k block reads
+// (C-hat twice, C twice) are shared by the block; 21 (k > 0) or 14 vector
+// streams belong to each right-hand side.
+double iter_bytes(rb_ctx* h, int k, size_t vb, size_t ab, int nrhs) {
   const double z = (double)h->nnz, n = (double)h->n;
-  const double spmv = 2.0 * (z * (ab + 4.0) + 4.0 * (n + 1));
-  const double vec_streams = (k > 0) ? 21.0 : 14.0;  // see DESIGN notes
-  return spmv + n * vb * (4.0 * k + vec_streams);
+  const double shared = 2.0 * (z * (ab + 4.0) + 4.0 * (n + 1)) + 4.0 * n * k * vb;
+  const double vec_streams = (k > 0) ? 21.0 : 14.0;
+  return shared / nrhs + n * vb * vec_streams;
 }
 
-// Setup of one FP64 solve: x_0, r_0, r~_0, rho_0 (eq. (3.5), Alg. 2 steps 2-4).
-int setup_solve(rb_ctx* h, const double* rhs, double* xb, bool x_nonzero, double tol, SolveOut* so) {
+// Setup of a blocked FP64 solve (Alg. 2 steps 2-4, eq. (3.5)) for slots
+// [0, nrhs): rhs[i], xb[i] are slot i's right-hand side and iterate; tol[i]
+// is relative to st[i].bnorm2 (set by the caller); skip[i] marks slots that
+// take no part and are marked done.  The shadow r~_{-1} (hence r~_0) is
+// shared; when (r~_0, r_0) = 0 for any slot every slot takes the next seed.
+int setup_block(rb_ctx* h, int nrhs, double* const* rhs, double* const* xb, const bool* x_nonzero,
+                const bool* skip, const double* tol, SolveOut* so) {
   const int k = h->k;
   const int64_t ld = h->npad;
-  int rc;
   const int max_itn = h->o.max_itn > 0 ? h->o.max_itn : (int)std::min<int64_t>(h->n, 20000);
-  // r_{-1} = b - A x_{-1}
-  if (x_nonzero) {
-    RB_CUDA_TRY(residual_norm(h->A.view(), rhs, xb, h->r, h->npad, h->st, h->partials, h->grids.spmv, h->us));
-    so->mv += 1;
-  } else {
-    RB_CUDA_TRY(cudaMemcpyAsync(h->r, rhs, sizeof(double) * h->npad, cudaMemcpyDeviceToDevice, h->us));
-  }
-  if (k > 0) {
-    DotArgs d{};
-    d.M = h->Chat; d.ld = ld; d.km = k; d.v = h->r; d.nd = 0;
-    RB_CUDA_TRY(dots(d, h->npad, h->st, h->partials, vec_grid(h), h->us));
-    // x_0 = x_{-1} + U (C-hat^T r_{-1});  r_0 = r_{-1} - C (C-hat^T r_{-1})
-    RB_CUDA_TRY(gemv_update(xb, h->U, ld, k, h->st->red, nullptr, 1.0, h->npad, vec_grid(h), h->us));
-    RB_CUDA_TRY(gemv_update(h->r, h->C, ld, k, h->st->red, nullptr, -1.0, h->npad, vec_grid(h), h->us));
+  for (int i = 0; i < nrhs; ++i) {
+    if (skip[i]) continue;
+    Slot& s = h->sl[i];
+    IterState* st = h->st + i;
+    // r_{-1} = b - A x_{-1}
+    if (x_nonzero[i]) {
+      RB_CUDA_TRY(residual_norm(h->A.view(), rhs[i], xb[i], s.r, h->npad, st, h->partials, h->grids.spmv, h->us));
+      so[i].mv += 1;
+    } else {
+      RB_CUDA_TRY(cudaMemcpyAsync(s.r, rhs[i], sizeof(double) * h->npad, cudaMemcpyDeviceToDevice, h->us));
+    }
+    if (k > 0) {
+      DotArgs d{};
+      d.M = h->Chat; d.ld = ld; d.km = k; d.v = s.r; d.nd = 0;
+      RB_CUDA_TRY(dots(d, h->npad, st, h->partials, vec_grid(h), h->us));
+      // x_0 = x_{-1} + U (C-hat^T r_{-1});  r_0 = r_{-1} - C (C-hat^T r_{-1})
+      RB_CUDA_TRY(gemv_update(xb[i], h->U, ld, k, st->red, nullptr, 1.0, h->npad, vec_grid(h), h->us));
+      RB_CUDA_TRY(gemv_update(s.r, h->C, ld, k, st->red, nullptr, -1.0, h->npad, vec_grid(h), h->us));
+    }
   }
   for (int attempt = 0; attempt < 4; ++attempt) {
     RB_CUDA_TRY(shadow(h->rt0, h->n, h->npad, h->o.shadow_seed + (uint64_t)attempt, h->us));
@@ -574,35 +645,71 @@ int setup_solve(rb_ctx* h, const double* rhs, double* xb, bool x_nonzero, double
       // r~_0 = r~_{-1} - C~ (D_c^{-1} C^T r~_{-1})
       RB_CUDA_TRY(gemv_update(h->rt0, h->Ct, ld, k, h->st->red, h->Dinv, -1.0, h->npad, vec_grid(h), h->us));
     }
-    DotArgs d{};
-    d.M = k > 0 ? h->C : nullptr; d.ld = ld; d.km = k; d.v = h->rt0;
-    d.nd = 2;
-    d.a[0] = h->rt0; d.b[0] = h->r;
-    d.a[1] = h->r; d.b[1] = h->r;
-    RB_CUDA_TRY(dots(d, h->npad, h->st, h->partials, vec_grid(h), h->us));
-    RB_CUDA_TRY(init_state(h->st, k, tol, max_itn, h->us));
-    rc = read_state(h);
+    for (int i = 0; i < nrhs; ++i) {
+      if (skip[i]) continue;
+      DotArgs d{};
+      d.M = k > 0 ? h->C : nullptr; d.ld = ld; d.km = k; d.v = h->rt0;
+      d.nd = 2;
+      d.a[0] = h->rt0; d.b[0] = h->sl[i].r;
+      d.a[1] = h->sl[i].r; d.b[1] = h->sl[i].r;
+      RB_CUDA_TRY(dots(d, h->npad, h->st + i, h->partials, vec_grid(h), h->us));
+      RB_CUDA_TRY(init_state(h->st + i, k, tol[i], max_itn, h->us));
+    }
+    int rc = read_state(h, nrhs);
     if (rc) return rc;
-    so->seeds = attempt + 1;
-    if (h->hst->status != RB_EBREAKDOWN_RHO) break;
+    bool redo = false;
+    for (int i = 0; i < nrhs; ++i) {
+      so[i].seeds = attempt + 1;
+      if (!skip[i] && h->hst[i].status == RB_EBREAKDOWN_RHO) redo = true;
+    }
+    if (!redo) break;
+  }
+  bool any_skip = false;
+  for (int i = 0; i < nrhs; ++i)
+    if (skip[i]) {
+      RB_CUDA_TRY(cudaMemcpyAsync(&h->st[i].done, &kOne, sizeof(int), cudaMemcpyHostToDevice, h->us));
+      any_skip = true;
+    }
+  return any_skip ? read_state(h, nrhs) : RB_OK;
+}
+
+bool all_done(rb_ctx* h, int nrhs) {
+  for (int i = 0; i < nrhs; ++i)
+    if (!h->hst[i].done) return false;
+  return true;
+}
+
+// p_1 = r_0 for every slot (Alg. 2 step 4 with beta_0 = 0); slot 0 writes to
+// the cycle store in update mode.
+template <typename T>
+int init_p(rb_ctx* h, int nrhs, bool cycle_slot0) {
+  const bool f32 = std::is_same<T, float>::value;
+  for (int i = 0; i < nrhs; ++i) {
+    Slot& s = h->sl[i];
+    void* dst = f32 ? (void*)s.fp : (void*)s.p;
+    const void* src = f32 ? (const void*)s.fr : (const void*)s.r;
+    if (i == 0 && cycle_slot0) dst = slotP<T>(h, 0, 0);
+    RB_CUDA_TRY(cudaMemcpyAsync(dst, src, sizeof(T) * h->npad, cudaMemcpyDeviceToDevice, h->us));
   }
   return RB_OK;
 }
 
-// Launch graphs until the device reports done.  Non-update mode.
+// Launch graphs until every slot reports done.  Non-update mode.
 template <typename T>
-int iterate_plain(rb_ctx* h) {
-  if (!h->g_plain.valid || h->g_k != h->k) {
-    int rc = capture<T>(h, &h->g_plain, poll_iters(h), 0, false);
+int iterate_plain(rb_ctx* h, int nrhs) {
+  if (!h->g_plain.valid || h->g_k != h->k || h->g_nrhs != nrhs) {
+    reset_graphs(h);
+    int rc = capture<T>(h, &h->g_plain, poll_iters(h), 0, false, nrhs);
     if (rc) return rc;
     h->g_k = h->k;
+    h->g_nrhs = nrhs;
   }
   for (;;) {
     RB_CUDA_TRY(cudaGraphLaunch(h->g_plain.exec, h->us));
-    count_launches((long long)poll_iters(h) * (h->k > 0 ? 5 : 4));
-    int rc = read_state(h);
+    count_launches((long long)poll_iters(h) * passes_per_iter(h));
+    int rc = read_state(h, nrhs);
     if (rc) return rc;
-    if (h->hst->done) break;
+    if (all_done(h, nrhs)) break;
   }
   return RB_OK;
 }
@@ -655,6 +762,7 @@ int cycle_update(rb_ctx* h, int bank, int nit, int ns) {
   rc = block_gemm<T>(h, oAY, Z, Y, kn);
   if (rc) return rc;
   rc = sync(h);
+  if (rc) return rc;
   pc.lap("gemm");
   // unit 2-norm columns
   std::vector<const T*> yc(oY.begin(), oY.end());
@@ -662,10 +770,7 @@ int cycle_update(rb_ctx* h, int bank, int nit, int ns) {
   rc = block_colnorm2<T>(h, yc, N2);
   if (rc) return rc;
   std::vector<double> f(kn);
-  for (int j = 0; j < kn; ++j) {
-    const double nn = N2[j];
-    f[j] = nn > 0 ? 1.0 / std::sqrt(nn) : 0.0;
-  }
+  for (int j = 0; j < kn; ++j) f[j] = N2[j] > 0 ? 1.0 / std::sqrt(N2[j]) : 0.0;
   RB_CUDA_TRY(cudaMemcpy(h->dR, f.data(), sizeof(double) * kn, cudaMemcpyHostToDevice));
   RB_CUDA_TRY(scale_cols<T>(Yn, ld, kn, h->dR, h->npad, h->us));
   RB_CUDA_TRY(scale_cols<T>(AYn, ld, kn, h->dR, h->npad, h->us));
@@ -677,11 +782,11 @@ int cycle_update(rb_ctx* h, int bank, int nit, int ns) {
   return rc;
 }
 
-// One solve's iterations in update mode: graphs of one cycle each, the
-// recycle update between cycles.  Candidate Y = U, A Y = C at the start;
-// p_1 = r_0 goes to bank 0, slot 0.
+// Iterations in update mode: graphs of one cycle each, the recycle update
+// between cycles from slot 0's vectors.  Candidate Y = U, A Y = C at the
+// start; the caller has put p_1 of slot 0 into bank 0, slot 0.
 template <typename T>
-int iterate_cycles(rb_ctx* h, SolveOut* so) {
+int iterate_cycles(rb_ctx* h, int nrhs, SolveOut* so) {
   const int64_t ld = h->npad;
   const bool f32 = std::is_same<T, float>::value;
   h->kY = h->k;
@@ -691,28 +796,29 @@ int iterate_cycles(rb_ctx* h, SolveOut* so) {
     RB_CUDA_TRY(cudaMemcpyAsync(h->AYc, f32 ? (const void*)h->fC : (const void*)h->C, sizeof(T) * ld * h->k,
                                 cudaMemcpyDeviceToDevice, h->us));
   }
-  RB_CUDA_TRY(cudaMemcpyAsync(slotP<T>(h, 0, 0), f32 ? (const void*)h->fr : (const void*)h->r, sizeof(T) * ld,
-                              cudaMemcpyDeviceToDevice, h->us));
-  if (h->g_k != h->k || !h->g_cycle[0].valid || !h->g_cycle[1].valid) {
+  if (h->g_k != h->k || h->g_nrhs != nrhs || !h->g_cycle[0].valid || !h->g_cycle[1].valid) {
+    reset_graphs(h);
     for (int bnk = 0; bnk < 2; ++bnk) {
-      int rc = capture<T>(h, &h->g_cycle[bnk], h->cyc, bnk, true);
+      int rc = capture<T>(h, &h->g_cycle[bnk], h->cyc, bnk, true, nrhs);
       if (rc) return rc;
     }
     h->g_k = h->k;
+    h->g_nrhs = nrhs;
   }
   int iters_before = 0;
+  bool slot0_open = true;
   for (int c = 0;; ++c) {
     const int bank = c & 1;
     RB_CUDA_TRY(cudaGraphLaunch(h->g_cycle[bank].exec, h->us));
-    count_launches((long long)h->cyc * (h->k > 0 ? 5 : 4));
-    int rc = read_state(h);
+    count_launches((long long)h->cyc * passes_per_iter(h));
+    int rc = read_state(h, nrhs);
     if (rc) return rc;
-    const IterState& hs = *h->hst;
+    const IterState& hs = h->hst[0];
     const int nit = hs.iter - iters_before;
     iters_before = hs.iter;
     const bool ok = (hs.status == RB_OK || hs.status == RB_ENOTCONV);
     const bool allowed = (h->o.update_cycles == 0) || (c < h->o.update_cycles);
-    if (ok && allowed && nit > 0) {
+    if (slot0_open && ok && allowed && nit > 0) {
       const int ns = nit - (hs.half ? 1 : 0);
       const auto t0 = std::chrono::steady_clock::now();
       rc = cycle_update<T>(h, bank, nit, ns);
@@ -720,27 +826,210 @@ int iterate_cycles(rb_ctx* h, SolveOut* so) {
       if (rc) return rc;
       so->cycles += 1;
     }
-    if (hs.done) break;
+    if (hs.done) slot0_open = false;
+    if (all_done(h, nrhs)) break;
   }
   return RB_OK;
 }
 
-int finish_solve(rb_ctx* h, SolveOut* so, bool check) {
+// Alg. 2 step 8 (x = x - U x_c) and the FP64 true residual of every slot.
+int finish_block(rb_ctx* h, int nrhs, SolveOut* so) {
   const int64_t ld = h->npad;
-  if (h->k > 0)   // Alg. 2 step 8: x = x - U x_c
-    RB_CUDA_TRY(gemv_update(h->x, h->U, ld, h->k, h->st->xc, nullptr, -1.0, h->npad, vec_grid(h), h->us));
-  if (check) {
-    RB_CUDA_TRY(residual_norm(h->A.view(), h->b, h->x, h->tmp, h->npad, h->st, h->partials, h->grids.spmv, h->us));
-    so->mv_check += 1;
+  for (int i = 0; i < nrhs; ++i) {
+    if (h->k > 0)
+      RB_CUDA_TRY(gemv_update(h->sl[i].x, h->U, ld, h->k, h->st[i].xc, nullptr, -1.0, h->npad, vec_grid(h), h->us));
+    RB_CUDA_TRY(residual_norm(h->A.view(), h->sl[i].b, h->sl[i].x, h->tmp, h->npad, h->st + i, h->partials,
+                              h->grids.spmv, h->us));
+    so[i].mv_check += 1;
   }
-  return read_state(h);
+  return read_state(h, nrhs);
+}
+
+// U_next = Y (promoted to FP64 when the candidate is FP32), U~_next = U_next,
+// and Alg. 2 step 1 for the new space.
+template <typename T>
+int adopt_candidate(rb_ctx* h, SolveOut* so) {
+  const int64_t ld = h->npad;
+  if (std::is_same<T, float>::value) {
+    for (int j = 0; j < h->kY; ++j)
+      RB_CUDA_TRY(to_double((const float*)h->Yc + (int64_t)j * ld, h->U + (int64_t)j * ld, ld, h->us));
+  } else {
+    RB_CUDA_TRY(cudaMemcpyAsync(h->U, h->Yc, sizeof(double) * ld * h->kY, cudaMemcpyDeviceToDevice, h->us));
+  }
+  RB_CUDA_TRY(cudaMemcpyAsync(h->Ut, h->U, sizeof(double) * ld * h->kY, cudaMemcpyDeviceToDevice, h->us));
+  int64_t mv = 0;
+  const auto t0 = std::chrono::steady_clock::now();
+  int rc = recycle_setup(h, h->kY, &mv);
+  so->ms_update += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  if (rc < 0) return rc;
+  so->mv_setup += mv;
+  h->update_epoch = h->matrix_epoch;
+  return RB_OK;
+}
+
+bool update_now(rb_ctx* h) {
+  return (h->o.recycle_mode == RB_RECYCLE_UPDATE_ALL) ||
+         (h->o.recycle_mode == RB_RECYCLE_UPDATE_FIRST && h->update_epoch != h->matrix_epoch);
+}
+
+int solve_fp64(rb_ctx* h, int nrhs, const bool* x_nonzero, SolveOut* so) {
+  double* rhs[kMaxRhs];
+  double* xb[kMaxRhs];
+  double tol[kMaxRhs];
+  bool skip[kMaxRhs] = {false, false, false, false};
+  for (int i = 0; i < nrhs; ++i) {
+    rhs[i] = h->sl[i].b;
+    xb[i] = h->sl[i].x;
+    tol[i] = h->o.tol;
+  }
+  int rc = setup_block(h, nrhs, rhs, xb, x_nonzero, skip, tol, so);
+  if (rc) return rc;
+  const bool upd = update_now(h);
+  if (!all_done(h, nrhs)) {
+    if ((rc = init_p<double>(h, nrhs, upd))) return rc;
+    rc = upd ? iterate_cycles<double>(h, nrhs, so) : iterate_plain<double>(h, nrhs);
+    if (rc) return rc;
+  }
+  rc = finish_block(h, nrhs, so);
+  if (rc) return rc;
+  for (int i = 0; i < nrhs; ++i) {
+    const IterState& hs = h->hst[i];
+    so[i].status = hs.status;
+    so[i].iters = hs.iter;
+    so[i].mv += 2 * (int64_t)hs.iter - (hs.half ? 1 : 0);
+    so[i].relres_rec = hs.bnorm2 > 0 ? std::sqrt(hs.rnorm2 / hs.bnorm2) : 0.0;
+    so[i].relres_true = hs.bnorm2 > 0 ? std::sqrt(hs.red[0] / hs.bnorm2) : 0.0;
+    so[i].bytes = (double)hs.iter * iter_bytes(h, h->k, 8, 8, nrhs);
+  }
+  if (upd && (h->hst[0].status == RB_OK || h->hst[0].status == RB_ENOTCONV) && h->kY > 0) {
+    rc = adopt_candidate<double>(h, so);
+    if (rc) return rc;
+  }
+  return RB_OK;
+}
+
+// Mixed precision: FP64 iterative refinement around an FP32 inner RBiCGSTAB.
+// Outer (per slot): r = b - A x in FP64; inner: A d = r with FP32 vectors,
+// FP32 SpMV and FP32 recycle blocks, FP64-class dot products and FP64
+// scalars, all unconverged slots together; x += d in FP64.  The refinement
+// aims for a tenth of the tolerance, so the last FP32 correction leaves a
+// forward error comparable to the FP64 solver's at the tolerance itself.
+int solve_mixed(rb_ctx* h, int nrhs, SolveOut* so) {
+  const int64_t ld = h->npad;
+  const int max_outer = 12;
+  const int max_itn = h->o.max_itn > 0 ? h->o.max_itn : (int)std::min<int64_t>(h->n, 20000);
+  double bn2[kMaxRhs], target[kMaxRhs], rn[kMaxRhs];
+  bool stop[kMaxRhs];
+  int total_it[kMaxRhs], last_status[kMaxRhs];
+  for (int i = 0; i < nrhs; ++i) {
+    bn2[i] = h->hst[i].red[0];
+    target[i] = 0.1 * h->o.tol * std::sqrt(bn2[i]);
+    rn[i] = 0.0;
+    stop[i] = false;
+    total_it[i] = 0;
+    last_status[i] = RB_OK;
+    so[i].outer = 0;
+  }
+  const bool upd = update_now(h);
+  bool did_update = false;
+  for (;;) {
+    bool any = false;
+    bool skip[kMaxRhs] = {true, true, true, true};
+    bool xnz[kMaxRhs] = {false, false, false, false};
+    double* rhs[kMaxRhs];
+    double* xb[kMaxRhs];
+    double tol_in[kMaxRhs];
+    for (int i = 0; i < nrhs; ++i) {
+      rhs[i] = h->sl[i].rin;
+      xb[i] = h->sl[i].xin;
+      tol_in[i] = 1e-6;
+      if (stop[i]) continue;
+      RB_CUDA_TRY(residual_norm(h->A.view(), h->sl[i].b, h->sl[i].x, h->sl[i].rin, h->npad, h->st + i, h->partials,
+                                h->grids.spmv, h->us));
+      so[i].mv_check += 1;
+    }
+    int rc = read_state(h, nrhs);
+    if (rc) return rc;
+    for (int i = 0; i < nrhs; ++i) {
+      if (stop[i]) continue;
+      rn[i] = std::sqrt(h->hst[i].red[0]);
+      if (!std::isfinite(rn[i])) {
+        so[i].status = RB_ENONFINITE;
+        stop[i] = true;
+      } else if (rn[i] <= target[i] || bn2[i] == 0.0) {
+        so[i].status = RB_OK;
+        stop[i] = true;
+      } else if (so[i].outer >= max_outer || total_it[i] >= max_itn) {
+        so[i].status = last_status[i] != RB_OK ? last_status[i] : RB_ENOTCONV;
+        stop[i] = true;
+      } else {
+        // inner system A d = r_outer, tolerance relative to ||r_outer||
+        skip[i] = false;
+        any = true;
+        tol_in[i] = std::max(target[i] / rn[i], 1e-6);
+      }
+    }
+    if (!any) break;
+    for (int i = 0; i < nrhs; ++i) {
+      if (skip[i]) continue;
+      RB_CUDA_TRY(cudaMemcpyAsync(&h->st[i].bnorm2, &h->st[i].red[0], sizeof(double), cudaMemcpyDeviceToDevice,
+                                  h->us));
+      RB_CUDA_TRY(cudaMemsetAsync(h->sl[i].xin, 0, sizeof(double) * ld, h->us));
+    }
+    rc = setup_block(h, nrhs, rhs, xb, xnz, skip, tol_in, so);
+    if (rc) return rc;
+    RB_CUDA_TRY(to_float(h->rt0, h->frt0, ld, h->us));
+    for (int i = 0; i < nrhs; ++i) {
+      if (skip[i]) continue;
+      RB_CUDA_TRY(to_float(h->sl[i].r, h->sl[i].fr, ld, h->us));
+      RB_CUDA_TRY(to_float(h->sl[i].xin, h->sl[i].fx, ld, h->us));
+    }
+    const bool cyc_now = upd && !did_update && !skip[0];
+    if (!all_done(h, nrhs)) {
+      if ((rc = init_p<float>(h, nrhs, cyc_now))) return rc;
+      if (cyc_now) {
+        // the first (longest) inner solve collects the cycles of the update
+        rc = iterate_cycles<float>(h, nrhs, so);
+        did_update = true;
+      } else {
+        rc = iterate_plain<float>(h, nrhs);
+      }
+      if (rc) return rc;
+    }
+    for (int i = 0; i < nrhs; ++i) {
+      if (skip[i]) continue;
+      const IterState& hs = h->hst[i];
+      total_it[i] += hs.iter;
+      so[i].mv += 2 * (int64_t)hs.iter - (hs.half ? 1 : 0);
+      last_status[i] = hs.status;
+      so[i].outer += 1;
+      // x += d, d = x_inner - U x_c (Alg. 2 step 8 of the inner solve)
+      RB_CUDA_TRY(add_float_to_double(h->sl[i].x, h->sl[i].fx, ld, h->us));
+      if (h->k > 0)
+        RB_CUDA_TRY(gemv_update(h->sl[i].x, h->U, ld, h->k, h->st[i].xc, nullptr, -1.0, h->npad, vec_grid(h), h->us));
+      if (hs.status != RB_OK && hs.status != RB_ENOTCONV) {
+        so[i].status = hs.status;
+        stop[i] = true;
+      }
+    }
+  }
+  for (int i = 0; i < nrhs; ++i) {
+    so[i].iters = total_it[i];
+    so[i].relres_true = bn2[i] > 0 ? rn[i] / std::sqrt(bn2[i]) : 0.0;
+    so[i].relres_rec = so[i].relres_true;
+    so[i].bytes = (double)total_it[i] * iter_bytes(h, h->k, 4, 4, nrhs);
+  }
+  if (did_update && h->kY > 0 && (so[0].status == RB_OK || so[0].status == RB_ENOTCONV)) {
+    int rc = adopt_candidate<float>(h, so);
+    if (rc) return rc;
+  }
+  return sync(h);
 }
 
 }  // namespace
 
 // ============================================================ C ABI
 static void release_a32(rb_ctx* h);
-
 
 extern "C" const char* rbicgstab_error_string(int status) {
   switch (status) {
@@ -784,11 +1073,11 @@ extern "C" int rbicgstab_create(rb_handle* out, const rb_opts* opts) {
   if (cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, h->dev) != cudaSuccess)
     return fail(RB_ECUDA);
   if (cudaStreamCreateWithFlags(&h->cs, cudaStreamNonBlocking) != cudaSuccess) return fail(RB_ECUDA);
-  h->st = dalloc<IterState>(1, &err);
+  h->st = dalloc<IterState>(kMaxRhs, &err);
   if (!h->st) return fail(err);
-  if (cudaMemset(h->st, 0, sizeof(IterState)) != cudaSuccess) return fail(RB_ECUDA);
-  if (cudaMallocHost(&h->hst, sizeof(IterState)) != cudaSuccess) return fail(RB_ENOMEM);
-  std::memset(h->hst, 0, sizeof(IterState));
+  if (cudaMemset(h->st, 0, sizeof(IterState) * kMaxRhs) != cudaSuccess) return fail(RB_ECUDA);
+  if (cudaMallocHost(&h->hst, sizeof(IterState) * kMaxRhs) != cudaSuccess) return fail(RB_ENOMEM);
+  std::memset(h->hst, 0, sizeof(IterState) * kMaxRhs);
   h->dflag = dalloc<int>(1, &err);
   if (!h->dflag) return fail(err);
   h->kcap = o.k_max;
@@ -810,12 +1099,11 @@ extern "C" int rbicgstab_destroy(rb_handle h) {
   release_a32(h);
   sell_free(&h->A);
   sell_free(&h->AT);
+  for (int i = 0; i < h->nslots; ++i) free_slot(h->sl[i]);
   void* ptrs[] = {h->rp, h->ci, h->cv, h->trp, h->tci, h->tsrc, h->tcv, h->U, h->Ut, h->C, h->Ct,
-                  h->Chat, h->T1, h->T2, h->Dinv, h->b, h->x, h->r, h->p, h->s, h->q, h->t,
-                  h->qraw, h->traw, h->rt0, h->tmp, h->rin, h->xin, h->fx, h->fr, h->fp, h->fs, h->fq, h->ft,
-                  h->fqraw, h->ftraw, h->frt0, h->fU, h->fC, h->fChat, h->st, h->partials,
-                  h->dflag, h->cstore, h->Yc, h->AYc, h->Yn, h->AYn, h->gwork, h->dG, h->dR,
-                  (void*)h->dptr};
+                  h->Chat, h->T1, h->T2, h->Dinv, h->rt0, h->tmp, h->tmp2, h->frt0, h->fU, h->fC, h->fChat,
+                  h->st, h->partials, h->dflag, h->cstore, h->Yc, h->AYc, h->Yn, h->AYn, h->gwork, h->dG,
+                  h->dR, (void*)h->dptr};
   for (void* p : ptrs) cudaFree(p);
   if (h->hst) cudaFreeHost(h->hst);
   if (h->cs) cudaStreamDestroy(h->cs);
@@ -845,7 +1133,7 @@ static int build_matrix_values(rb_ctx* h) {
 }
 
 extern "C" int rbicgstab_set_matrix(rb_handle h, int64_t n, int64_t nnz, const int32_t* row_ptr,
-                         const int32_t* col, const double* val, int where) {
+                                    const int32_t* col, const double* val, int where) {
   if (!h || n <= 0 || nnz < 0 || n >= (1ll << 31) || nnz >= (1ll << 31) || !row_ptr ||
       (nnz > 0 && (!col || !val)) || (where != RB_HOST && where != RB_DEVICE))
     return RB_EINVAL;
@@ -910,9 +1198,7 @@ extern "C" int rbicgstab_set_matrix(rb_handle h, int64_t n, int64_t nnz, const i
   const int kin = h->k;
   if (kin > 0) {
     int64_t mv = 0;
-    rc = recycle_setup(h, kin, &mv);
-    if (rc < 0) return rc;
-    return rc;
+    return recycle_setup(h, kin, &mv);
   }
   return RB_OK;
 }
@@ -937,7 +1223,7 @@ extern "C" int rbicgstab_set_values(rb_handle h, const double* val, int where) {
 }
 
 extern "C" int rbicgstab_set_recycle(rb_handle h, int32_t k, const double* U, const double* Ut, int64_t ld,
-                          int where) {
+                                     int where) {
   if (!h || k < 0 || (where != RB_HOST && where != RB_DEVICE)) return RB_EINVAL;
   if (k > h->kcap) return RB_EINVAL;
   if (!h->have_matrix) return RB_EDIM;
@@ -951,17 +1237,15 @@ extern "C" int rbicgstab_set_recycle(rb_handle h, int32_t k, const double* U, co
     if (rc) return rc;
   }
   if (k > 0) {
-    RB_CUDA_TRY(check_finite(h->U, npad * k, h->dflag, h->us));
-    int f1 = 0;
-    RB_CUDA_TRY(cudaMemcpyAsync(&f1, h->dflag, sizeof(int), cudaMemcpyDeviceToHost, h->us));
-    rc = sync(h);
-    if (rc) return rc;
-    RB_CUDA_TRY(check_finite(h->Ut, npad * k, h->dflag, h->us));
-    int f2 = 0;
-    RB_CUDA_TRY(cudaMemcpyAsync(&f2, h->dflag, sizeof(int), cudaMemcpyDeviceToHost, h->us));
-    rc = sync(h);
-    if (rc) return rc;
-    if (f1 || f2) {
+    int f[2] = {0, 0};
+    double* blocks[2] = {h->U, h->Ut};
+    for (int q = 0; q < 2; ++q) {
+      RB_CUDA_TRY(check_finite(blocks[q], npad * k, h->dflag, h->us));
+      RB_CUDA_TRY(cudaMemcpyAsync(&f[q], h->dflag, sizeof(int), cudaMemcpyDeviceToHost, h->us));
+      rc = sync(h);
+      if (rc) return rc;
+    }
+    if (f[0] || f[1]) {
       h->k = 0;
       reset_graphs(h);
       return RB_ENONFINITE;
@@ -991,15 +1275,15 @@ extern "C" int rbicgstab_apply(rb_handle h, const double* v, double* y, int tran
   if (!h->have_matrix) return RB_EDIM;
   int rc = copy_in(h->tmp, v, sizeof(double) * h->n, where, h->us);
   if (rc) return rc;
-  RB_CUDA_TRY(spmv<double>(transpose ? h->AT.view() : h->A.view(), h->tmp, h->qraw, 1.0, 0.0,
+  RB_CUDA_TRY(spmv<double>(transpose ? h->AT.view() : h->A.view(), h->tmp, h->tmp2, 1.0, 0.0,
                            h->grids.spmv, h->us));
-  rc = copy_out(y, h->qraw, sizeof(double) * h->n, where, h->us);
+  rc = copy_out(y, h->tmp2, sizeof(double) * h->n, where, h->us);
   if (rc) return rc;
   return sync(h);
 }
 
 extern "C" int rbicgstab_harmonic_ritz(int32_t m, const double* G, const double* H, int32_t k, double* Y,
-                            double* theta_re, double* theta_im, int32_t* k_used) {
+                                       double* theta_re, double* theta_im, int32_t* k_used) {
   if (m <= 0 || k <= 0 || k > m || !G || !H || !Y || !k_used) return RB_EINVAL;
   const int r = rb::harmonic_ritz(m, G, H, k, kRankTol, Y, theta_re, theta_im);
   if (r < 0) return RB_ENOTCONV;
@@ -1007,210 +1291,109 @@ extern "C" int rbicgstab_harmonic_ritz(int32_t m, const double* G, const double*
   return RB_OK;
 }
 
-static int solve_fp64(rb_ctx* h, SolveOut* so, bool x_nonzero) {
-  int rc = setup_solve(h, h->b, h->x, x_nonzero, h->o.tol, so);
-  if (rc) return rc;
-  const bool upd = (h->o.recycle_mode == RB_RECYCLE_UPDATE_ALL) ||
-                   (h->o.recycle_mode == RB_RECYCLE_UPDATE_FIRST && h->update_epoch != h->matrix_epoch);
-  if (!h->hst->done) {
-    if (upd) {
-      rc = iterate_cycles<double>(h, so);
-    } else {
-      // p_1 = r_0 (Alg. 2 step 4 with beta_0 = 0)
-      RB_CUDA_TRY(cudaMemcpyAsync(h->p, h->r, sizeof(double) * h->npad, cudaMemcpyDeviceToDevice, h->us));
-      rc = iterate_plain<double>(h);
-    }
-    if (rc) return rc;
-  }
-  rc = finish_solve(h, so, true);
-  if (rc) return rc;
-  const IterState& hs = *h->hst;
-  so->status = hs.status;
-  so->iters = hs.iter;
-  so->mv += 2 * (int64_t)hs.iter - (hs.half ? 1 : 0);
-  so->relres_rec = std::sqrt(hs.rnorm2 / hs.bnorm2);
-  so->relres_true = std::sqrt(hs.red[0] / hs.bnorm2);
-  if (hs.bnorm2 == 0) so->relres_rec = so->relres_true = 0.0;
-  so->bytes = (double)hs.iter * iter_bytes(h, h->k, 8, 8);
-  if (upd && (hs.status == RB_OK || hs.status == RB_ENOTCONV) && h->kY > 0) {
-    // U_next = Y (unit columns), U~_next = U_next; recompute C, C~, D_c
-    const int64_t ld = h->npad;
-    RB_CUDA_TRY(cudaMemcpyAsync(h->U, h->Yc, sizeof(double) * ld * h->kY, cudaMemcpyDeviceToDevice, h->us));
-    RB_CUDA_TRY(cudaMemcpyAsync(h->Ut, h->Yc, sizeof(double) * ld * h->kY, cudaMemcpyDeviceToDevice, h->us));
-    int64_t mv = 0;
-    const auto t0 = std::chrono::steady_clock::now();
-    rc = recycle_setup(h, h->kY, &mv);
-    so->ms_update += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
-    if (rc < 0) return rc;
-    so->mv_setup += mv;
-    h->update_epoch = h->matrix_epoch;
-  }
-  return RB_OK;
-}
-
-
-// Mixed precision: FP64 iterative refinement around an FP32 inner RBiCGSTAB.
-// Outer: r = b - A x in FP64; inner: A d = r with FP32 vectors, FP32 SpMV and
-// FP32 recycle blocks, FP64 dot products and scalars; x += d in FP64.
-static int solve_mixed(rb_ctx* h, SolveOut* so, bool x_nonzero) {
-  const int64_t ld = h->npad;
-  (void)x_nonzero;
-  const double bn2 = h->hst->red[0];
-  // refine to a tenth of the tolerance: the last FP32 correction then leaves
-  // a forward error comparable to the FP64 solver's at the tolerance itself
-  const double target = 0.1 * h->o.tol * std::sqrt(bn2);
-  const int max_outer = 12;
-  int outer = 0, total_it = 0, last_status = RB_OK;
-  const bool upd = (h->o.recycle_mode == RB_RECYCLE_UPDATE_ALL) ||
-                   (h->o.recycle_mode == RB_RECYCLE_UPDATE_FIRST && h->update_epoch != h->matrix_epoch);
-  bool did_update = false;
-  double rn = 0.0;
-  for (;;) {
-    RB_CUDA_TRY(residual_norm(h->A.view(), h->b, h->x, h->rin, h->npad, h->st, h->partials, h->grids.spmv, h->us));
-    so->mv_check += 1;
-    int rc = read_state(h);
-    if (rc) return rc;
-    rn = std::sqrt(h->hst->red[0]);
-    if (!std::isfinite(rn)) { so->status = RB_ENONFINITE; break; }
-    if (rn <= target || bn2 == 0.0) { so->status = RB_OK; break; }
-    if (outer >= max_outer || total_it >= (h->o.max_itn > 0 ? h->o.max_itn : (int)std::min<int64_t>(h->n, 20000))) {
-      so->status = last_status != RB_OK ? last_status : RB_ENOTCONV;
-      break;
-    }
-    // inner system A d = r_outer, tolerance relative to ||r_outer||
-    const double tol_in = std::max(target / rn, 1e-6);
-    RB_CUDA_TRY(cudaMemcpyAsync(&h->st->bnorm2, &h->st->red[0], sizeof(double), cudaMemcpyDeviceToDevice, h->us));
-    RB_CUDA_TRY(cudaMemsetAsync(h->xin, 0, sizeof(double) * ld, h->us));
-    rc = setup_solve(h, h->rin, h->xin, false, tol_in, so);
-    if (rc) return rc;
-    RB_CUDA_TRY(to_float(h->r, h->fr, ld, h->us));
-    RB_CUDA_TRY(to_float(h->r, h->fp, ld, h->us));
-    RB_CUDA_TRY(to_float(h->rt0, h->frt0, ld, h->us));
-    RB_CUDA_TRY(to_float(h->xin, h->fx, ld, h->us));
-    if (!h->hst->done) {
-      if (upd && !did_update) {
-        // the first (longest) inner solve collects the cycles of the update
-        rc = iterate_cycles<float>(h, so);
-        did_update = true;
-      } else {
-        rc = iterate_plain<float>(h);
-      }
-      if (rc) return rc;
-    }
-    rc = read_state(h);
-    if (rc) return rc;
-    const IterState& hs = *h->hst;
-    total_it += hs.iter;
-    so->mv += 2 * (int64_t)hs.iter - (hs.half ? 1 : 0);
-    last_status = hs.status;
-    // x += d, d = x_inner - U x_c (Alg. 2 step 8 of the inner solve)
-    RB_CUDA_TRY(add_float_to_double(h->x, h->fx, ld, h->us));
-    if (h->k > 0)
-      RB_CUDA_TRY(gemv_update(h->x, h->U, ld, h->k, h->st->xc, nullptr, -1.0, h->npad, vec_grid(h), h->us));
-    ++outer;
-    if (hs.status != RB_OK && hs.status != RB_ENOTCONV) { so->status = hs.status; break; }
-  }
-  so->iters = total_it;
-  so->seeds = 1;
-  so->relres_true = bn2 > 0 ? rn / std::sqrt(bn2) : 0.0;
-  so->relres_rec = so->relres_true;
-  so->bytes = (double)total_it * iter_bytes(h, h->k, 4, 4);
-  so->outer = outer;
-  if (did_update && h->kY > 0 && (so->status == RB_OK || so->status == RB_ENOTCONV)) {
-    // U_next = Y (FP32 candidate promoted to FP64), U~_next = U_next
-    for (int j = 0; j < h->kY; ++j)
-      RB_CUDA_TRY(to_double((const float*)h->Yc + (int64_t)j * ld, h->U + (int64_t)j * ld, ld, h->us));
-    RB_CUDA_TRY(cudaMemcpyAsync(h->Ut, h->U, sizeof(double) * ld * h->kY, cudaMemcpyDeviceToDevice, h->us));
-    int64_t mv = 0;
-    const auto t0 = std::chrono::steady_clock::now();
-    int rc2 = recycle_setup(h, h->kY, &mv);
-    so->ms_update += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
-    if (rc2 < 0) return rc2;
-    so->mv_setup += mv;
-    h->update_epoch = h->matrix_epoch;
-  }
-  return sync(h);
-}
-
-extern "C" int rbicgstab_solve(rb_handle h, const double* b, double* x, int where, rb_stats* st_out) {
-  if (!h || !b || !x || (where != RB_HOST && where != RB_DEVICE)) return RB_EINVAL;
+extern "C" int rbicgstab_solve_block(rb_handle h, int32_t nrhs, const double* B, double* X, int64_t ld,
+                                     int where, rb_stats* st_out) {
+  if (!h || !B || !X || nrhs < 1 || nrhs > kMaxRhs || (where != RB_HOST && where != RB_DEVICE)) return RB_EINVAL;
   if (!h->have_matrix) return RB_EDIM;
-  cudaEvent_t e0, e1;
-  cudaEventCreate(&e0);
-  cudaEventCreate(&e1);
-  cudaEventRecord(e0, h->us);
-  SolveOut so;
-  int rc = copy_in(h->b, b, sizeof(double) * h->n, where, h->us);
-  if (!rc) rc = copy_in(h->x, x, sizeof(double) * h->n, where, h->us);
+  if (nrhs > 1 && ld < h->n) return RB_EINVAL;
+  int rc = ensure_slots(h, nrhs);
   if (rc) return rc;
-  // finiteness of b and x, ||b||^2, ||x||^2
-  RB_CUDA_TRY(check_finite(h->b, h->n, h->dflag, h->us));
-  int fb = 0, fx = 0;
-  RB_CUDA_TRY(cudaMemcpyAsync(&fb, h->dflag, sizeof(int), cudaMemcpyDeviceToHost, h->us));
-  rc = sync(h);
-  if (rc) return rc;
-  RB_CUDA_TRY(check_finite(h->x, h->n, h->dflag, h->us));
-  RB_CUDA_TRY(cudaMemcpyAsync(&fx, h->dflag, sizeof(int), cudaMemcpyDeviceToHost, h->us));
-  DotArgs d{};
-  d.nd = 2;
-  d.a[0] = h->b; d.b[0] = h->b;
-  d.a[1] = h->x; d.b[1] = h->x;
-  double nb[2];
-  rc = run_dots(h, d, nb, 2);
-  if (rc) return rc;
-  if (fb || fx) return RB_ENONFINITE;
-  RB_CUDA_TRY(cudaMemcpyAsync(&h->st->bnorm2, &h->st->red[0], sizeof(double), cudaMemcpyDeviceToDevice, h->us));
-  const bool x_nonzero = nb[1] != 0.0;
-  h->hst->red[0] = nb[0];
-  rc = (h->o.precision == RB_MIXED) ? solve_mixed(h, &so, x_nonzero) : solve_fp64(h, &so, x_nonzero);
-  if (rc < 0 && rc != RB_ENOTCONV) return rc;
-  rc = copy_out(x, h->x, sizeof(double) * h->n, where, h->us);
-  if (rc) return rc;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  auto done = [&](int code) {
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    return code;
+  };
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return done(RB_ECUDA);
+  if (cudaEventRecord(e0, h->us) != cudaSuccess) return done(RB_ECUDA);
+  SolveOut so[kMaxRhs];
+  bool x_nonzero[kMaxRhs] = {false, false, false, false};
+  for (int i = 0; i < nrhs; ++i) {
+    Slot& s = h->sl[i];
+    rc = copy_in(s.b, B + (int64_t)i * ld, sizeof(double) * h->n, where, h->us);
+    if (!rc) rc = copy_in(s.x, X + (int64_t)i * ld, sizeof(double) * h->n, where, h->us);
+    if (rc) return done(rc);
+    // finiteness of b and x, ||b||^2, ||x||^2
+    int fb = 0, fx = 0;
+    if (check_finite(s.b, h->n, h->dflag, h->us) != cudaSuccess ||
+        cudaMemcpyAsync(&fb, h->dflag, sizeof(int), cudaMemcpyDeviceToHost, h->us) != cudaSuccess)
+      return done(RB_ECUDA);
+    if ((rc = sync(h))) return done(rc);
+    if (check_finite(s.x, h->n, h->dflag, h->us) != cudaSuccess ||
+        cudaMemcpyAsync(&fx, h->dflag, sizeof(int), cudaMemcpyDeviceToHost, h->us) != cudaSuccess)
+      return done(RB_ECUDA);
+    DotArgs d{};
+    d.nd = 2;
+    d.a[0] = s.b; d.b[0] = s.b;
+    d.a[1] = s.x; d.b[1] = s.x;
+    double nb[2];
+    if ((rc = run_dots(h, d, nb, 2, i))) return done(rc);
+    if (fb || fx) return done(RB_ENONFINITE);
+    if (cudaMemcpyAsync(&h->st[i].bnorm2, &h->st[i].red[0], sizeof(double), cudaMemcpyDeviceToDevice, h->us) !=
+        cudaSuccess)
+      return done(RB_ECUDA);
+    x_nonzero[i] = nb[1] != 0.0;
+    h->hst[i].red[0] = nb[0];
+  }
+  rc = (h->o.precision == RB_MIXED) ? solve_mixed(h, nrhs, so) : solve_fp64(h, nrhs, x_nonzero, so);
+  if (rc < 0 && rc != RB_ENOTCONV) return done(rc);
+  for (int i = 0; i < nrhs; ++i) {
+    rc = copy_out(X + (int64_t)i * ld, h->sl[i].x, sizeof(double) * h->n, where, h->us);
+    if (rc) return done(rc);
+  }
   cudaEventRecord(e1, h->us);
-  rc = sync(h);
-  if (rc) return rc;
+  if ((rc = sync(h))) return done(rc);
   float ms = 0;
   cudaEventElapsedTime(&ms, e0, e1);
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
-  if (st_out) {
-    st_out->iters = so.iters;
-    st_out->status = so.status;
-    st_out->k_used = h->k;
-    st_out->seeds_used = so.seeds;
-    st_out->matvecs = so.mv;
-    st_out->matvecs_setup = so.mv_setup;
-    st_out->matvecs_check = so.mv_check;
-    st_out->cycles = so.cycles;
-    st_out->outer = so.outer;
-    st_out->relres_rec = so.relres_rec;
-    st_out->relres_true = so.relres_true;
-    st_out->ms_total = ms;
-    st_out->bytes_model = so.bytes;
-    st_out->ms_update = so.ms_update;
+  int worst = RB_OK;
+  for (int i = 0; i < nrhs; ++i) {
+    if (so[i].status != RB_OK && worst == RB_OK) worst = so[i].status;
+    if (!st_out) continue;
+    rb_stats& o = st_out[i];
+    o.iters = so[i].iters;
+    o.status = so[i].status;
+    o.k_used = h->k;
+    o.seeds_used = so[i].seeds;
+    o.matvecs = so[i].mv;
+    o.matvecs_setup = so[0].mv_setup;
+    o.matvecs_check = so[i].mv_check;
+    o.cycles = so[0].cycles;
+    o.outer = so[i].outer;
+    o.relres_rec = so[i].relres_rec;
+    o.relres_true = so[i].relres_true;
+    o.ms_total = ms;
+    o.bytes_model = so[i].bytes;
+    o.ms_update = so[0].ms_update;
   }
-  return so.status;
+  return done(worst);
 }
 
+extern "C" int rbicgstab_solve(rb_handle h, const double* b, double* x, int where, rb_stats* st) {
+  return rbicgstab_solve_block(h, 1, b, x, h ? h->n : 0, where, st);
+}
 
 // Benchmark helper: average duration of each pass kernel, measured with CUDA
-// events on the handle's stream over `reps` iterations started from b.
+// events on the handle's stream over `reps` iterations started from B.
 template <typename T>
-static int time_passes_t(rb_ctx* h, int reps, double* ms) {
-  IterArgs<T> a = base_args<T>(h);
+static int time_passes_t(rb_ctx* h, int nrhs, int reps, double* ms) {
+  IterArgs<T> a = base_args<T>(h, nrhs);
   Grids g;
-  iteration_grids<T>(h->k, h->nsm, h->npad, &g);
+  iteration_grids<T>(h->k, h->nsm, h->npad, &g, nrhs);
   const int npass = 5;
   std::vector<cudaEvent_t> ev((size_t)reps * npass * 2);
   for (auto& e : ev) cudaEventCreate(&e);
-  for (int it = 0; it < reps; ++it)
+  int rc = RB_OK;
+  for (int it = 0; it < reps && !rc; ++it)
     for (int pz = 0; pz < npass; ++pz) {
       if (pz == P4 && h->k == 0) continue;
-      RB_CUDA_TRY(cudaEventRecord(ev[(it * npass + pz) * 2], h->us));
-      RB_CUDA_TRY(launch_pass<T>(pz, a, h->k, g, h->us));
-      RB_CUDA_TRY(cudaEventRecord(ev[(it * npass + pz) * 2 + 1], h->us));
+      if (cudaEventRecord(ev[(it * npass + pz) * 2], h->us) != cudaSuccess ||
+          launch_pass<T>(pz, a, h->k, g, h->us) != cudaSuccess ||
+          cudaEventRecord(ev[(it * npass + pz) * 2 + 1], h->us) != cudaSuccess) {
+        rc = RB_ECUDA;
+        break;
+      }
     }
-  int rc = read_state(h);
+  if (!rc) rc = read_state(h, nrhs);
   for (int pz = 0; pz < npass; ++pz) ms[pz] = 0.0;
   if (!rc) {
     for (int it = 0; it < reps; ++it)
@@ -1223,37 +1406,58 @@ static int time_passes_t(rb_ctx* h, int reps, double* ms) {
   }
   for (auto& e : ev) cudaEventDestroy(e);
   if (rc) return rc;
-  return h->hst->done ? (h->hst->status ? h->hst->status : RB_EBREAKDOWN_OMEGA) : RB_OK;
+  for (int i = 0; i < nrhs; ++i)
+    if (h->hst[i].done) return h->hst[i].status ? h->hst[i].status : RB_EBREAKDOWN_OMEGA;
+  return RB_OK;
 }
 
-extern "C" int rbicgstab_time_passes(rb_handle h, const double* b, int where, int32_t reps, double* ms) {
-  if (!h || !b || !ms || reps < 1 || reps > 1000 || (where != RB_HOST && where != RB_DEVICE)) return RB_EINVAL;
+extern "C" int rbicgstab_time_passes(rb_handle h, int32_t nrhs, const double* B, int64_t ld, int where,
+                                     int32_t reps, double* ms) {
+  if (!h || !B || !ms || reps < 1 || reps > 1000 || nrhs < 1 || nrhs > kMaxRhs ||
+      (where != RB_HOST && where != RB_DEVICE))
+    return RB_EINVAL;
   if (!h->have_matrix) return RB_EDIM;
-  int rc = copy_in(h->b, b, sizeof(double) * h->n, where, h->us);
+  if (nrhs > 1 && ld < h->n) return RB_EINVAL;
+  int rc = ensure_slots(h, nrhs);
   if (rc) return rc;
-  RB_CUDA_TRY(cudaMemsetAsync(h->x, 0, sizeof(double) * h->npad, h->us));
-  DotArgs d{};
-  d.nd = 1;
-  d.a[0] = h->b; d.b[0] = h->b;
-  double nb = 0;
-  rc = run_dots(h, d, &nb, 1);
-  if (rc) return rc;
-  RB_CUDA_TRY(cudaMemcpyAsync(&h->st->bnorm2, &h->st->red[0], sizeof(double), cudaMemcpyDeviceToDevice, h->us));
-  SolveOut so;
-  rc = setup_solve(h, h->b, h->x, false, 1e-300, &so);
-  if (rc) return rc;
-  RB_CUDA_TRY(cudaMemcpyAsync(h->p, h->r, sizeof(double) * h->npad, cudaMemcpyDeviceToDevice, h->us));
-  rc = read_state(h);
-  if (rc) return rc;
-  if (h->hst->done) return h->hst->status ? h->hst->status : RB_EINVAL;
-  if (h->o.precision == RB_MIXED) {
-    RB_CUDA_TRY(to_float(h->r, h->fr, h->npad, h->us));
-    RB_CUDA_TRY(to_float(h->r, h->fp, h->npad, h->us));
-    RB_CUDA_TRY(to_float(h->rt0, h->frt0, h->npad, h->us));
-    RB_CUDA_TRY(cudaMemsetAsync(h->fx, 0, sizeof(float) * h->npad, h->us));
-    return time_passes_t<float>(h, reps, ms);
+  SolveOut so[kMaxRhs];
+  double* rhs[kMaxRhs];
+  double* xb[kMaxRhs];
+  double tol[kMaxRhs];
+  bool xnz[kMaxRhs] = {false, false, false, false}, skip[kMaxRhs] = {false, false, false, false};
+  for (int i = 0; i < nrhs; ++i) {
+    Slot& s = h->sl[i];
+    rc = copy_in(s.b, B + (int64_t)i * ld, sizeof(double) * h->n, where, h->us);
+    if (rc) return rc;
+    RB_CUDA_TRY(cudaMemsetAsync(s.x, 0, sizeof(double) * h->npad, h->us));
+    DotArgs d{};
+    d.nd = 1;
+    d.a[0] = s.b; d.b[0] = s.b;
+    double nb = 0;
+    if ((rc = run_dots(h, d, &nb, 1, i))) return rc;
+    RB_CUDA_TRY(cudaMemcpyAsync(&h->st[i].bnorm2, &h->st[i].red[0], sizeof(double), cudaMemcpyDeviceToDevice,
+                                h->us));
+    rhs[i] = s.b;
+    xb[i] = s.x;
+    tol[i] = 1e-300;
   }
-  return time_passes_t<double>(h, reps, ms);
+  rc = setup_block(h, nrhs, rhs, xb, xnz, skip, tol, so);
+  if (rc) return rc;
+  rc = read_state(h, nrhs);
+  if (rc) return rc;
+  for (int i = 0; i < nrhs; ++i)
+    if (h->hst[i].done) return h->hst[i].status ? h->hst[i].status : RB_EINVAL;
+  if (h->o.precision == RB_MIXED) {
+    RB_CUDA_TRY(to_float(h->rt0, h->frt0, h->npad, h->us));
+    for (int i = 0; i < nrhs; ++i) {
+      RB_CUDA_TRY(to_float(h->sl[i].r, h->sl[i].fr, h->npad, h->us));
+      RB_CUDA_TRY(cudaMemsetAsync(h->sl[i].fx, 0, sizeof(float) * h->npad, h->us));
+    }
+    if ((rc = init_p<float>(h, nrhs, false))) return rc;
+    return time_passes_t<float>(h, nrhs, reps, ms);
+  }
+  if ((rc = init_p<double>(h, nrhs, false))) return rc;
+  return time_passes_t<double>(h, nrhs, reps, ms);
 }
 
 extern "C" long long rbicgstab_kernel_launches(void) { return g_launches.load(); }

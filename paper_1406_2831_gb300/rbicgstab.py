@@ -86,7 +86,8 @@ def lib():
     L.rbicgstab_solve.argtypes = [vp, dp, dp, ctypes.c_int, ctypes.POINTER(Stats)]
     L.rbicgstab_apply.argtypes = [vp, dp, dp, ctypes.c_int, ctypes.c_int]
     L.rbicgstab_harmonic_ritz.argtypes = [i32, dp, dp, i32, dp, dp, dp, ctypes.POINTER(i32)]
-    L.rbicgstab_time_passes.argtypes = [vp, dp, ctypes.c_int, i32, dp]
+    L.rbicgstab_solve_block.argtypes = [vp, i32, dp, dp, i64, ctypes.c_int, ctypes.POINTER(Stats)]
+    L.rbicgstab_time_passes.argtypes = [vp, i32, dp, i64, ctypes.c_int, i32, dp]
     L.rbicgstab_residual_noalloc.argtypes = [i64, dp, dp, dp, dp, dp, dp, dp, vp]
     L.rbicgstab_residual_noalloc.restype = ctypes.c_int
     L.rbicgstab_kernel_launches.argtypes = []
@@ -95,7 +96,7 @@ def lib():
     L.rbicgstab_error_string.restype = ctypes.c_char_p
     for name in ("rbicgstab_create", "rbicgstab_destroy", "rbicgstab_set_matrix", "rbicgstab_set_values",
                  "rbicgstab_set_recycle", "rbicgstab_get_recycle", "rbicgstab_solve", "rbicgstab_apply",
-                 "rbicgstab_harmonic_ritz", "rbicgstab_time_passes"):
+                 "rbicgstab_harmonic_ritz", "rbicgstab_time_passes", "rbicgstab_solve_block"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -249,6 +250,33 @@ class Solver:
         _check(lib().rbicgstab_solve(self._h, bp, xp, wb, ctypes.byref(st)), "rbicgstab_solve")
         return SolveResult(x=x, stats=st.as_dict())
 
+    def solve_block(self, B, X=None):
+        """Blocked solve of the nrhs <= RB_MAX_RHS systems A x_i = b_i given
+        as the rows of B (shape (nrhs, n); numpy array or CUDA tensor).  X
+        (same shape, updated in place when given) holds the initial guesses.
+        Returns SolveResult with x = X and stats = one dict per system."""
+        if X is None:
+            if _is_torch(B):
+                import torch
+                X = torch.zeros_like(B)
+            else:
+                X = np.zeros(np.shape(B))
+        if len(np.shape(B)) != 2 or tuple(np.shape(B)) != tuple(np.shape(X)):
+            raise ValueError("B and X must both have shape (nrhs, n)")
+        nrhs, n = int(np.shape(B)[0]), int(np.shape(B)[1])
+        bp, wb, kb = _ptr(B, np.float64)
+        if _is_torch(X):
+            xp, wx, kx = _ptr(X, np.float64)
+        else:
+            if not (isinstance(X, np.ndarray) and X.dtype == np.float64 and X.flags.c_contiguous):
+                X = np.ascontiguousarray(X, dtype=np.float64)
+            xp, wx, kx = X.ctypes.data, RB_HOST, X
+        if wb != wx:
+            raise ValueError("B and X must live in the same memory space")
+        st = (Stats * max(nrhs, 1))()
+        _check(lib().rbicgstab_solve_block(self._h, nrhs, bp, xp, n, wb, st), "rbicgstab_solve_block")
+        return SolveResult(x=X, stats=[st[i].as_dict() for i in range(nrhs)])
+
     def apply(self, v, transpose=False):
         """y = A v (or A^T v) with the library's SpMV."""
         vp, w, keep = _ptr(v, np.float64)
@@ -285,10 +313,13 @@ def kernel_launches() -> int:
 
 
 def time_passes(solver: "Solver", b, reps: int = 10):
-    """Average ms of passes P1..P5 (rbicgstab_time_passes); returns (ms[5], status)."""
+    """Average ms of passes P1..P5 (rbicgstab_time_passes) for one right-hand
+    side (b of shape (n,)) or a block (shape (nrhs, n)); returns (ms[5], status)."""
+    shape = tuple(np.shape(b))
+    nrhs, n = (1, shape[0]) if len(shape) == 1 else shape
     bp, w, keep = _ptr(b, np.float64)
     ms = np.zeros(5)
-    code = lib().rbicgstab_time_passes(solver._h, bp, w, int(reps), ms.ctypes.data)
+    code = lib().rbicgstab_time_passes(solver._h, int(nrhs), bp, int(n), w, int(reps), ms.ctypes.data)
     _check(code, "rbicgstab_time_passes")
     return ms, code
 

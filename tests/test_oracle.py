@@ -225,3 +225,30 @@ def test_sequence_recycling_reduces_matvecs_small_2d():
     assert all(i.relres_true <= 2 * spec.tol for i in plain.info)
     assert rec.matvecs_iter + rec.matvecs_setup < plain.matvecs_iter
     assert sum(rec.iters[1:]) < sum(plain.iters[1:])
+
+
+def test_sequence_first_block_order():
+    """policy "first_block": the right-hand sides of one matrix all use the
+    space in force when the matrix arrives, and the update built during the
+    first one's solve is adopted from the next matrix on."""
+    import scipy.sparse as sp
+    from oracle import rbicgstab as orb2
+    spec = inputs.config_small_2d(N=12)
+    P = spec.pattern
+    mats = [sp.csr_matrix((v, P.col, P.row_ptr), shape=(P.n, P.n)) for v in spec.values[:2]]
+    b1 = inputs.gaussian_rhs(P.n, 1)
+    rhs = [[spec.rhs[0][0], b1], [spec.rhs[1][0], b1]]
+    blk = orc.solve_sequence(mats, rhs, k=4, cycle_s=10, tol=1e-8, policy="first_block")
+    seq = orc.solve_sequence(mats, rhs, k=4, cycle_s=10, tol=1e-8, policy="first")
+    # the first solve is the same under both orders
+    assert np.array_equal(blk.x[0], seq.x[0])
+    # the second RHS of matrix 0 runs with no recycle space under first_block
+    x_plain, info = orb2.rbicgstab(mats[0], b1, orb2.empty_space(P.n), tol=1e-8)
+    assert np.array_equal(blk.x[1], x_plain) and blk.k_used[1] == 0
+    # ... and with the update of the first solve under first
+    assert seq.k_used[1] == 4
+    # matrix 1 starts from the update of matrix 0's first solve in both
+    U_after_first = orc.solve_sequence(mats[:1], [rhs[0][:1]], k=4, cycle_s=10, tol=1e-8).U_final
+    rec = orb2.recycle_setup(mats[1], U_after_first)
+    x_b, _ = orb2.rbicgstab(mats[1], b1, rec, tol=1e-8)
+    assert np.allclose(blk.x[3], x_b, rtol=0, atol=1e-12 * np.linalg.norm(x_b))
