@@ -87,7 +87,8 @@ typedef struct {
   int64_t matvecs_setup;   /* columns of C = A U and C~ = A^T U~ formed for this solve */
   int64_t matvecs_check;   /* true-residual products                                   */
   int32_t cycles;          /* recycle-update cycles performed                          */
-  int32_t outer;           /* refinement steps (RB_MIXED), else 1                      */
+  int32_t outer;           /* RB_MIXED: FP64 true-residual checks (residual            */
+                           /* replacements and restarts); else 1                       */
   double  relres_rec;      /* ||r_i|| / ||b|| of the recursive residual                */
   double  relres_true;     /* ||b - A x|| / ||b|| recomputed in FP64 after step 8      */
   double  ms_total;        /* wall time of the call (CUDA events)                      */

@@ -319,28 +319,13 @@ __device__ __forceinline__ void stage_slice(const IterArgs<T>& a, typename PipeS
   }
 }
 
-// L2 prefetch of slice sl (width w, first entry e0): its matrix entries
-// (columns and values, each one contiguous segment) and the 32 rows of each
-// C-hat column, one bulk prefetch per lane.
-template <typename T, int KMAX, int R>
-__device__ __forceinline__ void prefetch_slice(const IterArgs<T>& a, int64_t sl, int w, int64_t e0, int k) {
-  const int lane = threadIdx.x & 31;
-  const int kk = KMAX > 0 ? k : 0;
-  for (int q = lane; q < kk + 2; q += 32) {
-    if (q < kk) prefetch_l2(a.Chat + (int64_t)q * a.ld + sl * kSlice, 32 * sizeof(T));
-    else if (w > 0 && q == kk) prefetch_l2(a.A.col + e0, (unsigned)w * kSlice * 4);
-    else if (w > 0) prefetch_l2(a.A.val + e0, (unsigned)w * kSlice * sizeof(T));
-  }
-}
-
 // R right-hand sides (or FP32 data), one slice per step: y_r = A v_r stored
 // to out_r.  Per RHS r the block values live at sm.w[.][r*nvr + ...]:
 // RTQ -> slot 0 = (r~0, y_r), projections -> slots OFF + j = Chat_j^T y_r,
 // DOTS (k = 0) -> slots 0..3 = (s,t), (t,t), (r~0,t), (r~0,s) with s = v_r.
 // Software pipeline per warp: while slice i is gathered and projected, the
 // matrix entries and C-hat tile of slice i + 1 stream into the other stage
-// (cp.async), those of slice i + 2 are prefetched into L2, and the width /
-// start of slice i + 3 are loaded.  Lane j owns
+// (cp.async) and the width / start of slice i + 2 are loaded.  Lane j owns
 // column j of the projection (no cross-lane reduction); each slice's 32
 // products are summed in T and the total is carried across slices in the
 // accumulator (Dot2 for FP32).
@@ -360,9 +345,9 @@ __device__ __forceinline__ void spmv_multi(const IterArgs<T>& a, const T* const*
   const T* __restrict__ valp = a.A.val;
   typename PS::Warp& ws = ps.w[warp];
   Acc<T> accr[R], accd[R][4], accp[R][CPL];
-  // slice metadata: current (wc, ec), next (wn, en), the one after (wn2, en2)
-  int wc = 0, wn = 0, wn2 = 0;
-  int64_t ec = 0, en = 0, en2 = 0;
+  // slice metadata: current (wc, ec) and next (wn, en)
+  int wc = 0, wn = 0;
+  int64_t ec = 0, en = 0;
   if (w0 < ns) {
     wc = __ldg(a.A.width + w0);
     ec = __ldg(a.A.slice_ptr + w0);
@@ -373,20 +358,15 @@ __device__ __forceinline__ void spmv_multi(const IterArgs<T>& a, const T* const*
     wn = __ldg(a.A.width + w0 + nw);
     en = __ldg(a.A.slice_ptr + w0 + nw);
   }
-  if (w0 + 2 * nw < ns) {
-    wn2 = __ldg(a.A.width + w0 + 2 * nw);
-    en2 = __ldg(a.A.slice_ptr + w0 + 2 * nw);
-  }
   int stg = 0;
   for (int64_t sl = w0; sl < ns; sl += nw) {
-    const int64_t nx = sl + nw, nx2 = sl + 2 * nw, nx3 = sl + 3 * nw;
-    int wn3 = 0;
-    int64_t en3 = 0;
-    if (nx3 < ns) {
-      wn3 = __ldg(a.A.width + nx3);
-      en3 = __ldg(a.A.slice_ptr + nx3);
+    const int64_t nx = sl + nw, nx2 = sl + 2 * nw;
+    int wn2 = 0;
+    int64_t en2 = 0;
+    if (nx2 < ns) {
+      wn2 = __ldg(a.A.width + nx2);
+      en2 = __ldg(a.A.slice_ptr + nx2);
     }
-    if (nx2 < ns) prefetch_slice<T, KMAX, R>(a, nx2, wn2, en2, k);
     const int64_t row = sl * kSlice + lane;
     const T rv = (RTQ || DOTS) ? __ldg(a.rt0 + row) : T(0);
     if (NST == 2) {
@@ -461,8 +441,6 @@ __device__ __forceinline__ void spmv_multi(const IterArgs<T>& a, const T* const*
     ec = en;
     wn = wn2;
     en = en2;
-    wn2 = wn3;
-    en2 = en3;
   }
   cp_async_wait<0>();
   // warp sums into sm.w (inactive right-hand sides contribute zeros)

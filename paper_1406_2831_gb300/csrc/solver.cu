@@ -22,6 +22,7 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <functional>
 #include <type_traits>
 #include <vector>
 
@@ -76,7 +77,8 @@ struct Slot {
         *fqraw = nullptr, *ftraw = nullptr;
 };
 
-const int kOne = 1;   // source of the "done" flag written for masked slots
+const int kOne = 1;    // source of the "done" flag written for masked slots
+const int kZero = 0;   // ... and of the flag cleared when a solve resumes
 
 }  // namespace
 
@@ -694,9 +696,13 @@ int init_p(rb_ctx* h, int nrhs, bool cycle_slot0) {
   return RB_OK;
 }
 
+// Called after every graph replay with the states read back; may change
+// device state (a residual replacement) before the done flags are checked.
+using PollHook = std::function<int()>;
+
 // Launch graphs until every slot reports done.  Non-update mode.
 template <typename T>
-int iterate_plain(rb_ctx* h, int nrhs) {
+int iterate_plain(rb_ctx* h, int nrhs, const PollHook& hook = nullptr) {
   if (!h->g_plain.valid || h->g_k != h->k || h->g_nrhs != nrhs) {
     reset_graphs(h);
     int rc = capture<T>(h, &h->g_plain, poll_iters(h), 0, false, nrhs);
@@ -709,6 +715,7 @@ int iterate_plain(rb_ctx* h, int nrhs) {
     count_launches((long long)poll_iters(h) * passes_per_iter(h));
     int rc = read_state(h, nrhs);
     if (rc) return rc;
+    if (hook && (rc = hook())) return rc;
     if (all_done(h, nrhs)) break;
   }
   return RB_OK;
@@ -761,24 +768,15 @@ int cycle_update(rb_ctx* h, int bank, int nit, int ns) {
   if (rc) return rc;
   rc = block_gemm<T>(h, oAY, Z, Y, kn);
   if (rc) return rc;
-  rc = sync(h);
-  if (rc) return rc;
-  pc.lap("gemm");
-  // unit 2-norm columns
-  std::vector<const T*> yc(oY.begin(), oY.end());
-  std::vector<double> N2;
-  rc = block_colnorm2<T>(h, yc, N2);
-  if (rc) return rc;
-  std::vector<double> f(kn);
-  for (int j = 0; j < kn; ++j) f[j] = N2[j] > 0 ? 1.0 / std::sqrt(N2[j]) : 0.0;
-  RB_CUDA_TRY(cudaMemcpy(h->dR, f.data(), sizeof(double) * kn, cudaMemcpyHostToDevice));
-  RB_CUDA_TRY(scale_cols<T>(Yn, ld, kn, h->dR, h->npad, h->us));
-  RB_CUDA_TRY(scale_cols<T>(AYn, ld, kn, h->dR, h->npad, h->us));
+  // The candidate's columns are not rescaled here: the next cycle's
+  // harmonic-Ritz problem is invariant to a column scaling of W (with Z = A W
+  // scaled alike) and rescales by diag(Z^T Z) itself.  They are normalised
+  // once, when adopted as U.
   std::swap(h->Yc, h->Yn);
   std::swap(h->AYc, h->AYn);
   h->kY = kn;
   rc = sync(h);
-  pc.lap("normalise");
+  pc.lap("gemm");
   return rc;
 }
 
@@ -786,7 +784,7 @@ int cycle_update(rb_ctx* h, int bank, int nit, int ns) {
 // between cycles from slot 0's vectors.  Candidate Y = U, A Y = C at the
 // start; the caller has put p_1 of slot 0 into bank 0, slot 0.
 template <typename T>
-int iterate_cycles(rb_ctx* h, int nrhs, SolveOut* so) {
+int iterate_cycles(rb_ctx* h, int nrhs, SolveOut* so, const PollHook& hook = nullptr) {
   const int64_t ld = h->npad;
   const bool f32 = std::is_same<T, float>::value;
   h->kY = h->k;
@@ -827,6 +825,7 @@ int iterate_cycles(rb_ctx* h, int nrhs, SolveOut* so) {
       so->cycles += 1;
     }
     if (hs.done) slot0_open = false;
+    if (hook && (rc = hook())) return rc;
     if (all_done(h, nrhs)) break;
   }
   return RB_OK;
@@ -850,15 +849,26 @@ int finish_block(rb_ctx* h, int nrhs, SolveOut* so) {
 template <typename T>
 int adopt_candidate(rb_ctx* h, SolveOut* so) {
   const int64_t ld = h->npad;
+  const auto t0 = std::chrono::steady_clock::now();
   if (std::is_same<T, float>::value) {
     for (int j = 0; j < h->kY; ++j)
       RB_CUDA_TRY(to_double((const float*)h->Yc + (int64_t)j * ld, h->U + (int64_t)j * ld, ld, h->us));
   } else {
     RB_CUDA_TRY(cudaMemcpyAsync(h->U, h->Yc, sizeof(double) * ld * h->kY, cudaMemcpyDeviceToDevice, h->us));
   }
+  {   // unit 2-norm columns (the oracle's normalisation of Y, applied once)
+    std::vector<const double*> uc;
+    for (int j = 0; j < h->kY; ++j) uc.push_back(h->U + (int64_t)j * ld);
+    std::vector<double> N2;
+    int rc = block_colnorm2<double>(h, uc, N2);
+    if (rc) return rc;
+    std::vector<double> f(h->kY);
+    for (int j = 0; j < h->kY; ++j) f[j] = N2[j] > 0 ? 1.0 / std::sqrt(N2[j]) : 0.0;
+    RB_CUDA_TRY(cudaMemcpy(h->dR, f.data(), sizeof(double) * h->kY, cudaMemcpyHostToDevice));
+    RB_CUDA_TRY(scale_cols<double>(h->U, ld, h->kY, h->dR, h->npad, h->us));
+  }
   RB_CUDA_TRY(cudaMemcpyAsync(h->Ut, h->U, sizeof(double) * ld * h->kY, cudaMemcpyDeviceToDevice, h->us));
   int64_t mv = 0;
-  const auto t0 = std::chrono::steady_clock::now();
   int rc = recycle_setup(h, h->kY, &mv);
   so->ms_update += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   if (rc < 0) return rc;
@@ -908,31 +918,113 @@ int solve_fp64(rb_ctx* h, int nrhs, const bool* x_nonzero, SolveOut* so) {
   return RB_OK;
 }
 
-// Mixed precision: FP64 iterative refinement around an FP32 inner RBiCGSTAB.
-// Outer (per slot): r = b - A x in FP64; inner: A d = r with FP32 vectors,
-// FP32 SpMV and FP32 recycle blocks, FP64-class dot products and FP64
-// scalars, all unconverged slots together; x += d in FP64.  The refinement
-// aims for a tenth of the tolerance, so the last FP32 correction leaves a
-// forward error comparable to the FP64 solver's at the tolerance itself.
+// Mixed precision: an FP32 inner RBiCGSTAB (FP32 vectors, FP32 SpMV and FP32
+// recycle blocks, FP64-class dot products and FP64 scalars) with FP64
+// residual replacement ("reliable updates", Sleijpen and van der Vorst,
+// Computing 56, 1996).  The FP64 iterate x takes the FP32 correction
+// d = x_inner - U x_c (Alg. 2 step 8 of the inner solve) whenever the
+// recursive FP32 residual has fallen by kReplace since the last replacement
+// or reports convergence; the true residual b - A x is then formed in FP64
+// and, unless it meets the tolerance, replaces the recursive one while the
+// search direction and the scalars carry on.  So one Krylov process serves
+// the whole solve.  A breakdown, or a half-step exit whose true residual
+// misses the tolerance, restarts the inner solve from the current x (a
+// refinement step).  The target is a tenth of the tolerance, so the FP64
+// answer carries a forward error comparable to the FP64 solver's.
+constexpr double kReplace = 1e-2;
+
 int solve_mixed(rb_ctx* h, int nrhs, SolveOut* so) {
   const int64_t ld = h->npad;
-  const int max_outer = 12;
+  const int max_rounds = 12;
   const int max_itn = h->o.max_itn > 0 ? h->o.max_itn : (int)std::min<int64_t>(h->n, 20000);
-  double bn2[kMaxRhs], target[kMaxRhs], rn[kMaxRhs];
-  bool stop[kMaxRhs];
+  double bn2[kMaxRhs], target[kMaxRhs], rn[kMaxRhs], rlast[kMaxRhs];
+  bool stop[kMaxRhs], running[kMaxRhs];
   int total_it[kMaxRhs], last_status[kMaxRhs];
   for (int i = 0; i < nrhs; ++i) {
     bn2[i] = h->hst[i].red[0];
     target[i] = 0.1 * h->o.tol * std::sqrt(bn2[i]);
-    rn[i] = 0.0;
-    stop[i] = false;
+    rn[i] = rlast[i] = 0.0;
+    stop[i] = running[i] = false;
     total_it[i] = 0;
     last_status[i] = RB_OK;
     so[i].outer = 0;
   }
   const bool upd = update_now(h);
   bool did_update = false;
-  for (;;) {
+
+  // x += fx - U x_c for slot i, then fx = 0 and x_c = 0.
+  auto fold = [&](int i) -> int {
+    RB_CUDA_TRY(add_float_to_double(h->sl[i].x, h->sl[i].fx, ld, h->us));
+    if (h->k > 0) {
+      RB_CUDA_TRY(gemv_update(h->sl[i].x, h->U, ld, h->k, h->st[i].xc, nullptr, -1.0, h->npad, vec_grid(h), h->us));
+      RB_CUDA_TRY(cudaMemsetAsync(h->st[i].xc, 0, sizeof(double) * h->k, h->us));
+    }
+    RB_CUDA_TRY(cudaMemsetAsync(h->sl[i].fx, 0, sizeof(float) * ld, h->us));
+    return RB_OK;
+  };
+  // True residual of slot i into sl[i].rin and rn[i].
+  auto true_residual = [&](int i) -> int {
+    RB_CUDA_TRY(residual_norm(h->A.view(), h->sl[i].b, h->sl[i].x, h->sl[i].rin, h->npad, h->st + i, h->partials,
+                              h->grids.spmv, h->us));
+    RB_CUDA_TRY(cudaMemcpyAsync(&h->hst[i].red[0], &h->st[i].red[0], sizeof(double), cudaMemcpyDeviceToHost,
+                                h->us));
+    int rc = sync(h);
+    if (rc) return rc;
+    rn[i] = std::sqrt(h->hst[i].red[0]);
+    so[i].mv_check += 1;
+    return RB_OK;
+  };
+  // After each graph replay: residual replacement / convergence per slot.
+  // In update mode slot 0's search direction lives in the cycle store at a
+  // position fixed by the cycle graph, so a slot 0 that stopped inside a
+  // cycle is not resumed there: its true residual is checked at the end of
+  // the round and, if needed, the next round restarts it.
+  const bool trace = getenv("RB_TRACE") != nullptr;
+  bool cycles_running = false;
+  PollHook hook = [&]() -> int {
+    for (int i = 0; i < nrhs; ++i) {
+      if (!running[i]) continue;
+      const IterState& hs = h->hst[i];
+      if (trace)
+        fprintf(stderr, "rb_trace slot %d iter %d rn2 %.3e rlast %.3e done %d half %d status %d\n", i, hs.iter,
+                hs.rnorm2, rlast[i], hs.done, hs.half, hs.status);
+      const bool conv_rec = hs.done && hs.status == RB_OK && !hs.half && !(cycles_running && i == 0);
+      const bool due = !hs.done && hs.rnorm2 <= kReplace * kReplace * rlast[i] * rlast[i];
+      if (!conv_rec && !due) continue;
+      int rc = fold(i);
+      if (!rc) rc = true_residual(i);
+      if (rc) return rc;
+      so[i].outer += 1;
+      if (trace) fprintf(stderr, "rb_trace slot %d replace: true residual %.6e target %.3e\n", i, rn[i], target[i]);
+      if (!std::isfinite(rn[i]) || rn[i] <= target[i]) {
+        if (!hs.done) RB_CUDA_TRY(cudaMemcpyAsync(&h->st[i].done, &kOne, sizeof(int), cudaMemcpyHostToDevice, h->us));
+        h->hst[i].done = 1;
+        running[i] = false;
+        stop[i] = true;
+        so[i].status = std::isfinite(rn[i]) ? RB_OK : RB_ENONFINITE;
+        continue;
+      }
+      // replace the recursive residual and carry on.  The true residual is
+      // projected first (eq. (3.5): x += U C-hat^T r, r -= C C-hat^T r): the
+      // rounding of the FP32 iterate leaves a component along range(C) that
+      // the projected iteration could never reduce.
+      if (h->k > 0) {
+        DotArgs d{};
+        d.M = h->Chat; d.ld = ld; d.km = h->k; d.v = h->sl[i].rin; d.nd = 0;
+        RB_CUDA_TRY(dots(d, h->npad, h->st + i, h->partials, vec_grid(h), h->us));
+        RB_CUDA_TRY(gemv_update(h->sl[i].x, h->U, ld, h->k, h->st[i].red, nullptr, 1.0, h->npad, vec_grid(h), h->us));
+        RB_CUDA_TRY(gemv_update(h->sl[i].rin, h->C, ld, h->k, h->st[i].red, nullptr, -1.0, h->npad, vec_grid(h),
+                                h->us));
+      }
+      RB_CUDA_TRY(to_float(h->sl[i].rin, h->sl[i].fr, ld, h->us));
+      if (hs.done) RB_CUDA_TRY(cudaMemcpyAsync(&h->st[i].done, &kZero, sizeof(int), cudaMemcpyHostToDevice, h->us));
+      h->hst[i].done = 0;
+      rlast[i] = rn[i];
+    }
+    return sync(h);
+  };
+
+  for (int round = 0;; ++round) {
     bool any = false;
     bool skip[kMaxRhs] = {true, true, true, true};
     bool xnz[kMaxRhs] = {false, false, false, false};
@@ -942,57 +1034,54 @@ int solve_mixed(rb_ctx* h, int nrhs, SolveOut* so) {
     for (int i = 0; i < nrhs; ++i) {
       rhs[i] = h->sl[i].rin;
       xb[i] = h->sl[i].xin;
-      tol_in[i] = 1e-6;
+      tol_in[i] = 1.0;
       if (stop[i]) continue;
-      RB_CUDA_TRY(residual_norm(h->A.view(), h->sl[i].b, h->sl[i].x, h->sl[i].rin, h->npad, h->st + i, h->partials,
-                                h->grids.spmv, h->us));
-      so[i].mv_check += 1;
-    }
-    int rc = read_state(h, nrhs);
-    if (rc) return rc;
-    for (int i = 0; i < nrhs; ++i) {
-      if (stop[i]) continue;
-      rn[i] = std::sqrt(h->hst[i].red[0]);
+      int rc = true_residual(i);
+      if (rc) return rc;
       if (!std::isfinite(rn[i])) {
         so[i].status = RB_ENONFINITE;
         stop[i] = true;
       } else if (rn[i] <= target[i] || bn2[i] == 0.0) {
         so[i].status = RB_OK;
         stop[i] = true;
-      } else if (so[i].outer >= max_outer || total_it[i] >= max_itn) {
+      } else if (round >= max_rounds || total_it[i] >= max_itn) {
         so[i].status = last_status[i] != RB_OK ? last_status[i] : RB_ENOTCONV;
         stop[i] = true;
       } else {
-        // inner system A d = r_outer, tolerance relative to ||r_outer||
+        // inner system A d = r, converged when ||r - A d|| <= target
         skip[i] = false;
         any = true;
-        tol_in[i] = std::max(target[i] / rn[i], 1e-6);
+        tol_in[i] = target[i] / rn[i];
       }
     }
     if (!any) break;
     for (int i = 0; i < nrhs; ++i) {
+      running[i] = !skip[i];
       if (skip[i]) continue;
       RB_CUDA_TRY(cudaMemcpyAsync(&h->st[i].bnorm2, &h->st[i].red[0], sizeof(double), cudaMemcpyDeviceToDevice,
                                   h->us));
       RB_CUDA_TRY(cudaMemsetAsync(h->sl[i].xin, 0, sizeof(double) * ld, h->us));
+      rlast[i] = rn[i];
     }
-    rc = setup_block(h, nrhs, rhs, xb, xnz, skip, tol_in, so);
+    int rc = setup_block(h, nrhs, rhs, xb, xnz, skip, tol_in, so);
     if (rc) return rc;
     RB_CUDA_TRY(to_float(h->rt0, h->frt0, ld, h->us));
     for (int i = 0; i < nrhs; ++i) {
       if (skip[i]) continue;
+      // r_0 and the initial projection x_0 = U C-hat^T r of the inner solve
       RB_CUDA_TRY(to_float(h->sl[i].r, h->sl[i].fr, ld, h->us));
       RB_CUDA_TRY(to_float(h->sl[i].xin, h->sl[i].fx, ld, h->us));
     }
     const bool cyc_now = upd && !did_update && !skip[0];
+    cycles_running = cyc_now;
     if (!all_done(h, nrhs)) {
       if ((rc = init_p<float>(h, nrhs, cyc_now))) return rc;
       if (cyc_now) {
         // the first (longest) inner solve collects the cycles of the update
-        rc = iterate_cycles<float>(h, nrhs, so);
+        rc = iterate_cycles<float>(h, nrhs, so, hook);
         did_update = true;
       } else {
-        rc = iterate_plain<float>(h, nrhs);
+        rc = iterate_plain<float>(h, nrhs, hook);
       }
       if (rc) return rc;
     }
@@ -1002,16 +1091,18 @@ int solve_mixed(rb_ctx* h, int nrhs, SolveOut* so) {
       total_it[i] += hs.iter;
       so[i].mv += 2 * (int64_t)hs.iter - (hs.half ? 1 : 0);
       last_status[i] = hs.status;
-      so[i].outer += 1;
-      // x += d, d = x_inner - U x_c (Alg. 2 step 8 of the inner solve)
-      RB_CUDA_TRY(add_float_to_double(h->sl[i].x, h->sl[i].fx, ld, h->us));
-      if (h->k > 0)
-        RB_CUDA_TRY(gemv_update(h->sl[i].x, h->U, ld, h->k, h->st[i].xc, nullptr, -1.0, h->npad, vec_grid(h), h->us));
+      if (stop[i]) continue;   // converged at a replacement (x already folded)
+      running[i] = false;
+      // a breakdown, max_itn, or a half-step exit: fold the correction and
+      // let the next round restart from x
+      if ((rc = fold(i))) return rc;
       if (hs.status != RB_OK && hs.status != RB_ENOTCONV) {
         so[i].status = hs.status;
         stop[i] = true;
       }
     }
+    rc = sync(h);
+    if (rc) return rc;
   }
   for (int i = 0; i < nrhs; ++i) {
     so[i].iters = total_it[i];
