@@ -228,14 +228,44 @@ constexpr int kGR = 64;      // rows per shared-memory chunk
 constexpr int kGT = 4;       // output tile edge
 constexpr int kGC = 8;       // FP32 rows summed with plain FMAs before a compensated add
 
+// Asynchronous element copy global -> shared (4 or 8 bytes), grouped per thread.
+template <typename T>
+__device__ __forceinline__ void cp_async_el(T* smem, const T* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(s), "l"(gmem), "n"(sizeof(T)) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit_g() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait_g() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// Stage rows [r0, r0 + kGR) of the m columns of Z and W (row-major tiles
+// kGR x mp) with asynchronous copies; rows past npad are zeroed.
+template <typename T>
+__device__ __forceinline__ void gram_stage(const T* const* __restrict__ Z, const T* const* __restrict__ W, int m,
+                                           int mp, int64_t r0, int64_t npad, T* sz, T* sw) {
+  for (int e = threadIdx.x; e < kGR * m; e += blockDim.x) {
+    const int c = e / kGR, rr = e % kGR;
+    if (r0 + rr < npad) {
+      cp_async_el(sz + rr * mp + c, Z[c] + r0 + rr);
+      cp_async_el(sw + rr * mp + c, W[c] + r0 + rr);
+    } else {
+      sz[rr * mp + c] = T(0);
+      sw[rr * mp + c] = T(0);
+    }
+  }
+}
+
+// The rows of a block are staged in two buffers: the copies of the next
+// 64-row chunk are in flight while the current one is multiplied.
 template <typename T, int TPT>
 __global__ void __launch_bounds__(kBlock) k_gram_gh(const T* const* __restrict__ Z,
                                                    const T* const* __restrict__ W, int m, int mp,
                                                    int ntile_g, int ntile_h, int64_t npad,
                                                    double* __restrict__ work) {
   extern __shared__ __align__(16) unsigned char ghsm[];
-  T* sz = (T*)ghsm;               // kGR x mp
-  T* sw = sz + kGR * mp;          // kGR x mp
+  T* sbuf = (T*)ghsm;             // 2 stages x (Z tile, W tile), kGR x mp each
   const int nt = mp / kGT;        // tiles per edge
   const int ntot = ntile_g + ntile_h;
   // this thread's tiles: t = threadIdx.x + q * blockDim.x, q < TPT
@@ -253,16 +283,25 @@ __global__ void __launch_bounds__(kBlock) k_gram_gh(const T* const* __restrict__
   }
   Acc<T> acc[TPT][kGT][kGT];
   const int64_t nch = (npad + kGR - 1) / kGR;
-  for (int64_t ch = blockIdx.x; ch < nch; ch += gridDim.x) {
-    const int64_t r0 = ch * kGR;
+  const int tile_el = kGR * mp;
+  // padding columns m..mp-1 stay zero in both stages
+  for (int e = threadIdx.x; e < 2 * 2 * kGR * (mp - m); e += blockDim.x) {
+    const int q = e / (kGR * (mp - m)), rem = e % (kGR * (mp - m));
+    sbuf[q * tile_el + (rem / (mp - m)) * mp + m + rem % (mp - m)] = T(0);
+  }
+  if ((int64_t)blockIdx.x < nch)
+    gram_stage<T>(Z, W, m, mp, (int64_t)blockIdx.x * kGR, npad, sbuf, sbuf + tile_el);
+  cp_async_commit_g();
+  int it = 0;
+  for (int64_t ch = blockIdx.x; ch < nch; ch += gridDim.x, ++it) {
+    const int64_t nx = ch + gridDim.x;
+    T* nz = sbuf + ((it + 1) & 1) * 2 * tile_el;
+    if (nx < nch) gram_stage<T>(Z, W, m, mp, nx * kGR, npad, nz, nz + tile_el);
+    cp_async_commit_g();
+    cp_async_wait_g<1>();
     __syncthreads();
-    for (int e = threadIdx.x; e < kGR * mp; e += blockDim.x) {
-      const int c = e / kGR, rr = e % kGR;
-      const bool in = (c < m) && (r0 + rr < npad);
-      sz[rr * mp + c] = in ? Z[c][r0 + rr] : T(0);
-      sw[rr * mp + c] = in ? W[c][r0 + rr] : T(0);
-    }
-    __syncthreads();
+    const T* sz = sbuf + (it & 1) * 2 * tile_el;
+    const T* sw = sz + tile_el;
 #pragma unroll
     for (int q = 0; q < TPT; ++q) {
       if (q < ntl) {
@@ -316,7 +355,9 @@ __global__ void __launch_bounds__(kBlock) k_gram_gh(const T* const* __restrict__
         }
       }
     }
+    __syncthreads();   // this stage is refilled two chunks on
   }
+  cp_async_wait_g<0>();
   // block partials: G tiles then H tiles, 16 values per tile
   double* wb = work + (size_t)blockIdx.x * ntot * kGT * kGT;
   for (int q = 0; q < ntl; ++q) {
@@ -373,7 +414,7 @@ cudaError_t gram_gh(const T* const* Z, const T* const* W, int m, int64_t npad, d
   const int mp = (m + kGT - 1) / kGT * kGT, nt = mp / kGT;
   const int ntile_g = nt * (nt + 1) / 2, ntile_h = nt * nt;
   if (ntile_g + ntile_h > 4 * kBlock) return cudaErrorInvalidValue;
-  const size_t smem = sizeof(T) * 2 * kGR * (size_t)mp;
+  const size_t smem = sizeof(T) * 2 * 2 * kGR * (size_t)mp;
   if (ntile_g + ntile_h <= 2 * kBlock) {
     if (smem > 48 * 1024)
       cudaFuncSetAttribute(k_gram_gh<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

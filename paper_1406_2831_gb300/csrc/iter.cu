@@ -284,7 +284,10 @@ struct PipeSmem {
   static constexpr int PAD = 32 + 16 / (int)sizeof(T);
   static constexpr int NE = 8;   // matrix entries per row staged
   static constexpr size_t kStage = sizeof(T) * KT * PAD + 4 * NE * 32 + sizeof(T) * NE * 32;
-  static constexpr int NST = (kBlock / 32) * (2 * kStage + sizeof(T) * R * 32) <= 190 * 1024 ? 2 : 1;
+  // a single RHS keeps two stages per warp; a block of several RHS has more
+  // loads in flight per slice and runs faster with one stage and more warps
+  static constexpr int NST =
+      (R == 1 && (kBlock / 32) * (2 * kStage + sizeof(T) * R * 32) <= 190 * 1024) ? 2 : 1;
   struct Warp {
     T tile[NST][KT][PAD];
     int32_t col[NST][NE][32];
@@ -468,15 +471,17 @@ __device__ __forceinline__ void spmv_multi(const IterArgs<T>& a, const T* const*
   __syncthreads();   // the staging storage is reused by the reduction
 }
 
-// Dynamic shared memory of P1 / P3: the staging of the pipelined path.
+// Dynamic shared memory of P1 / P3: the staging of the pipelined path; and
+// the resident blocks per SM the kernels are compiled for.
 template <typename T, int KMAX, int R>
 struct P13Smem {
   static constexpr bool multi = ColProj<T, KMAX, R>::value || R > 1 || KMAX == 0;
   static constexpr size_t bytes = multi ? sizeof(PipeSmem<T, KMAX, R>) : 0;
+  static constexpr int min_blocks = R > 1 ? 3 : 2;
 };
 
 template <typename T, int KMAX, int R>
-__global__ void __launch_bounds__(kBlock, 2) k_p1(IterArgs<T> a) {
+__global__ void __launch_bounds__(kBlock, P13Smem<T, KMAX, R>::min_blocks) k_p1(IterArgs<T> a) {
   IterState* st = a.st;
   bool act[R];
   bool any = false;
@@ -513,7 +518,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_p1(IterArgs<T> a) {
 }
 
 template <typename T, int KMAX, int R>
-__global__ void __launch_bounds__(kBlock, 2) k_p3(IterArgs<T> a) {
+__global__ void __launch_bounds__(kBlock, P13Smem<T, KMAX, R>::min_blocks) k_p3(IterArgs<T> a) {
   IterState* st = a.st;
   bool act[R];
   bool any = false;
