@@ -49,6 +49,7 @@ constexpr double kRankTol = 1e-10;
 constexpr double kSvdDropF32 = 1e-6;
 constexpr double kRankTolF32 = 1e-6;
 constexpr int kMaxGram = 90;         // k + 2 s must not exceed this
+constexpr int kBanks = 3;            // cycle-store banks (see slotP)
 
 template <typename T>
 T* dalloc(int64_t count, int* err) {
@@ -86,6 +87,7 @@ struct rb_ctx {
   rb_opts o{};
   cudaStream_t us = nullptr;   // caller's stream
   cudaStream_t cs = nullptr;   // private stream used for graph capture
+  cudaStream_t ws = nullptr;   // recycle-update stream (overlaps the next cycle)
   int dev = 0, nsm = 0;
   // matrix
   int64_t n = 0, nnz = 0, npad = 0;
@@ -115,9 +117,9 @@ struct rb_ctx {
   double* partials = nullptr;
   int64_t partials_cap = 0;
   int* dflag = nullptr;
-  // cycle store for the recycle update: P: 2*cyc, S: cyc, QR: cyc, TR: cyc
-  // vectors of the inner precision (double for RB_FP64, float for RB_MIXED),
-  // and the candidate Y, A Y
+  // cycle store for the recycle update, kBanks banks of cyc vectors each for
+  // P, S, QR = A P and TR = A S, of the inner precision (double for RB_FP64,
+  // float for RB_MIXED), and the candidate Y, A Y
   int cyc = 0;
   void* cstore = nullptr;
   void *Yc = nullptr, *AYc = nullptr, *Yn = nullptr, *AYn = nullptr;
@@ -127,7 +129,7 @@ struct rb_ctx {
   double *dG = nullptr, *dR = nullptr;
   const double** dptr = nullptr;   // device pointer lists (4 * 128)
   Grids grids{};
-  GraphSlot g_plain, g_cycle[2];
+  GraphSlot g_plain, g_cycle[kBanks];
   int g_k = -1, g_nrhs = -1;
 };
 
@@ -152,7 +154,7 @@ int sync(rb_ctx* h) {
 }
 
 void reset_graphs(rb_ctx* h) {
-  for (GraphSlot* g : {&h->g_plain, &h->g_cycle[0], &h->g_cycle[1]}) {
+  for (GraphSlot* g : {&h->g_plain, &h->g_cycle[0], &h->g_cycle[1], &h->g_cycle[2]}) {
     if (g->exec) cudaGraphExecDestroy(g->exec);
     g->exec = nullptr;
     g->valid = false;
@@ -214,30 +216,42 @@ int ensure_partials(rb_ctx* h) {
   return RB_OK;
 }
 
-// Column pointer lists for gram / gemm_cols.
+// Column pointer lists for gram / gemm_cols, copied on stream s; the host
+// vector must live until s has passed the copy (callers synchronise s).
 template <typename P>
-int upload_ptrs(rb_ctx* h, int slot, const std::vector<P>& v) {
-  RB_CUDA_TRY(cudaMemcpy(h->dptr + slot * 128, v.data(), sizeof(double*) * v.size(),
-                         cudaMemcpyHostToDevice));
+int upload_ptrs(rb_ctx* h, int slot, const std::vector<P>& v, cudaStream_t s) {
+  RB_CUDA_TRY(cudaMemcpyAsync(h->dptr + slot * 128, v.data(), sizeof(double*) * v.size(),
+                              cudaMemcpyHostToDevice, s));
   return RB_OK;
 }
+template <typename P>
+int upload_ptrs(rb_ctx* h, int slot, const std::vector<P>& v) {
+  return upload_ptrs(h, slot, v, h->us);
+}
 
-// Out = X R (column lists) with R (m x kc column-major) given on the host.
+// Out = X R (column lists) with R (m x kc column-major) given on the host;
+// enqueued on stream s, which is synchronised before returning.
+template <typename T>
+int block_gemm(rb_ctx* h, const std::vector<T*>& out, const std::vector<const T*>& X,
+               const std::vector<double>& R, int kc, cudaStream_t s) {
+  const int m = (int)X.size();
+  if (kc == 0 || m == 0) return RB_OK;
+  int rc = upload_ptrs(h, 0, X, s);
+  if (rc) return rc;
+  rc = upload_ptrs(h, 1, out, s);
+  if (rc) return rc;
+  RB_CUDA_TRY(cudaMemcpyAsync(h->dR, R.data(), sizeof(double) * (size_t)m * kc, cudaMemcpyHostToDevice, s));
+  RB_CUDA_TRY(gemm_cols<T>((T* const*)(h->dptr + 128), (const T* const*)h->dptr, m, h->dR, kc,
+                           h->npad, vec_grid(h), s));
+  RB_CUDA_TRY(cudaStreamSynchronize(s));
+  return RB_OK;
+}
 template <typename T>
 int block_gemm(rb_ctx* h, const std::vector<T*>& out, const std::vector<const T*>& X,
                const std::vector<double>& R, int kc) {
-  const int m = (int)X.size();
-  if (kc == 0 || m == 0) return RB_OK;
-  int rc = sync(h);   // pointer lists and R are staged synchronously
+  int rc = sync(h);
   if (rc) return rc;
-  rc = upload_ptrs(h, 0, X);
-  if (rc) return rc;
-  rc = upload_ptrs(h, 1, out);
-  if (rc) return rc;
-  RB_CUDA_TRY(cudaMemcpy(h->dR, R.data(), sizeof(double) * (size_t)m * kc, cudaMemcpyHostToDevice));
-  RB_CUDA_TRY(gemm_cols<T>((T* const*)(h->dptr + 128), (const T* const*)h->dptr, m, h->dR, kc,
-                           h->npad, vec_grid(h), h->us));
-  return RB_OK;
+  return block_gemm<T>(h, out, X, R, kc, h->us);
 }
 
 int ensure_gwork(rb_ctx* h, int64_t need) {
@@ -272,29 +286,32 @@ int block_gram(rb_ctx* h, const std::vector<const T*>& X, const std::vector<cons
   return sync(h);
 }
 
-// G = Z^T Z and H = Z^T W in one pass (both m x m, column-major, on the host).
+// G = Z^T Z and H = Z^T W in one pass (both m x m, column-major, on the
+// host), on stream s, which is synchronised before returning.
 template <typename T>
 int block_gram_gh(rb_ctx* h, const std::vector<const T*>& Z, const std::vector<const T*>& W,
-                  std::vector<double>& G, std::vector<double>& H) {
+                  std::vector<double>& G, std::vector<double>& H, cudaStream_t s) {
   const int m = (int)Z.size();
   G.assign((size_t)m * m, 0.0);
   H.assign((size_t)m * m, 0.0);
   if (!m) return RB_OK;
-  int rc = sync(h);
+  int rc = upload_ptrs(h, 2, Z, s);
   if (rc) return rc;
-  rc = upload_ptrs(h, 2, Z);
-  if (rc) return rc;
-  rc = upload_ptrs(h, 3, W);
+  rc = upload_ptrs(h, 3, W, s);
   if (rc) return rc;
   const int grid = 2 * h->nsm;
-  rc = ensure_gwork(h, (int64_t)grid * gram_gh_work(m));
-  if (rc) return rc;
+  if (h->gwork_cap < (int64_t)grid * gram_gh_work(m)) {   // reallocation: nothing may use gwork meanwhile
+    RB_CUDA_TRY(cudaStreamSynchronize(s));
+    rc = ensure_gwork(h, (int64_t)grid * gram_gh_work(m));
+    if (rc) return rc;
+  }
   RB_CUDA_TRY(gram_gh<T>((const T* const*)(h->dptr + 256), (const T* const*)(h->dptr + 384), m, h->npad, h->dG,
-                         h->dG + (size_t)kMaxGram * kMaxGram, h->gwork, grid, h->us));
-  RB_CUDA_TRY(cudaMemcpyAsync(G.data(), h->dG, sizeof(double) * G.size(), cudaMemcpyDeviceToHost, h->us));
+                         h->dG + (size_t)kMaxGram * kMaxGram, h->gwork, grid, s));
+  RB_CUDA_TRY(cudaMemcpyAsync(G.data(), h->dG, sizeof(double) * G.size(), cudaMemcpyDeviceToHost, s));
   RB_CUDA_TRY(cudaMemcpyAsync(H.data(), h->dG + (size_t)kMaxGram * kMaxGram, sizeof(double) * H.size(),
-                              cudaMemcpyDeviceToHost, h->us));
-  return sync(h);
+                              cudaMemcpyDeviceToHost, s));
+  RB_CUDA_TRY(cudaStreamSynchronize(s));
+  return RB_OK;
 }
 
 // Squared 2-norms of the given columns.
@@ -371,7 +388,7 @@ int alloc_vectors(rb_ctx* h) {
     h->cyc = h->o.cycle_s;
     void** ys[] = {&h->cstore, &h->Yc, &h->AYc, &h->Yn, &h->AYn};
     for (void** y : ys) {
-      const int64_t cnt = (y == &h->cstore ? 5 * (int64_t)h->cyc : (int64_t)kc) * h->npad;
+      const int64_t cnt = (y == &h->cstore ? 4 * kBanks * (int64_t)h->cyc : (int64_t)kc) * h->npad;
       unsigned char* p = (unsigned char*)*y;
       rc = zero_alloc(&p, es * cnt, h);
       *y = p;
@@ -530,15 +547,23 @@ IterArgs<float> base_args<float>(rb_ctx* h, int nrhs) {
   return a;
 }
 
-// Cycle-store slots: P bank b slot j, S/QR/TR slot j.
+// Cycle-store slots, bank b, slot j: P, S, QR = A P, TR = A S.  Cycle c
+// uses bank c mod 3 and its last iteration writes p_{i+1} into slot 0 of the
+// next bank, while the update of cycle c - 1 reads bank (c - 1) mod 3.
 template <typename T>
 T* slotP(rb_ctx* h, int bank, int j) { return (T*)h->cstore + (int64_t)(bank * h->cyc + j) * h->npad; }
 template <typename T>
-T* slotS(rb_ctx* h, int j) { return (T*)h->cstore + (int64_t)(2 * h->cyc + j) * h->npad; }
+T* slotS(rb_ctx* h, int bank, int j) {
+  return (T*)h->cstore + (int64_t)((kBanks + bank) * h->cyc + j) * h->npad;
+}
 template <typename T>
-T* slotQ(rb_ctx* h, int j) { return (T*)h->cstore + (int64_t)(3 * h->cyc + j) * h->npad; }
+T* slotQ(rb_ctx* h, int bank, int j) {
+  return (T*)h->cstore + (int64_t)((2 * kBanks + bank) * h->cyc + j) * h->npad;
+}
 template <typename T>
-T* slotT(rb_ctx* h, int j) { return (T*)h->cstore + (int64_t)(4 * h->cyc + j) * h->npad; }
+T* slotT(rb_ctx* h, int bank, int j) {
+  return (T*)h->cstore + (int64_t)((3 * kBanks + bank) * h->cyc + j) * h->npad;
+}
 
 template <typename T>
 int capture(rb_ctx* h, GraphSlot* g, int iters, int bank, bool cycle_mode, int nrhs) {
@@ -554,10 +579,10 @@ int capture(rb_ctx* h, GraphSlot* g, int iters, int bank, bool cycle_mode, int n
     IterArgs<T> a = base_args<T>(h, nrhs);
     if (cycle_mode) {   // slot 0's vectors go to the cycle store
       a.p_in[0] = slotP<T>(h, bank, j);
-      a.p_out[0] = (j + 1 < h->cyc) ? slotP<T>(h, bank, j + 1) : slotP<T>(h, 1 - bank, 0);
-      a.s[0] = slotS<T>(h, j);
-      a.qraw[0] = slotQ<T>(h, j);
-      a.traw[0] = slotT<T>(h, j);
+      a.p_out[0] = (j + 1 < h->cyc) ? slotP<T>(h, bank, j + 1) : slotP<T>(h, (bank + 1) % kBanks, 0);
+      a.s[0] = slotS<T>(h, bank, j);
+      a.qraw[0] = slotQ<T>(h, bank, j);
+      a.traw[0] = slotT<T>(h, bank, j);
       if (h->k == 0) {
         a.q[0] = a.qraw[0];
         a.t[0] = a.traw[0];
@@ -728,6 +753,7 @@ int iterate_plain(rb_ctx* h, int nrhs, const PollHook& hook = nullptr) {
 template <typename T>
 int cycle_update(rb_ctx* h, int bank, int nit, int ns) {
   PhaseClock pc;
+  const cudaStream_t s = h->ws;
   const int64_t ld = h->npad;
   T* Yc = (T*)h->Yc;
   T* AYc = (T*)h->AYc;
@@ -740,16 +766,16 @@ int cycle_update(rb_ctx* h, int bank, int nit, int ns) {
   }
   for (int j = 0; j < nit; ++j) {
     W.push_back(slotP<T>(h, bank, j));
-    Z.push_back(slotQ<T>(h, j));
+    Z.push_back(slotQ<T>(h, bank, j));
   }
   for (int j = 0; j < ns; ++j) {
-    W.push_back(slotS<T>(h, j));
-    Z.push_back(slotT<T>(h, j));
+    W.push_back(slotS<T>(h, bank, j));
+    Z.push_back(slotT<T>(h, bank, j));
   }
   const int m = (int)W.size();
   if (m == 0) return RB_OK;
   std::vector<double> G, H;
-  int rc = block_gram_gh<T>(h, Z, W, G, H);
+  int rc = block_gram_gh<T>(h, Z, W, G, H, s);
   if (rc) return rc;
   pc.lap("gram");
   const int kt = std::min(h->o.k_max, m);
@@ -764,9 +790,9 @@ int cycle_update(rb_ctx* h, int bank, int nit, int ns) {
     oY.push_back(Yn + (int64_t)j * ld);
     oAY.push_back(AYn + (int64_t)j * ld);
   }
-  rc = block_gemm<T>(h, oY, W, Y, kn);
+  rc = block_gemm<T>(h, oY, W, Y, kn, s);
   if (rc) return rc;
-  rc = block_gemm<T>(h, oAY, Z, Y, kn);
+  rc = block_gemm<T>(h, oAY, Z, Y, kn, s);
   if (rc) return rc;
   // The candidate's columns are not rescaled here: the next cycle's
   // harmonic-Ritz problem is invariant to a column scaling of W (with Z = A W
@@ -775,14 +801,14 @@ int cycle_update(rb_ctx* h, int bank, int nit, int ns) {
   std::swap(h->Yc, h->Yn);
   std::swap(h->AYc, h->AYn);
   h->kY = kn;
-  rc = sync(h);
   pc.lap("gemm");
-  return rc;
+  return RB_OK;
 }
 
-// Iterations in update mode: graphs of one cycle each, the recycle update
-// between cycles from slot 0's vectors.  Candidate Y = U, A Y = C at the
-// start; the caller has put p_1 of slot 0 into bank 0, slot 0.
+// Iterations in update mode: graphs of one cycle each; the recycle update of
+// cycle c (from slot 0's vectors) runs on the update stream and the host
+// while cycle c + 1 iterates.  Candidate Y = U, A Y = C at the start; the
+// caller has put p_1 of slot 0 into bank 0, slot 0.
 template <typename T>
 int iterate_cycles(rb_ctx* h, int nrhs, SolveOut* so, const PollHook& hook = nullptr) {
   const int64_t ld = h->npad;
@@ -794,41 +820,52 @@ int iterate_cycles(rb_ctx* h, int nrhs, SolveOut* so, const PollHook& hook = nul
     RB_CUDA_TRY(cudaMemcpyAsync(h->AYc, f32 ? (const void*)h->fC : (const void*)h->C, sizeof(T) * ld * h->k,
                                 cudaMemcpyDeviceToDevice, h->us));
   }
-  if (h->g_k != h->k || h->g_nrhs != nrhs || !h->g_cycle[0].valid || !h->g_cycle[1].valid) {
+  bool have_graphs = h->g_k == h->k && h->g_nrhs == nrhs;
+  for (int b = 0; b < kBanks; ++b) have_graphs = have_graphs && h->g_cycle[b].valid;
+  if (!have_graphs) {
     reset_graphs(h);
-    for (int bnk = 0; bnk < 2; ++bnk) {
-      int rc = capture<T>(h, &h->g_cycle[bnk], h->cyc, bnk, true, nrhs);
+    for (int b = 0; b < kBanks; ++b) {
+      int rc = capture<T>(h, &h->g_cycle[b], h->cyc, b, true, nrhs);
       if (rc) return rc;
     }
     h->g_k = h->k;
     h->g_nrhs = nrhs;
   }
+  int rc = sync(h);   // the update stream reads the candidate set up above
+  if (rc) return rc;
   int iters_before = 0;
   bool slot0_open = true;
+  int pend_bank = -1, pend_nit = 0, pend_ns = 0;   // update owed for the last cycle
+  auto run_update = [&]() -> int {
+    if (pend_bank < 0) return RB_OK;
+    const auto t0 = std::chrono::steady_clock::now();
+    const int r = cycle_update<T>(h, pend_bank, pend_nit, pend_ns);
+    so->ms_update += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    so->cycles += 1;
+    pend_bank = -1;
+    return r;
+  };
   for (int c = 0;; ++c) {
-    const int bank = c & 1;
+    const int bank = c % kBanks;
     RB_CUDA_TRY(cudaGraphLaunch(h->g_cycle[bank].exec, h->us));
     count_launches((long long)h->cyc * passes_per_iter(h));
-    int rc = read_state(h, nrhs);
-    if (rc) return rc;
+    if ((rc = run_update())) return rc;   // overlaps cycle c on the GPU
+    if ((rc = read_state(h, nrhs))) return rc;
     const IterState& hs = h->hst[0];
     const int nit = hs.iter - iters_before;
     iters_before = hs.iter;
     const bool ok = (hs.status == RB_OK || hs.status == RB_ENOTCONV);
     const bool allowed = (h->o.update_cycles == 0) || (c < h->o.update_cycles);
     if (slot0_open && ok && allowed && nit > 0) {
-      const int ns = nit - (hs.half ? 1 : 0);
-      const auto t0 = std::chrono::steady_clock::now();
-      rc = cycle_update<T>(h, bank, nit, ns);
-      so->ms_update += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
-      if (rc) return rc;
-      so->cycles += 1;
+      pend_bank = bank;
+      pend_nit = nit;
+      pend_ns = nit - (hs.half ? 1 : 0);
     }
     if (hs.done) slot0_open = false;
     if (hook && (rc = hook())) return rc;
     if (all_done(h, nrhs)) break;
   }
-  return RB_OK;
+  return run_update();
 }
 
 // Alg. 2 step 8 (x = x - U x_c) and the FP64 true residual of every slot.
@@ -1164,6 +1201,7 @@ extern "C" int rbicgstab_create(rb_handle* out, const rb_opts* opts) {
   if (cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, h->dev) != cudaSuccess)
     return fail(RB_ECUDA);
   if (cudaStreamCreateWithFlags(&h->cs, cudaStreamNonBlocking) != cudaSuccess) return fail(RB_ECUDA);
+  if (cudaStreamCreateWithFlags(&h->ws, cudaStreamNonBlocking) != cudaSuccess) return fail(RB_ECUDA);
   h->st = dalloc<IterState>(kMaxRhs, &err);
   if (!h->st) return fail(err);
   if (cudaMemset(h->st, 0, sizeof(IterState) * kMaxRhs) != cudaSuccess) return fail(RB_ECUDA);
@@ -1186,6 +1224,7 @@ extern "C" int rbicgstab_create(rb_handle* out, const rb_opts* opts) {
 extern "C" int rbicgstab_destroy(rb_handle h) {
   if (!h) return RB_OK;
   cudaStreamSynchronize(h->us);
+  if (h->ws) cudaStreamSynchronize(h->ws);
   reset_graphs(h);
   release_a32(h);
   sell_free(&h->A);
@@ -1198,6 +1237,7 @@ extern "C" int rbicgstab_destroy(rb_handle h) {
   for (void* p : ptrs) cudaFree(p);
   if (h->hst) cudaFreeHost(h->hst);
   if (h->cs) cudaStreamDestroy(h->cs);
+  if (h->ws) cudaStreamDestroy(h->ws);
   delete h;
   return RB_OK;
 }
