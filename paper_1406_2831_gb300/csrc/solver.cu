@@ -1028,6 +1028,7 @@ int solve_mixed(rb_ctx* h, int nrhs, SolveOut* so) {
       const bool conv_rec = hs.done && hs.status == RB_OK && !hs.half && !(cycles_running && i == 0);
       const bool due = !hs.done && hs.rnorm2 <= kReplace * kReplace * rlast[i] * rlast[i];
       if (!conv_rec && !due) continue;
+      PhaseClock pr;
       int rc = fold(i);
       if (!rc) rc = true_residual(i);
       if (rc) return rc;
@@ -1057,10 +1058,12 @@ int solve_mixed(rb_ctx* h, int nrhs, SolveOut* so) {
       if (hs.done) RB_CUDA_TRY(cudaMemcpyAsync(&h->st[i].done, &kZero, sizeof(int), cudaMemcpyHostToDevice, h->us));
       h->hst[i].done = 0;
       rlast[i] = rn[i];
+      pr.lap("replace");
     }
     return sync(h);
   };
 
+  PhaseClock pcs;
   for (int round = 0;; ++round) {
     bool any = false;
     bool skip[kMaxRhs] = {true, true, true, true};
@@ -1111,6 +1114,7 @@ int solve_mixed(rb_ctx* h, int nrhs, SolveOut* so) {
     }
     const bool cyc_now = upd && !did_update && !skip[0];
     cycles_running = cyc_now;
+    pcs.lap("blk_setup");
     if (!all_done(h, nrhs)) {
       if ((rc = init_p<float>(h, nrhs, cyc_now))) return rc;
       if (cyc_now) {
@@ -1122,6 +1126,7 @@ int solve_mixed(rb_ctx* h, int nrhs, SolveOut* so) {
       }
       if (rc) return rc;
     }
+    pcs.lap("blk_iterate");
     for (int i = 0; i < nrhs; ++i) {
       if (skip[i]) continue;
       const IterState& hs = h->hst[i];
@@ -1151,6 +1156,7 @@ int solve_mixed(rb_ctx* h, int nrhs, SolveOut* so) {
     int rc = adopt_candidate<float>(h, so);
     if (rc) return rc;
   }
+  pcs.lap("blk_adopt");
   return sync(h);
 }
 
