@@ -34,6 +34,25 @@ struct Sell {
   int64_t nslices;
 };
 
+// Completion tickets of one two-level grid reduction (device.cuh,
+// grid_finish): one counter per group of blocks and one for the groups.
+// Every counter is back at 0 when the reducing kernel ends.
+constexpr int kTicketGroups = 128;
+struct GridTicket {
+  unsigned int top;
+  unsigned int group[kTicketGroups];
+};
+
+// Blocks per group of a grid of G blocks: 16, more when G > 16 x kTicketGroups.
+__host__ __device__ inline int grid_group_size(int G) {
+  return G <= 16 * kTicketGroups ? 16 : (G + kTicketGroups - 1) / kTicketGroups;
+}
+// Rows of nv doubles a grid reduction over G blocks needs in `partials`.
+__host__ __device__ inline int64_t grid_partial_rows(int G) {
+  const int gs = grid_group_size(G);
+  return (int64_t)G + (G + gs - 1) / gs;
+}
+
 // Solver state that lives on the device between kernels of one solve.  The
 // last block of each fused pass reduces the block partials in a fixed order
 // and updates these scalars (Alg. 2 step 6).
@@ -57,7 +76,7 @@ struct IterState {
   double xc[kMaxK];
   double cr[kMaxK];    // C^T r~_0 (zero in exact arithmetic)
   double red[kMaxNV];  // scratch for generic reductions
-  unsigned int ticket[8];
+  GridTicket ticket[8];
 };
 
 // Pass identifiers (index into IterState::ticket).

@@ -2,9 +2,9 @@
 //
 // Every fused pass accumulates nv per-thread partial sums in FP64.  A block
 // sums them through shared memory in a fixed order, writes one row of
-// `partials`, and takes a ticket.  The block that takes the last ticket sums
-// all rows (every thread takes a fixed subset of blocks) and runs the pass's
-// scalar step.  Results are bitwise reproducible run to run.
+// `partials`, and takes a ticket; the last block of each group of blocks sums
+// its group's rows, and the last group sums the group rows and runs the
+// pass's scalar step.  Results are bitwise reproducible run to run.
 //
 // FP64 adds are scarce on this GPU (two FP64 lanes per SM per clock), so the
 // block sum is a shared-memory transpose (one add per partial) rather than a
@@ -164,19 +164,26 @@ __device__ __forceinline__ void block_sum(Acc<T> (&acc)[NV], int nv, ReduceSmem<
 }
 
 // Second half of a grid reduction: every warp has written its sums to
-// sm.w[warp][0..nv).  Sums them across warps, publishes the block partial,
-// takes a ticket; returns true in every thread of the last block with
-// sm.res[0..nv) holding the grid totals.  `ticket` is reset to 0.
+// sm.w[warp][0..nv).  Sums them across warps, publishes the block partial
+// and takes a ticket; returns true in every thread of the last block with
+// sm.res[0..nv) holding the grid totals.  The tickets are left at 0.
 //
-// The last block sums the partial rows in chunks of FCH values (each thread
-// takes a fixed subset of rows, then a per-warp transpose and a cross-warp
-// sum), so the registers this tail needs do not grow with nv and do not
-// limit the occupancy of the kernel's main loop.
+// Two levels, so that no single block sums every block's partials: FP64 adds
+// run on few lanes per SM, and one block summing G x nv values serialised
+// the end of every pass.  Blocks form groups of gs consecutive blocks; the
+// last block of a group to finish sums the group's rows (in block order)
+// into a group row; the last group sums the group rows (in group order).
+// Fixed summation order: bitwise reproducible.  `partials` holds G + ceil(G /
+// gs) rows of nv doubles.
 template <int NV>
-__device__ bool grid_finish(int nv, ReduceCore<NV>& sm, RedT& tbuf, double* partials, unsigned int* ticket) {
+__device__ bool grid_finish(int nv, ReduceCore<NV>& sm, double* partials, GridTicket* ticket) {
   constexpr int NW = kBlock / 32;
-  constexpr int CH = kRedCH;
-  constexpr int FCH = 2 * CH;
+  const int G = gridDim.x;
+  const int gs = grid_group_size(G);
+  const int ng = (G + gs - 1) / gs;
+  const int g = blockIdx.x / gs;
+  const int gsz = min(gs, G - g * gs);
+  double* grows = partials + (size_t)G * nv;
   __syncthreads();
   for (int v = threadIdx.x; v < nv; v += blockDim.x) {
     double s = 0.0;
@@ -186,74 +193,51 @@ __device__ bool grid_finish(int nv, ReduceCore<NV>& sm, RedT& tbuf, double* part
   }
   if (threadIdx.x < nv) __threadfence();   // only the writers publish before the ticket
   __syncthreads();
+  if (threadIdx.x == 0) sm.last = (atomicAdd(&ticket->group[g], 1u) == (unsigned)gsz - 1u);
+  __syncthreads();
+  if (!sm.last) return false;
+  // last block of group g
+  __threadfence();
+  for (int v = threadIdx.x; v < nv; v += blockDim.x) {
+    const double* p = partials + (size_t)g * gs * nv + v;
+    double s = 0.0;
+#pragma unroll 4
+    for (int i = 0; i < gsz; ++i) s += __ldcg(p + (size_t)i * nv);
+    grows[(size_t)g * nv + v] = s;
+  }
+  if (threadIdx.x < nv) __threadfence();
+  __syncthreads();
   if (threadIdx.x == 0) {
-    unsigned int t = atomicAdd(ticket, 1u);
-    sm.last = (t == gridDim.x - 1);
+    ticket->group[g] = 0u;
+    sm.last = (atomicAdd(&ticket->top, 1u) == (unsigned)ng - 1u);
   }
   __syncthreads();
   if (!sm.last) return false;
+  // last group
   __threadfence();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll 1
-  for (int c0 = 0; c0 < nv; c0 += FCH) {
-    double tot[FCH];
-#pragma unroll
-    for (int u = 0; u < FCH; ++u) tot[u] = 0.0;
-    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
-      const double* pb = partials + (size_t)b * nv + c0;
-#pragma unroll
-      for (int u = 0; u < FCH; ++u)
-        if (c0 + u < nv) tot[u] += __ldcg(pb + u);
-    }
-#pragma unroll
-    for (int h = 0; h < FCH; h += CH) {
-#pragma unroll
-      for (int u = 0; u < CH; ++u) tbuf[warp][u][lane] = tot[h + u];
-      __syncwarp();
-      if (lane < CH && c0 + h + lane < nv) {
-        const double* row = tbuf[warp][lane];
-        double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-#pragma unroll
-        for (int j = 0; j < 32; j += 4) {
-          s0 += row[j];
-          s1 += row[j + 1];
-          s2 += row[j + 2];
-          s3 += row[j + 3];
-        }
-        sm.w[warp][c0 + h + lane] = (s0 + s1) + (s2 + s3);
-      }
-      __syncwarp();
-    }
-  }
-  __syncthreads();
   for (int v = threadIdx.x; v < nv; v += blockDim.x) {
     double s = 0.0;
-#pragma unroll
-    for (int w = 0; w < NW; ++w) s += sm.w[w][v];
+#pragma unroll 4
+    for (int i = 0; i < ng; ++i) s += __ldcg(grows + (size_t)i * nv + v);
     sm.res[v] = s;
   }
   __syncthreads();
-  if (threadIdx.x == 0) *ticket = 0u;
+  if (threadIdx.x == 0) ticket->top = 0u;
   return true;
-}
-
-template <int NV>
-__device__ __forceinline__ bool grid_finish(int nv, ReduceSmem<NV>& sm, double* partials, unsigned int* ticket) {
-  return grid_finish<NV>(nv, static_cast<ReduceCore<NV>&>(sm), sm.t, partials, ticket);
 }
 
 // Reduce per-thread accumulators acc[0..nv) (nv <= NV) over the grid.
 template <typename T, int NV>
 __device__ bool block_reduce_last(Acc<T> (&acc)[NV], int nv, ReduceSmem<NV>& sm, double* partials,
-                                  unsigned int* ticket) {
+                                  GridTicket* ticket) {
   warp_sums<NV>(acc, nv, sm);
-  return grid_finish<NV>(nv, sm, partials, ticket);
+  return grid_finish<NV>(nv, static_cast<ReduceCore<NV>&>(sm), partials, ticket);
 }
 
 // FP64 convenience form: per-thread doubles.
 template <int NV>
 __device__ bool block_reduce_last(double (&vals)[NV], int nv, ReduceSmem<NV>& sm, double* partials,
-                                  unsigned int* ticket) {
+                                  GridTicket* ticket) {
   Acc<double> acc[NV];
 #pragma unroll
   for (int v = 0; v < NV; ++v) acc[v].v = vals[v];

@@ -43,12 +43,21 @@ __device__ __forceinline__ void fail(IterState* st, int code) {
 }
 
 // ---------------------------------------------------------------- scalar steps
-__device__ void finish_p1(IterState* st, const double* res, int k) {
-  double rtq = res[0];
-  for (int j = 0; j < k; ++j) {
+// Each step runs in one warp of the last block, one warp per right-hand side.
+// The per-column loads and stores of IterState (zeta, gamma, c_r, x_c) are
+// spread over the lanes so that their memory latencies overlap instead of
+// adding up; recurrences over the columns stay in lane 0, in column order.
+// scr is warp-private shared scratch of at least k doubles.
+__device__ void finish_p1(IterState* st, const double* res, int k, double* scr) {
+  const int lane = threadIdx.x & 31;
+  for (int j = lane; j < k; j += 32) {
     st->zeta[j] = res[1 + j];
-    rtq -= st->cr[j] * res[1 + j];
+    scr[j] = st->cr[j];
   }
+  __syncwarp();
+  if (lane != 0) return;
+  double rtq = res[0];
+  for (int j = 0; j < k; ++j) rtq -= scr[j] * res[1 + j];
   st->rtq = rtq;
   if (rtq == 0.0 || !isfinite(rtq)) {
     fail(st, rtq == 0.0 ? RB_EBREAKDOWN_RHO : RB_ENONFINITE);
@@ -58,42 +67,60 @@ __device__ void finish_p1(IterState* st, const double* res, int k) {
 }
 
 __device__ void finish_p2(IterState* st, const double* res) {
+  if ((threadIdx.x & 31) != 0) return;
   st->snorm2 = res[0];
   if (!isfinite(res[0])) fail(st, RB_ENONFINITE);
   else if (res[0] <= st->thresh2) st->half = 1;
 }
 
 __device__ void finish_p3(IterState* st, const double* res, int k) {
-  for (int j = 0; j < k; ++j) st->gamma[j] = res[j];
+  for (int j = threadIdx.x & 31; j < k; j += 32) st->gamma[j] = res[j];
 }
 
 __device__ void finish_p4(IterState* st, const double* res, int k) {
-  const double s_t = res[0], t_t = res[1], rt_t = res[2], rt_s = res[3];
-  st->st = s_t; st->tt = t_t; st->rtt = rt_t; st->rts = rt_s;
-  if (t_t == 0.0 || !isfinite(t_t)) {
-    fail(st, t_t == 0.0 ? RB_EBREAKDOWN_OMEGA : RB_ENONFINITE);
-    return;
+  const int lane = threadIdx.x & 31;
+  double omega = 0.0, alpha = 0.0;
+  int ok = 0;
+  if (lane == 0) {
+    const double s_t = res[0], t_t = res[1], rt_t = res[2], rt_s = res[3];
+    st->st = s_t; st->tt = t_t; st->rtt = rt_t; st->rts = rt_s;
+    if (t_t == 0.0 || !isfinite(t_t)) {
+      fail(st, t_t == 0.0 ? RB_EBREAKDOWN_OMEGA : RB_ENONFINITE);
+    } else {
+      omega = s_t / t_t;
+      if (omega == 0.0) {
+        fail(st, RB_EBREAKDOWN_OMEGA);
+      } else {
+        alpha = st->alpha;
+        const double rho_new = rt_s - omega * rt_t;
+        st->beta = (rho_new / st->rho) * (alpha / omega);
+        st->omega = omega;
+        st->rho = rho_new;
+        ok = 1;
+      }
+    }
   }
-  const double omega = s_t / t_t;
-  if (omega == 0.0) {
-    fail(st, RB_EBREAKDOWN_OMEGA);
-    return;
-  }
-  const double rho_new = rt_s - omega * rt_t;
-  st->beta = (rho_new / st->rho) * (st->alpha / omega);
-  st->omega = omega;
-  for (int j = 0; j < k; ++j) st->xc[j] += st->alpha * st->zeta[j] + omega * st->gamma[j];
-  st->rho = rho_new;
+  ok = __shfl_sync(0xffffffffu, ok, 0);
+  if (!ok) return;
+  omega = __shfl_sync(0xffffffffu, omega, 0);
+  alpha = __shfl_sync(0xffffffffu, alpha, 0);
+  for (int j = lane; j < k; j += 32) st->xc[j] += alpha * st->zeta[j] + omega * st->gamma[j];
 }
 
 __device__ void finish_p5(IterState* st, const double* res, int k) {
-  st->iter += 1;
-  if (st->half) {
-    for (int j = 0; j < k; ++j) st->xc[j] += st->alpha * st->zeta[j];
-    st->rnorm2 = st->snorm2;
-    st->done = 1;
+  const int lane = threadIdx.x & 31;
+  if (st->half) {   // set by an earlier pass; the same in every lane
+    const double alpha = st->alpha;
+    for (int j = lane; j < k; j += 32) st->xc[j] += alpha * st->zeta[j];
+    if (lane == 0) {
+      st->iter += 1;
+      st->rnorm2 = st->snorm2;
+      st->done = 1;
+    }
     return;
   }
+  if (lane != 0) return;
+  st->iter += 1;
   const double rn2 = res[0];
   st->rnorm2 = rn2;
   if (!isfinite(rn2)) fail(st, RB_ENONFINITE);
@@ -101,6 +128,17 @@ __device__ void finish_p5(IterState* st, const double* res, int k) {
   else if (st->rho == 0.0) fail(st, RB_EBREAKDOWN_RHO);
   else if (st->iter >= st->max_itn) fail(st, RB_ENOTCONV);
 }
+
+// Scratch doubles per warp in a RedT buffer ([warp][kRedCH][33]).
+constexpr int kScr = kRedCH * 33;
+
+// Run a scalar step in the last block: warp r handles right-hand side r.
+#define RB_FINISH_WARPS(R, ACT, CALL)                       \
+  do {                                                      \
+    const int r_ = threadIdx.x >> 5;                        \
+    _Pragma("unroll") for (int rr_ = 0; rr_ < (R); ++rr_)   \
+      if (rr_ == r_ && (ACT)[rr_]) { const int r = rr_; CALL; } \
+  } while (0)
 
 
 // ---------------------------------------------------------------- helpers
@@ -270,28 +308,19 @@ __device__ __forceinline__ void prefetch_l2(const void* p, unsigned bytes) {
   asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(p), "r"(bytes) : "memory");
 }
 
-// Per-warp shared staging of the multi-RHS / FP32 SpMV + projection passes.
-// Each stage holds one slice's first NE matrix entries per row (columns and
-// values, as stored in SELL-32) and its C-hat tile transposed: column j's 32
-// rows contiguous with a row stride of 32 elements plus 16 bytes, which keeps
-// the 16-byte column reads of the projection free of bank conflicts.  Two
-// stages (one when they do not fit) let the next slice stream in while the
-// current one is gathered.  y holds the slice products y_r.  After the main
-// loop the storage serves the last block's reduction.
+// Per-warp shared memory of the multi-RHS / FP32 SpMV + projection passes:
+// the C-hat tile of the current slice, transposed (column j's 32 rows
+// contiguous, row stride 32 elements plus 16 bytes, which keeps the 16-byte
+// column reads of the projection free of bank conflicts), and the slice
+// products y_r.  After the main loop the storage serves the last block's
+// reduction.
 template <typename T, int KMAX, int R>
 struct PipeSmem {
   static constexpr int KT = KMAX > 0 ? KMAX : 1;
   static constexpr int PAD = 32 + 16 / (int)sizeof(T);
-  static constexpr int NE = 8;   // matrix entries per row staged
-  static constexpr size_t kStage = sizeof(T) * KT * PAD + 4 * NE * 32 + sizeof(T) * NE * 32;
-  // a single RHS keeps two stages per warp; a block of several RHS has more
-  // loads in flight per slice and runs faster with one stage and more warps
-  static constexpr int NST =
-      (R == 1 && (kBlock / 32) * (2 * kStage + sizeof(T) * R * 32) <= 190 * 1024) ? 2 : 1;
+  static constexpr int NE = 8;   // matrix entries per row loaded up front
   struct Warp {
-    T tile[NST][KT][PAD];
-    int32_t col[NST][NE][32];
-    T val[NST][NE][32];
+    T tile[KT][PAD];
     T y[R][32];
   };
   union {
@@ -300,35 +329,29 @@ struct PipeSmem {
   };
 };
 
-// Issue the copies of slice sl (width w, first entry e0) into stage stg.
+// Issue the copies of slice sl's C-hat tile (rows sl*32 .. sl*32+31 of the k
+// columns) into the warp's shared tile.
 template <typename T, int KMAX, int R>
-__device__ __forceinline__ void stage_slice(const IterArgs<T>& a, typename PipeSmem<T, KMAX, R>::Warp& ws, int stg,
-                                            int64_t sl, int w, int64_t e0, int k) {
-  constexpr int NE = PipeSmem<T, KMAX, R>::NE;
+__device__ __forceinline__ void stage_tile(const IterArgs<T>& a, typename PipeSmem<T, KMAX, R>::Warp& ws,
+                                           int64_t sl, int k) {
   constexpr int VC = 16 / (int)sizeof(T);   // values per 16-byte chunk
-  constexpr int VPR = 32 / VC;              // chunks per 32-entry row
+  constexpr int VPR = 32 / VC;              // chunks per 32-row column
   const int lane = threadIdx.x & 31;
-  const int we = w < NE ? w : NE;
-  for (int q = lane; q < we * 8; q += 32)
-    cp_async16(&ws.col[stg][q >> 3][(q & 7) * 4], a.A.col + e0 + (int64_t)(q >> 3) * kSlice + (q & 7) * 4);
-  for (int q = lane; q < we * VPR; q += 32)
-    cp_async16(&ws.val[stg][q / VPR][(q % VPR) * VC], a.A.val + e0 + (int64_t)(q / VPR) * kSlice + (q % VPR) * VC);
-  if (KMAX > 0) {
-    const int64_t base = sl * kSlice;
-    for (int q = lane; q < k * VPR; q += 32) {
-      const int j = q / VPR, c = q % VPR;
-      cp_async16(&ws.tile[stg][j][c * VC], a.Chat + (int64_t)j * a.ld + base + c * VC);
-    }
+  const int64_t base = sl * kSlice;
+  for (int q = lane; q < k * VPR; q += 32) {
+    const int j = q / VPR, c = q % VPR;
+    cp_async16(&ws.tile[j][c * VC], a.Chat + (int64_t)j * a.ld + base + c * VC);
   }
 }
 
-// R right-hand sides (or FP32 data), one slice per step: y_r = A v_r stored
-// to out_r.  Per RHS r the block values live at sm.w[.][r*nvr + ...]:
+// R right-hand sides (or FP32 data), one slice per warp and step: y_r = A v_r
+// stored to out_r.  Per RHS r the block values live at sm.w[.][r*nvr + ...]:
 // RTQ -> slot 0 = (r~0, y_r), projections -> slots OFF + j = Chat_j^T y_r,
 // DOTS (k = 0) -> slots 0..3 = (s,t), (t,t), (r~0,t), (r~0,s) with s = v_r.
-// Software pipeline per warp: while slice i is gathered and projected, the
-// matrix entries and C-hat tile of slice i + 1 stream into the other stage
-// (cp.async) and the width / start of slice i + 2 are loaded.  Lane j owns
+// Per slice the warp issues the asynchronous copy of the C-hat tile first (it
+// lands while the products are formed), loads the first NE entries of every
+// row straight into registers (all in flight together) and gathers v_r; the
+// next slice's width and start are loaded one step ahead.  Lane j owns
 // column j of the projection (no cross-lane reduction); each slice's 32
 // products are summed in T and the total is carried across slices in the
 // accumulator (Dot2 for FP32).
@@ -338,7 +361,6 @@ __device__ __forceinline__ void spmv_multi(const IterArgs<T>& a, const T* const*
                                            PipeSmem<T, KMAX, R>& ps) {
   using PS = PipeSmem<T, KMAX, R>;
   constexpr int NE = PS::NE;
-  constexpr int NST = PS::NST;
   constexpr int CPL = KMAX > 0 ? (KMAX + 31) / 32 : 1;
   constexpr int OFF = RTQ ? 1 : 0;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -348,54 +370,46 @@ __device__ __forceinline__ void spmv_multi(const IterArgs<T>& a, const T* const*
   const T* __restrict__ valp = a.A.val;
   typename PS::Warp& ws = ps.w[warp];
   Acc<T> accr[R], accd[R][4], accp[R][CPL];
-  // slice metadata: current (wc, ec) and next (wn, en)
-  int wc = 0, wn = 0;
-  int64_t ec = 0, en = 0;
+  int wn = 0;   // width and first entry of the warp's next slice
+  int64_t en = 0;
   if (w0 < ns) {
-    wc = __ldg(a.A.width + w0);
-    ec = __ldg(a.A.slice_ptr + w0);
-    stage_slice<T, KMAX, R>(a, ws, 0, w0, wc, ec, k);
+    wn = __ldg(a.A.width + w0);
+    en = __ldg(a.A.slice_ptr + w0);
   }
-  cp_async_commit();
-  if (w0 + nw < ns) {
-    wn = __ldg(a.A.width + w0 + nw);
-    en = __ldg(a.A.slice_ptr + w0 + nw);
-  }
-  int stg = 0;
   for (int64_t sl = w0; sl < ns; sl += nw) {
-    const int64_t nx = sl + nw, nx2 = sl + 2 * nw;
-    int wn2 = 0;
-    int64_t en2 = 0;
-    if (nx2 < ns) {
-      wn2 = __ldg(a.A.width + nx2);
-      en2 = __ldg(a.A.slice_ptr + nx2);
+    const int wc = wn;
+    const int64_t b = en + lane;
+    if (sl + nw < ns) {
+      wn = __ldg(a.A.width + sl + nw);
+      en = __ldg(a.A.slice_ptr + sl + nw);
+    }
+    if (KMAX > 0) {
+      __syncwarp();   // every lane is done with the previous slice's tile
+      stage_tile<T, KMAX, R>(a, ws, sl, k);
+      cp_async_commit();
     }
     const int64_t row = sl * kSlice + lane;
     const T rv = (RTQ || DOTS) ? __ldg(a.rt0 + row) : T(0);
-    if (NST == 2) {
-      __syncwarp();   // every lane is done with the stage about to be refilled
-      if (nx < ns) stage_slice<T, KMAX, R>(a, ws, stg ^ 1, nx, wn, en, k);
-      cp_async_commit();
-      cp_async_wait<1>();   // this thread's copies of the current stage landed
-    } else {
-      cp_async_wait<0>();
+    int cu[NE];
+    T au[NE];
+#pragma unroll
+    for (int u = 0; u < NE; ++u) {
+      cu[u] = u < wc ? __ldg(colp + b + (int64_t)u * kSlice) : 0;
+      au[u] = u < wc ? __ldg(valp + b + (int64_t)u * kSlice) : T(0);
     }
-    __syncwarp();   // ... and every lane's
     T y[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) y[r] = T(0);
 #pragma unroll
     for (int u = 0; u < NE; ++u) {
       if (u < wc) {
-        const int c = ws.col[stg][u][lane];
-        const T av = ws.val[stg][u][lane];
 #pragma unroll
         for (int r = 0; r < R; ++r)
-          if (act[r]) y[r] = fma_t(av, __ldg(v[r] + c), y[r]);
+          if (act[r]) y[r] = fma_t(au[u], __ldg(v[r] + cu[u]), y[r]);
       }
     }
     for (int j = NE; j < wc; ++j) {   // rows wider than NE entries
-      const int64_t e = ec + (int64_t)j * kSlice + lane;
+      const int64_t e = b + (int64_t)j * kSlice;
       const int cc = __ldg(colp + e);
       const T vv = __ldg(valp + e);
 #pragma unroll
@@ -418,7 +432,8 @@ __device__ __forceinline__ void spmv_multi(const IterArgs<T>& a, const T* const*
     if (KMAX > 0) {
 #pragma unroll
       for (int r = 0; r < R; ++r) ws.y[r][lane] = act[r] ? y[r] : T(0);
-      __syncwarp();
+      cp_async_wait<0>();   // this thread's tile copies landed
+      __syncwarp();         // ... and every lane's, and y is visible
 #pragma unroll
       for (int cc = 0; cc < CPL; ++cc) {
         const int j = lane + 32 * cc;
@@ -426,26 +441,14 @@ __device__ __forceinline__ void spmv_multi(const IterArgs<T>& a, const T* const*
           T part[R];
 #pragma unroll
           for (int r = 0; r < R; ++r) part[r] = T(0);
-          col_dot<R>(ws.tile[stg][j], ws.y, act, part);
+          col_dot<R>(ws.tile[j], ws.y, act, part);
 #pragma unroll
           for (int r = 0; r < R; ++r)
             if (act[r]) accp[r][cc].add1(part[r]);
         }
       }
     }
-    if (NST == 1) {
-      __syncwarp();   // the single stage is refilled for the next slice
-      if (nx < ns) stage_slice<T, KMAX, R>(a, ws, 0, nx, wn, en, k);
-      cp_async_commit();
-    } else {
-      stg ^= 1;
-    }
-    wc = wn;
-    ec = en;
-    wn = wn2;
-    en = en2;
   }
-  cp_async_wait<0>();
   // warp sums into sm.w (inactive right-hand sides contribute zeros)
 #pragma unroll
   for (int r = 0; r < R; ++r) {
@@ -468,16 +471,16 @@ __device__ __forceinline__ void spmv_multi(const IterArgs<T>& a, const T* const*
       }
     }
   }
-  __syncthreads();   // the staging storage is reused by the reduction
+  __syncthreads();   // the tile storage is reused by the reduction
 }
 
-// Dynamic shared memory of P1 / P3: the staging of the pipelined path; and
+// Dynamic shared memory of P1 / P3: the tile storage of the multi-RHS path; and
 // the resident blocks per SM the kernels are compiled for.
 template <typename T, int KMAX, int R>
 struct P13Smem {
   static constexpr bool multi = ColProj<T, KMAX, R>::value || R > 1 || KMAX == 0;
   static constexpr size_t bytes = multi ? sizeof(PipeSmem<T, KMAX, R>) : 0;
-  static constexpr int min_blocks = R > 1 ? 3 : 2;
+  static constexpr int min_blocks = !multi ? 2 : ((sizeof(T) == 8 || KMAX == 0) && R > 1 ? 3 : 4);
 };
 
 template <typename T, int KMAX, int R>
@@ -495,26 +498,24 @@ __global__ void __launch_bounds__(kBlock, P13Smem<T, KMAX, R>::min_blocks) k_p1(
   const int k = KMAX > 0 ? st[0].k : 0;
   const int nvr = 1 + k;
   bool last;
-  double* res;
+  double *res, *scr;   // grid totals; scratch of the scalar step (free after the reduction)
   if constexpr (!P13Smem<T, KMAX, R>::multi) {
     __shared__ ReduceSmem<NVR> sm;
     Acc<T> acc[NVR];
     spmv_project<T, KMAX, true>(a, a.p_in[0], a.qraw[0], acc, k);
     last = block_reduce_last<T, NVR>(acc, nvr, sm, a.partials, &st[0].ticket[P1]);
     res = sm.res;
+    scr = &sm.t[0][0][0];
   } else {
     __shared__ ReduceCore<R * NVR> sm;
     extern __shared__ __align__(16) unsigned char dsm[];
     auto& ps = *reinterpret_cast<PipeSmem<T, KMAX, R>*>(dsm);
     spmv_multi<T, KMAX, R, true, false, R * NVR>(a, a.p_in, a.qraw, act, k, nvr, sm, ps);
-    last = grid_finish<R * NVR>(R * nvr, sm, ps.t, a.partials, &st[0].ticket[P1]);
+    last = grid_finish<R * NVR>(R * nvr, sm, a.partials, &st[0].ticket[P1]);
     res = sm.res;
+    scr = &ps.t[0][0][0];
   }
-  if (last && threadIdx.x == 0) {
-#pragma unroll
-    for (int r = 0; r < R; ++r)
-      if (act[r]) finish_p1(&st[r], res + r * nvr, k);
-  }
+  if (last) RB_FINISH_WARPS(R, act, finish_p1(&st[r], res + r * nvr, k, scr + r * kScr));
 }
 
 template <typename T, int KMAX, int R>
@@ -545,17 +546,10 @@ __global__ void __launch_bounds__(kBlock, P13Smem<T, KMAX, R>::min_blocks) k_p3(
     extern __shared__ __align__(16) unsigned char dsm[];
     auto& ps = *reinterpret_cast<PipeSmem<T, KMAX, R>*>(dsm);
     spmv_multi<T, KMAX, R, false, DOTS, R * NVR>(a, a.s, a.traw, act, k, nvr, sm, ps);
-    last = grid_finish<R * NVR>(R * nvr, sm, ps.t, a.partials, &st[0].ticket[P3]);
+    last = grid_finish<R * NVR>(R * nvr, sm, a.partials, &st[0].ticket[P3]);
     res = sm.res;
   }
-  if (last && threadIdx.x == 0) {
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-      if (!act[r]) continue;
-      if (DOTS) finish_p4(&st[r], res + r * nvr, 0);
-      else finish_p3(&st[r], res + r * nvr, k);
-    }
-  }
+  if (last) RB_FINISH_WARPS(R, act, (DOTS ? finish_p4(&st[r], res + r * nvr, 0) : finish_p3(&st[r], res + r * nvr, k)));
 }
 
 // L2 prefetch, by one warp, of rows [row0, row0 + nrows) of the first ncols
@@ -740,11 +734,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_p2(IterArgs<T> a) {
     if (act[r]) warp_slot(acc[r], r, sm);
     else zero_slot(r, sm);
   }
-  if (grid_finish<R>(R, sm, a.partials, &st[0].ticket[P2]) && threadIdx.x == 0) {
-#pragma unroll
-    for (int r = 0; r < R; ++r)
-      if (act[r]) finish_p2(&st[r], sm.res + r);
-  }
+  if (grid_finish<R>(R, sm, a.partials, &st[0].ticket[P2])) RB_FINISH_WARPS(R, act, finish_p2(&st[r], sm.res + r));
 }
 
 // ---------------------------------------------------------------- P4 (k > 0)
@@ -826,11 +816,8 @@ __global__ void __launch_bounds__(kBlock, 2) k_p4(IterArgs<T> a) {
       if (act[r]) warp_slot(acc[r][d], 4 * r + d, sm);
       else zero_slot(4 * r + d, sm);
     }
-  if (grid_finish<4 * R>(4 * R, sm, a.partials, &st[0].ticket[P4]) && threadIdx.x == 0) {
-#pragma unroll
-    for (int r = 0; r < R; ++r)
-      if (act[r]) finish_p4(&st[r], sm.res + 4 * r, k);
-  }
+  if (grid_finish<4 * R>(4 * R, sm, a.partials, &st[0].ticket[P4]))
+    RB_FINISH_WARPS(R, act, finish_p4(&st[r], sm.res + 4 * r, k));
 }
 
 // ---------------------------------------------------------------- P5
@@ -930,11 +917,7 @@ __global__ void __launch_bounds__(kBlock, 3) k_p5(IterArgs<T> a) {
     if (act[r]) warp_slot(acc[r], r, sm);
     else zero_slot(r, sm);
   }
-  if (grid_finish<R>(R, sm, a.partials, &st[0].ticket[P5]) && threadIdx.x == 0) {
-#pragma unroll
-    for (int r = 0; r < R; ++r)
-      if (act[r]) finish_p5(&st[r], sm.res + r, k);
-  }
+  if (grid_finish<R>(R, sm, a.partials, &st[0].ticket[P5])) RB_FINISH_WARPS(R, act, finish_p5(&st[r], sm.res + r, k));
 }
 
 // ---------------------------------------------------------------- launchers

@@ -20,8 +20,8 @@ namespace {
 constexpr int kNaMaxBlocks = 1024;   // block partials the scratch array holds
 
 struct NaScratch {
-  double partials[kNaMaxBlocks];
-  unsigned int ticket;
+  double partials[kNaMaxBlocks + kNaMaxBlocks / 16 + 1];   // block rows + group rows
+  rb::GridTicket ticket;
 };
 
 // File-scope scratch.  In host code this name is only a stand-in for the
@@ -76,8 +76,8 @@ extern "C" int rbicgstab_residual_noalloc(int64_t n, const int32_t* row_ptr, con
   int rc = na_scratch(&sc);
   if (rc) return rc;
   cudaStream_t s = (cudaStream_t)cuda_stream;
-  // the completion ticket must start at zero; a memset allocates nothing
-  RB_CUDA_TRY(cudaMemsetAsync(&sc->ticket, 0, sizeof(unsigned int), s));
+  // the completion tickets must start at zero; a memset allocates nothing
+  RB_CUDA_TRY(cudaMemsetAsync(&sc->ticket, 0, sizeof(rb::GridTicket), s));
   const int64_t want = (n + rb::kBlock - 1) / rb::kBlock;
   const int grid = (int)(want < kNaMaxBlocks ? want : kNaMaxBlocks);
   rb::count_launches(1);

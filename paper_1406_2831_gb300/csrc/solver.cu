@@ -205,8 +205,10 @@ int run_dots(rb_ctx* h, const DotArgs& d, double* out, int cnt, int slot = 0) {
 
 int ensure_partials(rb_ctx* h) {
   // every kernel runs at most one full wave (<= 8 blocks of 256 threads per
-  // SM) and reduces at most kMaxRhs * kMaxNV values per block
-  const int64_t need = (int64_t)std::max(8 * h->nsm, std::max(h->grids.spmv, h->grids.vec)) * kMaxRhs * kMaxNV;
+  // SM) and reduces at most kMaxRhs * kMaxNV values per block; the grid
+  // reduction adds one row per group of blocks
+  const int gmax = std::max(8 * h->nsm, std::max(h->grids.spmv, h->grids.vec));
+  const int64_t need = grid_partial_rows(gmax) * kMaxRhs * kMaxNV;
   if (need <= h->partials_cap) return RB_OK;
   cudaFree(h->partials);
   int err = 0;
