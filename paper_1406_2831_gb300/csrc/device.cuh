@@ -59,6 +59,70 @@ struct Acc<float> {
   __device__ __forceinline__ double get() const { return (double)hi + (double)lo; }
 };
 
+// Two lanes of T handled together.  For float these are the packed FP32
+// instructions of this GPU (one instruction for both lanes, each lane
+// rounded exactly as the scalar _rn operation); for double, two scalar
+// operations.
+template <typename T>
+struct Pair;
+template <>
+struct Pair<float> {
+  using V = float2;
+  static __device__ __forceinline__ V mk(float a, float b) { return make_float2(a, b); }
+  static __device__ __forceinline__ V fma(V a, V b, V c) { return __ffma2_rn(a, b, c); }
+  static __device__ __forceinline__ V add(V a, V b) { return __fadd2_rn(a, b); }
+  static __device__ __forceinline__ V mul(V a, V b) { return __fmul2_rn(a, b); }
+  static __device__ __forceinline__ V neg(V a) { return make_float2(-a.x, -a.y); }
+};
+template <>
+struct Pair<double> {
+  using V = double2;
+  static __device__ __forceinline__ V mk(double a, double b) { return make_double2(a, b); }
+  static __device__ __forceinline__ V fma(V a, V b, V c) { return make_double2(__fma_rn(a.x, b.x, c.x), __fma_rn(a.y, b.y, c.y)); }
+  static __device__ __forceinline__ V add(V a, V b) { return make_double2(__dadd_rn(a.x, b.x), __dadd_rn(a.y, b.y)); }
+  static __device__ __forceinline__ V mul(V a, V b) { return make_double2(__dmul_rn(a.x, b.x), __dmul_rn(a.y, b.y)); }
+  static __device__ __forceinline__ V neg(V a) { return make_double2(-a.x, -a.y); }
+};
+
+// Two dot-product accumulators side by side: for float the Dot2 scheme of
+// Acc<float> on packed pairs (the same result in each lane as Acc<float>),
+// for double FP64 FMAs.  lane(h) returns lane h as a scalar accumulator.
+template <typename T>
+struct AccP;
+template <>
+struct AccP<float> {
+  using P = Pair<float>;
+  float2 hi = make_float2(0.0f, 0.0f), lo = make_float2(0.0f, 0.0f);
+  __device__ __forceinline__ void add(float2 a, float2 b) {
+    const float2 p = P::mul(a, b);
+    const float2 e = P::fma(a, b, P::neg(p));                 // a*b = p + e exactly
+    const float2 s = P::add(hi, p);                           // TwoSum(hi, p) = s + err
+    const float2 bb = P::add(s, P::neg(hi));
+    const float2 err = P::add(P::add(hi, P::neg(P::add(s, P::neg(bb)))), P::add(p, P::neg(bb)));
+    hi = s;
+    lo = P::add(lo, P::add(err, e));
+  }
+  __device__ __forceinline__ Acc<float> lane(int h) const {
+    Acc<float> a;
+    a.hi = h ? hi.y : hi.x;
+    a.lo = h ? lo.y : lo.x;
+    return a;
+  }
+};
+template <>
+struct AccP<double> {
+  double2 v = make_double2(0.0, 0.0);
+  __device__ __forceinline__ void add(double2 a, double2 b) {
+    v.x = __fma_rn(a.x, b.x, v.x);
+    v.y = __fma_rn(a.y, b.y, v.y);
+  }
+  __device__ __forceinline__ Acc<double> lane(int h) const {
+    Acc<double> a;
+    a.v = h ? v.y : v.x;
+    return a;
+  }
+};
+
 constexpr int kRedCH = 8;   // values per transpose chunk
 
 // Transpose buffer of the FP64 block sums: [warp][value][lane] (+1 pad).

@@ -920,15 +920,403 @@ __global__ void __launch_bounds__(kBlock, 3) k_p5(IterArgs<T> a) {
   if (grid_finish<R>(R, sm, a.partials, &st[0].ticket[P5])) RB_FINISH_WARPS(R, act, finish_p5(&st[r], sm.res + r, k));
 }
 
+// ---------------------------------------------------------------- staged streaming (R > 1)
+// A block of several right-hand sides streams up to k + 9 arrays per row
+// (P4: k columns of C, r~_0, t_raw and s per RHS).  Register-held loads
+// cannot keep enough of them in flight, so these passes stage tiles of
+// kBlock rows of every stream into shared memory with cp.async (16-byte
+// copies spread over the block's threads, NSTG tiles in flight) and then
+// compute one row per thread from the staged tile.  Blocks take tiles
+// round-robin; the arithmetic per row is the same as the register-held
+// path's, in the same order.
+template <typename T, int NSMAX>
+struct StageCfg {
+  static constexpr size_t per = (size_t)NSMAX * kBlock * sizeof(T);   // one tile of every stream
+  static constexpr int nstg = 3 * per <= 112 * 1024 ? 3 : 2;
+  static constexpr bool ok = 2 * per <= 200 * 1024;
+  static constexpr size_t bytes = ok ? nstg * per : 0;
+};
+
+template <typename T, int KMAX, int R>
+struct Staged {
+  static constexpr bool value = R > 1 && StageCfg<T, (KMAX + 2 * R + 1 > 5 * R ? KMAX + 2 * R + 1 : 5 * R)>::ok;
+  using P2 = StageCfg<T, KMAX + 2 * R>;
+  using P4 = StageCfg<T, KMAX + 2 * R + 1>;
+  using P5 = StageCfg<T, 5 * R>;
+};
+
+// Stream rows [0, npad) of kc columns of the column-major block C (leading
+// dimension ld) followed by the nv vectors vsrc[0..nv) (a list in shared
+// memory) through the NSTG-stage buffer `buf` ([stage][stream][kBlock]) and
+// call f(row, sb) for this thread's row of each tile, with stream s's value
+// at sb[s * kBlock].  Each thread always copies the same 16-byte chunk
+// position of a stream's tile.  Every thread of the block must call this.
+template <typename T, int NSTG, typename F>
+__device__ __forceinline__ void staged_rows(const T* __restrict__ C, int64_t ld, int kc, const T* const* vsrc, int nv,
+                                            int64_t npad, T* buf, F&& f) {
+  constexpr int VC = 16 / (int)sizeof(T);   // values per 16-byte copy
+  constexpr int CPS = kBlock / VC;          // copies per stream and tile
+  constexpr int SPP = kBlock / CPS;         // streams per pass of the block
+  const int ns = kc + nv;
+  const int64_t ntiles = (npad + kBlock - 1) / kBlock;
+  const int64_t stage = (int64_t)ns * kBlock;
+  const int64_t step = gridDim.x;
+  const int c = threadIdx.x % CPS, s0 = threadIdx.x / CPS;
+  auto issue = [&](int64_t tile, int stg) {
+    const int64_t row = tile * kBlock + (int64_t)c * VC;
+    if (tile < ntiles && row < npad) {
+      T* b = buf + stg * stage + c * VC;
+      for (int sidx = s0; sidx < ns; sidx += SPP) {
+        const T* src = sidx < kc ? C + (int64_t)sidx * ld : vsrc[sidx - kc];
+        cp_async16(b + (int64_t)sidx * kBlock, src + row);
+      }
+    }
+    cp_async_commit();
+  };
+  int64_t tile = blockIdx.x;
+#pragma unroll
+  for (int q = 0; q < NSTG - 1; ++q) issue(tile + q * step, q);
+  int stg = 0;
+  for (; tile < ntiles; tile += step) {
+    // refill the stage read in the previous step (all threads are past it)
+    issue(tile + (NSTG - 1) * step, stg == 0 ? NSTG - 1 : stg - 1);
+    cp_async_wait<NSTG - 1>();   // this thread's copies of `tile` landed
+    __syncthreads();             // ... and every thread's
+    const int64_t row = tile * kBlock + threadIdx.x;
+    if (row < npad) f(row, buf + stg * stage + threadIdx.x);
+    __syncthreads();
+    stg = stg == NSTG - 1 ? 0 : stg + 1;
+  }
+  cp_async_wait<0>();
+}
+
+// Warp sums of the pair accumulators acc[h][d] (right-hand sides 2h, 2h+1)
+// into the slots slot(r, d); inactive right-hand sides give zeros.
+template <typename T, int R, int ND, int NV, typename SlotF>
+__device__ __forceinline__ void pair_slots(const AccP<T> (&acc)[R / 2][ND], const bool (&act)[R], ReduceCore<NV>& sm,
+                                           SlotF slot) {
+#pragma unroll
+  for (int r = 0; r < R; ++r)
+#pragma unroll
+    for (int d = 0; d < ND; ++d) {
+      if (act[r]) warp_slot(acc[r / 2][d].lane(r & 1), slot(r, d), sm);
+      else zero_slot(slot(r, d), sm);
+    }
+}
+
+// Stream lists of the staged passes: slot r's vectors start at vix[r] (0 for
+// an inactive slot, whose values are read but never used).
+// P2 for R > 1: q = q_raw - C zeta, s = r - alpha q, ||s||^2.
+template <typename T, int KMAX, int R>
+__global__ void __launch_bounds__(kBlock, 1) k_p2_staged(IterArgs<T> a) {
+  using P = Pair<T>;
+  using V = typename P::V;
+  constexpr int H = R / 2;
+  IterState* st = a.st;
+  bool act[R];
+  bool any = false;
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    act[r] = (r < a.nrhs) && !st[r].done;
+    any |= act[r];
+  }
+  if (!any) return;
+  constexpr int KK = KMAX > 0 ? KMAX : 1;
+  using SC = typename Staged<T, KMAX, R>::P2;
+  extern __shared__ __align__(16) unsigned char dsm[];
+  __shared__ ReduceCore<R> sm;
+  __shared__ __align__(16) T zs[KK][R];   // zeta, interleaved by right-hand side
+  __shared__ const T* src[2 * R];
+  __shared__ int vix[R], nsrc;
+  const int k = KMAX > 0 ? st[0].k : 0;
+  if (threadIdx.x == 0) {
+    int n = 0;
+    for (int r = 0; r < R; ++r) {
+      vix[r] = act[r] ? k + n : 0;
+      if (act[r]) {
+        src[n++] = a.qraw[r];
+        src[n++] = a.r[r];
+      }
+    }
+    nsrc = n;
+  }
+  for (int e = threadIdx.x; e < R * KK; e += blockDim.x) {
+    const int j = e / R, r = e % R;
+    zs[j][r] = (act[r] && j < k) ? (T)st[r].zeta[j] : T(0);
+  }
+  V al[H];
+#pragma unroll
+  for (int h = 0; h < H; ++h) al[h] = P::neg(P::mk((T)st[2 * h].alpha, (T)st[2 * h + 1].alpha));
+  __syncthreads();
+  int vi[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) vi[r] = vix[r];
+  AccP<T> acc[H][1];
+  staged_rows<T, SC::nstg>(a.C, a.ld, k, src, nsrc, a.npad, reinterpret_cast<T*>(dsm), [&](int64_t row, const T* sb) {
+    V corr[H];
+#pragma unroll
+    for (int h = 0; h < H; ++h) corr[h] = P::mk(T(0), T(0));
+#pragma unroll
+    for (int j = 0; j < KMAX; ++j) {
+      if (j >= k) break;
+      const T c = sb[j * kBlock];
+      const V* z = reinterpret_cast<const V*>(zs[j]);
+#pragma unroll
+      for (int h = 0; h < H; ++h) corr[h] = P::fma(P::mk(c, c), z[h], corr[h]);
+    }
+#pragma unroll
+    for (int h = 0; h < H; ++h) {
+      const int r0 = 2 * h, r1 = 2 * h + 1;
+      V q = P::mk(sb[vi[r0] * kBlock], sb[vi[r1] * kBlock]);
+      const V rv = P::mk(sb[(vi[r0] + 1) * kBlock], sb[(vi[r1] + 1) * kBlock]);
+      if (KMAX > 0) q = P::add(q, P::neg(corr[h]));
+      const V sv = P::fma(al[h], q, rv);   // r - alpha q
+      acc[h][0].add(sv, sv);
+      if (act[r0]) {
+        if (KMAX > 0) a.q[r0][row] = q.x;
+        a.s[r0][row] = sv.x;
+      }
+      if (act[r1]) {
+        if (KMAX > 0) a.q[r1][row] = q.y;
+        a.s[r1][row] = sv.y;
+      }
+    }
+  });
+  pair_slots<T, R, 1>(acc, act, sm, [](int r, int) { return r; });
+  if (grid_finish<R>(R, sm, a.partials, &st[0].ticket[P2])) RB_FINISH_WARPS(R, act, finish_p2(&st[r], sm.res + r));
+}
+
+// P4 for R > 1: t = t_raw - C gamma; (s,t), (t,t), (r~0,t), (r~0,s).
+template <typename T, int KMAX, int R>
+__global__ void __launch_bounds__(kBlock, 1) k_p4_staged(IterArgs<T> a) {
+  using P = Pair<T>;
+  using V = typename P::V;
+  constexpr int H = R / 2;
+  IterState* st = a.st;
+  bool act[R];
+  bool any = false;
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    act[r] = (r < a.nrhs) && !st[r].done && !st[r].half;
+    any |= act[r];
+  }
+  if (!any) return;
+  using SC = typename Staged<T, KMAX, R>::P4;
+  extern __shared__ __align__(16) unsigned char dsm[];
+  __shared__ ReduceCore<4 * R> sm;
+  __shared__ __align__(16) T gs[KMAX][R];   // gamma, interleaved by right-hand side
+  __shared__ const T* src[2 * R + 1];
+  __shared__ int vix[R], nsrc;
+  const int k = st[0].k;
+  if (threadIdx.x == 0) {
+    int n = 0;
+    src[n++] = a.rt0;
+    for (int r = 0; r < R; ++r) {
+      vix[r] = act[r] ? k + n : 0;
+      if (act[r]) {
+        src[n++] = a.traw[r];
+        src[n++] = a.s[r];
+      }
+    }
+    nsrc = n;
+  }
+  for (int e = threadIdx.x; e < R * KMAX; e += blockDim.x) {
+    const int j = e / R, r = e % R;
+    gs[j][r] = (act[r] && j < k) ? (T)st[r].gamma[j] : T(0);
+  }
+  __syncthreads();
+  int vi[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) vi[r] = vix[r];
+  AccP<T> acc[H][4];
+  staged_rows<T, SC::nstg>(a.C, a.ld, k, src, nsrc, a.npad, reinterpret_cast<T*>(dsm), [&](int64_t row, const T* sb) {
+    V corr[H];
+#pragma unroll
+    for (int h = 0; h < H; ++h) corr[h] = P::mk(T(0), T(0));
+#pragma unroll
+    for (int j = 0; j < KMAX; ++j) {
+      if (j >= k) break;
+      const T c = sb[j * kBlock];
+      const V* g = reinterpret_cast<const V*>(gs[j]);
+#pragma unroll
+      for (int h = 0; h < H; ++h) corr[h] = P::fma(P::mk(c, c), g[h], corr[h]);
+    }
+    const T rs = sb[k * kBlock];
+    const V rv = P::mk(rs, rs);
+#pragma unroll
+    for (int h = 0; h < H; ++h) {
+      const int r0 = 2 * h, r1 = 2 * h + 1;
+      const V t = P::add(P::mk(sb[vi[r0] * kBlock], sb[vi[r1] * kBlock]), P::neg(corr[h]));
+      const V sv = P::mk(sb[(vi[r0] + 1) * kBlock], sb[(vi[r1] + 1) * kBlock]);
+      acc[h][0].add(sv, t);
+      acc[h][1].add(t, t);
+      acc[h][2].add(rv, t);
+      acc[h][3].add(rv, sv);
+      if (act[r0]) a.t[r0][row] = t.x;
+      if (act[r1]) a.t[r1][row] = t.y;
+    }
+  });
+  pair_slots<T, R, 4>(acc, act, sm, [](int r, int d) { return 4 * r + d; });
+  if (grid_finish<4 * R>(4 * R, sm, a.partials, &st[0].ticket[P4]))
+    RB_FINISH_WARPS(R, act, finish_p4(&st[r], sm.res + 4 * r, k));
+}
+
+// P5 for R > 1: x += alpha p + omega s; r = s - omega t; ||r||^2;
+// p_{i+1} = r + beta (p - omega q)  (half step: x += alpha p, r = s).
+template <typename T, int KMAX, int R>
+__global__ void __launch_bounds__(kBlock, 1) k_p5_staged(IterArgs<T> a) {
+  using P = Pair<T>;
+  using V = typename P::V;
+  constexpr int H = R / 2;
+  IterState* st = a.st;
+  bool act[R], half[R];
+  bool any = false, anyhalf = false;
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    act[r] = (r < a.nrhs) && !st[r].done;
+    half[r] = act[r] && st[r].half;
+    any |= act[r];
+    anyhalf |= half[r];
+  }
+  if (!any) return;
+  using SC = typename Staged<T, KMAX, R>::P5;
+  extern __shared__ __align__(16) unsigned char dsm[];
+  __shared__ ReduceCore<R> sm;
+  __shared__ const T* src[5 * R];
+  __shared__ int vix[R], nsrc;
+  if (threadIdx.x == 0) {
+    int n = 0;
+    for (int r = 0; r < R; ++r) {
+      vix[r] = act[r] ? n : 0;
+      if (act[r]) {
+        src[n++] = a.p_in[r];
+        src[n++] = a.s[r];
+        src[n++] = a.x[r];
+        if (!half[r]) {
+          src[n++] = a.t[r];
+          src[n++] = a.q[r];
+        }
+      }
+    }
+    nsrc = n;
+  }
+  const int k = KMAX > 0 ? st[0].k : 0;
+  T al[R], om[R], be[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    al[r] = (T)st[r].alpha;
+    om[r] = (T)st[r].omega;
+    be[r] = (T)st[r].beta;
+  }
+  __syncthreads();
+  int vi[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) vi[r] = vix[r];
+  AccP<T> acc[H][1];
+  staged_rows<T, SC::nstg>(a.C, a.ld, 0, src, nsrc, a.npad, reinterpret_cast<T*>(dsm), [&](int64_t row, const T* sb) {
+    if (!anyhalf) {
+#pragma unroll
+      for (int h = 0; h < H; ++h) {
+        const int r0 = 2 * h, r1 = 2 * h + 1;
+        const T* v0 = sb + vi[r0] * kBlock;
+        const T* v1 = sb + vi[r1] * kBlock;
+        const V p = P::mk(v0[0], v1[0]), s_ = P::mk(v0[kBlock], v1[kBlock]), x = P::mk(v0[2 * kBlock], v1[2 * kBlock]);
+        const V t = P::mk(v0[3 * kBlock], v1[3 * kBlock]), q = P::mk(v0[4 * kBlock], v1[4 * kBlock]);
+        const V om2 = P::mk(om[r0], om[r1]), nom = P::neg(om2);
+        const V rr = P::fma(nom, t, s_);                                        // s - omega t
+        const V xn = P::fma(om2, s_, P::fma(P::mk(al[r0], al[r1]), p, x));     // x + alpha p + omega s
+        const V pn = P::fma(P::mk(be[r0], be[r1]), P::fma(nom, q, p), rr);      // r + beta (p - omega q)
+        acc[h][0].add(rr, rr);
+        if (act[r0]) {
+          a.x[r0][row] = xn.x;
+          a.r[r0][row] = rr.x;
+          a.p_out[r0][row] = pn.x;
+        }
+        if (act[r1]) {
+          a.x[r1][row] = xn.y;
+          a.r[r1][row] = rr.y;
+          a.p_out[r1][row] = pn.y;
+        }
+      }
+      return;
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      if (!act[r]) continue;
+      const T* v = sb + vi[r] * kBlock;
+      const T p = v[0], s_ = v[kBlock], x = v[2 * kBlock];
+      if (half[r]) {
+        a.x[r][row] = fma_t(al[r], p, x);
+        a.r[r][row] = s_;
+        continue;
+      }
+      const T t = v[3 * kBlock], q = v[4 * kBlock];
+      const T rr = fma_t(-om[r], t, s_);
+      const T xn = fma_t(om[r], s_, fma_t(al[r], p, x));
+      const T pn = fma_t(be[r], fma_t(-om[r], q, p), rr);
+      // the lane of the pair accumulator that belongs to r
+      const V rr2 = (r & 1) ? P::mk(T(0), rr) : P::mk(rr, T(0));
+      acc[r / 2][0].add(rr2, rr2);
+      a.x[r][row] = xn;
+      a.r[r][row] = rr;
+      a.p_out[r][row] = pn;
+    }
+  });
+  pair_slots<T, R, 1>(acc, act, sm, [](int r, int) { return r; });
+  if (grid_finish<R>(R, sm, a.partials, &st[0].ticket[P5])) RB_FINISH_WARPS(R, act, finish_p5(&st[r], sm.res + r, k));
+}
+
+// Kernel and dynamic shared memory of P2 / P4 / P5 for one configuration.
+template <typename T, int KMAX, int R>
+struct StreamKernels {
+  static constexpr bool staged = Staged<T, KMAX, R>::value;
+  static constexpr int K4 = KMAX > 0 ? KMAX : 1;
+  static const void* p2() {
+    if constexpr (staged) return (const void*)k_p2_staged<T, KMAX, R>;
+    else return (const void*)k_p2<T, KMAX, R>;
+  }
+  static const void* p4() {
+    if constexpr (staged) return (const void*)k_p4_staged<T, K4, R>;
+    else return (const void*)k_p4<T, K4, R>;
+  }
+  static const void* p5() {
+    if constexpr (staged) return (const void*)k_p5_staged<T, KMAX, R>;
+    else return (const void*)k_p5<T, KMAX, R>;
+  }
+  static constexpr size_t d2 = staged ? Staged<T, KMAX, R>::P2::bytes : 0;
+  static constexpr size_t d4 = staged ? Staged<T, K4, R>::P4::bytes : 0;
+  static constexpr size_t d5 = staged ? Staged<T, KMAX, R>::P5::bytes : 0;
+};
+
+template <typename T, int KMAX, int R>
+static void launch_p2(const IterArgs<T>& a, const Grids& g, cudaStream_t s) {
+  using SK = StreamKernels<T, KMAX, R>;
+  if constexpr (SK::staged) k_p2_staged<T, KMAX, R><<<g.pass[P2], kBlock, SK::d2, s>>>(a);
+  else k_p2<T, KMAX, R><<<g.pass[P2], kBlock, 0, s>>>(a);
+}
+template <typename T, int KMAX, int R>
+static void launch_p4(const IterArgs<T>& a, const Grids& g, cudaStream_t s) {
+  using SK = StreamKernels<T, KMAX, R>;
+  constexpr int K4 = SK::K4;
+  if constexpr (SK::staged) k_p4_staged<T, K4, R><<<g.pass[P4], kBlock, SK::d4, s>>>(a);
+  else k_p4<T, K4, R><<<g.pass[P4], kBlock, 0, s>>>(a);
+}
+template <typename T, int KMAX, int R>
+static void launch_p5(const IterArgs<T>& a, const Grids& g, cudaStream_t s) {
+  using SK = StreamKernels<T, KMAX, R>;
+  if constexpr (SK::staged) k_p5_staged<T, KMAX, R><<<g.pass[P5], kBlock, SK::d5, s>>>(a);
+  else k_p5<T, KMAX, R><<<g.pass[P5], kBlock, 0, s>>>(a);
+}
+
 // ---------------------------------------------------------------- launchers
 template <typename T, int KMAX, int R>
 static cudaError_t launch_iter_kr(const IterArgs<T>& a, const Grids& g, cudaStream_t s) {
   constexpr size_t dsm = P13Smem<T, KMAX, R>::bytes;
   k_p1<T, KMAX, R><<<g.pass[P1], kBlock, dsm, s>>>(a);
-  k_p2<T, KMAX, R><<<g.pass[P2], kBlock, 0, s>>>(a);
+  launch_p2<T, KMAX, R>(a, g, s);
   k_p3<T, KMAX, R><<<g.pass[P3], kBlock, dsm, s>>>(a);
-  if (KMAX > 0) k_p4<T, (KMAX > 0 ? KMAX : 1), R><<<g.pass[P4], kBlock, 0, s>>>(a);
-  k_p5<T, KMAX, R><<<g.pass[P5], kBlock, 0, s>>>(a);
+  if (KMAX > 0) launch_p4<T, KMAX, R>(a, g, s);
+  launch_p5<T, KMAX, R>(a, g, s);
   return cudaGetLastError();
 }
 
@@ -937,10 +1325,10 @@ static cudaError_t launch_pass_kr(int pass, const IterArgs<T>& a, const Grids& g
   constexpr size_t dsm = P13Smem<T, KMAX, R>::bytes;
   switch (pass) {
     case P1: k_p1<T, KMAX, R><<<g.pass[P1], kBlock, dsm, s>>>(a); break;
-    case P2: k_p2<T, KMAX, R><<<g.pass[P2], kBlock, 0, s>>>(a); break;
+    case P2: launch_p2<T, KMAX, R>(a, g, s); break;
     case P3: k_p3<T, KMAX, R><<<g.pass[P3], kBlock, dsm, s>>>(a); break;
-    case P4: if (KMAX > 0) k_p4<T, (KMAX > 0 ? KMAX : 1), R><<<g.pass[P4], kBlock, 0, s>>>(a); break;
-    default: k_p5<T, KMAX, R><<<g.pass[P5], kBlock, 0, s>>>(a); break;
+    case P4: if (KMAX > 0) launch_p4<T, KMAX, R>(a, g, s); break;
+    default: launch_p5<T, KMAX, R>(a, g, s); break;
   }
   return cudaGetLastError();
 }
@@ -1007,10 +1395,10 @@ static void grids_kr(int nsm, int64_t npad, Grids* g) {
   const int64_t work13 = (npad + kBlock - 1) / kBlock;
   const int64_t workv = (npad / StreamVW<T, R>::value + kBlock - 1) / kBlock;
   constexpr size_t dsm = P13Smem<T, KMAX, R>::bytes;
-  const int o[5] = {occ((const void*)k_p1<T, KMAX, R>, nsm, dsm), occ((const void*)k_p2<T, KMAX, R>, nsm),
-                    occ((const void*)k_p3<T, KMAX, R>, nsm, dsm),
-                    occ((const void*)k_p4<T, (KMAX > 0 ? KMAX : 1), R>, nsm),
-                    occ((const void*)k_p5<T, KMAX, R>, nsm)};
+  using SK = StreamKernels<T, KMAX, R>;
+  const int o[5] = {occ((const void*)k_p1<T, KMAX, R>, nsm, dsm), occ(SK::p2(), nsm, SK::d2),
+                    occ((const void*)k_p3<T, KMAX, R>, nsm, dsm), occ(SK::p4(), nsm, SK::d4),
+                    occ(SK::p5(), nsm, SK::d5)};
   for (int p = 0; p < 5; ++p)
     g->pass[p] = (int)std::max<int64_t>(1, std::min<int64_t>((p == P1 || p == P3) ? work13 : workv, o[p]));
   g->spmv = std::max(g->pass[P1], g->pass[P3]);
