@@ -102,6 +102,14 @@ struct AccP<float> {
     hi = s;
     lo = P::add(lo, P::add(err, e));
   }
+  // Compensated add of one FP32 value per lane (TwoSum, error into lo).
+  __device__ __forceinline__ void add1(float2 x) {
+    const float2 s = P::add(hi, x);
+    const float2 bb = P::add(s, P::neg(hi));
+    const float2 err = P::add(P::add(hi, P::neg(P::add(s, P::neg(bb)))), P::add(x, P::neg(bb)));
+    hi = s;
+    lo = P::add(lo, err);
+  }
   __device__ __forceinline__ Acc<float> lane(int h) const {
     Acc<float> a;
     a.hi = h ? hi.y : hi.x;
@@ -115,6 +123,10 @@ struct AccP<double> {
   __device__ __forceinline__ void add(double2 a, double2 b) {
     v.x = __fma_rn(a.x, b.x, v.x);
     v.y = __fma_rn(a.y, b.y, v.y);
+  }
+  __device__ __forceinline__ void add1(double2 x) {
+    v.x += x.x;
+    v.y += x.y;
   }
   __device__ __forceinline__ Acc<double> lane(int h) const {
     Acc<double> a;

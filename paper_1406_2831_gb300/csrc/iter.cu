@@ -227,6 +227,30 @@ __device__ __forceinline__ void col_dot(const double* col, const double (*ys)[32
   }
 }
 
+// Dot products of one 32-row column (shared memory) with the slice products
+// of R right-hand sides stored row-major (yi[i][r], read as broadcasts), for
+// pairs of right-hand sides: part[h] = sum_i col[i] * (yi[i][2h], yi[i][2h+1]),
+// each lane summed in T in row order (the order of col_dot).
+template <typename T, int R>
+__device__ __forceinline__ void col_dot_pairs(const T* col, const T (*yi)[R], typename Pair<T>::V (&part)[R / 2]) {
+  using P = Pair<T>;
+  using V = typename P::V;
+  using C16 = typename Vec<T>::type;
+  constexpr int VC = Vec<T>::W;
+#pragma unroll
+  for (int u = 0; u < 32 / VC; ++u) {
+    const C16 cv = *reinterpret_cast<const C16*>(col + VC * u);
+    const T* c = reinterpret_cast<const T*>(&cv);
+#pragma unroll
+    for (int e = 0; e < VC; ++e) {
+      const V* yp = reinterpret_cast<const V*>(yi[VC * u + e]);
+      const V cc = P::mk(c[e], c[e]);
+#pragma unroll
+      for (int h = 0; h < R / 2; ++h) part[h] = P::fma(cc, yp[h], part[h]);
+    }
+  }
+}
+
 // ---------------------------------------------------------------- SpMV core
 // Rows sl*32+lane of two slices at once (sl1 < 0: only the first), so each
 // warp keeps two independent gather chains in flight (single RHS, FP64).
@@ -321,7 +345,10 @@ struct PipeSmem {
   static constexpr int NE = 8;   // matrix entries per row loaded up front
   struct Warp {
     T tile[KT][PAD];
-    T y[R][32];
+    union {
+      T y[R][32];    // slice products, one row per right-hand side (odd R)
+      T yi[32][R];   // slice products, right-hand sides interleaved (even R)
+    };
   };
   union {
     Warp w[kBlock / 32];
@@ -360,6 +387,10 @@ __device__ __forceinline__ void spmv_multi(const IterArgs<T>& a, const T* const*
                                            const bool (&act)[R], int k, int nvr, ReduceCore<NVT>& sm,
                                            PipeSmem<T, KMAX, R>& ps) {
   using PS = PipeSmem<T, KMAX, R>;
+  using P = Pair<T>;
+  using V = typename P::V;
+  constexpr bool PAIRS = R % 2 == 0;   // pairs of right-hand sides on packed instructions
+  constexpr int H = PAIRS ? R / 2 : 1;
   constexpr int NE = PS::NE;
   constexpr int CPL = KMAX > 0 ? (KMAX + 31) / 32 : 1;
   constexpr int OFF = RTQ ? 1 : 0;
@@ -369,7 +400,20 @@ __device__ __forceinline__ void spmv_multi(const IterArgs<T>& a, const T* const*
   const int32_t* __restrict__ colp = a.A.col;
   const T* __restrict__ valp = a.A.val;
   typename PS::Warp& ws = ps.w[warp];
-  Acc<T> accr[R], accd[R][4], accp[R][CPL];
+  // Every right-hand side is gathered and reduced unconditionally (no
+  // per-slot branches between the loads); an inactive one reads an active
+  // one's vector and only its stores and its block values are masked.
+  const T* vg[R];
+  {
+    int ra = 0;
+#pragma unroll
+    for (int r = R - 1; r >= 0; --r)
+      if (act[r]) ra = r;
+#pragma unroll
+    for (int r = 0; r < R; ++r) vg[r] = act[r] ? v[r] : v[ra];
+  }
+  Acc<T> accr1[R], accd1[R][4], accp1[R][CPL];   // R = 1
+  AccP<T> accr[H], accd[H][4], accp[H][CPL];      // pairs
   int wn = 0;   // width and first entry of the warp's next slice
   int64_t en = 0;
   if (w0 < ns) {
@@ -404,8 +448,7 @@ __device__ __forceinline__ void spmv_multi(const IterArgs<T>& a, const T* const*
     for (int u = 0; u < NE; ++u) {
       if (u < wc) {
 #pragma unroll
-        for (int r = 0; r < R; ++r)
-          if (act[r]) y[r] = fma_t(au[u], __ldg(v[r] + cu[u]), y[r]);
+        for (int r = 0; r < R; ++r) y[r] = fma_t(au[u], __ldg(vg[r] + cu[u]), y[r]);
       }
     }
     for (int j = NE; j < wc; ++j) {   // rows wider than NE entries
@@ -413,38 +456,65 @@ __device__ __forceinline__ void spmv_multi(const IterArgs<T>& a, const T* const*
       const int cc = __ldg(colp + e);
       const T vv = __ldg(valp + e);
 #pragma unroll
-      for (int r = 0; r < R; ++r)
-        if (act[r]) y[r] = fma_t(vv, __ldg(v[r] + cc), y[r]);
+      for (int r = 0; r < R; ++r) y[r] = fma_t(vv, __ldg(vg[r] + cc), y[r]);
     }
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
-      if (!act[r]) continue;
-      out[r][row] = y[r];
-      if (RTQ) accr[r].add(rv, y[r]);
-      if (DOTS) {
-        const T sv = __ldg(v[r] + row);
-        accd[r][0].add(sv, y[r]);
-        accd[r][1].add(y[r], y[r]);
-        accd[r][2].add(rv, y[r]);
-        accd[r][3].add(rv, sv);
+    for (int r = 0; r < R; ++r)
+      if (act[r]) out[r][row] = y[r];
+    if constexpr (PAIRS) {
+      const V rv2 = P::mk(rv, rv);
+#pragma unroll
+      for (int h = 0; h < H; ++h) {
+        const V yy = P::mk(y[2 * h], y[2 * h + 1]);
+        if (RTQ) accr[h].add(rv2, yy);
+        if (DOTS) {
+          const V sv = P::mk(__ldg(vg[2 * h] + row), __ldg(vg[2 * h + 1] + row));
+          accd[h][0].add(sv, yy);
+          accd[h][1].add(yy, yy);
+          accd[h][2].add(rv2, yy);
+          accd[h][3].add(rv2, sv);
+        }
+      }
+    } else {
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        if (RTQ) accr1[r].add(rv, y[r]);
+        if (DOTS) {
+          const T sv = __ldg(vg[r] + row);
+          accd1[r][0].add(sv, y[r]);
+          accd1[r][1].add(y[r], y[r]);
+          accd1[r][2].add(rv, y[r]);
+          accd1[r][3].add(rv, sv);
+        }
       }
     }
     if (KMAX > 0) {
 #pragma unroll
-      for (int r = 0; r < R; ++r) ws.y[r][lane] = act[r] ? y[r] : T(0);
+      for (int r = 0; r < R; ++r) {
+        if (PAIRS) ws.yi[lane][r] = y[r];
+        else ws.y[r][lane] = y[r];
+      }
       cp_async_wait<0>();   // this thread's tile copies landed
       __syncwarp();         // ... and every lane's, and y is visible
 #pragma unroll
       for (int cc = 0; cc < CPL; ++cc) {
         const int j = lane + 32 * cc;
         if (j < k) {
-          T part[R];
+          if constexpr (PAIRS) {
+            V part[H];
 #pragma unroll
-          for (int r = 0; r < R; ++r) part[r] = T(0);
-          col_dot<R>(ws.tile[j], ws.y, act, part);
+            for (int h = 0; h < H; ++h) part[h] = P::mk(T(0), T(0));
+            col_dot_pairs<T, R>(ws.tile[j], ws.yi, part);
 #pragma unroll
-          for (int r = 0; r < R; ++r)
-            if (act[r]) accp[r][cc].add1(part[r]);
+            for (int h = 0; h < H; ++h) accp[h][cc].add1(part[h]);
+          } else {
+            T part[R];
+#pragma unroll
+            for (int r = 0; r < R; ++r) part[r] = T(0);
+            col_dot<R>(ws.tile[j], ws.y, act, part);
+#pragma unroll
+            for (int r = 0; r < R; ++r) accp1[r][cc].add1(part[r]);
+          }
         }
       }
     }
@@ -453,13 +523,13 @@ __device__ __forceinline__ void spmv_multi(const IterArgs<T>& a, const T* const*
 #pragma unroll
   for (int r = 0; r < R; ++r) {
     if (RTQ) {
-      if (act[r]) warp_slot(accr[r], r * nvr, sm);
+      if (act[r]) warp_slot(PAIRS ? accr[r / 2].lane(r & 1) : accr1[r], r * nvr, sm);
       else zero_slot(r * nvr, sm);
     }
     if (DOTS) {
 #pragma unroll
       for (int d = 0; d < 4; ++d) {
-        if (act[r]) warp_slot(accd[r][d], r * nvr + d, sm);
+        if (act[r]) warp_slot(PAIRS ? accd[r / 2][d].lane(r & 1) : accd1[r][d], r * nvr + d, sm);
         else zero_slot(r * nvr + d, sm);
       }
     }
@@ -467,7 +537,7 @@ __device__ __forceinline__ void spmv_multi(const IterArgs<T>& a, const T* const*
 #pragma unroll
       for (int cc = 0; cc < CPL; ++cc) {
         const int j = lane + 32 * cc;
-        if (j < k) sm.w[warp][r * nvr + OFF + j] = act[r] ? accp[r][cc].get() : 0.0;
+        if (j < k) sm.w[warp][r * nvr + OFF + j] = act[r] ? (PAIRS ? accp[r / 2][cc].lane(r & 1) : accp1[r][cc]).get() : 0.0;
       }
     }
   }
