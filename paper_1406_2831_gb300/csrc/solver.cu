@@ -100,6 +100,10 @@ struct rb_ctx {
   SellBuf<float> A32;
   bool have_matrix = false;
   int matrix_epoch = 0, update_epoch = -1;
+  // Alg. 2 step 1 owed for the first setup_pending columns of U, U~ (-1:
+  // none).  A new matrix or an adopted update only marks the setup; the next
+  // solve runs it, so a setup that no solve would use is never computed.
+  int setup_pending = -1;
   // recycle space (column-major, leading dimension npad), k_used columns
   int k = 0, kcap = 0;
   double *U = nullptr, *Ut = nullptr, *C = nullptr, *Ct = nullptr, *Chat = nullptr;
@@ -489,6 +493,22 @@ int recycle_setup(rb_ctx* h, int kin, int64_t* setup_mv) {
   rc = sync(h);
   if (rc) return rc;
   return kk < kin ? RB_WRECYCLE_RANK : RB_OK;
+}
+
+// Defer Alg. 2 step 1 for kin columns of U, U~ to the next solve.
+void mark_setup(rb_ctx* h, int kin) {
+  h->k = 0;
+  reset_graphs(h);
+  h->setup_pending = kin;
+}
+
+// Run a deferred setup; its matrix-vector products are added to *setup_mv.
+int ensure_setup(rb_ctx* h, int64_t* setup_mv) {
+  if (h->setup_pending < 0) return RB_OK;
+  const int kin = h->setup_pending;
+  h->setup_pending = -1;
+  const int rc = recycle_setup(h, kin, setup_mv);
+  return rc == RB_WRECYCLE_RANK ? RB_OK : rc;
 }
 
 // ------------------------------------------------------------ iteration args
@@ -907,11 +927,8 @@ int adopt_candidate(rb_ctx* h, SolveOut* so) {
     RB_CUDA_TRY(scale_cols<double>(h->U, ld, h->kY, h->dR, h->npad, h->us));
   }
   RB_CUDA_TRY(cudaMemcpyAsync(h->Ut, h->U, sizeof(double) * ld * h->kY, cudaMemcpyDeviceToDevice, h->us));
-  int64_t mv = 0;
-  int rc = recycle_setup(h, h->kY, &mv);
+  mark_setup(h, h->kY);   // C, C~ and D_c for the new space: at the next solve
   so->ms_update += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
-  if (rc < 0) return rc;
-  so->mv_setup += mv;
   h->update_epoch = h->matrix_epoch;
   return RB_OK;
 }
@@ -1333,12 +1350,9 @@ extern "C" int rbicgstab_set_matrix(rb_handle h, int64_t n, int64_t nnz, const i
   if (rc) return rc;
   h->have_matrix = true;
   h->matrix_epoch += 1;
-  // keep U, U~ and recompute C, C~, D_c for the new matrix
-  const int kin = h->k;
-  if (kin > 0) {
-    int64_t mv = 0;
-    return recycle_setup(h, kin, &mv);
-  }
+  // keep U, U~; C, C~, D_c for the new matrix are recomputed by the next solve
+  const int kin = h->setup_pending >= 0 ? h->setup_pending : h->k;
+  if (kin > 0) mark_setup(h, kin);
   return RB_OK;
 }
 
@@ -1354,10 +1368,8 @@ extern "C" int rbicgstab_set_values(rb_handle h, const double* val, int where) {
   rc = build_matrix_values(h);
   if (rc) return rc;
   h->matrix_epoch += 1;
-  if (h->k > 0) {
-    int64_t mv = 0;
-    return recycle_setup(h, h->k, &mv);
-  }
+  const int kin = h->setup_pending >= 0 ? h->setup_pending : h->k;
+  if (kin > 0) mark_setup(h, kin);
   return RB_OK;
 }
 
@@ -1391,15 +1403,17 @@ extern "C" int rbicgstab_set_recycle(rb_handle h, int32_t k, const double* U, co
     }
   }
   int64_t mv = 0;
+  h->setup_pending = -1;
   return recycle_setup(h, k, &mv);
 }
 
 extern "C" int rbicgstab_get_recycle(rb_handle h, int32_t* k, double* U, double* Ut, int64_t ld, int where) {
   if (!h || !k || (where != RB_HOST && where != RB_DEVICE)) return RB_EINVAL;
-  *k = h->k;
-  if (h->k == 0) return RB_OK;
+  const int kk = h->setup_pending >= 0 ? h->setup_pending : h->k;
+  *k = kk;
+  if (kk == 0) return RB_OK;
   if ((U || Ut) && ld < h->n) return RB_EINVAL;
-  for (int j = 0; j < h->k; ++j) {
+  for (int j = 0; j < kk; ++j) {
     int rc = RB_OK;
     if (U) rc = copy_out(U + (int64_t)j * ld, colp(h->U, h->npad, j), sizeof(double) * h->n, where, h->us);
     if (!rc && Ut) rc = copy_out(Ut + (int64_t)j * ld, colp(h->Ut, h->npad, j), sizeof(double) * h->n, where, h->us);
@@ -1473,6 +1487,11 @@ extern "C" int rbicgstab_solve_block(rb_handle h, int32_t nrhs, const double* B,
       return done(RB_ECUDA);
     x_nonzero[i] = nb[1] != 0.0;
     h->hst[i].red[0] = nb[0];
+  }
+  {
+    int64_t mv = 0;
+    if ((rc = ensure_setup(h, &mv)) < 0) return done(rc);
+    so[0].mv_setup += mv;
   }
   rc = (h->o.precision == RB_MIXED) ? solve_mixed(h, nrhs, so) : solve_fp64(h, nrhs, x_nonzero, so);
   if (rc < 0 && rc != RB_ENOTCONV) return done(rc);
@@ -1559,6 +1578,10 @@ extern "C" int rbicgstab_time_passes(rb_handle h, int32_t nrhs, const double* B,
   if (nrhs > 1 && ld < h->n) return RB_EINVAL;
   int rc = ensure_slots(h, nrhs);
   if (rc) return rc;
+  {
+    int64_t mv = 0;
+    if ((rc = ensure_setup(h, &mv)) < 0) return rc;
+  }
   SolveOut so[kMaxRhs];
   double* rhs[kMaxRhs];
   double* xb[kMaxRhs];
