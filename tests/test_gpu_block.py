@@ -244,3 +244,31 @@ def test_time_passes_block(precision):
     ms, code = rb.time_passes(s, _rhs_block(A.n, 4), reps=3)
     assert code == rb.RB_OK
     assert np.all(ms > 0)
+
+
+def test_block_mixed_full_size_properties():
+    """System 1 of the 128^3 shifted sequence at full size (n = 2,097,152):
+    its four right-hand sides as one block in the mixed path with a fixed
+    k = 20 right-only space, the kernel configuration the benchmark times.
+    Checked by properties that hold at any size: every system's FP64 true
+    residual; the first system's solution against the FP64 oracle's solve
+    with the same space (both meet the tolerance, so they agree to the
+    conditioning of the system); and the iteration count against the
+    oracle's (FP32 arithmetic costs iterations, never fewer than half)."""
+    import scipy.sparse as sp
+    spec = inputs.config_shifted_3d(N=128, n_shifts=20, n_rhs=4, k=20)
+    P = spec.pattern
+    vals = spec.values[0]()
+    S = sp.csr_matrix((vals, P.col, P.row_ptr), shape=(P.n, P.n))
+    B = np.stack([g() for g in spec.rhs[0]])
+    U = inputs.random_recycle_basis(P.n, 20, 11)
+    s = rb.Solver(precision="mixed", recycle="fixed", k_max=20, tol=1e-8)
+    s.set_matrix(P.row_ptr, P.col, vals)
+    s.set_recycle(U)
+    res = s.solve_block(B)
+    for i in range(4):
+        assert res.stats[i]["status"] == rb.RB_OK
+        assert np.linalg.norm(B[i] - S @ res.x[i]) / np.linalg.norm(B[i]) <= 1e-8
+    xo, io = orb.rbicgstab(S, B[0], orb.recycle_setup(S, U), tol=1e-8)
+    assert _rel(res.x[0], xo) <= 1e-5, _rel(res.x[0], xo)
+    assert 0.5 * io.iters <= res.stats[0]["iters"] <= 2.0 * io.iters, (res.stats[0]["iters"], io.iters)
