@@ -198,8 +198,8 @@ int rbicgstab_time_passes(rb_handle h, int32_t nrhs, const double* B, int64_t ld
  * device memory (a framework that owns the allocator and forbids cudaMalloc,
  * work about to be captured into a CUDA graph, a service whose device memory
  * is sized once at start-up).  Nothing is allocated and no handle is needed:
- * the kernel's scratch (1024 block partial sums and a completion ticket,
- * about 8 KB) is a fixed device array that every GPU loading the library
+ * the kernel's scratch (1024 block and 65 group partial sums and the
+ * completion tickets, about 9 KB) is a fixed device array that every GPU loading the library
  * keeps until the process exits.  The first call on a device looks up that
  * array's address (which can load the module): make it before any stream
  * capture.  The call is ordered on `cuda_stream` (NULL = legacy default

@@ -6,10 +6,10 @@
 // forbids raw cudaMalloc, code about to be captured into a CUDA graph, or a
 // service that pre-sizes all device memory at start-up and must not grow it.
 // This entry point serves them.  The caller passes every input and output;
-// the only scratch this kernel needs (one partial sum per block and the
-// completion ticket of the grid reduction) lives in a fixed file-scope
-// device array of about 8 KB, which every GPU that loads the library keeps
-// until the process exits.
+// the only scratch this kernel needs (one partial sum per block and per
+// group of 16 blocks, and the completion tickets of the grid reduction)
+// lives in a fixed file-scope device array of about 9 KB, which every GPU
+// that loads the library keeps until the process exits.
 #include <mutex>
 
 #include "device.cuh"
