@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--quick", action="store_true", help="small grid for a smoke run (not a bench line)")
+    ap.add_argument("--rbicg", action="store_true",
+                    help="time Alg. 1 (RBiCG, primary + dual, FP64) on system 1 instead of the sequence")
     ap.add_argument("--passes-only", action="store_true",
                     help="set up one system and a k-column right-only recycle space, time the five "
                          "fused passes (recycled and plain) and exit; a short program for profilers")
@@ -224,6 +226,79 @@ def run_passes_only(args):
                       "status": code}
         del s
     return out
+
+
+def rbicg_iter_bytes_flops(n, z, k):
+    """Algorithmic HBM bytes and FP64 flops of one Alg. 1 iteration (primary +
+    dual, FP64, int32 columns): B1 two SpMVs (A, A^T) and k-column projections
+    (C-hat, C); B2 the corrections (C, C~) and (p~, q); B3 four axpys and three
+    dots; B4 the two search directions."""
+    v = 8
+    a = (v + 4) * z + 4 * (n + 1)
+    b1 = 2 * (a + v * n * (k + 2))
+    b2 = v * n * (2 * k + 3) + (2 * v * n if k else 0)
+    b3 = 12 * v * n
+    b4 = 6 * v * n
+    f1 = 2 * (2 * z + 2 * n * k)
+    f2 = 4 * n * k + 2 * n
+    f3 = 14 * n
+    f4 = 4 * n
+    return b1 + b2 + b3 + b4, f1 + f2 + f3 + f4
+
+
+def run_rbicg(args):
+    """Alg. 1 (RBiCG): the primary system and its dual solved together, FP64,
+    with a fixed k-column space, on system 1 of the sequence (right-hand side 1
+    as b, right-hand side 2 as b~)."""
+    import numpy as np
+    import torch
+
+    from paper_1406_2831_gb300 import inputs
+    from paper_1406_2831_gb300 import rbicgstab as rb
+
+    spec = inputs.config_shifted_3d(N=args.N, n_shifts=args.shifts, n_rhs=2, k=args.k)
+    P = spec.pattern
+    dev = torch.device("cuda", 0)
+    vals = torch.from_numpy(spec.values[0]()).to(dev)
+    b = torch.from_numpy(spec.rhs[0][0]()).to(dev)
+    bt = torch.from_numpy(spec.rhs[0][1]()).to(dev)
+    rp, col = torch.from_numpy(P.row_ptr).to(dev), torch.from_numpy(P.col).to(dev)
+    s = rb.Solver(k_max=args.k, recycle="fixed" if args.k else "none", precision="fp64")
+    s.set_matrix(rp, col, vals)
+    if args.k:
+        s.set_recycle(torch.from_numpy(inputs.random_recycle_basis(P.n, args.k, 11)).to(dev))
+    x, xt = torch.zeros_like(b), torch.zeros_like(b)
+    for _ in range(max(args.warmup, 1)):
+        x.zero_(); xt.zero_()
+        s.solve_dual(b, bt, x, xt)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    iters = []
+    e0.record()
+    for _ in range(args.steps):
+        x.zero_(); xt.zero_()
+        r, rd = s.solve_dual(b, bt, x, xt)
+        iters.append(r.stats["iters"])
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    it = float(np.mean(iters))
+    byt, fl = rbicg_iter_bytes_flops(P.n, P.nnz, args.k)
+    ms_it = ms / it
+    peak = measured_peaks()
+    fp64 = fp64_peak_tflops(torch)
+    gbs = byt / (ms_it * 1e-3) / 1e9
+    tfl = fl / (ms_it * 1e-3) / 1e12
+    return {"metric": "RBiCG (Alg. 1) primary+dual solves/sec at 1e-8 rel. residual", "value": round(1e3 / ms, 3),
+            "unit": "solves/s", "impl": "ours", "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"3d-7pt-conv-diff-{args.N}^3 system 1, b = RHS 1, b~ = RHS 2",
+                       "n": P.n, "nnz": P.nnz, "k": args.k, "recycle": "fixed random right-only space"},
+            "iters": it, "ms_per_solve": round(ms, 3), "ms_per_iter": round(ms_it, 5),
+            "relres": [r.stats["relres_true"], rd.stats["relres_true"]],
+            "roofline": {"hbm": {"achieved": round(gbs, 1), "peak": peak["hbm_gbs"], "unit": "GB/s",
+                                 "frac": round(gbs / peak["hbm_gbs"], 4), "bytes_per_iter": byt},
+                         "fp64": {"achieved": round(tfl, 3), "peak": round(fp64, 3), "unit": "TFLOP/s",
+                                  "frac": round(tfl / fp64, 4), "flops_per_iter": fl}}}
 
 
 def run_ours(args):
@@ -491,7 +566,9 @@ def run_reference(args):
 
 def main():
     args = parse()
-    if args.passes_only:
+    if args.rbicg:
+        line = run_rbicg(args)
+    elif args.passes_only:
         line = run_passes_only(args)
     else:
         line = run_reference(args) if args.impl == "reference" else run_ours(args)

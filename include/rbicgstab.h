@@ -164,6 +164,27 @@ int rbicgstab_solve(rb_handle h, const double* b, double* x, int where, rb_stats
 int rbicgstab_solve_block(rb_handle h, int32_t nrhs, const double* B, double* X, int64_t ld,
                           int where, rb_stats* st);
 
+/* Alg. 1 (RBiCG, Sec. 4): the primary system A x = b and the dual system
+ * A^T x~ = b~ solved together with the handle's recycle space (U, U~ as given
+ * to rbicgstab_set_recycle, or U~ = U; C = A U and C~ = A^T U~ biorthogonal,
+ * C-hat = C~ D_c^{-1}, C-check = C D_c^{-1}, eq. (3.4)), in FP64 whatever the
+ * handle's precision.  b, b~ and x, x~ are n-vectors (host or device per
+ * `where`); bt may be NULL, and then the shadow vector r~_{-1} of Alg. 2
+ * (seed opts.shadow_seed) is the dual right-hand side.  x and xt hold the
+ * initial guesses x_{-1}, x~_{-1} on entry (eq. (3.5) forms x_0, r_0, x~_0,
+ * r~_0) and the solutions after step 7 on return.  When (r_0, r~_0) = 0,
+ * x~_{-1} is replaced by the shadow vector (seed + 0, 1, 2) and the dual start
+ * formed again (step 3).  Converged when ||r_i|| <= tol ||b|| and
+ * ||r~_i|| <= tol ||b~|| on the recursive residuals.  st and st_dual, if not
+ * NULL, receive the primary and the dual system's records (iters, status and
+ * matvecs are shared; relres_* are each system's own; seeds_used counts the
+ * dual starts drawn).  The recycle space is not updated.  Returns RB_OK, or
+ * RB_EBREAKDOWN_RHO ((p~_i, q_i) = 0 or (r~_i, r_i) = 0), RB_ENOTCONV,
+ * RB_ENONFINITE (NaN/Inf in b, b~, x, x~ or during the iteration), with the
+ * last iterates in x, xt.  Errors: RB_EDIM (no matrix), RB_EINVAL, RB_ECUDA. */
+int rbicg_solve(rb_handle h, const double* b, const double* bt, double* x, double* xt, int where,
+                rb_stats* st, rb_stats* st_dual);
+
 /* y = A v (transpose = 0) or y = A^T v (transpose = 1) with the library's
  * FP64 SpMV kernels; v and y have n entries.  Errors: RB_EDIM, RB_EINVAL. */
 int rbicgstab_apply(rb_handle h, const double* v, double* y, int transpose, int where);

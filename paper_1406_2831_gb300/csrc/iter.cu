@@ -1496,4 +1496,118 @@ void iteration_grids(int k, int nsm, int64_t npad, Grids* g, int nrhs) {
 template void iteration_grids<double>(int, int, int64_t, Grids*, int);
 template void iteration_grids<float>(int, int, int64_t, Grids*, int);
 
+// ================================================================ RBiCG (Alg. 1)
+// The scalar steps of Alg. 1 for a primary system A x = b and its dual
+// A^T x~ = b~ (FP64, real, so conj(alpha) = alpha).  The vector work of an
+// iteration is composed on the host from the library's other kernels (see
+// the RBiCG driver); these two kernels close it:
+//
+//   k_bi_alpha  after z = A p, z~ = A^T p~ (with C-hat^T z and C^T z~ in the
+//               gamma fields of st[0], st[1]), q = z - C zeta, q~ = z~ - C~ zeta~
+//               (zeta~ = D_c^{-1} C^T z~) and (p~, q) in st[0].red[0]:
+//               alpha = (r~, r) / (p~, q), zeta_c += alpha zeta, zeta~_c += alpha zeta~
+//   k_b3        x += alpha p, x~ += alpha p~, r -= alpha q, r~ -= alpha q~;
+//               ||r||^2, ||r~||^2, (r~, r) -> convergence of both,
+//               beta = (r~_i, r_i) / (r~_{i-1}, r_{i-1})
+//   k_b4        p = r + beta p,  p~ = r~ + beta p~   (first line of the next iteration)
+//
+// st[0] carries the primary system's scalars (rho = (r~, r), alpha, beta,
+// zeta_c in `xc`, its threshold), st[1] the dual's (zeta~_c, threshold,
+// ||r~||^2).  Each kernel returns at once when st[0].done.
+
+__global__ void k_bi_alpha(IterState* st, const double* __restrict__ dinv) {
+  if (st[0].done) return;
+  const int lane = threadIdx.x & 31;
+  const int k = st[0].k;
+  double alpha = 0.0;
+  int ok = 0;
+  if (lane == 0) {
+    const double ptq = st[0].red[0];
+    if (ptq == 0.0 || !isfinite(ptq)) {
+      fail(&st[0], ptq == 0.0 ? RB_EBREAKDOWN_RHO : RB_ENONFINITE);
+    } else {
+      alpha = st[0].rho / ptq;
+      st[0].alpha = alpha;
+      ok = 1;
+    }
+  }
+  ok = __shfl_sync(0xffffffffu, ok, 0);
+  if (!ok) return;
+  alpha = __shfl_sync(0xffffffffu, alpha, 0);
+  for (int j = lane; j < k; j += 32) {
+    st[0].xc[j] += alpha * st[0].gamma[j];
+    st[1].xc[j] += alpha * (st[1].gamma[j] * dinv[j]);
+  }
+}
+
+__device__ void finish_b3(IterState* st, const double* res) {
+  if ((threadIdx.x & 31) != 0) return;
+  IterState* s0 = &st[0];
+  s0->iter += 1;
+  const double rn2 = res[0], rtn2 = res[1], rho_new = res[2];
+  s0->rnorm2 = rn2;
+  st[1].rnorm2 = rtn2;
+  st[1].iter = s0->iter;
+  if (!isfinite(rn2) || !isfinite(rtn2) || !isfinite(rho_new)) {
+    fail(s0, RB_ENONFINITE);
+  } else if (rn2 <= s0->thresh2 && rtn2 <= st[1].thresh2) {
+    s0->done = 1;
+  } else if (rho_new == 0.0) {
+    fail(s0, RB_EBREAKDOWN_RHO);
+  } else {
+    s0->beta = rho_new / s0->rho;
+    s0->rho = rho_new;
+    if (s0->iter >= s0->max_itn) fail(s0, RB_ENOTCONV);
+  }
+}
+
+__global__ void __launch_bounds__(kBlock) k_b3(BiArgs a) {
+  IterState* st = a.st;
+  if (st[0].done) return;
+  __shared__ ReduceSmem<3> sm;
+  const double alpha = st[0].alpha;
+  Acc<double> acc[3];
+  for (int64_t i = gtid(); i < a.npad; i += gstride()) {
+    const double r = fma_t(-alpha, a.q[i], a.r[i]);
+    const double rt = fma_t(-alpha, a.qt[i], a.rt[i]);
+    a.x[i] = fma_t(alpha, a.p[i], a.x[i]);
+    a.xt[i] = fma_t(alpha, a.pt[i], a.xt[i]);
+    a.r[i] = r;
+    a.rt[i] = rt;
+    acc[0].add(r, r);
+    acc[1].add(rt, rt);
+    acc[2].add(rt, r);
+  }
+  if (block_reduce_last<double, 3>(acc, 3, sm, a.partials, &st[0].ticket[P3]) && threadIdx.x < 32)
+    finish_b3(st, sm.res);
+}
+
+__global__ void __launch_bounds__(kBlock) k_b4(BiArgs a) {
+  IterState* st = a.st;
+  if (st[0].done) return;
+  const double beta = st[0].beta;
+  for (int64_t i = gtid(); i < a.npad; i += gstride()) {
+    a.p[i] = fma_t(beta, a.p[i], a.r[i]);
+    a.pt[i] = fma_t(beta, a.pt[i], a.rt[i]);
+  }
+}
+
+cudaError_t bicg_alpha(IterState* st, const double* dinv, cudaStream_t s) {
+  count_launches(1);
+  k_bi_alpha<<<1, 32, 0, s>>>(st, dinv);
+  return cudaGetLastError();
+}
+
+cudaError_t bicg_update(const BiArgs& a, int grid, cudaStream_t s) {
+  count_launches(2);
+  k_b3<<<grid, kBlock, 0, s>>>(a);
+  k_b4<<<grid, kBlock, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+int bicg_grid(int nsm, int64_t npad) {
+  const int64_t work = (npad + kBlock - 1) / kBlock;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(work, occ((const void*)k_b3, nsm)));
+}
+
 }  // namespace rb

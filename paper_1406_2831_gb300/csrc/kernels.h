@@ -56,6 +56,22 @@ void iteration_grids(int k, int nsm, int64_t npad, Grids* g, int nrhs);
 template <typename T>
 cudaError_t launch_pass(int pass, const IterArgs<T>& a, int k, const Grids& g, cudaStream_t s);
 
+// Alg. 1 (RBiCG) for a primary system and its dual, FP64: the vector
+// arrays and scalars of the closing passes (q, qt are the corrected
+// products).  st[0]: primary scalars, st[1]: dual.
+struct BiArgs {
+  int64_t npad;
+  double *x, *r, *p, *q;        // primary
+  double *xt, *rt, *pt, *qt;    // dual
+  IterState* st;
+  double* partials;
+};
+// alpha = (r~, r) / (p~, q) from st[0].red[0], and the zeta_c updates.
+cudaError_t bicg_alpha(IterState* st, const double* dinv, cudaStream_t s);
+// x, x~, r, r~ updates with the convergence test and beta; then p, p~.
+cudaError_t bicg_update(const BiArgs& a, int grid, cudaStream_t s);
+int bicg_grid(int nsm, int64_t npad);
+
 // ---------------------------------------------------------------- matrix.cu
 // Sparse matrix in SELL-32 form, owned by the library.
 template <typename T>

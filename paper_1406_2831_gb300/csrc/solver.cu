@@ -134,6 +134,8 @@ struct rb_ctx {
   const double** dptr = nullptr;   // device pointer lists (4 * 128)
   Grids grids{};
   GraphSlot g_plain, g_cycle[kBanks];
+  GraphSlot g_bicg;       // Alg. 1 iterations (primary + dual)
+  int g_bicg_k = -1;
   int g_k = -1, g_nrhs = -1;
 };
 
@@ -158,13 +160,14 @@ int sync(rb_ctx* h) {
 }
 
 void reset_graphs(rb_ctx* h) {
-  for (GraphSlot* g : {&h->g_plain, &h->g_cycle[0], &h->g_cycle[1], &h->g_cycle[2]}) {
+  for (GraphSlot* g : {&h->g_plain, &h->g_cycle[0], &h->g_cycle[1], &h->g_cycle[2], &h->g_bicg}) {
     if (g->exec) cudaGraphExecDestroy(g->exec);
     g->exec = nullptr;
     g->valid = false;
   }
   h->g_k = -1;
   h->g_nrhs = -1;
+  h->g_bicg_k = -1;
 }
 
 int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
@@ -1524,6 +1527,267 @@ extern "C" int rbicgstab_solve_block(rb_handle h, int32_t nrhs, const double* B,
     o.ms_update = so[0].ms_update;
   }
   return done(worst);
+}
+
+// ============================================================ RBiCG (Alg. 1)
+namespace {
+
+// Eq. (3.5) for the dual system: r~_{-1} = b~ - A^T x~_{-1} (x~_{-1} in s.x),
+// x~_0 = x~_{-1} + U~ C-check^T r~_{-1}, r~_0 = r~_{-1} - C~ C-check^T r~_{-1}
+// (C-check^T v = D_c^{-1} C^T v).  Slot 1 holds the dual system.
+int bicg_dual_start(rb_ctx* h) {
+  Slot& d = h->sl[1];
+  const int64_t ld = h->npad;
+  RB_CUDA_TRY(residual_norm(h->AT.view(), d.b, d.x, d.r, h->npad, h->st + 1, h->partials, h->grids.spmv, h->us));
+  if (h->k > 0) {
+    DotArgs da{};
+    da.M = h->C; da.ld = ld; da.km = h->k; da.v = d.r; da.nd = 0;
+    RB_CUDA_TRY(dots(da, h->npad, h->st + 1, h->partials, vec_grid(h), h->us));
+    RB_CUDA_TRY(gemv_update(d.x, h->Ut, ld, h->k, h->st[1].red, h->Dinv, 1.0, h->npad, vec_grid(h), h->us));
+    RB_CUDA_TRY(gemv_update(d.r, h->Ct, ld, h->k, h->st[1].red, h->Dinv, -1.0, h->npad, vec_grid(h), h->us));
+  }
+  return RB_OK;
+}
+
+BiArgs bicg_args(rb_ctx* h) {
+  Slot &p = h->sl[0], &d = h->sl[1];
+  BiArgs a{};
+  a.npad = h->npad;
+  a.x = p.x; a.r = p.r; a.p = p.p; a.q = p.qraw;
+  a.xt = d.x; a.rt = d.r; a.pt = d.p; a.qt = d.qraw;
+  a.st = h->st;
+  a.partials = h->partials;
+  return a;
+}
+
+// One iteration of Alg. 1 on stream s, composed of the library's kernels:
+//   z = A p, zeta = C-hat^T z        (the FP64 SpMV + projection pass, state st[0])
+//   z~ = A^T p~, C^T z~              (the same pass on A^T and C, state st[1])
+//   q = z - C zeta, q~ = z~ - C~ D_c^{-1} C^T z~   (in place over z, z~)
+//   (p~, q); alpha, zeta_c, zeta~_c; x, x~, r, r~, ||r||, ||r~||, beta; p, p~
+cudaError_t bicg_iteration(rb_ctx* h, const Grids& g13, int grid, cudaStream_t s) {
+  Slot &P = h->sl[0], &D = h->sl[1];
+  const int64_t ld = h->npad;
+  const int k = h->k;
+  cudaError_t e;
+  if (k == 0) {
+    if ((e = spmv<double>(h->A.view(), P.p, P.qraw, 1.0, 0.0, h->grids.spmv, s)) != cudaSuccess) return e;
+    if ((e = spmv<double>(h->AT.view(), D.p, D.qraw, 1.0, 0.0, h->grids.spmv, s)) != cudaSuccess) return e;
+  } else {
+    IterArgs<double> ap{};
+    ap.A = h->A.view();
+    ap.Chat = h->Chat;
+    ap.ld = ld;
+    ap.s[0] = P.p;
+    ap.traw[0] = P.qraw;
+    ap.st = h->st;
+    ap.partials = h->partials;
+    ap.npad = h->npad;
+    ap.nrhs = 1;
+    IterArgs<double> ad = ap;
+    ad.A = h->AT.view();
+    ad.Chat = h->C;
+    ad.s[0] = D.p;
+    ad.traw[0] = D.qraw;
+    ad.st = h->st + 1;
+    if ((e = launch_pass<double>(P3, ap, k, g13, s)) != cudaSuccess) return e;
+    if ((e = launch_pass<double>(P3, ad, k, g13, s)) != cudaSuccess) return e;
+    if ((e = gemv_update(P.qraw, h->C, ld, k, h->st[0].gamma, nullptr, -1.0, h->npad, vec_grid(h), s)) != cudaSuccess)
+      return e;
+    if ((e = gemv_update(D.qraw, h->Ct, ld, k, h->st[1].gamma, h->Dinv, -1.0, h->npad, vec_grid(h), s)) !=
+        cudaSuccess)
+      return e;
+  }
+  DotArgs d{};
+  d.nd = 1;
+  d.a[0] = D.p; d.b[0] = P.qraw;
+  if ((e = dots(d, h->npad, h->st, h->partials, vec_grid(h), s)) != cudaSuccess) return e;
+  if ((e = bicg_alpha(h->st, h->Dinv, s)) != cudaSuccess) return e;
+  return bicg_update(bicg_args(h), grid, s);
+}
+
+int capture_bicg(rb_ctx* h) {
+  GraphSlot* g = &h->g_bicg;
+  if (g->exec) cudaGraphExecDestroy(g->exec);
+  g->exec = nullptr;
+  g->valid = false;
+  Grids g13;
+  iteration_grids<double>(h->k, h->nsm, h->npad, &g13, 1);
+  const int grid = bicg_grid(h->nsm, h->npad);
+  cudaGraph_t graph = nullptr;
+  RB_CUDA_TRY(cudaStreamBeginCapture(h->cs, cudaStreamCaptureModeThreadLocal));
+  cudaError_t err = cudaSuccess;
+  for (int j = 0; j < poll_iters(h) && err == cudaSuccess; ++j) err = bicg_iteration(h, g13, grid, h->cs);
+  cudaError_t e2 = cudaStreamEndCapture(h->cs, &graph);
+  if (err != cudaSuccess || e2 != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    return RB_ECUDA;
+  }
+  cudaError_t e3 = cudaGraphInstantiate(&g->exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e3 != cudaSuccess) return RB_ECUDA;
+  g->valid = true;
+  h->g_bicg_k = h->k;
+  return RB_OK;
+}
+
+}  // namespace
+
+extern "C" int rbicg_solve(rb_handle h, const double* b, const double* bt, double* x, double* xt, int where,
+                           rb_stats* st, rb_stats* st_dual) {
+  if (!h || !b || !x || !xt || (where != RB_HOST && where != RB_DEVICE)) return RB_EINVAL;
+  if (!h->have_matrix) return RB_EDIM;
+  int rc = ensure_slots(h, 2);
+  if (rc) return rc;
+  SolveOut so{};
+  {
+    int64_t mv = 0;
+    if ((rc = ensure_setup(h, &mv)) < 0) return rc;
+    so.mv_setup = mv;
+  }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  auto done = [&](int code) {
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    return code;
+  };
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return done(RB_ECUDA);
+  if (cudaEventRecord(e0, h->us) != cudaSuccess) return done(RB_ECUDA);
+  const int64_t n = h->n, ld = h->npad;
+  Slot &P = h->sl[0], &D = h->sl[1];
+  // b, b~ (the shadow vector when bt is NULL), x_{-1}, x~_{-1}
+  if ((rc = copy_in(P.b, b, sizeof(double) * n, where, h->us))) return done(rc);
+  if (bt) {
+    if ((rc = copy_in(D.b, bt, sizeof(double) * n, where, h->us))) return done(rc);
+  } else {
+    RB_CUDA_TRY(shadow(D.b, n, h->npad, h->o.shadow_seed, h->us));
+  }
+  if ((rc = copy_in(P.x, x, sizeof(double) * n, where, h->us))) return done(rc);
+  if ((rc = copy_in(D.x, xt, sizeof(double) * n, where, h->us))) return done(rc);
+  double nb[2];
+  for (int i = 0; i < 2; ++i) {
+    Slot& s = h->sl[i];
+    int f = 0;
+    RB_CUDA_TRY(check_finite(s.b, n, h->dflag, h->us));
+    RB_CUDA_TRY(cudaMemcpyAsync(&f, h->dflag, sizeof(int), cudaMemcpyDeviceToHost, h->us));
+    if ((rc = sync(h))) return done(rc);
+    int fx = 0;
+    RB_CUDA_TRY(check_finite(s.x, n, h->dflag, h->us));
+    RB_CUDA_TRY(cudaMemcpyAsync(&fx, h->dflag, sizeof(int), cudaMemcpyDeviceToHost, h->us));
+    if ((rc = sync(h))) return done(rc);
+    if (f || fx) return done(RB_ENONFINITE);
+    DotArgs d{};
+    d.nd = 1;
+    d.a[0] = s.b; d.b[0] = s.b;
+    if ((rc = run_dots(h, d, &nb[i], 1, i))) return done(rc);
+  }
+  // eq. (3.5), primary: r_{-1} = b - A x_{-1}; x_0, r_0
+  RB_CUDA_TRY(residual_norm(h->A.view(), P.b, P.x, P.r, h->npad, h->st, h->partials, h->grids.spmv, h->us));
+  if (h->k > 0) {
+    DotArgs d{};
+    d.M = h->Chat; d.ld = ld; d.km = h->k; d.v = P.r; d.nd = 0;
+    RB_CUDA_TRY(dots(d, h->npad, h->st, h->partials, vec_grid(h), h->us));
+    RB_CUDA_TRY(gemv_update(P.x, h->U, ld, h->k, h->st[0].red, nullptr, 1.0, h->npad, vec_grid(h), h->us));
+    RB_CUDA_TRY(gemv_update(P.r, h->C, ld, h->k, h->st[0].red, nullptr, -1.0, h->npad, vec_grid(h), h->us));
+  }
+  // dual; step 3: a new x~_{-1} while (r_0, r~_0) = 0
+  if ((rc = bicg_dual_start(h))) return done(rc);
+  double red[3];
+  so.seeds = 0;
+  for (int attempt = 0;; ++attempt) {
+    DotArgs d{};
+    d.nd = 3;
+    d.a[0] = D.r; d.b[0] = P.r;
+    d.a[1] = P.r; d.b[1] = P.r;
+    d.a[2] = D.r; d.b[2] = D.r;
+    if ((rc = run_dots(h, d, red, 3, 0))) return done(rc);
+    if (red[0] != 0.0 || attempt == 3) break;
+    RB_CUDA_TRY(shadow(D.x, n, h->npad, h->o.shadow_seed + (uint64_t)attempt, h->us));
+    so.seeds = attempt + 1;
+    if ((rc = bicg_dual_start(h))) return done(rc);
+  }
+  // step 4 (p_0 = 0, beta_0 = 0): the first iteration's p_1 = r_0
+  RB_CUDA_TRY(cudaMemcpyAsync(P.p, P.r, sizeof(double) * ld, cudaMemcpyDeviceToDevice, h->us));
+  RB_CUDA_TRY(cudaMemcpyAsync(D.p, D.r, sizeof(double) * ld, cudaMemcpyDeviceToDevice, h->us));
+  if ((rc = read_state(h, 2))) return done(rc);
+  const int max_itn = h->o.max_itn > 0 ? h->o.max_itn : (int)std::min<int64_t>(n, 20000);
+  const double tol = h->o.tol;
+  for (int i = 0; i < 2; ++i) {
+    IterState& hs = h->hst[i];
+    hs.k = h->k;
+    for (int j = 0; j < h->k; ++j) hs.xc[j] = 0.0;
+    hs.iter = 0;
+    hs.half = 0;
+    hs.done = 0;
+    hs.status = RB_OK;
+    hs.max_itn = max_itn;
+    hs.thresh2 = tol * tol * nb[i];
+    hs.bnorm2 = nb[i];
+    hs.rnorm2 = i == 0 ? red[1] : red[2];
+    hs.alpha = hs.beta = hs.omega = 0.0;
+    hs.rho = red[0];
+  }
+  IterState& h0 = h->hst[0];
+  if (!std::isfinite(red[0]) || !std::isfinite(red[1]) || !std::isfinite(red[2])) {
+    h0.status = RB_ENONFINITE;
+    h0.done = 1;
+  } else if (red[1] <= h0.thresh2 && red[2] <= h->hst[1].thresh2) {
+    h0.done = 1;
+  } else if (red[0] == 0.0) {
+    h0.status = RB_EBREAKDOWN_RHO;
+    h0.done = 1;
+  }
+  RB_CUDA_TRY(cudaMemcpyAsync(h->st, h->hst, sizeof(IterState) * 2, cudaMemcpyHostToDevice, h->us));
+  // step 5: graphs of poll iterations until both systems converge or the solve stops
+  if (!h0.done) {
+    if (!h->g_bicg.valid || h->g_bicg_k != h->k) {
+      if ((rc = capture_bicg(h))) return done(rc);
+    }
+    for (;;) {
+      RB_CUDA_TRY(cudaGraphLaunch(h->g_bicg.exec, h->us));
+      count_launches((long long)poll_iters(h) * (h->k > 0 ? 8 : 6));
+      if ((rc = read_state(h, 2))) return done(rc);
+      if (h->hst[0].done) break;
+    }
+  }
+  // step 7 and the true residuals
+  if (h->k > 0) {
+    RB_CUDA_TRY(gemv_update(P.x, h->U, ld, h->k, h->st[0].xc, nullptr, -1.0, h->npad, vec_grid(h), h->us));
+    RB_CUDA_TRY(gemv_update(D.x, h->Ut, ld, h->k, h->st[1].xc, nullptr, -1.0, h->npad, vec_grid(h), h->us));
+  }
+  double tr[2];
+  RB_CUDA_TRY(residual_norm(h->A.view(), P.b, P.x, h->tmp, h->npad, h->st, h->partials, h->grids.spmv, h->us));
+  RB_CUDA_TRY(residual_norm(h->AT.view(), D.b, D.x, h->tmp2, h->npad, h->st + 1, h->partials, h->grids.spmv,
+                            h->us));
+  if ((rc = read_state(h, 2))) return done(rc);
+  tr[0] = h->hst[0].red[0];
+  tr[1] = h->hst[1].red[0];
+  if ((rc = copy_out(x, P.x, sizeof(double) * n, where, h->us))) return done(rc);
+  if ((rc = copy_out(xt, D.x, sizeof(double) * n, where, h->us))) return done(rc);
+  cudaEventRecord(e1, h->us);
+  if ((rc = sync(h))) return done(rc);
+  float ms = 0;
+  cudaEventElapsedTime(&ms, e0, e1);
+  const int status = h->hst[0].status;
+  const int iters = h->hst[0].iter;
+  rb_stats* outs[2] = {st, st_dual};
+  for (int i = 0; i < 2; ++i) {
+    if (!outs[i]) continue;
+    rb_stats& o = *outs[i];
+    o = rb_stats{};
+    o.iters = iters;
+    o.status = status;
+    o.k_used = h->k;
+    o.seeds_used = so.seeds + 1;
+    o.matvecs = 2 * (int64_t)iters;
+    o.matvecs_setup = so.mv_setup;
+    o.matvecs_check = 2;
+    o.outer = 1;
+    o.relres_rec = nb[i] > 0 ? std::sqrt(h->hst[i].rnorm2 / nb[i]) : 0.0;
+    o.relres_true = nb[i] > 0 ? std::sqrt(tr[i] / nb[i]) : 0.0;
+    o.ms_total = ms;
+  }
+  return done(status);
 }
 
 extern "C" int rbicgstab_solve(rb_handle h, const double* b, double* x, int where, rb_stats* st) {

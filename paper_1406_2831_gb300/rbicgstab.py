@@ -88,6 +88,7 @@ def lib():
     L.rbicgstab_harmonic_ritz.argtypes = [i32, dp, dp, i32, dp, dp, dp, ctypes.POINTER(i32)]
     L.rbicgstab_solve_block.argtypes = [vp, i32, dp, dp, i64, ctypes.c_int, ctypes.POINTER(Stats)]
     L.rbicgstab_time_passes.argtypes = [vp, i32, dp, i64, ctypes.c_int, i32, dp]
+    L.rbicg_solve.argtypes = [vp, dp, dp, dp, dp, ctypes.c_int, ctypes.POINTER(Stats), ctypes.POINTER(Stats)]
     L.rbicgstab_residual_noalloc.argtypes = [i64, dp, dp, dp, dp, dp, dp, dp, vp]
     L.rbicgstab_residual_noalloc.restype = ctypes.c_int
     L.rbicgstab_kernel_launches.argtypes = []
@@ -96,7 +97,8 @@ def lib():
     L.rbicgstab_error_string.restype = ctypes.c_char_p
     for name in ("rbicgstab_create", "rbicgstab_destroy", "rbicgstab_set_matrix", "rbicgstab_set_values",
                  "rbicgstab_set_recycle", "rbicgstab_get_recycle", "rbicgstab_solve", "rbicgstab_apply",
-                 "rbicgstab_harmonic_ritz", "rbicgstab_time_passes", "rbicgstab_solve_block"):
+                 "rbicgstab_harmonic_ritz", "rbicgstab_time_passes", "rbicgstab_solve_block",
+                 "rbicg_solve"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -276,6 +278,39 @@ class Solver:
         st = (Stats * max(nrhs, 1))()
         _check(lib().rbicgstab_solve_block(self._h, nrhs, bp, xp, n, wb, st), "rbicgstab_solve_block")
         return SolveResult(x=X, stats=[st[i].as_dict() for i in range(nrhs)])
+
+    def solve_dual(self, b, bt=None, x=None, xt=None):
+        """Alg. 1 (RBiCG): A x = b and A^T x~ = b~ together (rbicg_solve).
+        bt None: the shadow vector is b~.  x, xt (updated in place when
+        given) hold x_{-1}, x~_{-1}.  Returns (SolveResult for x,
+        SolveResult for x~)."""
+        def vec(v, like):
+            if v is None:
+                if _is_torch(like):
+                    import torch
+                    return torch.zeros_like(like)
+                return np.zeros(len(like))
+            if _is_torch(v):
+                return v
+            if not (isinstance(v, np.ndarray) and v.dtype == np.float64 and v.flags.c_contiguous):
+                v = np.ascontiguousarray(v, dtype=np.float64)
+            return v
+        x, xt = vec(x, b), vec(xt, b)
+        bp, wb, kb = _ptr(b, np.float64)
+        if bt is not None:
+            btp, wbt, kbt = _ptr(bt, np.float64)
+            if wbt != wb:
+                raise ValueError("b and bt must live in the same memory space")
+        else:
+            btp = None
+        xp, wx, kx = _ptr(x, np.float64)
+        xtp, wxt, kxt = _ptr(xt, np.float64)
+        if not (wb == wx == wxt):
+            raise ValueError("b, x and xt must live in the same memory space")
+        st, sd = Stats(), Stats()
+        _check(lib().rbicg_solve(self._h, bp, btp, xp, xtp, wb, ctypes.byref(st), ctypes.byref(sd)),
+               "rbicg_solve")
+        return SolveResult(x=x, stats=st.as_dict()), SolveResult(x=xt, stats=sd.as_dict())
 
     def apply(self, v, transpose=False):
         """y = A v (or A^T v) with the library's SpMV."""
