@@ -260,7 +260,7 @@ __device__ __forceinline__ void gram_stage(const T* const* __restrict__ Z, const
 // The rows of a block are staged in two buffers: the copies of the next
 // 64-row chunk are in flight while the current one is multiplied.
 template <typename T, int TPT>
-__global__ void __launch_bounds__(kBlock) k_gram_gh(const T* const* __restrict__ Z,
+__global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 2 : 1) k_gram_gh(const T* const* __restrict__ Z,
                                                    const T* const* __restrict__ W, int m, int mp,
                                                    int ntile_g, int ntile_h, int64_t npad,
                                                    double* __restrict__ work) {
@@ -281,7 +281,11 @@ __global__ void __launch_bounds__(kBlock) k_gram_gh(const T* const* __restrict__
       ta[ntl] = u / nt; tb[ntl] = u % nt; isg[ntl] = 0;
     }
   }
-  Acc<T> acc[TPT][kGT][kGT];
+  // FP32: pairs of output columns on packed instructions (same per-lane
+  // rounding as the scalar form); FP64: one accumulator per entry
+  constexpr bool F32 = std::is_same<T, float>::value;
+  Acc<T> acc[F32 ? 1 : TPT][kGT][F32 ? 1 : kGT];
+  AccP<float> accp[F32 ? TPT : 1][kGT][kGT / 2];
   const int64_t nch = (npad + kGR - 1) / kGR;
   const int tile_el = kGR * mp;
   // padding columns m..mp-1 stay zero in both stages
@@ -307,36 +311,36 @@ __global__ void __launch_bounds__(kBlock) k_gram_gh(const T* const* __restrict__
       if (q < ntl) {
         const T* za = sz + ta[q] * kGT;
         const T* yb = (isg[q] ? sz : sw) + tb[q] * kGT;
-        if constexpr (std::is_same<T, float>::value) {
+        if constexpr (F32) {
           // FP32 products summed with plain FMAs over kGC rows, each chunk
           // then added to the compensated (hi, lo) pair: per entry the error
           // is at most gamma_kGC * sum_i |z_i w_i| (gamma_8 ~ 4.8e-7), the
           // level of the FP32 columns themselves, at a quarter of the cost
-          // of compensating every product
+          // of compensating every product.  Columns j, j+1 of a tile row go
+          // through one packed FMA / TwoSum.
+          using P = Pair<float>;
 #pragma unroll 1
           for (int r0c = 0; r0c < kGR; r0c += kGC) {
-            float p[kGT][kGT];
+            float2 p[kGT][kGT / 2];
 #pragma unroll
             for (int i = 0; i < kGT; ++i)
 #pragma unroll
-              for (int j = 0; j < kGT; ++j) p[i][j] = 0.0f;
+              for (int j = 0; j < kGT / 2; ++j) p[i][j] = make_float2(0.0f, 0.0f);
 #pragma unroll
             for (int rr = r0c; rr < r0c + kGC; ++rr) {
-              T a[kGT], b[kGT];
-#pragma unroll
-              for (int u = 0; u < kGT; ++u) {
-                a[u] = za[rr * mp + u];
-                b[u] = yb[rr * mp + u];
-              }
+              const float4 a = *reinterpret_cast<const float4*>(za + rr * mp);
+              const float4 b = *reinterpret_cast<const float4*>(yb + rr * mp);
+              const float av[kGT] = {a.x, a.y, a.z, a.w};
+              const float2 bv[kGT / 2] = {make_float2(b.x, b.y), make_float2(b.z, b.w)};
 #pragma unroll
               for (int i = 0; i < kGT; ++i)
 #pragma unroll
-                for (int j = 0; j < kGT; ++j) p[i][j] = __fmaf_rn(a[i], b[j], p[i][j]);
+                for (int j = 0; j < kGT / 2; ++j) p[i][j] = P::fma(P::mk(av[i], av[i]), bv[j], p[i][j]);
             }
 #pragma unroll
             for (int i = 0; i < kGT; ++i)
 #pragma unroll
-              for (int j = 0; j < kGT; ++j) acc[q][i][j].add1(p[i][j]);
+              for (int j = 0; j < kGT / 2; ++j) accp[q][i][j].add1(p[i][j]);
           }
         } else {
 #pragma unroll 1
@@ -365,7 +369,12 @@ __global__ void __launch_bounds__(kBlock) k_gram_gh(const T* const* __restrict__
 #pragma unroll
     for (int i = 0; i < kGT; ++i)
 #pragma unroll
-      for (int j = 0; j < kGT; ++j) wb[(size_t)t * kGT * kGT + i * kGT + j] = acc[q][i][j].get();
+      for (int j = 0; j < kGT; ++j) {
+        double v;
+        if constexpr (F32) v = accp[q][i][j / 2].lane(j & 1).get();
+        else v = acc[q][i][j].get();
+        wb[(size_t)t * kGT * kGT + i * kGT + j] = v;
+      }
   }
 }
 
