@@ -95,24 +95,50 @@ __global__ void __launch_bounds__(kBlock) k_gemm_cols(T* const* __restrict__ out
   __syncthreads();
   constexpr int JB = 8;   // column loads issued together
   for (int64_t i = gtid(); i < npad; i += gstride()) {
-    T acc[KC];
+    if constexpr (std::is_same<T, float>::value) {
+      // pairs of output columns on packed FMAs (each lane rounded as fma_t)
+      using P = Pair<float>;
+      float2 acc[KC / 2];
 #pragma unroll
-    for (int c = 0; c < KC; ++c) acc[c] = T(0);
-    for (int j0 = 0; j0 < m; j0 += JB) {
-      T xv[JB];
+      for (int c = 0; c < KC / 2; ++c) acc[c] = make_float2(0.0f, 0.0f);
+      for (int j0 = 0; j0 < m; j0 += JB) {
+        float xv[JB];
 #pragma unroll
-      for (int u = 0; u < JB; ++u) xv[u] = (j0 + u < m) ? __ldg(sX[j0 + u] + i) : T(0);
+        for (int u = 0; u < JB; ++u) xv[u] = (j0 + u < m) ? __ldg(sX[j0 + u] + i) : 0.0f;
 #pragma unroll
-      for (int u = 0; u < JB; ++u) {
-        if (j0 + u >= m) break;
-        const T* rj = sR + (size_t)(j0 + u) * KC;
+        for (int u = 0; u < JB; ++u) {
+          if (j0 + u >= m) break;
+          const float2* rj = reinterpret_cast<const float2*>(sR + (size_t)(j0 + u) * KC);
+          const float2 xx = P::mk(xv[u], xv[u]);
 #pragma unroll
-        for (int c = 0; c < KC; ++c) acc[c] = fma_t(xv[u], rj[c], acc[c]);
+          for (int c = 0; c < KC / 2; ++c) acc[c] = P::fma(xx, rj[c], acc[c]);
+        }
       }
-    }
 #pragma unroll
-    for (int c = 0; c < KC; ++c)
-      if (c < kc) out[c][i] = acc[c];
+      for (int c = 0; c < KC / 2; ++c) {
+        if (2 * c < kc) out[2 * c][i] = acc[c].x;
+        if (2 * c + 1 < kc) out[2 * c + 1][i] = acc[c].y;
+      }
+    } else {
+      T acc[KC];
+#pragma unroll
+      for (int c = 0; c < KC; ++c) acc[c] = T(0);
+      for (int j0 = 0; j0 < m; j0 += JB) {
+        T xv[JB];
+#pragma unroll
+        for (int u = 0; u < JB; ++u) xv[u] = (j0 + u < m) ? __ldg(sX[j0 + u] + i) : T(0);
+#pragma unroll
+        for (int u = 0; u < JB; ++u) {
+          if (j0 + u >= m) break;
+          const T* rj = sR + (size_t)(j0 + u) * KC;
+#pragma unroll
+          for (int c = 0; c < KC; ++c) acc[c] = fma_t(xv[u], rj[c], acc[c]);
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < KC; ++c)
+        if (c < kc) out[c][i] = acc[c];
+    }
   }
 }
 
