@@ -194,6 +194,24 @@ def cpu_oracle_timing(N, shifts, k, its=10) -> dict:
     return json.loads(out.stdout.strip().splitlines()[-1])
 
 
+# ---------------------------------------------------------------- multi-rank helpers
+def max_over_ranks(value, dist, device):
+    """The largest of every rank's value (a job takes its slowest rank's time);
+    the value itself without a process group."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_step, steps, world, ms):
+    """Whole-job throughput: the units every rank processed over the slowest
+    rank's time (weak scaling: each rank runs its own replica)."""
+    return units_per_step * steps * world / (ms * 1e-3)
+
+
 # ---------------------------------------------------------------- our arm
 def run_passes_only(args):
     """Per-pass CUDA-event timings on one system of the sequence (no solves)."""
@@ -398,11 +416,7 @@ def run_ours(args):
         e1.record(stream)
         barrier()
         ck = clocks.stop() if clocks else None
-        ms = e0.elapsed_time(e1)
-        if dist is not None:
-            t = torch.tensor([ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(e0.elapsed_time(e1), dist, dev)
         return ms, logs, rb.kernel_launches() - l0, ck
 
     solves_per_step = sum(len(r) for r in rhs_d)
@@ -450,7 +464,7 @@ def run_ours(args):
     logs = res["rec"]["logs"]
     iters = [l["iters"] for l in logs]
     ms_step = res["rec"]["ms"] / args.steps
-    value = solves_per_step * args.steps * world / (res["rec"]["ms"] * 1e-3)
+    value = job_throughput(solves_per_step, args.steps, world, res["rec"]["ms"])
     dom = int(np.argmax(ms_pass))
     gbs = pb[dom] / (ms_pass[dom] * 1e-3) / 1e9
     gfs = pf[dom] / (ms_pass[dom] * 1e-3) / 1e9
@@ -491,21 +505,21 @@ def run_ours(args):
     if "plain" in res:
         lp = res["plain"]["logs"]
         itp = [l["iters"] for l in lp]
-        vp = solves_per_step * res["plain"]["steps"] * world / (res["plain"]["ms"] * 1e-3)
+        vp = job_throughput(solves_per_step, res["plain"]["steps"], world, res["plain"]["ms"])
         line["plain_fp64"] = {"solves_per_s": round(vp, 3), "iters_mean": round(statistics.mean(itp), 2),
                               "matvecs": int(sum(l["matvecs"] for l in lp)), "steps": res["plain"]["steps"],
                               "passes_ms": [round(v, 5) for v in ms_pass_plain]}
         line["recycled_over_plain"] = round(value / vp, 4)
         if "plain_block" in res:
             lb = res["plain_block"]["logs"]
-            vpb = solves_per_step * res["plain_block"]["steps"] * world / (res["plain_block"]["ms"] * 1e-3)
+            vpb = job_throughput(solves_per_step, res["plain_block"]["steps"], world, res["plain_block"]["ms"])
             line["plain_fp64_blocked"] = {"solves_per_s": round(vpb, 3), "rhs_block": blk,
                                           "iters_mean": round(statistics.mean(l["iters"] for l in lb), 2)}
             line["recycled_over_plain_blocked"] = round(value / vpb, 4)
     if "e2e" in res:
         Bi = (len(vals_h) * z * 8 + solves_per_step * n * 8) * 1 + solves_per_step * n * 8
         Bo = solves_per_step * n * 8
-        line["e2e"] = {"value": round(solves_per_step * world / (res["e2e"]["ms"] * 1e-3), 3), "unit": "solves/s",
+        line["e2e"] = {"value": round(job_throughput(solves_per_step, 1, world, res["e2e"]["ms"]), 3), "unit": "solves/s",
                        "h2d_bytes_per_step": int(Bi), "d2h_bytes_per_step": int(Bo)}
     if not args.no_cpu_baseline and world >= 1:
         try:
