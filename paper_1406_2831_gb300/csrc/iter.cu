@@ -251,6 +251,23 @@ __device__ __forceinline__ void col_dot_pairs(const T* col, const T (*yi)[R], ty
   }
 }
 
+// ---------------------------------------------------------------- cp.async
+// Asynchronous 16-byte global -> shared copies (L2 only), grouped per thread.
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+// Bring bytes [p, p + bytes) into L2 (no register or shared-memory cost);
+// p 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void prefetch_l2(const void* p, unsigned bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(p), "r"(bytes) : "memory");
+}
+
 // ---------------------------------------------------------------- SpMV core
 // Rows sl*32+lane of two slices at once (sl1 < 0: only the first), so each
 // warp keeps two independent gather chains in flight (single RHS, FP64).
@@ -288,9 +305,16 @@ __device__ __forceinline__ void sell_rows2(const Sell<T>& A, int64_t sl0, int64_
 // ---------------------------------------------------------------- P1 / P3
 // Single RHS, FP64, row-per-lane projection: y = A v stored to `out`;
 // acc[OFF + j] += Chat_j^T y (j < k); RTQ adds acc[0] += (r~0, y).
-template <typename T, int KMAX, bool RTQ>
+// STAGE: the C-hat rows of the warp's two slices are copied into the warp's
+// shared tiles (tile[h][j][lane], h = slice, j = column) with cp.async before
+// the gathers start, so those bytes are in flight during the SpMV and cost no
+// registers; otherwise they are loaded from global after the products.
+template <typename T, int KMAX, bool RTQ, bool STAGE>
 __device__ __forceinline__ void spmv_project(const IterArgs<T>& a, const T* __restrict__ v,
-                                             T* __restrict__ out, Acc<T>* acc, int k) {
+                                             T* __restrict__ out, Acc<T>* acc, int k, T* tile) {
+  constexpr int KT = KMAX > 0 ? KMAX : 1;
+  constexpr int VC = 16 / (int)sizeof(T);   // values per 16-byte chunk
+  constexpr int VPR = kSlice / VC;          // chunks per 32-row column
   const int lane = threadIdx.x & 31;
   const int64_t w0 = gtid() >> 5, nw = gstride() >> 5;
   constexpr int OFF = RTQ ? 1 : 0;
@@ -299,8 +323,21 @@ __device__ __forceinline__ void spmv_project(const IterArgs<T>& a, const T* __re
   const int64_t ld = a.ld, ns = a.A.nslices;
   for (int64_t sl = w0; sl < ns; sl += 2 * nw) {
     const int64_t sl1 = (sl + nw < ns) ? sl + nw : -1;
+    if constexpr (STAGE) {
+      __syncwarp();   // every lane is done with the previous tiles
+      for (int q = lane; q < k * VPR; q += 32) {
+        const int j = q / VPR, c = q % VPR;
+        cp_async16(tile + j * kSlice + c * VC, Chat + (int64_t)j * ld + sl * kSlice + c * VC);
+        if (sl1 >= 0) cp_async16(tile + (KT + j) * kSlice + c * VC, Chat + (int64_t)j * ld + sl1 * kSlice + c * VC);
+      }
+      cp_async_commit();
+    }
     T y[2];
     sell_rows2<T>(a.A, sl, sl1, lane, v, y[0], y[1]);
+    if constexpr (STAGE) {
+      cp_async_wait<0>();
+      __syncwarp();
+    }
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       if (h == 1 && sl1 < 0) break;
@@ -310,26 +347,9 @@ __device__ __forceinline__ void spmv_project(const IterArgs<T>& a, const T* __re
       if (RTQ) acc[0].add(__ldg(rt0 + row), yd);
 #pragma unroll
       for (int j = 0; j < KMAX; ++j)
-        if (j < k) acc[OFF + j].add(__ldg(Chat + j * ld + row), yd);
+        if (j < k) acc[OFF + j].add(STAGE ? tile[(h * KT + j) * kSlice + lane] : __ldg(Chat + j * ld + row), yd);
     }
   }
-}
-
-// ---------------------------------------------------------------- cp.async
-// Asynchronous 16-byte global -> shared copies (L2 only), grouped per thread.
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
-}
-// Bring bytes [p, p + bytes) into L2 (no register or shared-memory cost);
-// p 16-byte aligned, bytes a multiple of 16.
-__device__ __forceinline__ void prefetch_l2(const void* p, unsigned bytes) {
-  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(p), "r"(bytes) : "memory");
 }
 
 // Per-warp shared memory of the multi-RHS / FP32 SpMV + projection passes:
@@ -546,10 +566,23 @@ __device__ __forceinline__ void spmv_multi(const IterArgs<T>& a, const T* const*
 
 // Dynamic shared memory of P1 / P3: the tile storage of the multi-RHS path; and
 // the resident blocks per SM the kernels are compiled for.
+// Dynamic shared memory of the FP64 single-RHS P1 / P3: per warp the C-hat
+// tiles of its two current slices (k <= 24: two blocks per SM still fit),
+// reused after the main loop by the block reduction.
+template <typename T, int KMAX>
+struct TileSmem1 {
+  static constexpr bool staged = KMAX > 0 && KMAX <= 24;
+  static constexpr int KT = staged ? KMAX : 1;
+  union {
+    T tile[kBlock / 32][2 * KT * kSlice];
+    ReduceSmem<KMAX + 1> red;   // P1's reduction (k + 1 values) is the larger one
+  };
+};
+
 template <typename T, int KMAX, int R>
 struct P13Smem {
   static constexpr bool multi = ColProj<T, KMAX, R>::value || R > 1 || KMAX == 0;
-  static constexpr size_t bytes = multi ? sizeof(PipeSmem<T, KMAX, R>) : 0;
+  static constexpr size_t bytes = multi ? sizeof(PipeSmem<T, KMAX, R>) : sizeof(TileSmem1<T, KMAX>);
   static constexpr int min_blocks = !multi ? 2 : ((sizeof(T) == 8 || KMAX == 0) && R > 1 ? 3 : 4);
 };
 
@@ -570,9 +603,13 @@ __global__ void __launch_bounds__(kBlock, P13Smem<T, KMAX, R>::min_blocks) k_p1(
   bool last;
   double *res, *scr;   // grid totals; scratch of the scalar step (free after the reduction)
   if constexpr (!P13Smem<T, KMAX, R>::multi) {
-    __shared__ ReduceSmem<NVR> sm;
+    using TS = TileSmem1<T, KMAX>;
+    extern __shared__ __align__(16) unsigned char dsm[];
+    auto& ts = *reinterpret_cast<TS*>(dsm);
     Acc<T> acc[NVR];
-    spmv_project<T, KMAX, true>(a, a.p_in[0], a.qraw[0], acc, k);
+    spmv_project<T, KMAX, true, TS::staged>(a, a.p_in[0], a.qraw[0], acc, k, ts.tile[threadIdx.x >> 5]);
+    __syncthreads();   // the tiles are reused by the reduction
+    auto& sm = *reinterpret_cast<ReduceSmem<NVR>*>(dsm);
     last = block_reduce_last<T, NVR>(acc, nvr, sm, a.partials, &st[0].ticket[P1]);
     res = sm.res;
     scr = &sm.t[0][0][0];
@@ -606,9 +643,13 @@ __global__ void __launch_bounds__(kBlock, P13Smem<T, KMAX, R>::min_blocks) k_p3(
   bool last;
   double* res;
   if constexpr (!P13Smem<T, KMAX, R>::multi) {
-    __shared__ ReduceSmem<NVR> sm;
+    using TS = TileSmem1<T, KMAX>;
+    extern __shared__ __align__(16) unsigned char dsm[];
+    auto& ts = *reinterpret_cast<TS*>(dsm);
     Acc<T> acc[NVR];
-    spmv_project<T, KMAX, false>(a, a.s[0], a.traw[0], acc, k);
+    spmv_project<T, KMAX, false, TS::staged>(a, a.s[0], a.traw[0], acc, k, ts.tile[threadIdx.x >> 5]);
+    __syncthreads();   // the tiles are reused by the reduction
+    auto& sm = *reinterpret_cast<ReduceSmem<NVR>*>(dsm);
     last = block_reduce_last<T, NVR>(acc, nvr, sm, a.partials, &st[0].ticket[P3]);
     res = sm.res;
   } else {
