@@ -1543,10 +1543,10 @@ template void iteration_grids<float>(int, int, int64_t, Grids*, int);
 // iteration is composed on the host from the library's other kernels (see
 // the RBiCG driver); these two kernels close it:
 //
-//   k_bi_alpha  after z = A p, z~ = A^T p~ (with C-hat^T z and C^T z~ in the
-//               gamma fields of st[0], st[1]), q = z - C zeta, q~ = z~ - C~ zeta~
-//               (zeta~ = D_c^{-1} C^T z~) and (p~, q) in st[0].red[0]:
-//               alpha = (r~, r) / (p~, q), zeta_c += alpha zeta, zeta~_c += alpha zeta~
+//   k_b2        after z = A p, z~ = A^T p~ (with C-hat^T z and C^T z~ in the
+//               gamma fields of st[0], st[1]): q = z - C zeta, q~ = z~ - C~ zeta~
+//               in place (zeta~ = D_c^{-1} C^T z~) and (p~, q) -> st[0].red[0]
+//   k_bi_alpha  alpha = (r~, r) / (p~, q), zeta_c += alpha zeta, zeta~_c += alpha zeta~
 //   k_b3        x += alpha p, x~ += alpha p~, r -= alpha q, r~ -= alpha q~;
 //               ||r||^2, ||r~||^2, (r~, r) -> convergence of both,
 //               beta = (r~_i, r_i) / (r~_{i-1}, r_{i-1})
@@ -1602,6 +1602,35 @@ __device__ void finish_b3(IterState* st, const double* res) {
   }
 }
 
+__global__ void __launch_bounds__(kBlock) k_b2(BiArgs a, const double* __restrict__ C,
+                                               const double* __restrict__ Ct, int64_t ld,
+                                               const double* __restrict__ dinv) {
+  IterState* st = a.st;
+  if (st[0].done) return;
+  __shared__ double cz[2][kMaxK];   // -zeta and -D_c^{-1} C^T z~
+  __shared__ ReduceSmem<1> sm;
+  const int k = st[0].k;
+  if (threadIdx.x < k) {
+    cz[0][threadIdx.x] = -st[0].gamma[threadIdx.x];
+    cz[1][threadIdx.x] = -(st[1].gamma[threadIdx.x] * dinv[threadIdx.x]);
+  }
+  __syncthreads();
+  Acc<double> acc[1];
+  for (int64_t i = gtid(); i < a.npad; i += gstride()) {
+    double u = 0.0, ut = 0.0;
+    for (int j = 0; j < k; ++j) {
+      u = fma(C[j * ld + i], cz[0][j], u);
+      ut = fma(Ct[j * ld + i], cz[1][j], ut);
+    }
+    const double q = a.q[i] + u;
+    a.q[i] = q;
+    a.qt[i] = a.qt[i] + ut;
+    acc[0].add(a.pt[i], q);
+  }
+  if (block_reduce_last<double, 1>(acc, 1, sm, a.partials, &st[0].ticket[P2]) && threadIdx.x == 0)
+    st[0].red[0] = sm.res[0];
+}
+
 __global__ void __launch_bounds__(kBlock) k_b3(BiArgs a) {
   IterState* st = a.st;
   if (st[0].done) return;
@@ -1639,6 +1668,13 @@ cudaError_t bicg_alpha(IterState* st, const double* dinv, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+cudaError_t bicg_project(const BiArgs& a, const double* C, const double* Ct, int64_t ld, const double* dinv,
+                         int grid, cudaStream_t s) {
+  count_launches(1);
+  k_b2<<<grid, kBlock, 0, s>>>(a, C, Ct, ld, dinv);
+  return cudaGetLastError();
+}
+
 cudaError_t bicg_update(const BiArgs& a, int grid, cudaStream_t s) {
   count_launches(2);
   k_b3<<<grid, kBlock, 0, s>>>(a);
@@ -1648,7 +1684,8 @@ cudaError_t bicg_update(const BiArgs& a, int grid, cudaStream_t s) {
 
 int bicg_grid(int nsm, int64_t npad) {
   const int64_t work = (npad + kBlock - 1) / kBlock;
-  return (int)std::max<int64_t>(1, std::min<int64_t>(work, occ((const void*)k_b3, nsm)));
+  const int o = std::min(occ((const void*)k_b2, nsm), occ((const void*)k_b3, nsm));
+  return (int)std::max<int64_t>(1, std::min<int64_t>(work, o));
 }
 
 }  // namespace rb

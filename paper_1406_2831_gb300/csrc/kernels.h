@@ -66,6 +66,11 @@ struct BiArgs {
   IterState* st;
   double* partials;
 };
+// q = z - C zeta, q~ = z~ - C~ D_c^{-1} C^T z~ in place over a.q, a.qt (zeta,
+// C^T z~ in the gamma fields of st[0], st[1]; k = st[0].k) and (p~, q) ->
+// st[0].red[0].
+cudaError_t bicg_project(const BiArgs& a, const double* C, const double* Ct, int64_t ld, const double* dinv,
+                         int grid, cudaStream_t s);
 // alpha = (r~, r) / (p~, q) from st[0].red[0], and the zeta_c updates.
 cudaError_t bicg_alpha(IterState* st, const double* dinv, cudaStream_t s);
 // x, x~, r, r~ updates with the convergence test and beta; then p, p~.

@@ -1563,8 +1563,8 @@ BiArgs bicg_args(rb_ctx* h) {
 // One iteration of Alg. 1 on stream s, composed of the library's kernels:
 //   z = A p, zeta = C-hat^T z        (the FP64 SpMV + projection pass, state st[0])
 //   z~ = A^T p~, C^T z~              (the same pass on A^T and C, state st[1])
-//   q = z - C zeta, q~ = z~ - C~ D_c^{-1} C^T z~   (in place over z, z~)
-//   (p~, q); alpha, zeta_c, zeta~_c; x, x~, r, r~, ||r||, ||r~||, beta; p, p~
+//   q = z - C zeta, q~ = z~ - C~ D_c^{-1} C^T z~   (in place over z, z~) and (p~, q)
+//   alpha, zeta_c, zeta~_c; x, x~, r, r~, ||r||, ||r~||, beta; p, p~
 cudaError_t bicg_iteration(rb_ctx* h, const Grids& g13, int grid, cudaStream_t s) {
   Slot &P = h->sl[0], &D = h->sl[1];
   const int64_t ld = h->npad;
@@ -1592,16 +1592,14 @@ cudaError_t bicg_iteration(rb_ctx* h, const Grids& g13, int grid, cudaStream_t s
     ad.st = h->st + 1;
     if ((e = launch_pass<double>(P3, ap, k, g13, s)) != cudaSuccess) return e;
     if ((e = launch_pass<double>(P3, ad, k, g13, s)) != cudaSuccess) return e;
-    if ((e = gemv_update(P.qraw, h->C, ld, k, h->st[0].gamma, nullptr, -1.0, h->npad, vec_grid(h), s)) != cudaSuccess)
-      return e;
-    if ((e = gemv_update(D.qraw, h->Ct, ld, k, h->st[1].gamma, h->Dinv, -1.0, h->npad, vec_grid(h), s)) !=
-        cudaSuccess)
-      return e;
+    if ((e = bicg_project(bicg_args(h), h->C, h->Ct, ld, h->Dinv, grid, s)) != cudaSuccess) return e;
   }
-  DotArgs d{};
-  d.nd = 1;
-  d.a[0] = D.p; d.b[0] = P.qraw;
-  if ((e = dots(d, h->npad, h->st, h->partials, vec_grid(h), s)) != cudaSuccess) return e;
+  if (k == 0) {
+    DotArgs d{};
+    d.nd = 1;
+    d.a[0] = D.p; d.b[0] = P.qraw;
+    if ((e = dots(d, h->npad, h->st, h->partials, vec_grid(h), s)) != cudaSuccess) return e;
+  }
   if ((e = bicg_alpha(h->st, h->Dinv, s)) != cudaSuccess) return e;
   return bicg_update(bicg_args(h), grid, s);
 }
