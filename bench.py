@@ -476,8 +476,11 @@ def run_ours(args):
             "achieved": round(gbs, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
             "frac": round(hbm_frac, 4), "traffic": TRAFFIC.get((args.precision, f"P{dom + 1}", N, args.k, R0)),
             "peak_source": peaks["source"],
-            "fp64_alu": {"achieved_tflops": round(gfs / 1e3, 4), "peak_tflops": round(peak_fp64, 3),
-                         "frac": round(alu_frac, 4), "peak_source": "measured (torch float64 matmul)"},
+            "alu": ({"dtype": "f64", "achieved_tflops": round(gfs / 1e3, 4), "peak_tflops": round(peak_fp64, 3),
+                     "frac": round(alu_frac, 4), "peak_source": "measured (torch float64 matmul)"}
+                    if args.precision == "fp64" else
+                    {"dtype": "f32 data, Dot2 accumulators", "achieved_tflops": round(gfs / 1e3, 4),
+                     "peak_tflops": None, "frac": None}),
             "passes_ms": [round(v, 5) for v in ms_pass], "passes_bytes": pb,
             "iteration": {"ms": round(iter_ms, 5), "GB/s": round(iter_gbs, 1),
                           "frac": round(iter_gbs / peaks["hbm_gbs"], 4)}}
