@@ -1538,10 +1538,10 @@ template void iteration_grids<double>(int, int, int64_t, Grids*, int);
 template void iteration_grids<float>(int, int, int64_t, Grids*, int);
 
 // ================================================================ RBiCG (Alg. 1)
-// The scalar steps of Alg. 1 for a primary system A x = b and its dual
-// A^T x~ = b~ (FP64, real, so conj(alpha) = alpha).  The vector work of an
-// iteration is composed on the host from the library's other kernels (see
-// the RBiCG driver); these two kernels close it:
+// Alg. 1 for a primary system A x = b and its dual A^T x~ = b~ (FP64, real,
+// so conj(alpha) = alpha).  An iteration starts with the FP64 SpMV +
+// projection pass on A (with C-hat) and on A^T (with C); these kernels do
+// the rest of it:
 //
 //   k_b2        after z = A p, z~ = A^T p~ (with C-hat^T z and C^T z~ in the
 //               gamma fields of st[0], st[1]): q = z - C zeta, q~ = z~ - C~ zeta~
