@@ -166,6 +166,15 @@ def fp64_peak_tflops(torch) -> float:
     return 2 * 4096 ** 3 / (best * 1e-3) / 1e12
 
 
+def sequence_config(N, n, z, args, cycle_s, tol, world) -> dict:
+    """The workload named in both arms' JSON lines: the shifted 3D sequence."""
+    return {"workload": f"3d-7pt-conv-diff-{N}^3-shifted", "n": n, "nnz": z,
+            "shifts": args.shifts, "rhs_per_shift": args.rhs, "k": args.k, "cycle_s": cycle_s,
+            "tol": tol, "recycle": "update from the first RHS of each matrix (harmonic Ritz), in force from the next matrix",
+            "precision": args.precision, "rhs_block": max(1, min(args.block, 4)),
+            "parallelism": f"replicas x{world}", "l2": "inputs larger than L2 (no flush)"}
+
+
 # ---------------------------------------------------------------- CPU baseline (oracle)
 CPU_SNIPPET = r"""
 import json, os, sys, time
@@ -181,7 +190,8 @@ U = inputs.random_recycle_basis(P.n, {k}, 11) if {k} else None
 t0 = time.perf_counter(); rec = orb.recycle_setup(S, U) if {k} else None; t_setup = time.perf_counter() - t0
 t0 = time.perf_counter(); orb.rbicgstab(S, b, rec, tol=1e-30, max_itn={its}, true_residual=False)
 t_it = (time.perf_counter() - t0) / {its}
-print(json.dumps({{"t_iter": t_it, "t_setup": t_setup}}))
+print(json.dumps({{"t_iter": t_it, "t_setup": t_setup, "n": int(P.n), "nnz": int(S.nnz),
+                  "cycle_s": spec.cycle_s, "tol": spec.tol}}))
 """
 
 
@@ -490,11 +500,7 @@ def run_ours(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if args.precision == "fp64" else "f32-inner/f64-refined",
         "data": "synthetic (seeded stencil systems and Gaussian right-hand sides)",
-        "config": {"workload": f"3d-7pt-conv-diff-{N}^3-shifted", "n": n, "nnz": z,
-                   "shifts": args.shifts, "rhs_per_shift": args.rhs, "k": args.k, "cycle_s": spec.cycle_s,
-                   "tol": spec.tol, "recycle": "update from the first RHS of each matrix (harmonic Ritz), in force from the next matrix",
-                   "precision": args.precision, "rhs_block": blk, "parallelism": f"replicas x{world}",
-                   "l2": "inputs larger than L2 (no flush)"},
+        "config": sequence_config(N, n, z, args, spec.cycle_s, spec.tol, world),
         "recycled": {"solves_per_s": round(value, 3), "iters_mean": round(statistics.mean(iters), 2),
                      "iters_total": int(sum(iters)), "matvecs": int(sum(l["matvecs"] for l in logs)),
                      "matvecs_setup": int(sum(l["matvecs_setup"] for l in logs)),
@@ -565,17 +571,20 @@ def run_reference(args):
     if os.path.exists(fx):
         vals = [float(l) for l in open(fx) if l.strip() and not l.startswith("#")]
         mean_it = statistics.mean(vals)
+    it_src = f"the oracle's stored mean of {mean_it:.1f} iterations/solve" if mean_it is not None else None
     if mean_it is None:
         mean_it = 100.0
+        it_src = "100 iterations/solve (no stored oracle count for this grid)"
     value = 1.0 / (t_it * mean_it + t_setup / args.rhs)
     return {"impl": "reference", "metric": METRIC, "value": round(value, 5), "unit": "solves/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(1e3 * (t_it * its + t_setup), 3), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"3d-7pt-conv-diff-{N}^3-shifted", "k": args.k, "tol": 1e-8},
+            "config": sequence_config(N, samples[0]["n"], samples[0]["nnz"], args, samples[0]["cycle_s"],
+                                      samples[0]["tol"], args.gpus),
             "cpu_baseline": {"value": round(value, 5), "unit": "solves/s", "cores": 1, "kind": "oracle",
                              "sample": f"per step: oracle Alg. 2 (k={args.k}) setup + {its} iterations on "
-                                       f"system 1 at full size, extrapolated to {mean_it:.1f} iterations/solve"},
+                                       f"system 1 at full size, extrapolated to {it_src}"},
             "e2e": {"value": round(value, 5), "unit": "solves/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0},
             "wall_s": round(wall, 1)}
