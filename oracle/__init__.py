@@ -16,6 +16,8 @@ rbicgstab  Alg. 2 (RBiCGSTAB) with eq. (3.5) ("minusXR") initial projection,
            the recycle-space update.
 recycle    harmonic Ritz extraction for the recycle-space update between
            systems, and the mode-S sequence driver.
+rbicg      Alg. 1 (RBiCG): the primary system and its dual together, with a
+           two-sided recycle space.
 dense      small dense helpers used by the pins (principal angles).
 
 Parity status: every function is pinned by a ``-m "not gpu"`` test against a
