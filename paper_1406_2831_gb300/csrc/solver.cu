@@ -1037,7 +1037,7 @@ int solve_mixed(rb_ctx* h, int nrhs, SolveOut* so) {
   // In update mode slot 0's search direction lives in the cycle store at a
   // position fixed by the cycle graph, so a slot 0 that stopped inside a
   // cycle is not resumed there: its true residual is checked at the end of
-  // the round and, if needed, the next round restarts it.
+  // the outer (refinement) step and, if needed, the next outer step restarts it.
   const bool trace = getenv("RB_TRACE") != nullptr;
   bool cycles_running = false;
   PollHook hook = [&]() -> int {
@@ -1158,7 +1158,7 @@ int solve_mixed(rb_ctx* h, int nrhs, SolveOut* so) {
       if (stop[i]) continue;   // converged at a replacement (x already folded)
       running[i] = false;
       // a breakdown, max_itn, or a half-step exit: fold the correction and
-      // let the next round restart from x
+      // let the next outer (refinement) step restart from x
       if ((rc = fold(i))) return rc;
       if (hs.status != RB_OK && hs.status != RB_ENOTCONV) {
         so[i].status = hs.status;
