@@ -205,7 +205,7 @@ def test_block_sequence_update_parity(precision):
         assert abs(sum(got) - sum(ref.iters)) <= 0.05 * sum(ref.iters)
     else:
         # FP32 iterations follow another trajectory than the FP64 oracle's:
-        # judge the recycling effect (later blocks need fewer iterations than
+        # check the recycling effect (later blocks need fewer iterations than
         # the first, which has no recycle space)
         assert np.mean(got[4:]) < np.mean(got[:4])
     # the update of the first block spans the oracle's harmonic-Ritz space.
