@@ -33,6 +33,8 @@ __all__ = [
     "random_recycle_basis",
     "config_small_2d",
     "config_shifted_3d",
+    "ParamSpec",
+    "config_param_3d",
 ]
 
 
@@ -260,3 +262,66 @@ def config_shifted_3d(N: int = 128, c: float = 10.0, n_shifts: int = 20, n_rhs: 
         rhs = [[gaussian_rhs(L.n, 100 + 4 * j + kk) for kk in range(n_rhs)] for j in range(n_shifts)]
     return SequenceSpec(pattern=L, values=values, rhs=rhs, k=k, cycle_s=25, tol=1e-8,
                         label=f"3d-7pt-{N}^3-shifted-{n_shifts}x{n_rhs}")
+
+
+@dataclass
+class ParamSpec:
+    """A parametrised operator A(p) = sum_k p_k A_k on one pattern (every A_k
+    stored as values on ``pattern``), an output matrix and a right-hand side,
+    and the parameter steps of a sequence."""
+
+    pattern: CSR
+    basis: list          # float64[nnz] per parameter: the values of dA/dp_k
+    names: list          # parameter names
+    p0: np.ndarray       # float64[n_params]
+    C_out: np.ndarray    # float64[m, n]
+    b: np.ndarray        # float64[n]
+    steps: list          # parameter vectors of the sequence (steps[0] = p0)
+    k: int
+    tol: float
+    label: str
+
+    def values(self, p) -> np.ndarray:
+        """Values of A(p) on the pattern."""
+        v = np.zeros_like(self.basis[0])
+        for pk, Ak in zip(p, self.basis):
+            v += pk * Ak
+        return v
+
+
+def config_param_3d(N: int = 100, kappa: float = 1.0, c: float = 10.0, n_steps: int = 6,
+                    step: float = 1.01, m_out: int = 16, k: int = 20) -> ParamSpec:
+    """3D 7-point convection-diffusion on an N^3 grid with 8 parameters:
+    diffusion kappa_r and convection c_r on 4 regions r = 2[x >= 1/2] +
+    [y >= 1/2] (cell centres x = (i+1) h, y = (j+1) h; each region is a pair
+    of octants stacked in z).  Face diffusion is the mean of the two cells'
+    kappa, convection is upwind c_r (1,1,1).grad (the operator of
+    ``conv_diff_3d`` with per-cell coefficients).  A(p) is linear in p, so
+    dA/dp_k is the operator with coefficient 1 on region r and 0 elsewhere.
+    Steps p_{j+1} = step * p_j; C_out ~ N(0,1) (m_out x n, seed 3); b ~ N(0,1)
+    (seed 4)."""
+    h = 1.0 / (N + 1)
+    n = N ** 3
+    idx = np.arange(n, dtype=np.int64)
+    x = (idx % N + 1) * h
+    y = ((idx // N) % N + 1) * h
+    region = 2 * (x >= 0.5).astype(np.int64) + (y >= 0.5).astype(np.int64)
+    basis, names = [], []
+    zero = np.zeros(n)
+    pattern = None
+    for r in range(4):
+        A = conv_diff_3d(N, zero, kappa=(region == r).astype(np.float64))
+        basis.append(A.val)
+        names.append(f"kappa_{r}")
+        pattern = A if pattern is None else pattern
+    for r in range(4):
+        A = conv_diff_3d(N, (region == r).astype(np.float64), kappa=zero)
+        basis.append(A.val)
+        names.append(f"c_{r}")
+    p0 = np.array([kappa] * 4 + [c] * 4, dtype=np.float64)
+    steps = [p0 * step ** j for j in range(n_steps)]
+    C_out = np.random.default_rng(3).standard_normal((m_out, n))
+    b = gaussian_rhs(n, 4)
+    pat = CSR(n=n, row_ptr=pattern.row_ptr, col=pattern.col, val=np.zeros_like(pattern.val))
+    return ParamSpec(pattern=pat, basis=basis, names=names, p0=p0, C_out=C_out, b=b, steps=steps,
+                     k=k, tol=1e-8, label=f"3d-7pt-{N}^3-8-params")
