@@ -35,6 +35,7 @@ __all__ = [
     "config_shifted_3d",
     "ParamSpec",
     "config_param_3d",
+    "example1",
 ]
 
 
@@ -325,3 +326,34 @@ def config_param_3d(N: int = 100, kappa: float = 1.0, c: float = 10.0, n_steps: 
     pat = CSR(n=n, row_ptr=pattern.row_ptr, col=pattern.col, val=np.zeros_like(pattern.val))
     return ParamSpec(pattern=pat, basis=basis, names=names, p0=p0, C_out=C_out, b=b, steps=steps,
                      k=k, tol=1e-8, label=f"3d-7pt-{N}^3-8-params")
+
+
+def example1(N: int = 40, a: float = 10.0):
+    """Example 1 of Sec. 5: -(u_x)_x - (u_y)_y + a u_x - a u_y = 0 on the unit
+    square, an (N+2) x (N+2) vertex grid (N^2 = 1600 unknowns at N = 40),
+    u = 1 on the south and west boundaries and 0 on the north and east ones.
+    The discretisation is unstated; central differences reproduce the
+    paper's Table 1 (first-order upwind does not).  h^2-scaled row weights:
+    centre 4, west -1 - a h/2, east -1 + a h/2, south -1 + a h/2, north
+    -1 - a h/2; the boundary values move to b.  The paper starts from a
+    vector of all ones and stops at relative tolerance 1e-10.
+    Returns (A as CSR, b, x_{-1})."""
+    h = 1.0 / (N + 1)
+    n = N * N
+    idx = np.arange(n, dtype=np.int64)
+    i = idx % N
+    j = idx // N
+    w_west, w_east = -1.0 - 0.5 * a * h, -1.0 + 0.5 * a * h
+    w_south, w_north = -1.0 + 0.5 * a * h, -1.0 - 0.5 * a * h
+    cols = np.full((n, 5), -1, dtype=np.int64)
+    vals = np.zeros((n, 5))
+    for slot, off, m, w in [(0, -N, j > 0, w_south), (1, -1, i > 0, w_west),
+                            (3, 1, i < N - 1, w_east), (4, N, j < N - 1, w_north)]:
+        cols[m, slot] = idx[m] + off
+        vals[m, slot] = w
+    cols[:, 2] = idx
+    vals[:, 2] = 4.0
+    b = np.zeros(n)
+    b[i == 0] -= w_west * 1.0     # u = 1 on the west boundary
+    b[j == 0] -= w_south * 1.0    # u = 1 on the south boundary
+    return _assemble(n, cols, vals), b, np.ones(n)

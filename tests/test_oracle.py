@@ -212,6 +212,39 @@ def test_table1_example1_principal_cosines():
     R, L, _ = invariant_subspaces(A, 10)
     got = principal_cosines(R, L)
     assert np.abs(got - want).max() <= 5e-5
+    # the generator of the Example 1 system builds the same operator
+    E1, _, _ = inputs.example1()
+    assert np.array_equal(E1.to_scipy().toarray(), A)
+
+
+def _example1_runs():
+    """The three runs of Sec. 5 on Example 1: no recycling, U = 5 exact right
+    eigenvectors with U~ = U, and U, U~ = 5 right and 5 left eigenvectors
+    (smallest-magnitude eigenvalues); x_{-1} = ones, tol 1e-10."""
+    E1, b, x0 = inputs.example1()
+    A = E1.to_scipy()
+    R, L, _ = invariant_subspaces(A.toarray(), 5)
+    out = {}
+    for name, rec in [("none", None), ("right", orb.recycle_setup(A, R)), ("both", orb.recycle_setup(A, R, L))]:
+        x, info = orb.rbicgstab(A, b, rec, x_m1=x0, tol=1e-10)
+        out[name] = (x, info)
+    return A, b, out
+
+
+def test_example1_left_right_study():
+    """Sec. 5, Example 1: recycling the right invariant subspace pays, and
+    adding the left one changes little (the paper's finding for this nearly
+    normal operator, whose left and right subspaces are close by Table 1).
+    Each run meets the tolerance; the discrete solution obeys the maximum
+    principle of the M-matrix (values between the boundary values 0 and 1)."""
+    A, b, runs = _example1_runs()
+    its = {k: v[1].iters for k, v in runs.items()}
+    for x, info in runs.values():
+        assert info.status == orb.OK
+        assert np.linalg.norm(b - A @ x) <= 2e-10 * np.linalg.norm(b)
+        assert x.min() > 0.0 and x.max() < 1.0
+    assert its["right"] < 0.9 * its["none"] and its["both"] < 0.9 * its["none"]
+    assert abs(its["right"] - its["both"]) <= 0.1 * its["none"]
 
 
 # ---------------------------------------------------------------- recycling pays (Sec. 6.2)
