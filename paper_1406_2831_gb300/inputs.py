@@ -36,6 +36,8 @@ __all__ = [
     "ParamSpec",
     "config_param_3d",
     "example1",
+    "config_batch_2d",
+    "config_large_27pt",
 ]
 
 
@@ -213,7 +215,9 @@ def random_recycle_basis(n: int, k: int, seed: int) -> np.ndarray:
 @dataclass
 class SequenceSpec:
     """A sequence of systems: matrices share one pattern; ``rhs[i]`` lists the
-    right-hand sides solved with matrix i."""
+    right-hand sides solved with matrix i.  ``pattern``, the entries of
+    ``values`` and of ``rhs`` may be callables that build them on demand
+    (the large workloads)."""
 
     pattern: CSR
     values: list        # list of float64[nnz] per matrix (lazy callables allowed)
@@ -357,3 +361,54 @@ def example1(N: int = 40, a: float = 10.0):
     b[i == 0] -= w_west * 1.0     # u = 1 on the west boundary
     b[j == 0] -= w_south * 1.0    # u = 1 on the south boundary
     return _assemble(n, cols, vals), b, np.ones(n)
+
+
+def config_batch_2d(n_systems: int = 256, side_lo: int = 100, side_hi: int = 450,
+                    shifts=(0.0, 1e-2, 1e-1, 1.0), k: int = 10, seed: int = 2) -> list:
+    """A sweep of independent parameter samples of uneven sizes: system i is
+    the 2D operator of ``conv_diff_2d`` on an N_i x N_i grid with
+    N_i ~ U{side_lo..side_hi} and p_i ~ U[1, 50] (seed ``seed``), carrying a
+    sequence of len(shifts) matrices A_i + sigma I (sigma added to the
+    h^2-scaled diagonal, E = I) with one right-hand side N(0,1) (seed
+    1000 + i) solved for each.  Returned as one SequenceSpec per system with
+    lazy values; k = 10, s = 25, tol 1e-8."""
+    rng = np.random.default_rng(seed)
+    sides = rng.integers(side_lo, side_hi + 1, size=n_systems)
+    ps = rng.uniform(1.0, 50.0, size=n_systems)
+    out = []
+    for i, (N, p) in enumerate(zip(sides, ps)):
+        N = int(N)
+
+        def pattern(N=N, p=float(p)):
+            return conv_diff_2d(N, p)
+
+        def make_vals(sig, N=N, p=float(p)):
+            def f():
+                A = conv_diff_2d(N, p)
+                return shifted_values(A, np.ones(A.n), sig)
+            return f
+
+        b = (lambda n=N * N, sd=1000 + i: gaussian_rhs(n, sd))
+        out.append(SequenceSpec(pattern=pattern, values=[make_vals(sg) for sg in shifts],
+                                rhs=[[b] for _ in shifts], k=k, cycle_s=25, tol=1e-8,
+                                label=f"2d-{N}x{N}-p{p:.2f}"))
+    return out
+
+
+def config_large_27pt(Nx: int = 256, Ny: int = 256, Nz: int = 128, c0: float = 10.0,
+                      drift: float = 1.02, n_systems: int = 10, k: int = 30, seed: int = 5) -> SequenceSpec:
+    """The large 27-point sequence: ``stencil27_noisy`` on Nx x Ny x Nz with
+    convection c_j = c0 drift^j (j = 0..n_systems-1) and one fixed noise draw
+    (seed ``seed``), so only the convection entries change along the
+    sequence; one RHS N(0,1) (seed 200 + j) per system; k = 30, s = 25, tol
+    1e-8.  Values are generated on demand (224M nonzeros at full size)."""
+    cs = [c0 * drift ** j for j in range(n_systems)]
+
+    def make_vals(c):
+        return lambda: stencil27_noisy(Nx, Ny, Nz, c, seed=seed).val
+
+    n = Nx * Ny * Nz
+    rhs = [[(lambda sd=200 + j: gaussian_rhs(n, sd))] for j in range(n_systems)]
+    return SequenceSpec(pattern=lambda: stencil27_noisy(Nx, Ny, Nz, c0, seed=seed),
+                        values=[make_vals(c) for c in cs], rhs=rhs, k=k, cycle_s=25, tol=1e-8,
+                        label=f"3d-27pt-{Nx}x{Ny}x{Nz}-noisy-drift")
