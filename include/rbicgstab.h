@@ -189,6 +189,18 @@ int rbicg_solve(rb_handle h, const double* b, const double* bt, double* x, doubl
  * FP64 SpMV kernels; v and y have n entries.  Errors: RB_EDIM, RB_EINVAL. */
 int rbicgstab_apply(rb_handle h, const double* v, double* y, int transpose, int where);
 
+/* out_e = scale * u_i * v_j for every entry e = (i, j) of the matrix's
+ * sparsity pattern, in the CSR order given to rbicgstab_set_matrix (nnz
+ * values).  With u = lam, v = x and scale = -1 this is the gradient
+ * dL/dA_ij = -lam_i x_j of a functional L of the solution of A x = b, lam the
+ * solution of the dual system A^T lam = dL/dx (Sec. 2's A^* x~ = b~; solve
+ * it with rbicg_solve).  u, v (n entries) and out (nnz entries) are device
+ * pointers (where = RB_DEVICE; RB_HOST is rejected with RB_EINVAL).
+ * Errors: RB_EINVAL (null pointer, host memory, non-finite scale), RB_EDIM
+ * (no matrix), RB_ECUDA. */
+int rbicgstab_pattern_outer(rb_handle h, const double* u, const double* v, double scale, double* out,
+                            int where);
+
 /* Harmonic-Ritz selection on the host (the small dense step of the recycle
  * update, run between cycles of s iterations, Sec. 6.2): given G = Z^T Z and
  * H = Z^T W (m x m, column-major) for a subspace W with Z = A W, return in Y

@@ -1,0 +1,57 @@
+"""``torch.autograd.Function`` for x = A^{-1} b on the library's solver.
+
+The values of A (on the pattern given to ``Solver.set_matrix``) and b are the
+differentiable inputs.  Forward: ``set_values`` and one solve (Alg. 2, with
+the handle's recycle space).  Backward, for an upstream gradient g = dL/dx:
+the dual system A^T lam = g (the dual system of Sec. 2, A^* x~ = b~ with
+b~ = g) is solved by ``rbicg_solve`` (Alg. 1 solves a primary system and its
+dual together; the primary is the forward system again), with the recycle
+space's left half U~ serving the dual; then
+
+    dL/db = lam,    dL/dA_ij = -lam_i x_j   (``rbicgstab_pattern_outer``).
+
+A parametrisation A(p) = sum_k p_k A_k written in torch upstream of the
+values chains to dL/dp_k = -lam^T A_k x by autograd.  Argument marshalling
+only: both solves and the gradient assembly run in the library's kernels.
+"""
+from __future__ import annotations
+
+import torch
+
+from . import rbicgstab as rb
+
+
+class RecycledSolve(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, values, b, solver):
+        values = values.detach().contiguous()
+        b = b.detach().contiguous()
+        solver.set_values(values)
+        res = solver.solve(b)
+        if res.stats["status"] != rb.RB_OK:
+            raise RuntimeError(f"forward solve: {rb.error_string(res.stats['status'])}")
+        x = res.x
+        ctx.solver = solver
+        ctx.version = solver.values_version
+        ctx.save_for_backward(values, b, x)
+        return x
+
+    @staticmethod
+    def backward(ctx, gx):
+        values, b, x = ctx.saved_tensors
+        s = ctx.solver
+        if s.values_version != ctx.version:   # the solver moved on: put this step's matrix back
+            s.set_values(values)
+        _, dual = s.solve_dual(b, gx.detach().contiguous())
+        if dual.stats["status"] != rb.RB_OK:
+            raise RuntimeError(f"dual solve: {rb.error_string(dual.stats['status'])}")
+        lam = dual.x
+        gvals = s.pattern_outer(lam, x, -1.0) if ctx.needs_input_grad[0] else None
+        gb = lam if ctx.needs_input_grad[1] else None
+        return gvals, gb, None
+
+
+def solve(solver: rb.Solver, values: torch.Tensor, b: torch.Tensor) -> torch.Tensor:
+    """x with A(values) x = b, differentiable in values and b (CUDA float64
+    tensors; the solver holds the pattern from ``set_matrix``)."""
+    return RecycledSolve.apply(values, b, solver)

@@ -77,6 +77,27 @@ cudaError_t gemv_update(double* y, const double* M, int64_t ld, int k, const dou
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------- pattern outer product
+// out[e] = scale * u[i] * v[col[e]] for every entry e of row i of a CSR
+// pattern (one thread per row; rows of stencil operators are short).
+__global__ void k_pattern_outer(int64_t n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                                const double* __restrict__ u, const double* __restrict__ v, double scale,
+                                double* __restrict__ out) {
+  for (int64_t i = gtid(); i < n; i += gstride()) {
+    const double su = scale * u[i];
+    const int32_t e1 = rp[i + 1];
+    for (int32_t e = rp[i]; e < e1; ++e) out[e] = su * v[ci[e]];
+  }
+}
+
+cudaError_t pattern_outer(int64_t n, const int32_t* rp, const int32_t* ci, const double* u, const double* v,
+                          double scale, double* out, int grid, cudaStream_t s) {
+  count_launches(1);
+  if (n <= 0) return cudaSuccess;
+  k_pattern_outer<<<grid, kBlock, 0, s>>>(n, rp, ci, u, v, scale, out);
+  return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------- block GEMM
 // Out(:, c) = X R(:, c): each thread owns one row, reads the m entries of
 // X's row once and forms all kc <= KC outputs in registers (KC is a

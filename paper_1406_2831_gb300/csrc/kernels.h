@@ -129,6 +129,10 @@ struct DotArgs {
 };
 cudaError_t dots(const DotArgs& d, int64_t npad, IterState* st, double* partials, int grid,
                  cudaStream_t s);
+// out[e] = scale * u[i] * v[ci[e]] over the entries e of each row i of the
+// CSR pattern (rp, ci) with n rows (device arrays; out in CSR order).
+cudaError_t pattern_outer(int64_t n, const int32_t* rp, const int32_t* ci, const double* u, const double* v,
+                          double scale, double* out, int grid, cudaStream_t s);
 // y[i] += sign * sum_j M[j*ld+i] * c[j], c read from device memory (c_scale[j]
 // multiplies c[j] when non-null).
 cudaError_t gemv_update(double* y, const double* M, int64_t ld, int k, const double* c,

@@ -1438,6 +1438,14 @@ extern "C" int rbicgstab_apply(rb_handle h, const double* v, double* y, int tran
   return sync(h);
 }
 
+extern "C" int rbicgstab_pattern_outer(rb_handle h, const double* u, const double* v, double scale, double* out,
+                                       int where) {
+  if (!h || !u || !v || !out || where != RB_DEVICE || !std::isfinite(scale)) return RB_EINVAL;
+  if (!h->have_matrix) return RB_EDIM;
+  RB_CUDA_TRY(pattern_outer(h->n, h->rp, h->ci, u, v, scale, out, vec_grid(h), h->us));
+  return sync(h);
+}
+
 extern "C" int rbicgstab_harmonic_ritz(int32_t m, const double* G, const double* H, int32_t k, double* Y,
                                        double* theta_re, double* theta_im, int32_t* k_used) {
   if (m <= 0 || k <= 0 || k > m || !G || !H || !Y || !k_used) return RB_EINVAL;

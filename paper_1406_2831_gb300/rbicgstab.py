@@ -85,6 +85,7 @@ def lib():
     L.rbicgstab_get_recycle.argtypes = [vp, ctypes.POINTER(i32), dp, dp, i64, ctypes.c_int]
     L.rbicgstab_solve.argtypes = [vp, dp, dp, ctypes.c_int, ctypes.POINTER(Stats)]
     L.rbicgstab_apply.argtypes = [vp, dp, dp, ctypes.c_int, ctypes.c_int]
+    L.rbicgstab_pattern_outer.argtypes = [vp, dp, dp, ctypes.c_double, dp, ctypes.c_int]
     L.rbicgstab_harmonic_ritz.argtypes = [i32, dp, dp, i32, dp, dp, dp, ctypes.POINTER(i32)]
     L.rbicgstab_solve_block.argtypes = [vp, i32, dp, dp, i64, ctypes.c_int, ctypes.POINTER(Stats)]
     L.rbicgstab_time_passes.argtypes = [vp, i32, dp, i64, ctypes.c_int, i32, dp]
@@ -98,7 +99,7 @@ def lib():
     for name in ("rbicgstab_create", "rbicgstab_destroy", "rbicgstab_set_matrix", "rbicgstab_set_values",
                  "rbicgstab_set_recycle", "rbicgstab_get_recycle", "rbicgstab_solve", "rbicgstab_apply",
                  "rbicgstab_harmonic_ritz", "rbicgstab_time_passes", "rbicgstab_solve_block",
-                 "rbicg_solve"):
+                 "rbicg_solve", "rbicgstab_pattern_outer"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -163,6 +164,8 @@ class Solver:
         self._h = ctypes.c_void_p()
         _check(L.rbicgstab_create(ctypes.byref(self._h), ctypes.byref(o)), "rbicgstab_create")
         self.n = 0
+        self.nnz = 0
+        self.values_version = 0   # counts set_matrix / set_values calls
         self.opts = o
 
     def close(self):
@@ -192,10 +195,14 @@ class Solver:
         nnz = len(val)
         _check(lib().rbicgstab_set_matrix(self._h, n, nnz, rp, cp, vp, w1), "rbicgstab_set_matrix")
         self.n = n
+        self.nnz = nnz
+        self.values_version += 1
 
     def set_values(self, val):
         vp, w, keep = _ptr(val, np.float64)
-        return _check(lib().rbicgstab_set_values(self._h, vp, w), "rbicgstab_set_values")
+        rc = _check(lib().rbicgstab_set_values(self._h, vp, w), "rbicgstab_set_values")
+        self.values_version += 1
+        return rc
 
     def set_recycle(self, U, Ut=None) -> int:
         """Set U (n x k) and U~ (None: U~ = U).  Returns the status (RB_OK or the rank warning)."""
@@ -324,6 +331,20 @@ class Solver:
             yp = y.ctypes.data
         _check(lib().rbicgstab_apply(self._h, vp, yp, int(bool(transpose)), w), "rbicgstab_apply")
         return y
+
+    def pattern_outer(self, u, v, scale=1.0):
+        """out_e = scale * u_i * v_j over the entries (i, j) of the matrix's
+        pattern in the CSR order of set_matrix (rbicgstab_pattern_outer);
+        u, v are CUDA tensors, the result a CUDA tensor of nnz values."""
+        import torch
+        if not (_is_torch(u) and _is_torch(v) and u.is_cuda and v.is_cuda):
+            raise ValueError("pattern_outer takes CUDA tensors")
+        up, _, ku = _ptr(u, np.float64)
+        vp2, _, kv = _ptr(v, np.float64)
+        out = torch.empty(self.nnz, dtype=torch.float64, device=u.device)
+        _check(lib().rbicgstab_pattern_outer(self._h, up, vp2, float(scale), out.data_ptr(), RB_DEVICE),
+               "rbicgstab_pattern_outer")
+        return out
 
 
 def residual_noalloc(row_ptr, col, val, x, b, r, rnorm2, stream=None, n=None) -> int:
