@@ -564,8 +564,6 @@ __device__ __forceinline__ void spmv_multi(const IterArgs<T>& a, const T* const*
   __syncthreads();   // the tile storage is reused by the reduction
 }
 
-// Dynamic shared memory of P1 / P3: the tile storage of the multi-RHS path; and
-// the resident blocks per SM the kernels are compiled for.
 // Dynamic shared memory of the FP64 single-RHS P1 / P3: per warp the C-hat
 // tiles of its two current slices (k <= 24: two blocks per SM still fit),
 // reused after the main loop by the block reduction.
@@ -579,6 +577,8 @@ struct TileSmem1 {
   };
 };
 
+// Dynamic shared memory of P1 / P3 (the tile storage of the multi-RHS path, or
+// TileSmem1), and the resident blocks per SM the kernels are compiled for.
 template <typename T, int KMAX, int R>
 struct P13Smem {
   static constexpr bool multi = ColProj<T, KMAX, R>::value || R > 1 || KMAX == 0;
