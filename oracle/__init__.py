@@ -18,6 +18,8 @@ recycle    harmonic Ritz extraction for the recycle-space update between
            systems, and the mode-S sequence driver.
 rbicg      Alg. 1 (RBiCG): the primary system and its dual together, with a
            two-sided recycle space.
+bicgstab_l BiCGstab(l) (Sleijpen-Fokkema), plain and on the recycling
+           projected operator: the breakdown-robust variant (l = 1 is Alg. 2).
 adjoint    gradient of L = ||C_out x||^2 with respect to b, the entries of A
            and the parameters of A(p), from one dual solve A^T lam = dL/dx
            with the recycle space's roles swapped.
