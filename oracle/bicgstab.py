@@ -65,7 +65,11 @@ def bicgstab(A, b, x0=None, tol=1e-8, max_itn=None, shadow_seed=DEFAULT_SEED,
             p = r + beta * (p - omega * v)
         v = A @ p
         info.matvecs += 1
-        alpha = rho / np.dot(rt, v)
+        rtv = np.dot(rt, v)
+        if rtv == 0.0:                # (r~, v) = 0: alpha undefined
+            info.status = BREAKDOWN_RHO
+            break
+        alpha = rho / rtv
         s = r - alpha * v
         snorm = np.linalg.norm(s)
         if snorm <= thresh:

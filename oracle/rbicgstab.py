@@ -16,6 +16,10 @@ Readings where the paper is silent (each listed in the design notes):
   ||r_0|| <= tol ||b|| returns immediately.  A half step whose s meets the
   test ends with x += alpha p, x_c += alpha zeta, r = s.
 * (r_0, r~_0) = 0 (step 3): redraw r~_{-1} with seed + 1, at most 3 times.
+* (r~_0, q_i) = 0 or (r~_0, r_i) = 0 inside the iteration leaves alpha or
+  beta undefined: the solve stops with the rho breakdown status (no
+  look-ahead, as for step 3); (t, t) = 0 or omega = 0 stop it with the omega
+  breakdown status.
 * Matvec counting: one per A-product in the iteration, one for r_{-1} when
   x_{-1} != 0, and setup products (C = A U, C~ = A^T U~) counted apart.
 
@@ -187,7 +191,12 @@ def rbicgstab(A, b, rec: RecycleSpace | None = None, x_m1=None, tol=1e-8, max_it
             store.AP.append(q.copy())
         zeta = Chat.T @ q
         q = q - C @ zeta
-        alpha = np.dot(rt0, r) / np.dot(rt0, q)
+        rtq = np.dot(rt0, q)
+        if rtq == 0.0:                            # (r~_0, q_i) = 0: no alpha (reading, module doc)
+            info.status = BREAKDOWN_RHO
+            info.iters = i - 1
+            break
+        alpha = np.dot(rt0, r) / rtq
         s = r - alpha * q
         if np.linalg.norm(s) <= thresh:          # half step (reading, see module doc)
             x = x + alpha * p
@@ -230,7 +239,11 @@ def rbicgstab(A, b, rec: RecycleSpace | None = None, x_m1=None, tol=1e-8, max_it
         if rn <= thresh:
             converged = True
             break
-        beta = (np.dot(rt0, r) / np.dot(rt0, r_prev)) * (alpha / omega)
+        rho = np.dot(rt0, r)
+        if rho == 0.0:                            # (r~_0, r_i) = 0: no beta (reading, module doc)
+            info.status = BREAKDOWN_RHO
+            break
+        beta = (rho / np.dot(rt0, r_prev)) * (alpha / omega)
     if cycle_s:
         flush()
     if not converged and info.status == OK:

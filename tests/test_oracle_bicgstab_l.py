@@ -73,6 +73,11 @@ def test_ell2_survives_where_bicgstab_collapses():
     b = inputs.gaussian_rhs(N * N, 1)
     x1, i1 = obl.bicgstab_l(A, b, 1, tol=1e-8, max_itn=2000)
     assert i1.status != orb.OK or np.linalg.norm(b - A @ x1) > 1e-6 * np.linalg.norm(b)
+    # Alg. 2 itself stops at its breakdown guards with finite iterates
+    with np.errstate(divide="raise", invalid="raise", over="raise"):
+        xa, ia = orb.rbicgstab(A, b, None, tol=1e-8, max_itn=2000)
+    assert ia.status in (orb.BREAKDOWN_RHO, orb.BREAKDOWN_OMEGA, orb.NOTCONV)
+    assert np.all(np.isfinite(xa))
     for ell in (2, 4):
         x, info = obl.bicgstab_l(A, b, ell, tol=1e-8, max_itn=2000)
         assert info.status == orb.OK, ell
