@@ -201,6 +201,15 @@ int rbicgstab_apply(rb_handle h, const double* v, double* y, int transpose, int 
 int rbicgstab_pattern_outer(rb_handle h, const double* u, const double* v, double scale, double* out,
                             int where);
 
+/* The singular value decomposition used to biorthogonalise C and C~ (the
+ * host step of Alg. 2 step 1; Sec. 3 requires C~^T C diagonal with positive
+ * entries): M = C~^T C (k x k, column-major) = P diag(sigma) Q^T with P, Q
+ * orthogonal (k x k, column-major) and sigma descending (k entries); the
+ * library then rotates U <- U Q, C <- C Q, U~ <- U~ P, C~ <- C~ P.  One-sided
+ * Jacobi; pure host code, needs no device.  Errors: RB_EINVAL (k < 1 or
+ * k > 256, null pointer), RB_ENONFINITE (non-finite entry of M). */
+int rbicgstab_svd_small(int32_t k, const double* M, double* P, double* sigma, double* Q);
+
 /* Harmonic-Ritz selection on the host (the small dense step of the recycle
  * update, run between cycles of s iterations, Sec. 6.2): given G = Z^T Z and
  * H = Z^T W (m x m, column-major) for a subspace W with Z = A W, return in Y

@@ -1446,6 +1446,14 @@ extern "C" int rbicgstab_pattern_outer(rb_handle h, const double* u, const doubl
   return sync(h);
 }
 
+extern "C" int rbicgstab_svd_small(int32_t k, const double* M, double* P, double* sigma, double* Q) {
+  if (k < 1 || k > 256 || !M || !P || !sigma || !Q) return RB_EINVAL;
+  for (int64_t i = 0; i < (int64_t)k * k; ++i)
+    if (!std::isfinite(M[i])) return RB_ENONFINITE;
+  rb::svd_small(k, M, P, sigma, Q);
+  return RB_OK;
+}
+
 extern "C" int rbicgstab_harmonic_ritz(int32_t m, const double* G, const double* H, int32_t k, double* Y,
                                        double* theta_re, double* theta_im, int32_t* k_used) {
   if (m <= 0 || k <= 0 || k > m || !G || !H || !Y || !k_used) return RB_EINVAL;

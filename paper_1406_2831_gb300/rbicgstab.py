@@ -87,6 +87,7 @@ def lib():
     L.rbicgstab_apply.argtypes = [vp, dp, dp, ctypes.c_int, ctypes.c_int]
     L.rbicgstab_pattern_outer.argtypes = [vp, dp, dp, ctypes.c_double, dp, ctypes.c_int]
     L.rbicgstab_harmonic_ritz.argtypes = [i32, dp, dp, i32, dp, dp, dp, ctypes.POINTER(i32)]
+    L.rbicgstab_svd_small.argtypes = [i32, dp, dp, dp, dp]
     L.rbicgstab_solve_block.argtypes = [vp, i32, dp, dp, i64, ctypes.c_int, ctypes.POINTER(Stats)]
     L.rbicgstab_time_passes.argtypes = [vp, i32, dp, i64, ctypes.c_int, i32, dp]
     L.rbicg_solve.argtypes = [vp, dp, dp, dp, dp, ctypes.c_int, ctypes.POINTER(Stats), ctypes.POINTER(Stats)]
@@ -99,7 +100,7 @@ def lib():
     for name in ("rbicgstab_create", "rbicgstab_destroy", "rbicgstab_set_matrix", "rbicgstab_set_values",
                  "rbicgstab_set_recycle", "rbicgstab_get_recycle", "rbicgstab_solve", "rbicgstab_apply",
                  "rbicgstab_harmonic_ritz", "rbicgstab_time_passes", "rbicgstab_solve_block",
-                 "rbicg_solve", "rbicgstab_pattern_outer"):
+                 "rbicg_solve", "rbicgstab_pattern_outer", "rbicgstab_svd_small"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -378,6 +379,19 @@ def time_passes(solver: "Solver", b, reps: int = 10):
     code = lib().rbicgstab_time_passes(solver._h, int(nrhs), bp, int(n), w, int(reps), ms.ctypes.data)
     _check(code, "rbicgstab_time_passes")
     return ms, code
+
+
+def svd_small(M: np.ndarray):
+    """Host SVD of the library's biorthogonalisation (rbicgstab_svd_small):
+    M = P diag(sigma) Q^T, sigma descending."""
+    k = M.shape[0]
+    Mf = np.asfortranarray(M, dtype=np.float64)
+    P = np.zeros((k, k), order="F")
+    Q = np.zeros((k, k), order="F")
+    sig = np.zeros(k)
+    _check(lib().rbicgstab_svd_small(k, Mf.ctypes.data, P.ctypes.data, sig.ctypes.data, Q.ctypes.data),
+           "rbicgstab_svd_small")
+    return P, sig, Q
 
 
 def harmonic_ritz(G: np.ndarray, H: np.ndarray, k: int):

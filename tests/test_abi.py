@@ -1,6 +1,8 @@
 """C-ABI checks that need no GPU: the library loads, exports every entry point
-declared in include/rbicgstab.h, and its host-only harmonic-Ritz step agrees
-with the oracle's (a different algorithm on the same pencil)."""
+declared in include/rbicgstab.h, its host-only harmonic-Ritz step agrees
+with the oracle's (a different algorithm on the same pencil), and its host
+SVD (the biorthogonalisation of Alg. 2 step 1) is a valid SVD with the
+singular values LAPACK computes."""
 import ctypes
 import os
 import re
@@ -24,7 +26,7 @@ def L():
 
 def _declared():
     src = open(os.path.join(ROOT, "include", "rbicgstab.h")).read()
-    return sorted(set(re.findall(r"\b(rbicgstab_\w+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b(rbicg(?:stab)?_\w+)\s*\(", src)))
 
 
 def test_exports_every_declared_symbol(L):
@@ -98,3 +100,43 @@ def test_host_harmonic_ritz_exact_eigenvector(L):
 def test_harmonic_ritz_rejects_bad_args(L):
     with pytest.raises(rb.RbError):
         rb.harmonic_ritz(np.eye(3), np.eye(3), 5)
+
+
+def _check_svd(M, P, sig, Q, tol=1e-13):
+    k = M.shape[0]
+    s1 = np.linalg.svd(M, compute_uv=False)
+    assert np.all(np.diff(sig) <= 0)
+    assert np.max(np.abs(sig - s1)) <= tol * s1[0]
+    assert np.linalg.norm(P @ np.diag(sig) @ Q.T - M) <= tol * np.linalg.norm(M)
+    assert np.linalg.norm(Q.T @ Q - np.eye(k)) <= tol * k
+    live = sig > 1e-8 * sig[0]
+    assert np.linalg.norm(P[:, live].T @ P[:, live] - np.eye(live.sum())) <= tol * k
+
+
+@pytest.mark.parametrize("k", [1, 5, 20, 40])
+def test_host_svd_of_a_biorthogonalisation_gram(L, k):
+    """M = C~^T C for random tall C, C~ (the setup's Gram matrix)."""
+    rng = np.random.default_rng(k)
+    C = rng.standard_normal((300, k))
+    Ct = rng.standard_normal((300, k)) + 0.5 * C
+    M = Ct.T @ C
+    P, sig, Q = rb.svd_small(M)
+    _check_svd(M, P, sig, Q)
+
+
+def test_host_svd_rank_deficient(L):
+    rng = np.random.default_rng(3)
+    M = rng.standard_normal((10, 3)) @ rng.standard_normal((3, 10))
+    P, sig, Q = rb.svd_small(M)
+    assert np.all(sig[3:] <= 1e-13 * sig[0])
+    _check_svd(M, P, sig, Q)
+
+
+def test_host_svd_rejects_bad_args(L):
+    M = np.eye(3)
+    out = [np.zeros(9), np.zeros(3), np.zeros(9)]
+    assert L.rbicgstab_svd_small(0, M.ctypes.data, out[0].ctypes.data, out[1].ctypes.data,
+                                 out[2].ctypes.data) == rb.C["RB_EINVAL"]
+    M[1, 2] = np.nan
+    assert L.rbicgstab_svd_small(3, M.ctypes.data, out[0].ctypes.data, out[1].ctypes.data,
+                                 out[2].ctypes.data) == rb.C["RB_ENONFINITE"]
