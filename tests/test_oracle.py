@@ -125,6 +125,26 @@ def test_biorthogonality_and_projector():
     assert np.linalg.norm(rec.Ct.T @ info.r0) <= 1e-12 * np.linalg.norm(rec.Ct) * np.linalg.norm(info.r0)
 
 
+@pytest.mark.parametrize("two_sided", [False, True])
+def test_projector_is_the_oblique_projector_of_the_raw_spaces(two_sided):
+    """C C-hat^T is the projector onto range(A U) along range(A^T U~)^perp:
+    C M^+ C~^T with the unrotated C = A U, C~ = A^T U~ and M = C~^T C, whatever
+    basis the biorthogonalisation picks; and U C-hat^T, the map the iterate
+    correction uses, is U M^+ C~^T."""
+    A = inputs.conv_diff_2d(14, 9.0).to_scipy()
+    n = A.shape[0]
+    U = inputs.random_recycle_basis(n, 5, 21)
+    Ut = inputs.random_recycle_basis(n, 5, 22) if two_sided else U
+    rec = orb.recycle_setup(A, U, Ut if two_sided else None)
+    C, Ct = A @ U, A.T @ Ut
+    Mp = np.linalg.pinv(Ct.T @ C)
+    want = C @ Mp @ Ct.T
+    got = rec.C @ rec.Chat.T
+    assert np.linalg.norm(got - want) <= 1e-12 * np.linalg.norm(want)
+    assert np.linalg.norm(rec.U @ rec.Chat.T - U @ Mp @ Ct.T) <= 1e-12 * np.linalg.norm(U @ Mp @ Ct.T)
+    assert np.linalg.norm(got @ got - got) <= 1e-12 * np.linalg.norm(got)   # a projector
+
+
 def test_residuals_stay_in_null_space_of_chat():
     A, b, rec, x, info = _recycled_run()
     for (xi, xci, ri) in info.iterates[:40]:
