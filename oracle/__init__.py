@@ -18,6 +18,9 @@ recycle    harmonic Ritz extraction for the recycle-space update between
            systems, and the mode-S sequence driver.
 rbicg      Alg. 1 (RBiCG): the primary system and its dual together, with a
            two-sided recycle space.
+recycle_two_sided
+           the two-sided Petrov-Galerkin update from RBiCG cycles (the
+           reading of the generator Sec. 6.2 defers to the RBiCG paper).
 bicgstab_l BiCGstab(l) (Sleijpen-Fokkema), plain and on the recycling
            projected operator: the breakdown-robust variant (l = 1 is Alg. 2).
 adjoint    gradient of L = ||C_out x||^2 with respect to b, the entries of A
