@@ -5,9 +5,10 @@
 //   * harmonic_ritz: the eigenproblem of the recycle update between cycles
 //     (Sec. 6.2): column scaling, restriction to the numerical range of W by
 //     a symmetric eigendecomposition of the scaled G = Z^T Z (Householder
-//     tridiagonalisation + implicit QL), reduction to a standard problem,
-//     Householder-Hessenberg + Francis double-shift QR for the eigenvalues
-//     (Golub & Van Loan, Matrix Computations, Sec. 7.4-7.5), and complex
+//     tridiagonalisation + implicit symmetric QR steps with the Wilkinson
+//     shift, Golub & Van Loan, Matrix Computations, Sec. 8.3), reduction to
+//     a standard problem, Householder-Hessenberg + Francis double-shift QR
+//     for the eigenvalues (Sec. 7.4-7.5), and complex
 //     inverse iteration on the Hessenberg form for the selected eigenvectors.
 // These are deliberately different algorithms from the LAPACK routines the
 // CPU oracle calls, so agreement between the two is evidence for both.
@@ -117,133 +118,142 @@ static void hessenberg(int n, std::vector<double>& h, std::vector<double>* refl 
   }
 }
 
-// Eigenvalues of an upper Hessenberg matrix by the Francis double-shift QR
-// iteration with deflation on small subdiagonal entries.  Returns false if an
-// eigenvalue needed more than 60 iterations.
+// Householder reflector P = I - beta v v^T (v[0] = 1) of a 2- or 3-vector u,
+// chosen so that P u is a multiple of e_1.  beta = 0 for u = 0.
+static double reflector(int len, const double* u, double* v) {
+  double nrm2 = 0.0;
+  for (int i = 0; i < len; ++i) nrm2 += u[i] * u[i];
+  v[0] = 1.0;
+  for (int i = 1; i < len; ++i) v[i] = 0.0;
+  if (nrm2 == 0.0) return 0.0;
+  const double nrm = std::sqrt(nrm2);
+  const double head = u[0] + (u[0] >= 0.0 ? nrm : -nrm);   // no cancellation
+  double vv = 1.0;
+  for (int i = 1; i < len; ++i) {
+    v[i] = u[i] / head;
+    vv += v[i] * v[i];
+  }
+  return 2.0 / vv;
+}
+
+// One Francis double-shift step (Golub & Van Loan, Alg. 7.5.1) on the
+// unreduced window H[lo..hi, lo..hi] of the row-major n x n Hessenberg
+// matrix a.  The shifts are the roots of x^2 - tr x + det; only the window is
+// transformed, which is all the eigenvalues need.
+static void francis_step(int n, std::vector<double>& a, int lo, int hi, double tr, double det) {
+  auto H = [&](int i, int j) -> double& { return a[(size_t)i * n + j]; };
+  // first column of (H - mu1 I)(H - mu2 I) restricted to the window
+  double u[3];
+  u[0] = H(lo, lo) * H(lo, lo) + H(lo, lo + 1) * H(lo + 1, lo) - tr * H(lo, lo) + det;
+  u[1] = H(lo + 1, lo) * (H(lo, lo) + H(lo + 1, lo + 1) - tr);
+  u[2] = H(lo + 1, lo) * H(lo + 2, lo + 1);
+  double v[3];
+  for (int k = lo; k <= hi - 1; ++k) {
+    const int len = (k <= hi - 2) ? 3 : 2;
+    const double beta = reflector(len, u, v);
+    if (beta != 0.0) {
+      // rows k..k+len-1 from the bulge column on
+      for (int j = std::max(lo, k - 1); j <= hi; ++j) {
+        double w = 0.0;
+        for (int r = 0; r < len; ++r) w += v[r] * H(k + r, j);
+        w *= beta;
+        for (int r = 0; r < len; ++r) H(k + r, j) -= w * v[r];
+      }
+      // columns k..k+len-1 down to the row that becomes the next bulge
+      const int last = std::min(k + len, hi);
+      for (int i = lo; i <= last; ++i) {
+        double w = 0.0;
+        for (int r = 0; r < len; ++r) w += H(i, k + r) * v[r];
+        w *= beta;
+        for (int r = 0; r < len; ++r) H(i, k + r) -= w * v[r];
+      }
+    }
+    if (k > lo) {   // the reflector has annihilated the old bulge below H(k, k-1)
+      for (int r = 1; r < len; ++r) H(k + r, k - 1) = 0.0;
+    }
+    if (k <= hi - 2) {   // the next bulge: column k below the subdiagonal
+      u[0] = H(k + 1, k);
+      u[1] = H(k + 2, k);
+      u[2] = (k + 3 <= hi) ? H(k + 3, k) : 0.0;
+    }
+  }
+}
+
+// Eigenvalues of a real 2 x 2 block [[p, q], [r, s]].
+static void eig2(double p, double q, double r, double s, double* re, double* im) {
+  const double half_tr = 0.5 * (p + s), half_diff = 0.5 * (p - s);
+  const double disc = half_diff * half_diff + q * r;
+  if (disc >= 0.0) {
+    const double root = std::sqrt(disc);
+    const double big = half_tr + (half_tr >= 0.0 ? root : -root);   // larger magnitude
+    re[0] = big;
+    re[1] = big != 0.0 ? (p * s - q * r) / big : 0.0;
+    im[0] = im[1] = 0.0;
+  } else {
+    const double root = std::sqrt(-disc);
+    re[0] = re[1] = half_tr;
+    im[0] = root;
+    im[1] = -root;
+  }
+}
+
+// Eigenvalues of an upper Hessenberg matrix (row-major, destroyed) by the
+// Francis double-shift QR algorithm with deflation (Golub & Van Loan,
+// Alg. 7.5.2): subdiagonal entries below eps * (|h_ii| + |h_{i-1,i-1}|) are
+// set to zero, a trailing 1 x 1 or 2 x 2 block is read off, otherwise the
+// trailing unreduced window takes a Francis step shifted by the eigenvalues
+// of its last 2 x 2 block.  Every tenth step without deflation uses an ad hoc
+// pair of complex shifts displaced from the corner by the size of the last
+// two subdiagonals, to break cycles.  Returns false after 60 steps without
+// deflation.
 static bool hqr(int n, std::vector<double>& a, std::vector<double>& wr, std::vector<double>& wi) {
   auto H = [&](int i, int j) -> double& { return a[(size_t)i * n + j]; };
   const double eps = 2.220446049250313e-16;
-  double anorm = 0.0;
-  for (int i = 0; i < n; ++i)
-    for (int j = std::max(i - 1, 0); j < n; ++j) anorm += std::fabs(H(i, j));
-  int nn = n - 1;
-  double t = 0.0;
-  while (nn >= 0) {
-    int its = 0, l;
-    for (;;) {
-      for (l = nn; l >= 1; --l) {
-        double s = std::fabs(H(l - 1, l - 1)) + std::fabs(H(l, l));
-        if (s == 0.0) s = anorm;
-        if (std::fabs(H(l, l - 1)) <= eps * s) {
-          H(l, l - 1) = 0.0;
-          break;
-        }
-      }
-      double x = H(nn, nn);
-      if (l == nn) {
-        wr[nn] = x + t;
-        wi[nn] = 0.0;
-        --nn;
+  double hnorm = 0.0;
+  for (double x : a) hnorm = std::max(hnorm, std::fabs(x));
+  int hi = n - 1, steps = 0;
+  while (hi >= 0) {
+    int lo = hi;
+    while (lo > 0) {
+      double ref = std::fabs(H(lo, lo)) + std::fabs(H(lo - 1, lo - 1));
+      if (ref == 0.0) ref = hnorm;
+      if (std::fabs(H(lo, lo - 1)) <= eps * ref) {
+        H(lo, lo - 1) = 0.0;
         break;
       }
-      double y = H(nn - 1, nn - 1);
-      double w = H(nn, nn - 1) * H(nn - 1, nn);
-      if (l == nn - 1) {
-        const double p = 0.5 * (y - x);
-        const double q = p * p + w;
-        const double z = std::sqrt(std::fabs(q));
-        x += t;
-        if (q >= 0.0) {
-          const double zz = p + (p >= 0 ? z : -z);
-          wr[nn - 1] = wr[nn] = x + zz;
-          if (zz != 0.0) wr[nn] = x - w / zz;
-          wi[nn - 1] = wi[nn] = 0.0;
-        } else {
-          wr[nn - 1] = wr[nn] = x + p;
-          wi[nn - 1] = z;
-          wi[nn] = -z;
-        }
-        nn -= 2;
-        break;
-      }
-      if (its == 60) return false;
-      if (its == 10 || its == 20 || its == 40) {
-        t += x;
-        for (int i = 0; i <= nn; ++i) H(i, i) -= x;
-        const double s = std::fabs(H(nn, nn - 1)) + std::fabs(H(nn - 1, nn - 2));
-        x = y = 0.75 * s;
-        w = -0.4375 * s * s;
-      }
-      ++its;
-      int m;
-      double p = 0, q = 0, r = 0, z;
-      for (m = nn - 2; m >= l; --m) {
-        z = H(m, m);
-        r = x - z;
-        const double s0 = y - z;
-        p = (r * s0 - w) / H(m + 1, m) + H(m, m + 1);
-        q = H(m + 1, m + 1) - z - r - s0;
-        r = H(m + 2, m + 1);
-        const double s = std::fabs(p) + std::fabs(q) + std::fabs(r);
-        p /= s;
-        q /= s;
-        r /= s;
-        if (m == l) break;
-        const double u = std::fabs(H(m, m - 1)) * (std::fabs(q) + std::fabs(r));
-        const double v = std::fabs(p) * (std::fabs(H(m - 1, m - 1)) + std::fabs(z) + std::fabs(H(m + 1, m + 1)));
-        if (u <= eps * v) break;
-      }
-      for (int i = m + 2; i <= nn; ++i) {
-        H(i, i - 2) = 0.0;
-        if (i != m + 2) H(i, i - 3) = 0.0;
-      }
-      for (int kk = m; kk <= nn - 1; ++kk) {
-        if (kk != m) {
-          p = H(kk, kk - 1);
-          q = H(kk + 1, kk - 1);
-          r = (kk != nn - 1) ? H(kk + 2, kk - 1) : 0.0;
-          x = std::fabs(p) + std::fabs(q) + std::fabs(r);
-          if (x != 0.0) {
-            p /= x;
-            q /= x;
-            r /= x;
-          }
-        }
-        const double ss = std::sqrt(p * p + q * q + r * r);
-        const double s = p >= 0 ? ss : -ss;
-        if (s == 0.0) continue;
-        if (kk == m) {
-          if (l != m) H(kk, kk - 1) = -H(kk, kk - 1);
-        } else {
-          H(kk, kk - 1) = -s * x;
-        }
-        p += s;
-        x = p / s;
-        y = q / s;
-        z = r / s;
-        q /= p;
-        r /= p;
-        for (int j = kk; j <= nn; ++j) {
-          p = H(kk, j) + q * H(kk + 1, j);
-          if (kk != nn - 1) {
-            p += r * H(kk + 2, j);
-            H(kk + 2, j) -= p * z;
-          }
-          H(kk + 1, j) -= p * y;
-          H(kk, j) -= p * x;
-        }
-        const int mmin = nn < kk + 3 ? nn : kk + 3;
-        for (int i = l; i <= mmin; ++i) {
-          p = x * H(i, kk) + y * H(i, kk + 1);
-          if (kk != nn - 1) {
-            p += z * H(i, kk + 2);
-            H(i, kk + 2) -= p * r;
-          }
-          H(i, kk + 1) -= p * q;
-          H(i, kk) -= p;
-        }
-      }
+      --lo;
     }
+    if (lo == hi) {
+      wr[hi] = H(hi, hi);
+      wi[hi] = 0.0;
+      hi -= 1;
+      steps = 0;
+      continue;
+    }
+    if (lo == hi - 1) {
+      double re[2], im[2];
+      eig2(H(hi - 1, hi - 1), H(hi - 1, hi), H(hi, hi - 1), H(hi, hi), re, im);
+      wr[hi - 1] = re[0];
+      wi[hi - 1] = im[0];
+      wr[hi] = re[1];
+      wi[hi] = im[1];
+      hi -= 2;
+      steps = 0;
+      continue;
+    }
+    if (steps == 60) return false;
+    ++steps;
+    double tr, det;
+    if (steps % 10 == 0) {
+      const double d = std::fabs(H(hi, hi - 1)) + std::fabs(H(hi - 1, hi - 2));
+      const double cre = H(hi, hi) + 0.5 * d, cim = 0.8 * d;
+      tr = 2.0 * cre;
+      det = cre * cre + cim * cim;
+    } else {
+      tr = H(hi - 1, hi - 1) + H(hi, hi);
+      det = H(hi - 1, hi - 1) * H(hi, hi) - H(hi - 1, hi) * H(hi, hi - 1);
+    }
+    francis_step(n, a, lo, hi, tr, det);
   }
   return true;
 }
@@ -314,11 +324,61 @@ static std::vector<cd> inverse_iteration(int n, const std::vector<double>& Hs, c
 }
 
 // ---------------------------------------------------------------- symmetric eig
+// Symmetric tridiagonal T (diagonal d, off-diagonal e[i] between i and i+1)
+// to diagonal form by the symmetric QR algorithm (Golub & Van Loan,
+// Alg. 8.3.3): negligible off-diagonals are set to zero, the trailing
+// unreduced block takes one implicit QR step with the Wilkinson shift
+// (Alg. 8.3.2), a Givens rotation in plane (k, k+1) chasing the bulge from
+// the top of the block to its bottom.  Every rotation is applied to the
+// columns of Q (row-major), so A = Q T Q^T is kept.  Returns false if the
+// step count exceeds 60 per eigenvalue.
+static bool tridiagonal_qr(int m, std::vector<double>& d, std::vector<double>& e, std::vector<double>& Q) {
+  const double eps = 2.220446049250313e-16;
+  int hi = m - 1, steps = 0;
+  while (hi > 0) {
+    for (int i = 0; i < hi; ++i)
+      if (std::fabs(e[i]) <= eps * (std::fabs(d[i]) + std::fabs(d[i + 1]))) e[i] = 0.0;
+    if (e[hi - 1] == 0.0) {
+      --hi;
+      continue;
+    }
+    int lo = hi - 1;
+    while (lo > 0 && e[lo - 1] != 0.0) --lo;
+    if (++steps > 60 * m) return false;
+    // Wilkinson shift: the eigenvalue of the trailing 2 x 2 block nearer d[hi]
+    const double delta = 0.5 * (d[hi - 1] - d[hi]);
+    const double off = e[hi - 1];
+    const double mu = d[hi] - off * off / (delta + std::copysign(std::hypot(delta, off), delta));
+    // rotation G_k = [[c, s], [-s, c]] on rows/columns (k, k+1), T <- G T G^T
+    double x = d[lo] - mu, z = e[lo];
+    for (int k = lo; k < hi; ++k) {
+      const double r = std::hypot(x, z);
+      const double c = r > 0.0 ? x / r : 1.0, s = r > 0.0 ? z / r : 0.0;
+      if (k > lo) e[k - 1] = r;   // the bulge at (k+1, k-1) is folded into e[k-1]
+      const double dk = d[k], ek = e[k], dk1 = d[k + 1];
+      d[k] = c * c * dk + 2.0 * c * s * ek + s * s * dk1;
+      d[k + 1] = s * s * dk - 2.0 * c * s * ek + c * c * dk1;
+      e[k] = c * s * (dk1 - dk) + (c * c - s * s) * ek;
+      if (k + 1 < hi) {   // new bulge at (k+2, k); the next rotation removes it
+        z = s * e[k + 1];
+        e[k + 1] *= c;
+        x = e[k];
+      }
+      for (int row = 0; row < m; ++row) {
+        double* q = &Q[(size_t)row * m];
+        const double qa = q[k], qb = q[k + 1];
+        q[k] = c * qa + s * qb;
+        q[k + 1] = c * qb - s * qa;
+      }
+    }
+  }
+  return true;
+}
+
 // Symmetric S (m x m, column-major) = V diag(lam) V^T: Householder reduction
 // to tridiagonal form with the transformation accumulated (Golub & Van Loan,
-// Sec. 8.3.1), then the implicit symmetric QL iteration with Wilkinson-type
-// shifts on the tridiagonal matrix, rotating V along (Sec. 8.3.3).
-static void sym_eig(int m, const std::vector<double>& S, std::vector<double>& lam, std::vector<double>& V) {
+// Sec. 8.3.1), then the symmetric QR algorithm above.
+static bool sym_eig(int m, const std::vector<double>& S, std::vector<double>& lam, std::vector<double>& V) {
   // A row-major working copy; Q accumulates the reflections (A = Q T Q^T).
   std::vector<double> A(S);   // symmetric: row- and column-major coincide
   std::vector<double> Q((size_t)m * m, 0.0);
@@ -364,55 +424,12 @@ static void sym_eig(int m, const std::vector<double>& S, std::vector<double>& la
   std::vector<double> d(m), e(m, 0.0);
   for (int i = 0; i < m; ++i) d[i] = a(i, i);
   for (int i = 0; i + 1 < m; ++i) e[i] = a(i + 1, i);   // e[i] couples i and i+1
-  const double eps = 2.220446049250313e-16;
-  for (int l = 0; l < m; ++l) {
-    for (int iter = 0; iter < 100; ++iter) {
-      int mm = l;
-      for (; mm < m - 1; ++mm) {
-        const double dd = std::fabs(d[mm]) + std::fabs(d[mm + 1]);
-        if (std::fabs(e[mm]) <= eps * dd) break;
-      }
-      if (mm == l) break;
-      // shift from the leading 2x2 block, chase the bulge from mm up to l
-      double g = (d[l + 1] - d[l]) / (2.0 * e[l]);
-      double r = std::hypot(g, 1.0);
-      g = d[mm] - d[l] + e[l] / (g + (g >= 0 ? r : -r));
-      double s = 1.0, c = 1.0, pp = 0.0;
-      int i = mm - 1;
-      bool early = false;
-      for (; i >= l; --i) {
-        const double f = s * e[i], b = c * e[i];
-        r = std::hypot(f, g);
-        e[i + 1] = r;
-        if (r == 0.0) {
-          d[i + 1] -= pp;
-          e[mm] = 0.0;
-          early = true;
-          break;
-        }
-        s = f / r;
-        c = g / r;
-        g = d[i + 1] - pp;
-        r = (d[i] - g) * s + 2.0 * c * b;
-        pp = s * r;
-        d[i + 1] = g + pp;
-        g = c * r - b;
-        for (int k = 0; k < m; ++k) {
-          const double qf = Q[(size_t)k * m + i + 1];
-          Q[(size_t)k * m + i + 1] = s * Q[(size_t)k * m + i] + c * qf;
-          Q[(size_t)k * m + i] = c * Q[(size_t)k * m + i] - s * qf;
-        }
-      }
-      if (early) continue;
-      d[l] -= pp;
-      e[l] = g;
-      e[mm] = 0.0;
-    }
-  }
+  if (!tridiagonal_qr(m, d, e, Q)) return false;
   lam = d;
   V.assign((size_t)m * m, 0.0);
   for (int i = 0; i < m; ++i)
     for (int j = 0; j < m; ++j) V[i + (size_t)j * m] = Q[(size_t)i * m + j];   // column j = eigenvector j
+  return true;
 }
 
 // ---------------------------------------------------------------- harmonic Ritz
@@ -432,10 +449,10 @@ int harmonic_ritz(int m, const double* G, const double* Hm, int k, double tol_ra
       Hs[i + (size_t)j * m] = d[i] * Hm[i + (size_t)j * m] * d[j];
     }
   // Restrict the pencil to the dominant eigenspace of Gs: Gs = V L V^T by
-  // cyclic Jacobi rotations; keep eigenvalues > tol_rank * max (numerical
+  // the symmetric eigendecomposition above; keep eigenvalues > tol_rank * max (numerical
   // rank of W); with T = V_r L_r^{-1/2}, M = T^T Hs T and M z = (1/theta) z.
   std::vector<double> lam, V;
-  sym_eig(m, Gs, lam, V);
+  if (!sym_eig(m, Gs, lam, V)) return -1;
   double lmax = 0.0;
   for (double v : lam) lmax = std::max(lmax, v);
   if (!(lmax > 0)) return 0;

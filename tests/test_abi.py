@@ -140,3 +140,55 @@ def test_host_svd_rejects_bad_args(L):
     M[1, 2] = np.nan
     assert L.rbicgstab_svd_small(3, M.ctypes.data, out[0].ctypes.data, out[1].ctypes.data,
                                  out[2].ctypes.data) == rb.C["RB_ENONFINITE"]
+
+
+def _theta_sorted(t):
+    t = np.asarray(t, dtype=complex)
+    return t[np.lexsort((t.imag, t.real, np.round(np.abs(t), 12)))]
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_host_harmonic_ritz_complex_pairs(L, seed):
+    """With Z^T Z = I the pencil reduces to H y = (1/theta) y, so the theta are
+    the reciprocals of H's eigenvalues (LAPACK through numpy); a random real H
+    has complex pairs, each returned as [Re y, Im y] spanning H's invariant
+    subspace of the pair."""
+    rng = np.random.default_rng(100 + seed)
+    m = 14
+    H = rng.standard_normal((m, m))
+    mu = np.linalg.eigvals(H)
+    assert np.any(np.abs(mu.imag) > 1e-3)
+    y, th = rb.harmonic_ritz(np.eye(m), H, m)
+    assert len(th) == m
+    want = _theta_sorted(1.0 / mu)
+    got = _theta_sorted(th)
+    assert np.abs(got - want).max() <= 1e-10 * np.abs(want).max()
+    # each selected column block is invariant under H: H Y = Y M for a small M
+    k = 6
+    y6, th6 = rb.harmonic_ritz(np.eye(m), H, k)
+    Mfit = np.linalg.lstsq(y6, H @ y6, rcond=None)[0]
+    assert np.linalg.norm(H @ y6 - y6 @ Mfit) <= 1e-10 * np.linalg.norm(H) * np.linalg.norm(y6)
+    ref = _theta_sorted(1.0 / mu)[: len(th6)]
+    assert np.abs(_theta_sorted(th6) - ref).max() <= 1e-10 * np.abs(ref).max()
+
+
+def test_host_harmonic_ritz_defective_block(L):
+    """H = S J S^-1 with a 2 x 2 Jordan block for the eigenvalue of largest
+    magnitude (2.5): its theta = 0.4 appears twice, accurate to the square
+    root of the rounding unit that a defective eigenvalue allows, and the
+    first returned direction lies in the block's invariant subspace."""
+    rng = np.random.default_rng(11)
+    m = 10
+    J = np.diag(np.concatenate([[2.5, 2.5], np.linspace(0.3, 1.9, m - 2)]))
+    J[0, 1] = 1.0
+    S = rng.standard_normal((m, m)) + 3 * np.eye(m)
+    H = S @ J @ np.linalg.inv(S)
+    y, th = rb.harmonic_ritz(np.eye(m), H, 2)
+    assert len(th) == 2
+    assert np.abs(np.asarray(th) - 0.4).max() <= 1e-6
+    Qb, _ = np.linalg.qr(S[:, :2])
+    u = y[:, 0] / np.linalg.norm(y[:, 0])
+    assert np.linalg.norm(u - Qb @ (Qb.T @ u)) <= 1e-6
+    y_all, th_all = rb.harmonic_ritz(np.eye(m), H, m)
+    want = np.sort(1.0 / np.diag(J))
+    assert np.abs(np.sort(np.real(th_all)) - want).max() <= 1e-6
