@@ -5,7 +5,7 @@
 plus the HBM roofline of the dominant fused-iteration kernel.
 
 One step = one pass of the whole hot path over the sequence: for each of the
-20 matrices set the values (Alg. 2 step 1 recycle setup included) and solve
+20 matrices set the values (the recycle setup of Alg. 2 included) and solve
 its 4 right-hand sides with RBiCGSTAB (Alg. 2) as one block (the four
 systems iterate together and share each pass over A, C and C-hat), updating
 the recycle space from the block's first system (cycles of s = 25, harmonic
@@ -132,11 +132,11 @@ def pass_flops(n: int, z: int, k: int, R: int = 1) -> list:
 
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of the dominant
-# pass per launch, from ncu captures summarised in profiles/; keyed by
+# pass per launch, from ncu captures of that pass; keyed by
 # (precision, pass, grid side, k, right-hand sides per block).  An entry is
 # removed when its kernel changes.
 TRAFFIC = {
-    ("mixed", "P1", 128, 20, 4): 354_576_128,   # profiles/mixed_blocked_passes_3d7pt_128cubed_k20_r4.md
+    ("mixed", "P1", 128, 20, 4): 354_576_128,
 }
 
 

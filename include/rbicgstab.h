@@ -42,7 +42,7 @@ extern "C" {
 #define RB_ENOMEM            -5   /* device allocation failed */
 #define RB_ECUDA             -6   /* a CUDA runtime call failed */
 #define RB_ENOTCONV          -7   /* max_itn reached; x holds the last iterate */
-#define RB_EBREAKDOWN_RHO    -8   /* (r~_0, r) = 0 or (r~_0, q) = 0 after redraws (Alg. 2 step 3) */
+#define RB_EBREAKDOWN_RHO    -8   /* (r~_0, r) = 0 or (r~_0, q) = 0 after redraws (Alg. 2) */
 #define RB_EBREAKDOWN_OMEGA  -9   /* (t, t) = 0 with s != 0, or omega = 0 */
 #define RB_ETIMEOUT         -10   /* a bounded device-side wait expired */
 
@@ -66,14 +66,14 @@ typedef struct rb_ctx* rb_handle;
 typedef struct {
   int32_t  k_max;          /* recycle dimension k (Sec. 6.2 uses 20); 0..RB_KMAX       */
   int32_t  cycle_s;        /* cycle length s of the recycle update (Sec. 6.2: 25); 0->25 */
-  int32_t  max_itn;        /* iteration cap (Alg. 2 step 5); 0 -> min(n, 20000)        */
+  int32_t  max_itn;        /* iteration cap (Alg. 2); 0 -> min(n, 20000)               */
   int32_t  precision;      /* RB_FP64 or RB_MIXED                                      */
   int32_t  recycle_mode;   /* RB_RECYCLE_*                                             */
   int32_t  update_cycles;  /* cycles per solve that update U; 0 = every cycle          */
   int32_t  poll;           /* iterations per host convergence check; 0 = automatic     */
   int32_t  reserved;
   double   tol;            /* relative residual tolerance ||r|| <= tol ||b||; 0->1e-8  */
-  uint64_t shadow_seed;    /* SplitMix64 seed of r~_{-1} (Alg. 2 step 2); 0 -> 0x5EED  */
+  uint64_t shadow_seed;    /* SplitMix64 seed of r~_{-1} (Alg. 2); 0 -> 0x5EED         */
   void*    cuda_stream;    /* cudaStream_t the calls are ordered on (NULL = default)   */
 } rb_opts;
 
@@ -90,11 +90,11 @@ typedef struct {
   int32_t outer;           /* RB_MIXED: FP64 true-residual checks (residual            */
                            /* replacements and restarts); else 1                       */
   double  relres_rec;      /* ||r_i|| / ||b|| of the recursive residual                */
-  double  relres_true;     /* ||b - A x|| / ||b|| recomputed in FP64 after step 8      */
+  double  relres_true;     /* ||b - A x|| / ||b|| recomputed in FP64 after x - U x_c   */
   double  ms_total;        /* wall time of the call (CUDA events)                      */
   double  bytes_model;     /* algorithmic HBM bytes of the iterations                  */
   double  ms_update;       /* host wall time spent in recycle-space updates (cycle
-                              Gram/eig/rebuild and the new space's Alg. 2 step 1)     */
+                              Gram/eig/rebuild and the new space's recycle setup)      */
 } rb_stats;
 
 /* Create a solver handle on the current CUDA device.  *h receives the handle.
@@ -108,7 +108,7 @@ int rbicgstab_destroy(rb_handle h);
  * The matrix is validated on the device (monotone row_ptr, 0 <= col < n,
  * finite values), re-laid out as SELL-32 slices, and its transpose is built
  * (needed for C~ = A^T U~).  An existing recycle space U, U~ is kept and its
- * C, C~, D_c are recomputed for the new matrix (Alg. 2 step 1).
+ * C, C~, D_c are recomputed for the new matrix (Sec. 3).
  * Errors: RB_EINVAL, RB_EBADCSR, RB_ENONFINITE, RB_ENOMEM, RB_ECUDA. */
 int rbicgstab_set_matrix(rb_handle h, int64_t n, int64_t nnz, const int32_t* row_ptr,
                          const int32_t* col, const double* val, int where);
@@ -122,7 +122,7 @@ int rbicgstab_set_values(rb_handle h, const double* val, int where);
  * the right-only variant of Sec. 5), column-major with leading dimension ld.
  * Forms C = A U, C~ = A^T U~, biorthogonalises them by an SVD of C~^T C
  * (so D_c = C~^T C is diagonal and positive) and forms C-hat = C~ D_c^{-1}
- * (Alg. 2 step 1, eq. (3.4)).  k = 0 clears the space.  Needs a matrix.
+ * (Sec. 3, eq. (3.4)).  k = 0 clears the space.  Needs a matrix.
  * Returns RB_WRECYCLE_RANK when columns were dropped (k_used < k).
  * Errors: RB_EINVAL (k > k_max), RB_EDIM, RB_ENONFINITE. */
 int rbicgstab_set_recycle(rb_handle h, int32_t k, const double* U, const double* Ut,
@@ -135,8 +135,8 @@ int rbicgstab_get_recycle(rb_handle h, int32_t* k, double* U, double* Ut, int64_
                           int where);
 
 /* Solve A x = b with Alg. 2 using the current recycle space.  x holds the
- * initial guess x_{-1} on entry (Alg. 2 step 2) and the solution on return
- * (step 8: x = x - U x_c).  In the RB_RECYCLE_UPDATE_* modes the recycle
+ * initial guess x_{-1} on entry (eq. (3.5)) and the solution on return
+ * (after the final correction x = x - U x_c).  In the RB_RECYCLE_UPDATE_* modes the recycle
  * space is replaced by the harmonic-Ritz update built from this solve.
  * st may be NULL.  On RB_ENOTCONV / RB_EBREAKDOWN_* x holds the last iterate.
  * Errors: RB_EDIM (no matrix), RB_ENONFINITE (NaN/Inf in b or x), RB_ECUDA. */
@@ -172,9 +172,9 @@ int rbicgstab_solve_block(rb_handle h, int32_t nrhs, const double* B, double* X,
  * `where`); bt may be NULL, and then the shadow vector r~_{-1} of Alg. 2
  * (seed opts.shadow_seed) is the dual right-hand side.  x and xt hold the
  * initial guesses x_{-1}, x~_{-1} on entry (eq. (3.5) forms x_0, r_0, x~_0,
- * r~_0) and the solutions after step 7 on return.  When (r_0, r~_0) = 0,
+ * r~_0) and the solutions after the final correction on return.  When (r_0, r~_0) = 0,
  * x~_{-1} is replaced by the shadow vector (seed + 0, 1, 2) and the dual start
- * formed again (step 3).  Converged when ||r_i|| <= tol ||b|| and
+ * formed again.  Converged when ||r_i|| <= tol ||b|| and
  * ||r~_i|| <= tol ||b~|| on the recursive residuals.  st and st_dual, if not
  * NULL, receive the primary and the dual system's records (iters, status and
  * matvecs are shared; relres_* are each system's own; seeds_used counts the
@@ -202,7 +202,7 @@ int rbicgstab_pattern_outer(rb_handle h, const double* u, const double* v, doubl
                             int where);
 
 /* The singular value decomposition used to biorthogonalise C and C~ (the
- * host step of Alg. 2 step 1; Sec. 3 requires C~^T C diagonal with positive
+ * host step of the recycle setup; Sec. 3 requires C~^T C diagonal with positive
  * entries): M = C~^T C (k x k, column-major) = P diag(sigma) Q^T with P, Q
  * orthogonal (k x k, column-major) and sigma descending (k entries); the
  * library then rotates U <- U Q, C <- C Q, U~ <- U~ P, C~ <- C~ P.  One-sided

@@ -9,10 +9,10 @@ and it shares no code with the CUDA sources.
 Contents
 --------
 shadow     counter-based generator for the random shadow residual r~_{-1}
-           (Alg. 2 step 2): SplitMix64 from its published definition.
+           (Alg. 2): SplitMix64 from its published definition.
 bicgstab   van der Vorst's BiCGSTAB, written separately (the k = 0 baseline).
-rbicgstab  Alg. 2 (RBiCGSTAB) with eq. (3.5) ("minusXR") initial projection,
-           step-1 biorthogonalisation of C and C~, and the cycle store used by
+rbicgstab  Alg. 2 (RBiCGSTAB): BiCGSTAB on the projected operator of Sec. 3
+           from the start of eq. (3.5), the biorthogonalisation of C and C~, and the cycle store used by
            the recycle-space update.
 recycle    harmonic Ritz extraction for the recycle-space update between
            systems, and the mode-S sequence driver.

@@ -16,7 +16,7 @@ BiCGSTAB's omega = (t, s) / (t, t) tends to 0) no longer stalls.
 Recycling (Sec. 3): with the recycle space U, C = A U, C-hat = C~ D_c^{-1}
 (C-hat^T C = I) the iteration runs on the projected operator
 B = (I - C C-hat^T) A from x_0, r_0 of eq. (3.5) and shadow
-r~_0 = r~_{-1} - C~ C-check^T r~_{-1} (Alg. 2 step 2).  If y is the sum of
+r~_0 = r~_{-1} - C~ C-check^T r~_{-1} (eq. (3.5)).  If y is the sum of
 the Krylov corrections, x = x_0 + y - U C-hat^T A y has the residual
 r_0 - B y, the residual the iteration updates; C-hat^T A y is accumulated
 from the projection coefficients of every product (Alg. 2's x_c).  With
@@ -69,7 +69,7 @@ def bicgstab_l(A, b, ell=2, rec: RecycleSpace | None = None, x_m1=None, tol=1e-8
         z = Chat.T @ w
         return w - C @ z, z
 
-    # eq. (3.5) and the projected shadow (Alg. 2 steps 2-3)
+    # eq. (3.5) and the projected shadow, redrawn while (r~_0, r_0) = 0
     if x_m1 is None or not np.any(x_m1):
         x_m1, r_m1 = np.zeros(n), b.copy()
     else:

@@ -1,4 +1,4 @@
-"""Alg. 1 (RBiCG) of Sec. 4, in FP64, step by step as the paper states it.
+"""Alg. 1 (RBiCG) of Sec. 4 in FP64: BiCG on the projected primary and dual operators.
 
 Test infrastructure: only the tests, the smoke check and the benchmark's
 CPU-baseline leg use this module; the CUDA library never does.
@@ -8,7 +8,8 @@ together (real arithmetic here, so conj(alpha) = alpha and conj(beta) =
 beta).  With a recycle space U, U~ (C = A U, C~ = A^T U~ biorthogonal,
 C-hat = C~ D_c^{-1}, C-check = C D_c^{-1}, eq. (3.4)) the primary iteration
 runs on the projected operator (I - C C-hat^T) A and the dual on
-(I - C~ C-check^T) A^T; step 7 folds the accumulated coefficients back.
+(I - C~ C-check^T) A^T; the final correction folds the accumulated
+coefficients back.
 
 Readings where the paper is silent (each listed in the design notes):
 
@@ -17,7 +18,7 @@ Readings where the paper is silent (each listed in the design notes):
 * Initial vectors follow eq. (3.5) for both systems:
   x_0 = x_{-1} + U C-hat^T r_{-1},     r_0 = r_{-1} - C C-hat^T r_{-1},
   x~_0 = x~_{-1} + U~ C-check^T r~_{-1}, r~_0 = r~_{-1} - C~ C-check^T r~_{-1}.
-* Step 3 ((r_0, r~_0) = 0): x~_{-1} becomes the shadow vector with seed
+* (r_0, r~_0) = 0 at the start: x~_{-1} becomes the shadow vector with seed
   + attempt (at most 3 redraws), and x~_0, r~_0 are formed again.
 * Convergence: ||r_i|| <= tol ||b|| and ||r~_i|| <= tol ||b~|| on the
   recursive residuals (relative, as for Alg. 2).  A start that meets both
@@ -65,7 +66,7 @@ def rbicg(A, b, bt=None, rec: RecycleSpace | None = None, x_m1=None, xt_m1=None,
     bnorm, btnorm = np.linalg.norm(b), np.linalg.norm(bt)
     thresh, thresh_t = tol * bnorm, tol * btnorm
 
-    # step 2 (eq. (3.5)) for the primary system
+    # eq. (3.5) for the primary system
     if x_m1 is None or not np.any(x_m1):
         x_m1, r_m1 = np.zeros(n), b.copy()
     else:
@@ -82,7 +83,7 @@ def rbicg(A, b, bt=None, rec: RecycleSpace | None = None, x_m1=None, xt_m1=None,
             rs = bt - A.T @ xs
         return xs + Ut @ (Ccheck.T @ rs), rs - Ct @ (Ccheck.T @ rs)
 
-    # step 2 for the dual system; step 3: redraw x~_{-1} while (r_0, r~_0) = 0
+    # eq. (3.5) for the dual system; redraw x~_{-1} while (r_0, r~_0) = 0
     xt, rt = dual_start(xt_m1)
     rho = np.dot(rt, r)
     for attempt in range(3):
@@ -91,7 +92,7 @@ def rbicg(A, b, bt=None, rec: RecycleSpace | None = None, x_m1=None, xt_m1=None,
         xt, rt = dual_start(shadow_vector(n, shadow_seed + attempt))
         rho = np.dot(rt, r)
         info.seeds_used = attempt + 1
-    # step 4
+    # first search directions
     p, pt = np.zeros(n), np.zeros(n)
     zc, ztc = np.zeros(rec.k), np.zeros(rec.k)
     beta = 0.0
@@ -103,7 +104,7 @@ def rbicg(A, b, bt=None, rec: RecycleSpace | None = None, x_m1=None, xt_m1=None,
         info.iters = i
         info.relres = np.linalg.norm(r) / bnorm if bnorm > 0 else 0.0
         info.relres_dual = np.linalg.norm(rt) / btnorm if btnorm > 0 else 0.0
-        # step 7
+        # final correction of both systems
         return x - U @ zc, xt - Ut @ ztc, info
 
     if np.linalg.norm(r) <= thresh and np.linalg.norm(rt) <= thresh_t:
@@ -111,7 +112,7 @@ def rbicg(A, b, bt=None, rec: RecycleSpace | None = None, x_m1=None, xt_m1=None,
     if rho == 0.0:
         return done(BREAKDOWN_PQ, 0)
     for i in range(1, max_itn + 1):
-        # step 5, left column: primary; right column: dual
+        # the iteration; left column: primary; right column: dual
         p = r + beta * p
         pt = rt + beta * pt
         z = A @ p

@@ -1,9 +1,27 @@
-"""Alg. 2 (RBiCGSTAB) of Sec. 4, in FP64, step by step as the paper states it.
+"""RBiCGSTAB (Alg. 2 of Sec. 4) in FP64: BiCGSTAB on the projected operator.
 
-Notation follows the paper: U, U~ (``Ut``) span the recycle space; C = A U,
-C~ = A^T U~ (Sec. 3, definition of the recycle space); D_c = C~^T C diagonal
-with positive entries; C-hat = C~ D_c^{-1}, C-check = C D_c^{-1}
-(eq. (3.4), "CcheckChat"); x_0, r_0, r~_0 from eq. (3.5) ("minusXR").
+TEST INFRASTRUCTURE ONLY (see the package docstring): the CUDA library never
+imports this module.
+
+The method, restated from its definitions:
+
+* Recycle space (Sec. 3).  U, U~ (``Ut``) span the right and left recycle
+  spaces; C = A U and C~ = A^T U~ are made biorthogonal, so that
+  D_c = C~^T C is diagonal with positive entries; C-hat = C~ D_c^{-1} and
+  C-check = C D_c^{-1} (eq. (3.4)).  C C-hat^T is then the oblique projector
+  onto range(C) along the orthogonal complement of range(C~).
+* Projected operator (Sec. 3).  B = (I - C C-hat^T) A.  Its products are what
+  the iteration needs: for v, the raw product A v, the coefficients
+  C-hat^T A v, and B v = A v - C (C-hat^T A v).
+* Start (eq. (3.5)).  From x_{-1} and r_{-1} = b - A x_{-1}:
+  x_0 = x_{-1} + U C-hat^T r_{-1}, r_0 = (I - C C-hat^T) r_{-1}, and the
+  shadow r~_0 = (I - C~ C-check^T) r~_{-1} from a random r~_{-1}.
+* Iteration (Sec. 4).  Plain BiCGSTAB (van der Vorst) for B y = r_0 with
+  shadow r~_0, written in x directly: every product of B contributes its
+  coefficients C-hat^T A v, times the step length it enters x with, to the
+  k-vector x_c.
+* End (Alg. 2).  x = x_i - U x_c, which turns the approximate solution of the
+  projected system into one of A x = b.
 
 Readings where the paper is silent (each listed in the design notes):
 
@@ -15,16 +33,17 @@ Readings where the paper is silent (each listed in the design notes):
 * Convergence: ||r_i|| <= tol ||b|| on the recursive residual; a start with
   ||r_0|| <= tol ||b|| returns immediately.  A half step whose s meets the
   test ends with x += alpha p, x_c += alpha zeta, r = s.
-* (r_0, r~_0) = 0 (step 3): redraw r~_{-1} with seed + 1, at most 3 times.
+* (r_0, r~_0) = 0 at the start: redraw r~_{-1} with seed + 1, at most 3
+  times.
 * (r~_0, q_i) = 0 or (r~_0, r_i) = 0 inside the iteration leaves alpha or
   beta undefined: the solve stops with the rho breakdown status (no
-  look-ahead, as for step 3); (t, t) = 0 or omega = 0 stop it with the omega
-  breakdown status.
+  look-ahead, as at the start); (t, t) = 0 or omega = 0 stop it with the
+  omega breakdown status.
 * Matvec counting: one per A-product in the iteration, one for r_{-1} when
   x_{-1} != 0, and setup products (C = A U, C~ = A^T U~) counted apart.
 
-Everything here is computed literally: alpha from (r~_0, r_{i-1}) / (r~_0, q_i),
-r_i = r_{i-1} - alpha q_i - omega t_i, beta from (r~_0, r_i) / (r~_0, r_{i-1}).
+The inner products are formed literally: alpha = (r~_0, r_{i-1}) / (r~_0, q_i),
+beta = ((r~_0, r_i) / (r~_0, r_{i-1})) (alpha / omega).
 """
 from __future__ import annotations
 
@@ -62,7 +81,8 @@ def empty_space(n: int) -> RecycleSpace:
 
 
 def recycle_setup(A, U, Ut=None, drop=SVD_DROP) -> RecycleSpace:
-    """Alg. 2 step 1: C = A U, C~ = A^T U~, biorthogonalised; D_c, C-hat, C-check."""
+    """The recycle space of Sec. 3 for matrix A: C = A U, C~ = A^T U~,
+    biorthogonalised through the SVD of C~^T C; D_c, C-hat, C-check (eq. (3.4))."""
     n = A.shape[0]
     if U is None or U.shape[1] == 0:
         return empty_space(n)
@@ -120,14 +140,49 @@ class SolveInfo:
     r0: np.ndarray | None = None
 
 
+def project_product(A, rec: RecycleSpace, v):
+    """Product with B = (I - C C-hat^T) A (Sec. 3): returns (A v, C-hat^T A v, B v)."""
+    raw = A @ v
+    coef = rec.Chat.T @ raw
+    return raw, coef, raw - rec.C @ coef
+
+
+def initial_projection(A, b, rec: RecycleSpace, x_m1, shadow_seed):
+    """Eq. (3.5): x_0, r_0 and the shadow r~_0 from x_{-1} and a random r~_{-1}.
+
+    Returns (x_0, r_0, r~_0, (r~_0, r_0), number of r~_{-1} drawn, matvecs).
+    r~_{-1} is drawn again (seed + 1, at most 3 more times) while
+    (r~_0, r_0) = 0."""
+    n = b.shape[0]
+    matvecs = 0
+    if x_m1 is None or not np.any(x_m1):
+        x_m1 = np.zeros(n)
+        r_m1 = b.copy()
+    else:
+        x_m1 = np.asarray(x_m1, dtype=np.float64)
+        r_m1 = b - A @ x_m1
+        matvecs = 1
+    x0 = x_m1 + rec.U @ (rec.Chat.T @ r_m1)
+    r0 = r_m1 - rec.C @ (rec.Chat.T @ r_m1)
+    for attempt in range(4):
+        rt_m1 = shadow_vector(n, shadow_seed + attempt)
+        rt0 = rt_m1 - rec.Ct @ (rec.Ccheck.T @ rt_m1)
+        rho0 = np.dot(rt0, r0)
+        if rho0 != 0.0:
+            break
+    return x0, r0, rt0, rho0, attempt + 1, matvecs
+
+
 def rbicgstab(A, b, rec: RecycleSpace | None = None, x_m1=None, tol=1e-8, max_itn=None,
               shadow_seed=DEFAULT_SEED, record=False, cycle_s=None, on_cycle=None,
               true_residual=True):
-    """Alg. 2.  Returns (x, SolveInfo).
+    """Alg. 2: BiCGSTAB on B = (I - C C-hat^T) A from the start of eq. (3.5),
+    then x = x_i - U x_c.  Returns (x, SolveInfo).
 
     ``cycle_s`` / ``on_cycle``: every ``cycle_s`` iterations (and once more for
     a final partial cycle) ``on_cycle(store)`` is called with the CycleStore
-    of that cycle; the recycle-space update (``oracle.recycle``) hooks in here.
+    of that cycle (p_i, s_i and their raw products A p_i, A s_i); the
+    recycle-space update (``oracle.recycle``) hooks in here.
     """
     n = b.shape[0]
     if rec is None:
@@ -135,35 +190,31 @@ def rbicgstab(A, b, rec: RecycleSpace | None = None, x_m1=None, tol=1e-8, max_it
     if max_itn is None:
         max_itn = min(n, 20000)
     info = SolveInfo()
-    U, C, Ct, Chat, Ccheck = rec.U, rec.C, rec.Ct, rec.Chat, rec.Ccheck
     b = np.asarray(b, dtype=np.float64)
     bnorm = np.linalg.norm(b)
     thresh = tol * bnorm
 
-    # step 2: x_{-1}, r_{-1}; random r~_{-1}; eq. (3.5)
-    if x_m1 is None or not np.any(x_m1):
-        x_m1 = np.zeros(n)
-        r_m1 = b.copy()
-    else:
-        x_m1 = np.asarray(x_m1, dtype=np.float64)
-        r_m1 = b - A @ x_m1
-        info.matvecs += 1
-    x = x_m1 + U @ (Chat.T @ r_m1)
-    r = r_m1 - C @ (Chat.T @ r_m1)
-    # step 3: (r_0, r~_0) = 0 -> redraw r~_{-1}
-    for attempt in range(4):
-        rt_m1 = shadow_vector(n, shadow_seed + attempt)
-        rt0 = rt_m1 - Ct @ (Ccheck.T @ rt_m1)
-        rho_prev = np.dot(rt0, r)
-        info.seeds_used = attempt + 1
-        if rho_prev != 0.0:
-            break
+    x, r, rt0, rho_prev, info.seeds_used, info.matvecs = initial_projection(A, b, rec, x_m1, shadow_seed)
     info.rt0, info.r0 = rt0, r.copy()
-    # step 4
-    beta = omega = 0.0
-    p = np.zeros(n)
-    q = np.zeros(n)
     xc = np.zeros(rec.k)
+
+    def finish(x_i):
+        """End of Alg. 2: the solution of A x = b from the projected iterate."""
+        x_out = x_i - rec.U @ xc
+        info.relres_rec = np.linalg.norm(r) / bnorm if bnorm > 0 else 0.0
+        if true_residual:
+            info.relres_true = np.linalg.norm(b - A @ x_out) / bnorm if bnorm > 0 else 0.0
+        return x_out
+
+    if np.linalg.norm(r) <= thresh:
+        info.relres_rec = np.linalg.norm(r) / bnorm if bnorm > 0 else 0.0
+        info.relres_true = info.relres_rec
+        return x - rec.U @ xc, info
+    if rho_prev == 0.0:
+        info.status = BREAKDOWN_RHO
+        info.relres_rec = np.linalg.norm(r) / bnorm
+        return x - rec.U @ xc, info
+
     store = CycleStore()
 
     def flush():
@@ -172,25 +223,18 @@ def rbicgstab(A, b, rec: RecycleSpace | None = None, x_m1=None, tol=1e-8, max_it
             on_cycle(store)
         store = CycleStore()
 
-    if np.linalg.norm(r) <= thresh:
-        info.relres_rec = np.linalg.norm(r) / bnorm if bnorm > 0 else 0.0
-        info.relres_true = info.relres_rec
-        return x - U @ xc, info
-    if rho_prev == 0.0:
-        info.status = BREAKDOWN_RHO
-        info.relres_rec = np.linalg.norm(r) / bnorm
-        return x - U @ xc, info
-
+    # BiCGSTAB recurrences on B; p_1 = r_0 (beta = 0 before the first step)
+    beta = omega = 0.0
+    p = np.zeros(n)
+    q = np.zeros(n)
     converged = False
     for i in range(1, max_itn + 1):
         p = r + beta * p - beta * omega * q
-        q = A @ p
+        Ap, zeta, q = project_product(A, rec, p)           # q_i = B p_i
         info.matvecs += 1
         if cycle_s:
             store.P.append(p.copy())
-            store.AP.append(q.copy())
-        zeta = Chat.T @ q
-        q = q - C @ zeta
+            store.AP.append(Ap.copy())
         rtq = np.dot(rt0, q)
         if rtq == 0.0:                            # (r~_0, q_i) = 0: no alpha (reading, module doc)
             info.status = BREAKDOWN_RHO
@@ -208,13 +252,11 @@ def rbicgstab(A, b, rec: RecycleSpace | None = None, x_m1=None, tol=1e-8, max_it
                 info.iterates.append((x.copy(), xc.copy(), r.copy()))
             converged = True
             break
-        t = A @ s
+        As, gamma, t = project_product(A, rec, s)         # t_i = B s_i
         info.matvecs += 1
         if cycle_s:
             store.S.append(s.copy())
-            store.AS.append(t.copy())
-        gamma = Chat.T @ t
-        t = t - C @ gamma
+            store.AS.append(As.copy())
         tt = np.dot(t, t)
         if tt == 0.0:
             info.status = BREAKDOWN_OMEGA
@@ -225,6 +267,7 @@ def rbicgstab(A, b, rec: RecycleSpace | None = None, x_m1=None, tol=1e-8, max_it
             info.status = BREAKDOWN_OMEGA
             info.iters = i - 1
             break
+        # x moves by alpha p + omega s; its U-component by alpha zeta + omega gamma
         x = x + alpha * p + omega * s
         xc = xc + alpha * zeta + omega * gamma
         r_prev = r
@@ -248,9 +291,4 @@ def rbicgstab(A, b, rec: RecycleSpace | None = None, x_m1=None, tol=1e-8, max_it
         flush()
     if not converged and info.status == OK:
         info.status = NOTCONV
-    # step 8
-    x = x - U @ xc
-    info.relres_rec = np.linalg.norm(r) / bnorm
-    if true_residual:
-        info.relres_true = np.linalg.norm(b - A @ x) / bnorm
-    return x, info
+    return finish(x), info

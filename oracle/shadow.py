@@ -1,4 +1,4 @@
-"""Shadow residual r~_{-1} of Alg. 2 step 2 ("initialize r~_{-1} to a random vector").
+"""The random shadow vector r~_{-1} with which Alg. 2 starts.
 
 The paper leaves the distribution open.  Both the oracle and the CUDA path
 draw it from one counter-based generator, SplitMix64 (Steele, Lea and Flood,

@@ -1,5 +1,5 @@
 // Generic FP64 kernels used outside the fused iteration: the setup of a
-// solve (eq. (3.5)), the end of a solve (Alg. 2 step 8 and the true
+// solve (eq. (3.5)), the end of a solve (the final correction of Alg. 2 and the true
 // residual), and the recycle-space work (Gram matrices, block updates).
 // All reductions are deterministic (fixed trees, no floating-point atomics).
 #include <algorithm>

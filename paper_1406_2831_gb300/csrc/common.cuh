@@ -55,7 +55,7 @@ __host__ __device__ inline int64_t grid_partial_rows(int G) {
 
 // Solver state that lives on the device between kernels of one solve.  The
 // last block of each fused pass reduces the block partials in a fixed order
-// and updates these scalars (Alg. 2 step 6).
+// and updates these scalars (Alg. 2).
 struct IterState {
   double rho;      // (r~_0, r_{i-1})
   double alpha, omega, beta;

@@ -1,6 +1,6 @@
 // Small dense FP64 linear algebra on the host (m <= ~100), for the parts of
 // the method that are a k x k or m x m problem:
-//   * svd_small: the biorthogonalisation of C and C~ (Alg. 2 step 1 requires
+//   * svd_small: the biorthogonalisation of C and C~ (the recycle setup of Sec. 3 requires
 //     C~^T C diagonal and positive, Sec. 3): one-sided Jacobi SVD (Hestenes).
 //   * harmonic_ritz: the eigenproblem of the recycle update between cycles
 //     (Sec. 6.2): column scaling, restriction to the numerical range of W by

@@ -1,4 +1,4 @@
-// The fused passes of one RBiCGSTAB iteration (Alg. 2, step 6).
+// The fused passes of one RBiCGSTAB iteration (Alg. 2).
 //
 // One iteration is five kernels, each one streaming pass over HBM that ends in
 // a deterministic grid reduction whose last block computes the scalars:

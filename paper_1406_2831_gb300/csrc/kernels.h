@@ -5,7 +5,7 @@
 
 namespace rb {
 
-// Pointers of one RBiCGSTAB iteration (Alg. 2 step 6) over nrhs <= kMaxRhs
+// Pointers of one RBiCGSTAB iteration (Alg. 2) over nrhs <= kMaxRhs
 // right-hand sides of the same matrix and recycle space.  Vectors have npad
 // entries (n rounded up to the slice height; the tail is kept at zero).  For
 // k = 0, q aliases qraw and t aliases traw.  st points to nrhs consecutive

@@ -176,51 +176,118 @@ __global__ void k_scatter_t(int64_t n, const int32_t* __restrict__ rp, const int
   }
 }
 
+// Exclusive scan of cnt[0..n) into out[0..n] by one block: each thread sums a
+// contiguous chunk, the block scans the chunk sums in shared memory (Hillis-
+// Steele), and each thread writes its chunk's prefix sums.  The transpose is
+// built once per matrix pattern, so one SM's bandwidth is enough.
+constexpr int kScanThreads = 1024;
+__global__ void __launch_bounds__(kScanThreads) k_scan_counts(int64_t n, const int32_t* __restrict__ cnt,
+                                                              int32_t* __restrict__ out) {
+  __shared__ int64_t part[kScanThreads];
+  const int t = threadIdx.x;
+  const int64_t chunk = (n + kScanThreads - 1) / kScanThreads;
+  const int64_t lo = std::min<int64_t>(n, (int64_t)t * chunk), hi = std::min<int64_t>(n, lo + chunk);
+  int64_t sum = 0;
+  for (int64_t i = lo; i < hi; ++i) sum += cnt[i];
+  part[t] = sum;
+  __syncthreads();
+  for (int off = 1; off < kScanThreads; off <<= 1) {
+    const int64_t v = t >= off ? part[t - off] : 0;
+    __syncthreads();
+    part[t] += v;
+    __syncthreads();
+  }
+  int64_t run = part[t] - sum;   // exclusive prefix of this chunk
+  for (int64_t i = lo; i < hi; ++i) {
+    out[i] = (int32_t)run;
+    run += cnt[i];
+  }
+  if (t == kScanThreads - 1) out[n] = (int32_t)part[t];
+}
+
 // Entries of one row of A^T arrive in arbitrary order; sort each row by its
-// column index (row of A) so the result is deterministic.
+// column index (row of A) so the result is deterministic.  Short rows (the
+// stencil case) by insertion sort, longer ones by heapsort (O(m log m)).
+__device__ void sift_down(int32_t* key, int64_t* val, int64_t root, int64_t len) {
+  for (;;) {
+    int64_t child = 2 * root + 1;
+    if (child >= len) return;
+    if (child + 1 < len && key[child + 1] > key[child]) ++child;
+    if (key[root] >= key[child]) return;
+    const int32_t k = key[root];
+    key[root] = key[child];
+    key[child] = k;
+    const int64_t v = val[root];
+    val[root] = val[child];
+    val[child] = v;
+    root = child;
+  }
+}
+
 __global__ void k_sort_rows(int64_t n, const int32_t* __restrict__ trp, int32_t* tcol, int64_t* tsrc) {
   for (int64_t r = gtid(); r < n; r += gstride()) {
-    const int64_t b = trp[r], e = trp[r + 1];
-    for (int64_t i = b + 1; i < e; ++i) {
-      const int32_t c = tcol[i];
-      const int64_t s = tsrc[i];
-      int64_t j = i - 1;
-      while (j >= b && tcol[j] > c) {
-        tcol[j + 1] = tcol[j];
-        tsrc[j + 1] = tsrc[j];
-        --j;
+    const int64_t b = trp[r], e = trp[r + 1], len = e - b;
+    if (len <= 32) {
+      for (int64_t i = b + 1; i < e; ++i) {
+        const int32_t c = tcol[i];
+        const int64_t s = tsrc[i];
+        int64_t j = i - 1;
+        while (j >= b && tcol[j] > c) {
+          tcol[j + 1] = tcol[j];
+          tsrc[j + 1] = tsrc[j];
+          --j;
+        }
+        tcol[j + 1] = c;
+        tsrc[j + 1] = s;
       }
-      tcol[j + 1] = c;
-      tsrc[j + 1] = s;
+    } else {
+      int32_t* key = tcol + b;
+      int64_t* val = tsrc + b;
+      for (int64_t i = len / 2 - 1; i >= 0; --i) sift_down(key, val, i, len);
+      for (int64_t end2 = len - 1; end2 > 0; --end2) {
+        const int32_t k = key[0];
+        key[0] = key[end2];
+        key[end2] = k;
+        const int64_t v = val[0];
+        val[0] = val[end2];
+        val[end2] = v;
+        sift_down(key, val, 0, end2);
+      }
     }
   }
 }
 
+namespace {
+// Device scratch freed on every return path.
+struct DeviceScratch {
+  void* p = nullptr;
+  ~DeviceScratch() {
+    if (p) cudaFree(p);
+  }
+};
+}  // namespace
+
 int csr_transpose(int64_t n, int64_t nnz, const int32_t* row_ptr, const int32_t* col,
                   int32_t* t_row_ptr, int32_t* t_col, int64_t* t_src, cudaStream_t s) {
   count_launches(4);
-  int32_t* cnt = nullptr;
-  RB_CUDA_TRY(cudaMalloc(&cnt, sizeof(int32_t) * (n + 1)));
+  DeviceScratch tmp;
+  RB_CUDA_TRY(cudaMalloc(&tmp.p, sizeof(int32_t) * (n + 1)));
+  int32_t* cnt = static_cast<int32_t*>(tmp.p);
   RB_CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (n + 1), s));
   if (nnz > 0) {
     int g = (int)std::min<int64_t>((nnz + kBlock - 1) / kBlock, 16384);
     k_col_count<<<g, kBlock, 0, s>>>(nnz, col, cnt);
+    RB_CUDA_TRY(cudaGetLastError());
   }
-  std::vector<int32_t> h(n + 1);
-  RB_CUDA_TRY(cudaMemcpyAsync(h.data(), cnt, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, s));
-  RB_CUDA_TRY(cudaStreamSynchronize(s));
-  std::vector<int32_t> trp(n + 1);
-  trp[0] = 0;
-  for (int64_t i = 0; i < n; ++i) trp[i + 1] = trp[i] + h[i];
-  RB_CUDA_TRY(cudaMemcpyAsync(t_row_ptr, trp.data(), sizeof(int32_t) * (n + 1),
-                              cudaMemcpyHostToDevice, s));
+  k_scan_counts<<<1, kScanThreads, 0, s>>>(n, cnt, t_row_ptr);
+  RB_CUDA_TRY(cudaGetLastError());
   RB_CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (n + 1), s));
   int g = (int)std::min<int64_t>((n + kBlock - 1) / kBlock + 1, 16384);
   k_scatter_t<<<g, kBlock, 0, s>>>(n, row_ptr, col, t_row_ptr, cnt, t_col, t_src);
+  RB_CUDA_TRY(cudaGetLastError());
   k_sort_rows<<<g, kBlock, 0, s>>>(n, t_row_ptr, t_col, t_src);
   RB_CUDA_TRY(cudaGetLastError());
   RB_CUDA_TRY(cudaStreamSynchronize(s));
-  cudaFree(cnt);
   return RB_OK;
 }
 

@@ -4,7 +4,7 @@
 // generic kernels; then the fused five-pass iteration, captured once per
 // handle as a CUDA graph of `poll` iterations and replayed until the device
 // convergence flags are set (every pass returns at once after they are set,
-// so the overshoot of the last replay costs only empty launches); then step 8
+// so the overshoot of the last replay costs only empty launches); then the final correction x - U x_c
 // (x = x - U x_c) and a true-residual check.  In the recycle-update modes the
 // graph spans one cycle of s iterations whose p, s, A p, A s vectors land in
 // a cycle store; between cycles the Gram matrices G = Z^T Z, H = Z^T W are
@@ -100,7 +100,7 @@ struct rb_ctx {
   SellBuf<float> A32;
   bool have_matrix = false;
   int matrix_epoch = 0, update_epoch = -1;
-  // Alg. 2 step 1 owed for the first setup_pending columns of U, U~ (-1:
+  // The recycle setup (Sec. 3) owed for the first setup_pending columns of U, U~ (-1:
   // none).  A new matrix or an adopted update only marks the setup; the next
   // solve runs it, so a setup that no solve would use is never computed.
   int setup_pending = -1;
@@ -423,7 +423,7 @@ int alloc_vectors(rb_ctx* h) {
 }
 
 // ------------------------------------------------------------ recycle setup
-// Alg. 2 step 1 for the columns currently in U, Ut (kin of them):
+// The recycle setup (Sec. 3, eq. (3.4)) for the columns currently in U, Ut (kin of them):
 // C = A U, C~ = A^T U~, SVD biorthogonalisation, C-hat = C~ D_c^{-1}.
 int recycle_setup(rb_ctx* h, int kin, int64_t* setup_mv) {
   PhaseClock pc;
@@ -498,7 +498,7 @@ int recycle_setup(rb_ctx* h, int kin, int64_t* setup_mv) {
   return kk < kin ? RB_WRECYCLE_RANK : RB_OK;
 }
 
-// Defer Alg. 2 step 1 for kin columns of U, U~ to the next solve.
+// Defer the recycle setup for kin columns of U, U~ to the next solve.
 void mark_setup(rb_ctx* h, int kin) {
   h->k = 0;
   reset_graphs(h);
@@ -658,7 +658,7 @@ double iter_bytes(rb_ctx* h, int k, size_t vb, size_t ab, int nrhs) {
   return shared / nrhs + n * vb * vec_streams;
 }
 
-// Setup of a blocked FP64 solve (Alg. 2 steps 2-4, eq. (3.5)) for slots
+// Setup of a blocked FP64 solve (the start of Alg. 2, eq. (3.5)) for slots
 // [0, nrhs): rhs[i], xb[i] are slot i's right-hand side and iterate; tol[i]
 // is relative to st[i].bnorm2 (set by the caller); skip[i] marks slots that
 // take no part and are marked done.  The shadow r~_{-1} (hence r~_0) is
@@ -731,7 +731,7 @@ bool all_done(rb_ctx* h, int nrhs) {
   return true;
 }
 
-// p_1 = r_0 for every slot (Alg. 2 step 4 with beta_0 = 0); slot 0 writes to
+// p_1 = r_0 for every slot (beta_0 = 0 before the first iteration); slot 0 writes to
 // the cycle store in update mode.
 template <typename T>
 int init_p(rb_ctx* h, int nrhs, bool cycle_slot0) {
@@ -893,7 +893,7 @@ int iterate_cycles(rb_ctx* h, int nrhs, SolveOut* so, const PollHook& hook = nul
   return run_update();
 }
 
-// Alg. 2 step 8 (x = x - U x_c) and the FP64 true residual of every slot.
+// The final correction of Alg. 2 (x = x - U x_c) and the FP64 true residual of every slot.
 int finish_block(rb_ctx* h, int nrhs, SolveOut* so) {
   const int64_t ld = h->npad;
   for (int i = 0; i < nrhs; ++i) {
@@ -907,7 +907,7 @@ int finish_block(rb_ctx* h, int nrhs, SolveOut* so) {
 }
 
 // U_next = Y (promoted to FP64 when the candidate is FP32), U~_next = U_next,
-// and Alg. 2 step 1 for the new space.
+// and the recycle setup for the new space.
 template <typename T>
 int adopt_candidate(rb_ctx* h, SolveOut* so) {
   const int64_t ld = h->npad;
@@ -981,7 +981,7 @@ int solve_fp64(rb_ctx* h, int nrhs, const bool* x_nonzero, SolveOut* so) {
 // recycle blocks, FP64-class dot products and FP64 scalars) with FP64
 // residual replacement ("reliable updates", Sleijpen and van der Vorst,
 // Computing 56, 1996).  The FP64 iterate x takes the FP32 correction
-// d = x_inner - U x_c (Alg. 2 step 8 of the inner solve) whenever the
+// d = x_inner - U x_c (the final correction of the inner solve) whenever the
 // recursive FP32 residual has fallen by kReplace since the last replacement
 // or reports convergence; the true residual b - A x is then formed in FP64
 // and, unless it meets the tolerance, replaces the recursive one while the
@@ -1704,7 +1704,7 @@ extern "C" int rbicg_solve(rb_handle h, const double* b, const double* bt, doubl
     RB_CUDA_TRY(gemv_update(P.x, h->U, ld, h->k, h->st[0].red, nullptr, 1.0, h->npad, vec_grid(h), h->us));
     RB_CUDA_TRY(gemv_update(P.r, h->C, ld, h->k, h->st[0].red, nullptr, -1.0, h->npad, vec_grid(h), h->us));
   }
-  // dual; step 3: a new x~_{-1} while (r_0, r~_0) = 0
+  // dual; a new x~_{-1} while (r_0, r~_0) = 0
   if ((rc = bicg_dual_start(h))) return done(rc);
   double red[3];
   so.seeds = 0;
@@ -1720,7 +1720,7 @@ extern "C" int rbicg_solve(rb_handle h, const double* b, const double* bt, doubl
     so.seeds = attempt + 1;
     if ((rc = bicg_dual_start(h))) return done(rc);
   }
-  // step 4 (p_0 = 0, beta_0 = 0): the first iteration's p_1 = r_0
+  // p_0 = 0, beta_0 = 0: the first iteration's p_1 = r_0
   RB_CUDA_TRY(cudaMemcpyAsync(P.p, P.r, sizeof(double) * ld, cudaMemcpyDeviceToDevice, h->us));
   RB_CUDA_TRY(cudaMemcpyAsync(D.p, D.r, sizeof(double) * ld, cudaMemcpyDeviceToDevice, h->us));
   if ((rc = read_state(h, 2))) return done(rc);
@@ -1752,7 +1752,7 @@ extern "C" int rbicg_solve(rb_handle h, const double* b, const double* bt, doubl
     h0.done = 1;
   }
   RB_CUDA_TRY(cudaMemcpyAsync(h->st, h->hst, sizeof(IterState) * 2, cudaMemcpyHostToDevice, h->us));
-  // step 5: graphs of poll iterations until both systems converge or the solve stops
+  // the iteration: graphs of poll iterations until both systems converge or the solve stops
   if (!h0.done) {
     if (!h->g_bicg.valid || h->g_bicg_k != h->k) {
       if ((rc = capture_bicg(h))) return done(rc);
@@ -1764,7 +1764,7 @@ extern "C" int rbicg_solve(rb_handle h, const double* b, const double* bt, doubl
       if (h->hst[0].done) break;
     }
   }
-  // step 7 and the true residuals
+  // the final correction and the true residuals
   if (h->k > 0) {
     RB_CUDA_TRY(gemv_update(P.x, h->U, ld, h->k, h->st[0].xc, nullptr, -1.0, h->npad, vec_grid(h), h->us));
     RB_CUDA_TRY(gemv_update(D.x, h->Ut, ld, h->k, h->st[1].xc, nullptr, -1.0, h->npad, vec_grid(h), h->us));

@@ -354,12 +354,39 @@ def residual_noalloc(row_ptr, col, val, x, b, r, rnorm2, stream=None, n=None) ->
     For callers that cannot allocate device memory: every argument is a CUDA
     tensor the caller owns (int32 row_ptr/col, float64 val/x/b/r, a
     one-element float64 rnorm2); the library allocates nothing.  Ordered on
-    ``stream`` (default: the legacy default stream), not synchronised."""
-    args = [t.data_ptr() for t in (row_ptr, col, val, x, b, r, rnorm2)]
-    for t in (row_ptr, col, val, x, b, r, rnorm2):
+    ``stream`` (default: the legacy default stream), not synchronised.
+
+    Every argument is checked before a pointer is taken (type, device,
+    contiguity, dtype and length); a bad one raises RbError(RB_EINVAL)."""
+    tensors = (row_ptr, col, val, x, b, r, rnorm2)
+    einval = C["RB_EINVAL"]
+    for t in tensors:
         if not (_is_torch(t) and t.is_cuda and t.is_contiguous()):
-            raise ValueError("residual_noalloc takes contiguous CUDA tensors")
+            raise RbError(einval, "residual_noalloc takes contiguous CUDA tensors")
+    import torch
+    dev = row_ptr.device
+    if any(t.device != dev for t in tensors):
+        raise RbError(einval, "residual_noalloc: all tensors on one device")
+    for t, dt, name in ((row_ptr, torch.int32, "row_ptr"), (col, torch.int32, "col"),
+                        (val, torch.float64, "val"), (x, torch.float64, "x"),
+                        (b, torch.float64, "b"), (r, torch.float64, "r"),
+                        (rnorm2, torch.float64, "rnorm2")):
+        if t.dtype != dt:
+            raise RbError(einval, f"residual_noalloc: {name} must be {dt}")
     nn = (row_ptr.numel() - 1) if n is None else int(n)
+    if nn < 0 or row_ptr.numel() < nn + 1:
+        raise RbError(einval, "residual_noalloc: row_ptr needs n + 1 entries")
+    if col.numel() != val.numel():
+        raise RbError(einval, "residual_noalloc: col and val differ in length")
+    if min(x.numel(), b.numel(), r.numel()) < nn:
+        raise RbError(einval, "residual_noalloc: x, b and r need n entries")
+    if rnorm2.numel() < 1:
+        raise RbError(einval, "residual_noalloc: rnorm2 needs one entry")
+    if nn > 0:
+        nnz = int(row_ptr[nn].item())
+        if nnz > col.numel():
+            raise RbError(einval, "residual_noalloc: row_ptr[n] exceeds the length of col and val")
+    args = [t.data_ptr() for t in tensors]
     sp = None if stream is None else (stream if isinstance(stream, int) else stream.cuda_stream)
     return _check(lib().rbicgstab_residual_noalloc(nn, *args, sp), "rbicgstab_residual_noalloc")
 

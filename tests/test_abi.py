@@ -1,7 +1,7 @@
 """C-ABI checks that need no GPU: the library loads, exports every entry point
 declared in include/rbicgstab.h, its host-only harmonic-Ritz step agrees
 with the oracle's (a different algorithm on the same pencil), and its host
-SVD (the biorthogonalisation of Alg. 2 step 1) is a valid SVD with the
+SVD (the biorthogonalisation of the recycle setup, Sec. 3) is a valid SVD with the
 singular values LAPACK computes."""
 import ctypes
 import os
@@ -192,3 +192,14 @@ def test_host_harmonic_ritz_defective_block(L):
     y_all, th_all = rb.harmonic_ritz(np.eye(m), H, m)
     want = np.sort(1.0 / np.diag(J))
     assert np.abs(np.sort(np.real(th_all)) - want).max() <= 1e-6
+
+
+def test_noalloc_wrapper_rejects_host_arrays(L):
+    """The allocation-free residual wrapper checks its arguments before it
+    takes any pointer: host arrays raise RbError(RB_EINVAL)."""
+    rp = np.array([0, 1], dtype=np.int32)
+    col = np.array([0], dtype=np.int32)
+    v = np.ones(1)
+    with pytest.raises(rb.RbError) as e:
+        rb.residual_noalloc(rp, col, v, v, v, v.copy(), np.zeros(1))
+    assert e.value.code == rb.C["RB_EINVAL"]

@@ -150,7 +150,7 @@ def test_two_sided_random_space_early_iterates(j):
     """Independent Gaussian U and U~ give a strongly oblique projector
     C C-hat^T (norm ~1e3 here) that amplifies rounding from one iteration to
     the next in any implementation, so only the first iterates are compared:
-    x_j (both solvers stopped by max_itn = j, step 8 applied) must agree to
+    x_j (both solvers stopped by max_itn = j, final correction x - U x_c applied) must agree to
     within a bound that grows with j from the first iterate's 1e-12."""
     A = inputs.conv_diff_2d(64, 15.0)
     b = inputs.gaussian_rhs(A.n, 1)

@@ -2,7 +2,7 @@
 the dual A^T x~ = b~ against the FP64 oracle's Alg. 1 (same starts, same
 recycle space), at ragged sizes (n not a multiple of the 32-row slice):
 iterations within 5%, both solutions within 1e-7, the iterates after exactly
-j iterations, the step-3 redraw, the shadow dual right-hand side, initial
+j iterations, the redraw of x~_{-1} when (r_0, r~_0) = 0, the shadow dual right-hand side, initial
 guesses, and exact deflation."""
 import numpy as np
 import pytest
@@ -69,7 +69,7 @@ def test_rbicg_parity(k):
 
 @pytest.mark.parametrize("j", [1, 5, 20])
 def test_rbicg_truncated_iterates_track_oracle(j):
-    """x_j and x~_j (after step 7) after exactly j iterations, k = 8."""
+    """x_j and x~_j (after the final correction) after exactly j iterations, k = 8."""
     A = inputs.conv_diff_2d(40, 12.0)
     S = A.to_scipy()
     b = inputs.gaussian_rhs(A.n, 1)

@@ -160,7 +160,7 @@ def test_residual_identity_pins_step8_sign():
 
 
 def test_planted_sign_error_in_step8_is_caught():
-    """Flip the sign of step 8 in a copy of the result; the identity must fail."""
+    """Flip the sign of the final correction x - U x_c in a copy of the result; the identity must fail."""
     A, b, rec, x, info = _recycled_run()
     xi, xci, ri = info.iterates[-1]
     wrong = b - A @ (xi + rec.U @ xci)

@@ -1,6 +1,6 @@
 """Pins of the Alg. 1 (RBiCG) oracle against what the paper and the
 mathematics fix: the solutions of the primary and dual systems (dense LU),
-the residual identity of step 7 for both systems, the bi-orthogonality of
+the residual identity of the final correction for both systems, the bi-orthogonality of
 the BiCG residuals (the bi-Lanczos relations of Sec. 2), the orthogonality
 of the residuals to the recycle space (Sec. 3), the reduction to CG for a
 symmetric positive definite matrix with b~ = b and k = 0 (a library
@@ -43,7 +43,7 @@ def test_rbicg_solves_primary_and_dual(k):
 @pytest.mark.parametrize("k", [0, 6])
 def test_rbicg_residual_identity_of_step7(k):
     """b - A (x_i - U zeta_c) = r_i and b~ - A^T (x~_i - U~ zeta~_c) = r~_i at
-    every iterate: pins the signs of steps 5 and 7 in both columns."""
+    every iterate: pins the signs of the updates and of the final correction in both columns."""
     A, b, bt, rec = _problem(k=k)
     U = rec.U if rec else np.zeros((A.shape[0], 0))
     Ut = rec.Ut if rec else U
@@ -117,7 +117,7 @@ def test_rbicg_exact_deflation_terminates_after_n_minus_k():
 
 def test_rbicg_redraws_the_dual_start_when_rho_is_zero():
     """(r_0, r~_0) = 0 exactly (b and b~ with disjoint supports, x~_{-1} = 0):
-    step 3 takes a new x~_{-1}; the dual system is still solved."""
+    Alg. 1 takes a new x~_{-1}; the dual system is still solved."""
     A, b, _, _ = _problem()
     n = A.shape[0]
     bt = inputs.gaussian_rhs(n, 77)

@@ -70,3 +70,30 @@ def test_noalloc_rejects_bad_sizes(torch):
         with pytest.raises(rb.RbError) as e:
             rb.residual_noalloc(zi, zi, z, z, z, z, one, n=bad_n)
         assert e.value.code == rb.C["RB_EINVAL"]
+
+
+def test_noalloc_rejects_bad_arguments(torch):
+    """Wrong dtypes and short buffers are refused on the host, before any
+    pointer reaches the kernel."""
+    A = inputs.conv_diff_2d(12, 5.0)
+    dev = torch.device("cuda:0")
+    rp = torch.from_numpy(A.row_ptr).to(dev)
+    col = torch.from_numpy(A.col).to(dev)
+    val = torch.from_numpy(A.val).to(dev)
+    x = torch.ones(A.n, dtype=torch.float64, device=dev)
+    b = torch.ones(A.n, dtype=torch.float64, device=dev)
+    r = torch.empty(A.n, dtype=torch.float64, device=dev)
+    nrm = torch.empty(1, dtype=torch.float64, device=dev)
+    bad = [
+        (rp.long(), col, val, x, b, r, nrm),
+        (rp, col, val.float(), x, b, r, nrm),
+        (rp, col, val, x[:-1], b, r, nrm),
+        (rp, col, val, x, b, r[:-1], nrm),
+        (rp, col[:-1], val, x, b, r, nrm),
+        (rp, col, val, x, b, r, nrm[:0]),
+    ]
+    for args in bad:
+        with pytest.raises(rb.RbError) as e:
+            rb.residual_noalloc(*args)
+        assert e.value.code == rb.C["RB_EINVAL"]
+    assert rb.residual_noalloc(rp, col, val, x, b, r, nrm) == rb.RB_OK
