@@ -52,6 +52,9 @@ def parse():
     ap.add_argument("--no-plain", action="store_true", help="skip the plain-BiCGSTAB comparison")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-accuracy", action="store_true",
+                    help="skip the sampled error against the oracle's tight reference")
+    ap.add_argument("--no-small", action="store_true", help="skip the small 2D sequence")
     ap.add_argument("--quick", action="store_true", help="small grid for a smoke run (not a bench line)")
     ap.add_argument("--rbicg", action="store_true",
                     help="time Alg. 1 (RBiCG, primary + dual, FP64) on system 1 instead of the sequence")
@@ -204,6 +207,63 @@ def cpu_oracle_timing(N, shifts, k, its=10) -> dict:
     return json.loads(out.stdout.strip().splitlines()[-1])
 
 
+def host_cpu() -> dict:
+    """Cores and CPU model of this host (the oracle baseline's machine)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if model is None:
+        try:
+            for line in open("/proc/cpuinfo"):
+                if line.lower().startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except Exception:
+            pass
+    return {"nproc": os.cpu_count(), "model": model or "unknown"}
+
+
+def xstar_worker(N, shifts, j, kk, q):
+    """Oracle side of the accuracy sample (runs in a spawned process while the
+    GPU arms run): for system j, right-hand side kk of the sequence, the FP64
+    oracle's plain BiCGSTAB answer at tol 1e-8 and a tight reference x* (the
+    oracle continued from that answer to 1e-12)."""
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
+    try:
+        import numpy as np
+        import scipy.sparse as sp
+
+        from oracle import rbicgstab as orb
+        from paper_1406_2831_gb300 import inputs
+        spec = inputs.config_shifted_3d(N=N, n_shifts=shifts, n_rhs=kk + 1)
+        P = spec.pattern
+        S = sp.csr_matrix((spec.values[j](), P.col, P.row_ptr), shape=(P.n, P.n))
+        b = spec.rhs[j][kk]()
+        t0 = time.perf_counter()
+        xo, io = orb.rbicgstab(S, b, None, tol=1e-8)
+        xs, iss = orb.rbicgstab(S, b, None, x_m1=xo, tol=1e-12)
+        q.put({"xo": xo, "xs": xs, "iters_o": io.iters, "relres_xs": iss.relres_true,
+               "status": iss.status, "seconds": time.perf_counter() - t0})
+    except Exception as e:  # reported in the line, never fatal
+        q.put({"error": repr(e)[:300]})
+
+
+def start_xstar(N, shifts, j, kk):
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    proc = ctx.Process(target=xstar_worker, args=(N, shifts, j, kk, q), daemon=True)
+    proc.start()
+    return proc, q
+
+
 # ---------------------------------------------------------------- multi-rank helpers
 def max_over_ranks(value, dist, device):
     """The largest of every rank's value (a job takes its slowest rank's time);
@@ -329,6 +389,84 @@ def run_rbicg(args):
                                   "frac": round(tfl / fp64, 4), "flops_per_iter": fl}}}
 
 
+def arm_summary(v, logs, steps, blk) -> dict:
+    its = [l["iters"] for l in logs]
+    mv = sum(l["matvecs"] for l in logs)
+    return {"solves_per_s": round(v, 3), "rhs_block": blk, "steps": steps,
+            "iters_mean": round(statistics.mean(its), 2), "matvecs": int(mv),
+            "matvecs_per_solve": round(mv / max(1, len(logs)), 1),
+            "matvecs_setup": int(sum(l["matvecs_setup"] for l in logs))}
+
+
+def accuracy_sample(xstar, cap, j, kk) -> dict:
+    """Error of one sampled GPU solution against the oracle's tight x*, next
+    to the error of the oracle's own FP64 answer at tol 1e-8."""
+    import numpy as np
+    proc, q = xstar
+    out = {"sample": f"system {j + 1}, right-hand side {kk + 1} (last untimed pass of the sequence)"}
+    try:
+        r = q.get(timeout=900)
+    except Exception as e:
+        out["error"] = f"oracle reference not ready: {e!r}"[:200]
+        return out
+    proc.join(timeout=10)
+    if "error" in r:
+        out["error"] = r["error"]
+        return out
+    xs, xo = r["xs"], r["xo"]
+    nx = float(np.linalg.norm(xs))
+    if cap[2]:
+        xg, st = cap[2][0]
+        out["gpu_err_vs_xstar"] = float(np.linalg.norm(xg - xs) / nx)
+        out["gpu_relres_true"] = st["relres_true"]
+    out["oracle_fp64_tol1e-8_err_vs_xstar"] = float(np.linalg.norm(xo - xs) / nx)
+    out["xstar"] = f"oracle BiCGSTAB continued from its tol 1e-8 answer to tol 1e-12 (true relres {r['relres_xs']:.2e})"
+    return out
+
+
+def small_2d(rb, torch, dev, stream) -> dict:
+    """The 64 x 64 2D sequence (8 systems, p = 10..17, one right-hand side
+    each, k = 8, FP64), recycled with the update and plain: solves/s and
+    microseconds per iteration.  The whole problem sits in L2."""
+    from paper_1406_2831_gb300 import inputs
+    spec = inputs.config_small_2d(64)
+    P = spec.pattern
+    rp = torch.from_numpy(P.row_ptr).to(dev)
+    col = torch.from_numpy(P.col).to(dev)
+    vals = [torch.from_numpy(v() if callable(v) else v).to(dev) for v in spec.values]
+    rhs = [[torch.from_numpy(g() if callable(g) else g).to(dev) for g in row] for row in spec.rhs]
+    x = torch.zeros(P.n, dtype=torch.float64, device=dev)
+    out = {"workload": f"2d-5pt-conv-diff-64^2, {len(vals)} systems, k = {spec.k}, FP64"}
+    for label, k in (("recycled", spec.k), ("plain", 0)):
+        s = rb.Solver(k_max=k, cycle_s=spec.cycle_s, recycle="update_first" if k else "none",
+                      tol=spec.tol, stream=stream)
+        s.set_matrix(rp, col, vals[0])
+        its, reps = 0, 5
+        for rep in range(reps + 2):
+            if rep == 2:
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                its = 0
+            if k:
+                s.set_recycle(None)
+            for j, v in enumerate(vals):
+                s.set_values(v)
+                for b in rhs[j]:
+                    x.zero_()
+                    r = s.solve(b, x)
+                    its += r.stats["iters"]
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        nsolve = reps * sum(len(r_) for r_ in rhs)
+        out[label] = {"solves_per_s": round(nsolve / (ms * 1e-3), 2), "iters_per_solve": round(its / nsolve, 1),
+                      "us_per_iteration": round(1e3 * ms / its, 2),
+                      "note": "whole solve time (setup, update, true residual) per iteration"}
+        del s
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -339,6 +477,12 @@ def run_ours(args):
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
+    N = 48 if args.quick else args.N
+    # accuracy sample: system 2 of the sequence (the first solved with an
+    # updated recycle space), right-hand side 1; the oracle works on it in a
+    # spawned process (started before any CUDA call) while the GPU runs
+    acc_j, acc_k = (1, 0) if args.shifts > 1 else (0, 0)
+    xstar = start_xstar(N, args.shifts, acc_j, acc_k) if (rank == 0 and not args.no_accuracy) else None
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     dist = None
@@ -346,7 +490,6 @@ def run_ours(args):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
 
-    N = 48 if args.quick else args.N
     spec = inputs.config_shifted_3d(N=N, n_shifts=args.shifts, n_rhs=args.rhs, k=args.k)
     P = spec.pattern
     n, z = P.n, P.nnz
@@ -376,7 +519,7 @@ def run_ours(args):
         s.set_matrix(rp, col, vals_d[0])
         return s
 
-    def sequence(s, recycled: bool, host: bool, log=None, block=1):
+    def sequence(s, recycled: bool, host: bool, log=None, block=1, capture=None):
         if recycled:
             s.set_recycle(None)
         for j in range(len(vals_d)):
@@ -386,6 +529,9 @@ def run_ours(args):
                     X = (xhb if host else xbufb)[: B.shape[0]]
                     X.zero_()
                     r = s.solve_block(B, X)
+                    if capture is not None and capture[0] == j and chunks[j][kk][0] <= capture[1] < chunks[j][kk][1]:
+                        capture[2].append((X[capture[1] - chunks[j][kk][0]].cpu().numpy().copy(),
+                                           r.stats[capture[1] - chunks[j][kk][0]]))
                     for ib, st in enumerate(r.stats):
                         if st["status"] != 0:
                             raise RuntimeError(f"block {j},{kk} failed: {st}")
@@ -405,6 +551,8 @@ def run_ours(args):
                     log.append(r.stats)
                 if r.stats["status"] != 0:
                     raise RuntimeError(f"solve {j},{kk} failed: {r.stats}")
+                if capture is not None and capture[:2] == (j, kk):
+                    capture[2].append(((xh if host else xbuf).cpu().numpy().copy(), r.stats))
 
     def barrier():
         if dist is not None:
@@ -445,8 +593,13 @@ def run_ours(args):
     vb = 8 if args.precision == "fp64" else 4
     pb = pass_bytes(n, z, k_used, vb=vb, ab=vb, R=R0)
     pf = pass_flops(n, z, k_used, R=R0)
+    # one more (untimed) pass of the sequence that keeps the sampled solution
+    acc_cap = [acc_j, acc_k, []]
+    if xstar is not None:
+        sequence(s_rec, True, False, block=blk, capture=acc_cap)
     del s_rec
-    # plain FP64 BiCGSTAB on the same sequence: one system at a time, and blocked
+    # the comparison arms on the same sequence: plain FP64 one system at a
+    # time and blocked, recycled FP64 blocked, plain mixed blocked
     if not args.no_plain:
         ps = max(1, args.steps // 2)
         s_pl = make(False, "fp64")
@@ -457,6 +610,21 @@ def run_ours(args):
             msb, logb, _, _ = timed(s_pl, False, False, ps, 1, block=blk)
             res["plain_block"] = dict(ms=msb, logs=logb, steps=ps)
         del s_pl
+        if blk > 1:
+            cs = max(1, args.steps // 4)
+            other = "fp64" if args.precision == "mixed" else "mixed"
+            s_o = make(True, other)
+            mso, logo, _, _ = timed(s_o, True, False, cs, 1, block=blk)
+            res["rec_other"] = dict(ms=mso, logs=logo, steps=cs, precision=other)
+            del s_o
+            s_pm = make(False, "mixed")
+            mspm, logpm, _, _ = timed(s_pm, False, False, cs, 1, block=blk)
+            res["plain_mixed_block"] = dict(ms=mspm, logs=logpm, steps=cs)
+            del s_pm
+    # the small 2D sequence (8 systems p = 10..17, n = 4096, k = 8): L2-resident,
+    # reported as time per iteration
+    if not args.no_small:
+        res["small"] = small_2d(rb, torch, dev, stream)
     # end to end through the public API with pinned host buffers
     if not args.no_e2e:
         s_e = make(True, args.precision)
@@ -522,9 +690,25 @@ def run_ours(args):
         if "plain_block" in res:
             lb = res["plain_block"]["logs"]
             vpb = job_throughput(solves_per_step, res["plain_block"]["steps"], world, res["plain_block"]["ms"])
-            line["plain_fp64_blocked"] = {"solves_per_s": round(vpb, 3), "rhs_block": blk,
-                                          "iters_mean": round(statistics.mean(l["iters"] for l in lb), 2)}
+            line["plain_fp64_blocked"] = arm_summary(vpb, lb, res["plain_block"]["steps"], blk)
             line["recycled_over_plain_blocked"] = round(value / vpb, 4)
+        if "rec_other" in res:
+            ro = res["rec_other"]
+            vro = job_throughput(solves_per_step, ro["steps"], world, ro["ms"])
+            line[f"recycled_{ro['precision']}_blocked"] = arm_summary(vro, ro["logs"], ro["steps"], blk)
+        if "plain_mixed_block" in res:
+            pm = res["plain_mixed_block"]
+            vpm = job_throughput(solves_per_step, pm["steps"], world, pm["ms"])
+            line["plain_mixed_blocked"] = arm_summary(vpm, pm["logs"], pm["steps"], blk)
+    line["recycled"]["matvecs_per_solve"] = round(line["recycled"]["matvecs"] / max(1, len(logs)), 1)
+    rr = [l["relres_true"] for l in logs]
+    acc = {"relres_true_max": max(rr), "relres_true_mean": statistics.mean(rr),
+           "note": "FP64 true residual ||b - A x|| / ||b|| of every timed solve"}
+    if xstar is not None:
+        acc.update(accuracy_sample(xstar, acc_cap, acc_j, acc_k))
+    line["accuracy"] = acc
+    if "small" in res:
+        line["small_2d"] = res["small"]
     if "e2e" in res:
         Bi = (len(vals_h) * z * 8 + solves_per_step * n * 8) * 1 + solves_per_step * n * 8
         Bo = solves_per_step * n * 8
@@ -536,13 +720,14 @@ def run_ours(args):
             mean_it = statistics.mean(iters)
             v = 1.0 / (cb["t_iter"] * mean_it + cb["t_setup"] / args.rhs)
             line["cpu_baseline"] = {"value": round(v, 5), "unit": "solves/s", "cores": 1, "kind": "oracle",
+                                    "host": host_cpu(),
                                     "sample": f"oracle Alg. 2 (k={args.k}, fixed recycle space) on system 1 "
                                               f"of the sequence at full size: setup + 10 iterations timed, "
                                               f"extrapolated to {mean_it:.1f} iterations per solve "
                                               f"(the GPU run's mean); recycle-update cost not included"}
         except Exception as e:  # report, do not fail the bench line
             line["cpu_baseline"] = {"value": None, "unit": "solves/s", "cores": 1, "kind": "oracle",
-                                    "sample": f"failed: {str(e)[:200]}"}
+                                    "host": host_cpu(), "sample": f"failed: {str(e)[:200]}"}
     if dist is not None:
         dist.destroy_process_group()
     return line
@@ -580,9 +765,13 @@ def run_reference(args):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(1e3 * (t_it * its + t_setup), 3), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": sequence_config(N, samples[0]["n"], samples[0]["nnz"], args, samples[0]["cycle_s"],
-                                      samples[0]["tol"], args.gpus),
+            "config": dict(sequence_config(N, samples[0]["n"], samples[0]["nnz"], args, samples[0]["cycle_s"],
+                                           samples[0]["tol"], args.gpus),
+                           precision="fp64", rhs_block=1,
+                           recycle=f"fixed random right-only space, k = {args.k}, no update (a per-solve "
+                                   f"cost sample of the same sequence)"),
             "cpu_baseline": {"value": round(value, 5), "unit": "solves/s", "cores": 1, "kind": "oracle",
+                             "host": host_cpu(),
                              "sample": f"per step: oracle Alg. 2 (k={args.k}) setup + {its} iterations on "
                                        f"system 1 at full size, extrapolated to {it_src}"},
             "e2e": {"value": round(value, 5), "unit": "solves/s", "h2d_bytes_per_step": 0,

@@ -246,15 +246,63 @@ def test_time_passes_block(precision):
     assert np.all(ms > 0)
 
 
-def test_block_mixed_full_size_properties():
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("grid", ["2d-45", "3d-13"])
+def test_block_benchmark_kernels_small(precision, grid):
+    """The benchmark's kernel configuration at sizes dense LU can check:
+    k = 20 (the 24-column kernel bucket), a block of R = 4 right-hand sides,
+    ragged n (2025 = 63 slices + 9 rows; 2197 = 68 slices + 21 rows).  Every
+    slot's solution is as close to the exact one (dense LU) as the FP64
+    oracle's answer with the same space (within 2x), or within 1e-7.  FP64
+    slots also track the oracle's own solve: iterations within 5%, x within
+    1e-7."""
+    import scipy.linalg as sla
+    if grid == "2d-45":
+        A = inputs.conv_diff_2d(45, 15.0)
+    else:
+        spec = inputs.config_shifted_3d(N=13, n_shifts=5, n_rhs=1, k=20)
+        P = spec.pattern
+        A = inputs.CSR(P.n, P.row_ptr, P.col, spec.values[2]())
+    S = A.to_scipy()
+    D = S.toarray()
+    U = inputs.random_recycle_basis(A.n, 20, 23)
+    B = _rhs_block(A.n, 4, seed0=60)
+    s = _solver(A, precision=precision, recycle="fixed", k_max=20, tol=1e-8)
+    s.set_recycle(U)
+    res = s.solve_block(B)
+    rec = orb.recycle_setup(S, U)
+    for i in range(4):
+        st = res.stats[i]
+        assert st["status"] == rb.RB_OK, st
+        assert st["k_used"] == 20
+        assert np.linalg.norm(B[i] - S @ res.x[i]) / np.linalg.norm(B[i]) <= 1e-8
+        xstar = sla.solve(D, B[i])
+        xo, io = orb.rbicgstab(S, B[i], rec, tol=1e-8)
+        assert _rel(res.x[i], xstar) <= max(2.0 * _rel(xo, xstar), 1e-7), (i, _rel(res.x[i], xstar), _rel(xo, xstar))
+        if precision == "fp64":
+            assert _iters_close(st["iters"], io.iters), (i, st["iters"], io.iters)
+            assert _rel(res.x[i], xo) <= XTOL
+
+
+def _tight_reference(S, b, rec, x_start):
+    """x* for the full-size checks: the oracle continued from its own
+    tol = 1e-8 answer down to ||b - A x|| <= 1e-12 ||b||."""
+    xs, info = orb.rbicgstab(S, b, rec, x_m1=x_start, tol=1e-12)
+    assert info.status == orb.OK and info.relres_true <= 2e-12, (info.status, info.relres_true)
+    return xs
+
+
+@pytest.mark.slow
+def test_block_mixed_full_size_against_tight_reference():
     """System 1 of the 128^3 shifted sequence at full size (n = 2,097,152):
     its four right-hand sides as one block in the mixed path with a fixed
-    k = 20 right-only space, the kernel configuration the benchmark times.
-    Checked by properties that hold at any size: every system's FP64 true
-    residual; the first system's solution against the FP64 oracle's solve
-    with the same space (both meet the tolerance, so they agree to the
-    conditioning of the system); and the iteration count against the
-    oracle's (FP32 arithmetic costs iterations, never fewer than half)."""
+    k = 20 right-only space, the kernel configuration the benchmark times
+    (FP32 passes, 24-column bucket, R = 4).  Every system meets the FP64
+    tolerance on its true residual.  The first system's solution is compared
+    with a tight reference x* (the oracle continued to 1e-12): it must be as
+    close to x* as the oracle's own tol = 1e-8 answer with the same space
+    (within 2x), or within 1e-7.  FP32 arithmetic costs iterations: the
+    count stays within [0.9, 1.6]x the oracle's (measured ratio ~1.3)."""
     import scipy.sparse as sp
     spec = inputs.config_shifted_3d(N=128, n_shifts=20, n_rhs=4, k=20)
     P = spec.pattern
@@ -269,6 +317,11 @@ def test_block_mixed_full_size_properties():
     for i in range(4):
         assert res.stats[i]["status"] == rb.RB_OK
         assert np.linalg.norm(B[i] - S @ res.x[i]) / np.linalg.norm(B[i]) <= 1e-8
-    xo, io = orb.rbicgstab(S, B[0], orb.recycle_setup(S, U), tol=1e-8)
-    assert _rel(res.x[0], xo) <= 1e-5, _rel(res.x[0], xo)
-    assert 0.5 * io.iters <= res.stats[0]["iters"] <= 2.0 * io.iters, (res.stats[0]["iters"], io.iters)
+    rec = orb.recycle_setup(S, U)
+    xo, io = orb.rbicgstab(S, B[0], rec, tol=1e-8)
+    xs = _tight_reference(S, B[0], rec, xo)
+    e_gpu, e_ora = _rel(res.x[0], xs), _rel(xo, xs)
+    print(f"mixed 128^3: |x-x*|/|x*| gpu {e_gpu:.3e} oracle(1e-8) {e_ora:.3e}; "
+          f"iters gpu {res.stats[0]['iters']} oracle {io.iters}")
+    assert e_gpu <= max(2.0 * e_ora, 1e-7), (e_gpu, e_ora)
+    assert 0.9 * io.iters <= res.stats[0]["iters"] <= 1.6 * io.iters, (res.stats[0]["iters"], io.iters)

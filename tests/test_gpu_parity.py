@@ -145,7 +145,7 @@ def test_recycled_fixed_parity(N, k):
     assert np.abs(off).max() <= 1e-10 * np.abs(np.diag(M)).max()
 
 
-@pytest.mark.parametrize("j", [1, 2, 5, 10])
+@pytest.mark.parametrize("j", [1, 2, 5])
 def test_two_sided_random_space_early_iterates(j):
     """Independent Gaussian U and U~ give a strongly oblique projector
     C C-hat^T (norm ~1e3 here) that amplifies rounding from one iteration to
@@ -162,7 +162,7 @@ def test_two_sided_random_space_early_iterates(j):
     S = A.to_scipy()
     xo, io = orb.rbicgstab(S, b, orb.recycle_setup(S, U, Ut), tol=1e-8, max_itn=j)
     assert res.stats["iters"] == io.iters == j
-    bound = {1: 1e-12, 2: 1e-10, 5: 1e-5, 10: 1.0}[j]
+    bound = {1: 1e-12, 2: 1e-10, 5: 1e-5}[j]
     assert _rel(res.x, xo) <= bound
 
 
@@ -223,8 +223,11 @@ def test_sequence_update_first_parity():
     each later recycle space comes out of an ill-conditioned harmonic-Ritz
     problem on Krylov vectors (a 1e-15 perturbation of G, H moves U by ~1e-7),
     so U is compared by principal angles (<= 1e-5) and every later solve by
-    iteration count (10% or 3 per solve, 5% over the sequence) and solution
-    (<= 1e-7)."""
+    iteration count and solution (<= 1e-7 or the conditioning bound).  The
+    per-solve count bound is the oracle's own measured spread: with G and H
+    perturbed by 1e-15 (relative, 16 trials) its later solves took 46-53
+    iterations against 46-49 unperturbed, a spread of 7; so each solve is
+    within max(8, 15%), and the sequence total within 5%."""
     spec = inputs.config_small_2d(N=32)
     mats = _seq_mats(spec)
     ref = orc.solve_sequence(mats, spec.rhs, k=spec.k, cycle_s=spec.cycle_s, tol=spec.tol, policy="first")
@@ -245,7 +248,7 @@ def test_sequence_update_first_parity():
     assert got_iters[0] == ref.iters[0]
     assert _rel(xs[0], ref.x[0]) <= 1e-10
     for gi, oi in zip(got_iters, ref.iters):
-        assert abs(gi - oi) <= max(3, int(0.1 * oi)), (got_iters, ref.iters)
+        assert abs(gi - oi) <= max(8, int(0.15 * oi)), (got_iters, ref.iters)
     assert abs(sum(got_iters) - sum(ref.iters)) <= 0.05 * sum(ref.iters)
     # two solutions that both meet the tolerance differ by at most
     # ||A^-1|| (||r_gpu|| + ||r_oracle||); the paths share the first solve
@@ -396,13 +399,14 @@ def test_empty_rows_apply():
 
 # ---------------------------------------------------------------- full size (128^3)
 @pytest.mark.slow
-def test_full_size_shifted_3d_properties():
-    """System 1 of the 128^3 shifted sequence at full size (n = 2,097,152).
-    At this size rounding moves even the oracle's iteration count between
-    orderings and machines (284-299) and its solutions by ~1e-6, so the
-    checks are properties that hold at any size: the FP64 true residual of
-    the GPU solution, the iteration count within 15% of the oracle's, the
-    iterate after exactly j iterations, and SpMV rows computed one by one."""
+def test_full_size_shifted_3d_against_tight_reference():
+    """System 1 of the 128^3 shifted sequence at full size (n = 2,097,152),
+    plain FP64.  The GPU solution is compared with a tight reference x* (the
+    oracle continued from its own 1e-8 answer to 1e-12): it must be as close
+    to x* as the oracle's tol = 1e-8 answer (within 2x), or within 1e-7, and
+    take a number of iterations within 5% of the oracle's.  Then the
+    iterate after exactly j iterations, plain and with a k = 20 space, and
+    SpMV rows computed one by one from the CSR definition."""
     spec = inputs.config_shifted_3d(N=128, n_shifts=20, n_rhs=1)
     P = spec.pattern
     vals = spec.values[0]()
@@ -414,7 +418,13 @@ def test_full_size_shifted_3d_properties():
     assert res.stats["status"] == rb.RB_OK
     assert np.linalg.norm(b - S @ res.x) / np.linalg.norm(b) <= 1.5e-8
     xo, io = orb.rbicgstab(S, b, None, tol=1e-8)
-    assert abs(res.stats["iters"] - io.iters) <= 0.15 * io.iters, (res.stats["iters"], io.iters)
+    xs, info = orb.rbicgstab(S, b, None, x_m1=xo, tol=1e-12)
+    assert info.status == orb.OK and info.relres_true <= 2e-12, (info.status, info.relres_true)
+    e_gpu, e_ora = _rel(res.x, xs), _rel(xo, xs)
+    print(f"fp64 128^3: |x-x*|/|x*| gpu {e_gpu:.3e} oracle(1e-8) {e_ora:.3e}; "
+          f"iters gpu {res.stats['iters']} oracle {io.iters}")
+    assert e_gpu <= max(2.0 * e_ora, 1e-7), (e_gpu, e_ora)
+    assert abs(res.stats["iters"] - io.iters) <= 0.05 * io.iters, (res.stats["iters"], io.iters)
     # truncated iterates, plain and with a k = 20 right-only space
     U = inputs.random_recycle_basis(P.n, 20, 11)
     rec = orb.recycle_setup(S, U)
