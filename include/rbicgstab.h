@@ -255,6 +255,40 @@ int rbicgstab_residual_noalloc(int64_t n, const int32_t* row_ptr, const int32_t*
                                const double* val, const double* x, const double* b, double* r,
                                double* rnorm2, void* cuda_stream);
 
+/* Gram step of the recycle update (the harmonic-Ritz update after each cycle,
+ * Sec. 6.2; the selection rule is the harmonic-Ritz reading of that update):
+ * G = Z^T Z and H = Z^T W for the FP32 column blocks of the mixed path,
+ * W = [Y, P, S] and Z = [AY, AP, AS] (AP = A P etc.), m = ky + nit + ns
+ * columns each.  Every block is on the device, column-major with leading
+ * dimension ld (a multiple of 4, >= n, 16-byte aligned columns); Y and AY
+ * have ky <= kcap columns, P, AP nit <= scap, S, AS ns <= scap (kcap, scap:
+ * the recycle dimension and cycle length, which fix the tile layout).
+ * G, H: host arrays of m x m doubles, column-major; G is symmetric.
+ * path: RB_GRAM_AUTO uses the tensor cores (tcgen05, TF32 pairs, FP64
+ * sums over CTAs) when the layout fits (2 * (r8(kcap) + 2 r8(scap)) <= 224,
+ * r8 = round up to 8), else the CUDA-core kernel; RB_GRAM_CUDACORE forces
+ * the latter, RB_GRAM_TENSOR the former (RB_EINVAL if it does not fit).
+ * This is the kernel the solver runs between cycles; the entry point exists
+ * so that it can be checked on its own.  It allocates its own scratch, runs
+ * on cuda_stream and synchronises it.  Errors: RB_EINVAL (arguments,
+ * m > 90), RB_ENOMEM, RB_ECUDA, RB_ETIMEOUT (a bounded device wait of the
+ * tensor-core kernel expired; outputs undefined). */
+#define RB_GRAM_AUTO     0
+#define RB_GRAM_CUDACORE 1
+#define RB_GRAM_TENSOR   2
+int rbicgstab_update_gram(int64_t n, int64_t ld, int32_t ky, int32_t nit, int32_t ns, int32_t kcap,
+                          int32_t scap, const float* Y, const float* AY, const float* P, const float* AP,
+                          const float* S, const float* AS, double* G, double* H, int32_t path,
+                          void* cuda_stream);
+
+/* Layout statistics of the current matrix A on the device (SELL-32, slices of
+ * 32 rows): the number of slices and of stencil slices, those whose rows use
+ * no more distinct column offsets (col - row) than the slice's longest row
+ * and whose gathers stay inside the matrix; the fused SpMV passes form their
+ * column indices from per-slice offsets there instead of loading them.
+ * Errors: RB_EINVAL (NULL argument), RB_EDIM (no matrix). */
+int rbicgstab_sell_stats(rb_handle h, int64_t* nslices, int64_t* stencil_slices);
+
 /* Number of CUDA kernels this library has launched in the process so far
  * (each graph replay adds the kernels its graph holds).  Thread-safe. */
 long long rbicgstab_kernel_launches(void);

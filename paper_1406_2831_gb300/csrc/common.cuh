@@ -25,6 +25,16 @@ constexpr int kMaxRhs = RB_MAX_RHS; // right-hand sides one blocked solve iterat
 // SELL-32 view of a sparse matrix: slice `sl` holds rows sl*32 .. sl*32+31;
 // entry j of row sl*32+lane sits at slice_ptr[sl] + j*32 + lane.  Padding
 // entries have val = 0 and col = the row itself.
+//
+// Stencil slices.  A slice whose rows together use at most `width` distinct
+// column offsets (col - row), every one of which stays inside [0, n) for all
+// 32 rows, is laid out in offset order: entry j of row r has col = r + o_j,
+// with an explicit zero where the row has no such entry.  Its offsets are
+// stored once, offs[sl * offs_stride + j] (j < width), so a kernel may form
+// the gather addresses without loading col.  Other slices keep the CSR order;
+// their first offs entry is kNoStencil.  col stays valid for every slice.
+constexpr int32_t kNoStencil = INT32_MIN;
+constexpr int kMaxStencil = 32;
 template <typename T>
 struct Sell {
   const int64_t* slice_ptr;  // [nslices + 1]
@@ -32,6 +42,8 @@ struct Sell {
   const int32_t* col;
   const T* val;
   int64_t nslices;
+  const int32_t* offs;       // [nslices * offs_stride]
+  int offs_stride;           // power of two <= kMaxStencil
 };
 
 // Completion tickets of one two-level grid reduction (device.cuh,

@@ -434,19 +434,27 @@ __device__ __forceinline__ void spmv_multi(const IterArgs<T>& a, const T* const*
   }
   Acc<T> accr1[R], accd1[R][4], accp1[R][CPL];   // R = 1
   AccP<T> accr[H], accd[H][4], accp[H][CPL];      // pairs
-  int wn = 0;   // width and first entry of the warp's next slice
+  // width, first entry and column offset `lane` of the warp's next slice
+  const int ostride = a.A.offs_stride;
+  int wn = 0;
   int64_t en = 0;
+  int32_t on = 0;
   if (w0 < ns) {
     wn = __ldg(a.A.width + w0);
     en = __ldg(a.A.slice_ptr + w0);
+    on = lane < ostride ? __ldg(a.A.offs + w0 * ostride + lane) : 0;
   }
   for (int64_t sl = w0; sl < ns; sl += nw) {
     const int wc = wn;
     const int64_t b = en + lane;
+    const int32_t oc = on;
     if (sl + nw < ns) {
       wn = __ldg(a.A.width + sl + nw);
       en = __ldg(a.A.slice_ptr + sl + nw);
+      on = lane < ostride ? __ldg(a.A.offs + (sl + nw) * ostride + lane) : 0;
     }
+    // stencil slice: entry j's column is row + offset j (no column loads)
+    const bool stencil = __shfl_sync(0xffffffffu, oc, 0) != kNoStencil;
     if (KMAX > 0) {
       __syncwarp();   // every lane is done with the previous slice's tile
       stage_tile<T, KMAX, R>(a, ws, sl, k);
@@ -458,7 +466,8 @@ __device__ __forceinline__ void spmv_multi(const IterArgs<T>& a, const T* const*
     T au[NE];
 #pragma unroll
     for (int u = 0; u < NE; ++u) {
-      cu[u] = u < wc ? __ldg(colp + b + (int64_t)u * kSlice) : 0;
+      const int32_t ou = __shfl_sync(0xffffffffu, oc, u);
+      cu[u] = u < wc ? (stencil ? (int32_t)row + ou : __ldg(colp + b + (int64_t)u * kSlice)) : 0;
       au[u] = u < wc ? __ldg(valp + b + (int64_t)u * kSlice) : T(0);
     }
     T y[R];
@@ -473,7 +482,8 @@ __device__ __forceinline__ void spmv_multi(const IterArgs<T>& a, const T* const*
     }
     for (int j = NE; j < wc; ++j) {   // rows wider than NE entries
       const int64_t e = b + (int64_t)j * kSlice;
-      const int cc = __ldg(colp + e);
+      const int32_t oj = __shfl_sync(0xffffffffu, oc, j & 31);
+      const int cc = stencil ? (int32_t)row + oj : __ldg(colp + e);
       const T vv = __ldg(valp + e);
 #pragma unroll
       for (int r = 0; r < R; ++r) y[r] = fma_t(vv, __ldg(vg[r] + cc), y[r]);

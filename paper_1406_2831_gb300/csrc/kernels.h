@@ -86,9 +86,12 @@ struct SellBuf {
   int32_t* col = nullptr;
   T* val = nullptr;
   int64_t* perm = nullptr;   // SELL position -> CSR position (or -1 for padding)
+  int32_t* offs = nullptr;   // per-slice column offsets of stencil slices (see Sell)
+  int offs_stride = 1;
   int64_t nslices = 0;
   int64_t cap = 0;           // entries incl. padding
-  Sell<T> view() const { return Sell<T>{slice_ptr, width, col, val, nslices}; }
+  int64_t stencil_slices = 0;
+  Sell<T> view() const { return Sell<T>{slice_ptr, width, col, val, nslices, offs, offs_stride}; }
 };
 
 // Validate CSR on the device; *bad receives 0 (ok), RB_EBADCSR or RB_ENONFINITE.
@@ -157,6 +160,23 @@ int gram_gh_work(int m);
 template <typename T>
 cudaError_t gram_gh(const T* const* Z, const T* const* W, int m, int64_t npad, double* G, double* H,
                     double* work, int grid, cudaStream_t s);
+// The recycle update's Gram matrices on the tensor cores (gram_tc.cu):
+// G = Z^T Z and H = Z^T W (m x m each, column-major, FP64, on the device) for
+// FP32 column blocks Z = [AY, AP, AS], W = [Y, P, S], each block column-major
+// with leading dimension ld, cols[b] <= cap[b] columns in use (the caps fix the
+// shared-memory layout; Z's and W's caps and column counts pair up).
+// `work` holds gram_tc_work_floats(cap, grid) floats; `err` (device int,
+// zeroed by the caller) becomes nonzero if a CTA gave up a bounded wait.
+constexpr int kMaxGramTc = 128;
+struct GramTcBlocks {
+  const float* ptr[6];   // AY, AP, AS, Y, P, S
+  int cols[6];
+  int cap[6];
+};
+bool gram_tc_eligible(const int cap[6]);
+size_t gram_tc_work_floats(const int cap[6], int grid);
+int gram_tc(const GramTcBlocks& blk, int64_t n, int64_t ld, double* G, double* H, float* work, int* err,
+            int grid, cudaStream_t s);
 // st->red[j] = ||M_j||^2 for column pointers M[0..k) (deterministic).
 template <typename T>
 cudaError_t colnorm2(const T* const* M, int k, int64_t npad, IterState* st, double* partials, int grid,

@@ -8,12 +8,27 @@
 // slice padded to its longest row with (col = row, val = 0).  Stencil rows
 // differ in length only at the boundary, so padding is small.
 #include <algorithm>
+#include <cstdlib>
 #include <vector>
 
 #include "device.cuh"
 #include "kernels.h"
 
 namespace rb {
+
+namespace {
+// Device scratch freed on every return path.
+struct DeviceScratch {
+  void* p = nullptr;
+  ~DeviceScratch() {
+    if (p) cudaFree(p);
+  }
+};
+}  // namespace
+
+__global__ void k_fill_i32(int64_t cnt, int32_t* __restrict__ p, int32_t v) {
+  for (int64_t i = gtid(); i < cnt; i += gstride()) p[i] = v;
+}
 
 // ---------------------------------------------------------------- validation
 __global__ void k_validate_rows(int64_t n, int64_t nnz, const int32_t* __restrict__ rp, int* flag) {
@@ -67,10 +82,48 @@ __global__ void k_slice_width(int64_t n, int64_t nslices, const int32_t* __restr
   }
 }
 
+// Stencil slices (see Sell in common.cuh): the sorted union of the column
+// offsets of the slice's rows, kept when it has exactly `width` members (no
+// extra entries) and every row's gathers stay inside [0, n).  One thread per
+// slice; the search is quadratic in the width, which is small.
+__global__ void k_slice_stencil(int64_t n, int64_t nslices, const int32_t* __restrict__ rp,
+                                const int32_t* __restrict__ col, const int32_t* __restrict__ width,
+                                int stride, int32_t* __restrict__ offs, unsigned long long* count) {
+  for (int64_t sl = gtid(); sl < nslices; sl += gstride()) {
+    const int w = width[sl];
+    const int64_t r0 = sl * kSlice;
+    bool ok = w > 0 && w <= stride && r0 + kSlice <= n;
+    int32_t O[kMaxStencil];
+    int u = 0;
+    for (int l = 0; ok && l < kSlice; ++l) {
+      const int64_t r = r0 + l;
+      for (int64_t e = rp[r]; ok && e < rp[r + 1]; ++e) {
+        const int32_t d = (int32_t)((int64_t)col[e] - r);
+        int pos = 0;
+        while (pos < u && O[pos] < d) ++pos;
+        if (pos < u && O[pos] == d) continue;
+        if (u == w) {
+          ok = false;
+          break;
+        }
+        for (int q = u; q > pos; --q) O[q] = O[q - 1];
+        O[pos] = d;
+        ++u;
+      }
+    }
+    ok = ok && u == w && r0 + O[0] >= 0 && r0 + kSlice - 1 + O[u - 1] < n;
+    for (int j = 0; j < stride; ++j) offs[sl * stride + j] = ok && j < w ? O[j] : 0;
+    if (!ok) offs[sl * stride] = kNoStencil;
+    else atomicAdd(count, 1ull);
+  }
+}
+
+// SELL entries: CSR order (padding (row, 0) at the end of short rows), or,
+// for a stencil slice, offset order with (r + o_j, 0) where row r lacks o_j.
 __global__ void k_sell_fill(int64_t n, int64_t nslices, const int32_t* __restrict__ rp,
                             const int32_t* __restrict__ col, const int64_t* __restrict__ sp,
-                            const int32_t* __restrict__ width, int32_t* __restrict__ scol,
-                            int64_t* __restrict__ perm) {
+                            const int32_t* __restrict__ width, const int32_t* __restrict__ offs, int stride,
+                            int32_t* __restrict__ scol, int64_t* __restrict__ perm) {
   const int64_t total = nslices * kSlice;
   for (int64_t r = gtid(); r < total; r += gstride()) {
     const int64_t sl = r / kSlice;
@@ -78,9 +131,20 @@ __global__ void k_sell_fill(int64_t n, int64_t nslices, const int32_t* __restric
     const int w = width[sl];
     const int64_t b = (r < n) ? rp[r] : 0;
     const int len = (r < n) ? (int)(rp[r + 1] - b) : 0;
+    const bool stencil = offs[sl * stride] != kNoStencil;
     for (int j = 0; j < w; ++j) {
       const int64_t pos = sp[sl] + (int64_t)j * kSlice + lane;
-      if (j < len) {
+      if (stencil) {
+        const int32_t c = (int32_t)(r + offs[sl * stride + j]);
+        int64_t src = -1;
+        for (int e = 0; e < len; ++e)
+          if (col[b + e] == c) {
+            src = b + e;
+            break;
+          }
+        scol[pos] = c;
+        perm[pos] = src;
+      } else if (j < len) {
         scol[pos] = col[b + j];
         perm[pos] = b + j;
       } else {
@@ -107,6 +171,7 @@ void sell_free(SellBuf<T>* b) {
   cudaFree(b->col);
   cudaFree(b->val);
   cudaFree(b->perm);
+  cudaFree(b->offs);
   *b = SellBuf<T>();
 }
 template void sell_free<double>(SellBuf<double>*);
@@ -114,7 +179,7 @@ template void sell_free<float>(SellBuf<float>*);
 
 int sell_build(int64_t n, int64_t nnz, const int32_t* row_ptr, const int32_t* col,
                SellBuf<double>* out, cudaStream_t s) {
-  count_launches(2);
+  count_launches(3);
   sell_free(out);
   const int64_t nslices = (n + kSlice - 1) / kSlice;
   out->nslices = nslices;
@@ -138,11 +203,33 @@ int sell_build(int64_t n, int64_t nnz, const int32_t* row_ptr, const int32_t* co
   RB_CUDA_TRY(cudaMalloc(&out->col, sizeof(int32_t) * cap));
   RB_CUDA_TRY(cudaMalloc(&out->val, sizeof(double) * cap));
   RB_CUDA_TRY(cudaMalloc(&out->perm, sizeof(int64_t) * cap));
+  int wmax = 0;
+  for (int64_t i = 0; i < nslices; ++i) wmax = std::max(wmax, w[i]);
+  int stride = 1;
+  while (stride < wmax && stride < kMaxStencil) stride *= 2;
+  out->offs_stride = stride;
+  RB_CUDA_TRY(cudaMalloc(&out->offs, sizeof(int32_t) * std::max<int64_t>(nslices * stride, 1)));
+  DeviceScratch cnt;
+  RB_CUDA_TRY(cudaMalloc(&cnt.p, sizeof(unsigned long long)));
+  unsigned long long* dcount = static_cast<unsigned long long*>(cnt.p);
+  RB_CUDA_TRY(cudaMemsetAsync(dcount, 0, sizeof(unsigned long long), s));
+  // RB_SELL_GENERIC in the environment keeps every slice in CSR order (the
+  // stencil layout's results are bitwise equal; this switch lets tests check it)
+  if (nslices && getenv("RB_SELL_GENERIC") == nullptr) {
+    k_slice_stencil<<<grid, kBlock, 0, s>>>(n, nslices, row_ptr, col, out->width, stride, out->offs, dcount);
+    RB_CUDA_TRY(cudaGetLastError());
+  } else if (nslices) {
+    k_fill_i32<<<grid, kBlock, 0, s>>>(nslices * stride, out->offs, kNoStencil);
+    RB_CUDA_TRY(cudaGetLastError());
+  }
   int g2 = (int)std::min<int64_t>((nslices * kSlice + kBlock - 1) / kBlock + 1, 16384);
-  k_sell_fill<<<g2, kBlock, 0, s>>>(n, nslices, row_ptr, col, out->slice_ptr, out->width,
+  k_sell_fill<<<g2, kBlock, 0, s>>>(n, nslices, row_ptr, col, out->slice_ptr, out->width, out->offs, stride,
                                     out->col, out->perm);
   RB_CUDA_TRY(cudaGetLastError());
+  unsigned long long hcount = 0;
+  RB_CUDA_TRY(cudaMemcpyAsync(&hcount, dcount, sizeof(hcount), cudaMemcpyDeviceToHost, s));
   RB_CUDA_TRY(cudaStreamSynchronize(s));  // keeps host vectors alive until copies finish
+  out->stencil_slices = (int64_t)hcount;
   return RB_OK;
 }
 
@@ -256,16 +343,6 @@ __global__ void k_sort_rows(int64_t n, const int32_t* __restrict__ trp, int32_t*
     }
   }
 }
-
-namespace {
-// Device scratch freed on every return path.
-struct DeviceScratch {
-  void* p = nullptr;
-  ~DeviceScratch() {
-    if (p) cudaFree(p);
-  }
-};
-}  // namespace
 
 int csr_transpose(int64_t n, int64_t nnz, const int32_t* row_ptr, const int32_t* col,
                   int32_t* t_row_ptr, int32_t* t_col, int64_t* t_src, cudaStream_t s) {

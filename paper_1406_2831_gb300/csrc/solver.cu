@@ -108,7 +108,11 @@ struct rb_ctx {
   int k = 0, kcap = 0;
   double *U = nullptr, *Ut = nullptr, *C = nullptr, *Ct = nullptr, *Chat = nullptr;
   double *T1 = nullptr, *T2 = nullptr;   // scratch blocks (kcap columns each)
-  double* Dinv = nullptr;                // 1 / D_c (device)
+  double* Dinv = nullptr;                // ones (device): coefficient scale of the dual's C^T products
+  // Mpt (k x k, column-major, host): C-hat = C~ Mpt.  The pseudo-inverse
+  // transpose of M = C~^T C when the columns are kept as computed, diag(1 / D_c)
+  // after a rank-reducing biorthogonalisation.
+  std::vector<double> Mpt;
   float *fU = nullptr, *fC = nullptr, *fChat = nullptr;
   // per right-hand-side vectors; shared r~_0 and scratch
   Slot sl[kMaxRhs];
@@ -121,6 +125,7 @@ struct rb_ctx {
   double* partials = nullptr;
   int64_t partials_cap = 0;
   int* dflag = nullptr;
+  int* tcerr = nullptr;   // bounded-wait failures of the tensor-core Gram
   // cycle store for the recycle update, kBanks banks of cyc vectors each for
   // P, S, QR = A P and TR = A S, of the inner precision (double for RB_FP64,
   // float for RB_MIXED), and the candidate Y, A Y
@@ -323,6 +328,45 @@ int block_gram_gh(rb_ctx* h, const std::vector<const T*>& Z, const std::vector<c
   return RB_OK;
 }
 
+// G = Z^T Z and H = Z^T W on the tensor cores for FP32 column blocks (see
+// gram_tc.cu); same outputs and stream discipline as block_gram_gh.
+// Returns RB_ETIMEOUT if a CTA gave up a bounded wait.
+int block_gram_gh_tc(rb_ctx* h, const GramTcBlocks& blk, std::vector<double>& G, std::vector<double>& H,
+                     cudaStream_t s) {
+  const int m = blk.cols[0] + blk.cols[1] + blk.cols[2];
+  G.assign((size_t)m * m, 0.0);
+  H.assign((size_t)m * m, 0.0);
+  if (!m) return RB_OK;
+  const int grid = h->nsm;
+  const int64_t need = (int64_t)((gram_tc_work_floats(blk.cap, grid) + 1) / 2);
+  if (h->gwork_cap < need) {   // reallocation: nothing may use gwork meanwhile
+    RB_CUDA_TRY(cudaStreamSynchronize(s));
+    int rc = ensure_gwork(h, need);
+    if (rc) return rc;
+  }
+  RB_CUDA_TRY(cudaMemsetAsync(h->tcerr, 0, sizeof(int), s));
+  int rc = gram_tc(blk, h->n, h->npad, h->dG, h->dG + (size_t)kMaxGram * kMaxGram, (float*)h->gwork, h->tcerr,
+                   grid, s);
+  if (rc) return rc;
+  int herr = 0;
+  RB_CUDA_TRY(cudaMemcpyAsync(G.data(), h->dG, sizeof(double) * G.size(), cudaMemcpyDeviceToHost, s));
+  RB_CUDA_TRY(cudaMemcpyAsync(H.data(), h->dG + (size_t)kMaxGram * kMaxGram, sizeof(double) * H.size(),
+                              cudaMemcpyDeviceToHost, s));
+  RB_CUDA_TRY(cudaMemcpyAsync(&herr, h->tcerr, sizeof(int), cudaMemcpyDeviceToHost, s));
+  RB_CUDA_TRY(cudaStreamSynchronize(s));
+  return herr ? RB_ETIMEOUT : RB_OK;
+}
+
+// Whether the cycle Gram of this handle runs on the tensor cores: FP32
+// columns and a tile layout that fits (k + 2 s small enough); RB_GRAM_CUDACORE
+// in the environment selects the CUDA-core kernel instead.
+bool use_gram_tc(rb_ctx* h) {
+  static const bool off = getenv("RB_GRAM_CUDACORE") != nullptr;
+  if (off) return false;
+  const int cap[6] = {h->o.k_max, h->cyc, h->cyc, h->o.k_max, h->cyc, h->cyc};
+  return gram_tc_eligible(cap);
+}
+
 // Squared 2-norms of the given columns.
 template <typename T>
 int block_colnorm2(rb_ctx* h, const std::vector<const T*>& M, std::vector<double>& out) {
@@ -423,8 +467,15 @@ int alloc_vectors(rb_ctx* h) {
 }
 
 // ------------------------------------------------------------ recycle setup
-// The recycle setup (Sec. 3, eq. (3.4)) for the columns currently in U, Ut (kin of them):
-// C = A U, C~ = A^T U~, SVD biorthogonalisation, C-hat = C~ D_c^{-1}.
+// The recycle setup (Sec. 3, eq. (3.4)) for the columns currently in U, Ut
+// (kin of them): C = A U, C~ = A^T U~, M = C~^T C and its SVD M = P S Q^T.
+// The iteration needs only the oblique projector C C-hat^T, the coefficient
+// map C-hat^T and U in the same basis.  With the biorthogonalised columns of
+// Sec. 3 (U Q, C Q, U~ P, C~ P, D_c = S) the projector is C M^+ C~^T, so
+// when M has full numerical rank the columns are kept as computed and
+// C-hat = C~ M^+^T (one n x k x k product instead of four rotations); when
+// singular values fall below the drop tolerance the rotations are applied
+// and the weak directions dropped (k_used < k, RB_WRECYCLE_RANK).
 int recycle_setup(rb_ctx* h, int kin, int64_t* setup_mv) {
   PhaseClock pc;
   h->k = 0;
@@ -455,8 +506,6 @@ int recycle_setup(rb_ctx* h, int kin, int64_t* setup_mv) {
   if (sig[0] > 0)
     while (kk < kin && sig[kk] >= drop * sig[0]) ++kk;
   if (kk == 0) return RB_OK;
-  // U <- U Q, C <- C Q, U~ <- U~ P, C~ <- C~ P (first kk columns of P, Q)
-  std::vector<double> Qk(Q.begin(), Q.begin() + (size_t)kin * kk), Pk(P.begin(), P.begin() + (size_t)kin * kk);
   auto cols = [&](double* base, int cnt) {
     std::vector<double*> v;
     for (int j = 0; j < cnt; ++j) v.push_back(colp(base, ld, j));
@@ -467,26 +516,40 @@ int recycle_setup(rb_ctx* h, int kin, int64_t* setup_mv) {
     for (int j = 0; j < cnt; ++j) v.push_back(colp(base, ld, j));
     return v;
   };
-  struct Job {
-    double** src;
-    const std::vector<double>* R;
-  };
-  Job jobs[] = {{&h->U, &Qk}, {&h->C, &Qk}, {&h->Ut, &Pk}, {&h->Ct, &Pk}};
-  for (Job& jb : jobs) {
-    rc = block_gemm<double>(h, cols(h->T1, kk), ccols(*jb.src, kin), *jb.R, kk);
+  if (kk == kin) {
+    // Mpt = M^+^T = P S^-1 Q^T;  C-hat = C~ Mpt
+    h->Mpt.assign((size_t)kin * kin, 0.0);
+    for (int c = 0; c < kin; ++c)
+      for (int r = 0; r < kin; ++r) {
+        double acc = 0.0;
+        for (int j = 0; j < kin; ++j) acc += P[r + (size_t)j * kin] * Q[c + (size_t)j * kin] / sig[j];
+        h->Mpt[r + (size_t)c * kin] = acc;
+      }
+    rc = block_gemm<double>(h, cols(h->Chat, kin), ccols(h->Ct, kin), h->Mpt, kin);
     if (rc) return rc;
-    std::swap(*jb.src, h->T1);
+  } else {
+    // U <- U Q, C <- C Q, U~ <- U~ P, C~ <- C~ P (first kk columns), C-hat = C~ D_c^-1
+    std::vector<double> Qk(Q.begin(), Q.begin() + (size_t)kin * kk), Pk(P.begin(), P.begin() + (size_t)kin * kk);
+    struct Job {
+      double** src;
+      const std::vector<double>* R;
+    };
+    Job jobs[] = {{&h->U, &Qk}, {&h->C, &Qk}, {&h->Ut, &Pk}, {&h->Ct, &Pk}};
+    for (Job& jb : jobs) {
+      rc = block_gemm<double>(h, cols(h->T1, kk), ccols(*jb.src, kin), *jb.R, kk);
+      if (rc) return rc;
+      std::swap(*jb.src, h->T1);
+    }
+    h->Mpt.assign((size_t)kk * kk, 0.0);
+    for (int j = 0; j < kk; ++j) h->Mpt[j + (size_t)j * kk] = 1.0 / sig[j];
+    rc = block_gemm<double>(h, cols(h->Chat, kk), ccols(h->Ct, kk), h->Mpt, kk);
+    if (rc) return rc;
   }
   rc = sync(h);
   if (rc) return rc;
   pc.lap("setup_gemm");
-  std::vector<double> dinv(kk);
-  for (int j = 0; j < kk; ++j) dinv[j] = 1.0 / sig[j];
-  RB_CUDA_TRY(cudaMemcpyAsync(h->Chat, h->Ct, sizeof(double) * ld * kk, cudaMemcpyDeviceToDevice, h->us));
-  rc = sync(h);
-  if (rc) return rc;
-  RB_CUDA_TRY(cudaMemcpy(h->Dinv, dinv.data(), sizeof(double) * kk, cudaMemcpyHostToDevice));
-  RB_CUDA_TRY(scale_cols<double>(h->Chat, ld, kk, h->Dinv, h->npad, h->us));
+  std::vector<double> ones(kk, 1.0);
+  RB_CUDA_TRY(cudaMemcpy(h->Dinv, ones.data(), sizeof(double) * kk, cudaMemcpyHostToDevice));
   h->k = kk;
   if (h->o.precision == RB_MIXED) {
     RB_CUDA_TRY(to_float(h->U, h->fU, ld * kk, h->us));
@@ -694,8 +757,8 @@ int setup_block(rb_ctx* h, int nrhs, double* const* rhs, double* const* xb, cons
       DotArgs d{};
       d.M = h->C; d.ld = ld; d.km = k; d.v = h->rt0; d.nd = 0;
       RB_CUDA_TRY(dots(d, h->npad, h->st, h->partials, vec_grid(h), h->us));
-      // r~_0 = r~_{-1} - C~ (D_c^{-1} C^T r~_{-1})
-      RB_CUDA_TRY(gemv_update(h->rt0, h->Ct, ld, k, h->st->red, h->Dinv, -1.0, h->npad, vec_grid(h), h->us));
+      // r~_0 = r~_{-1} - C~ C-check^T r~_{-1} = r~_{-1} - C-hat (C^T r~_{-1})
+      RB_CUDA_TRY(gemv_update(h->rt0, h->Chat, ld, k, h->st->red, nullptr, -1.0, h->npad, vec_grid(h), h->us));
     }
     for (int i = 0; i < nrhs; ++i) {
       if (skip[i]) continue;
@@ -800,7 +863,21 @@ int cycle_update(rb_ctx* h, int bank, int nit, int ns) {
   const int m = (int)W.size();
   if (m == 0) return RB_OK;
   std::vector<double> G, H;
-  int rc = block_gram_gh<T>(h, Z, W, G, H, s);
+  int rc;
+  if (std::is_same<T, float>::value && use_gram_tc(h)) {
+    GramTcBlocks blk;
+    const float* src[6] = {(const float*)AYc, (const float*)slotQ<T>(h, bank, 0), (const float*)slotT<T>(h, bank, 0),
+                           (const float*)Yc, (const float*)slotP<T>(h, bank, 0), (const float*)slotS<T>(h, bank, 0)};
+    const int cols[3] = {h->kY, nit, ns};
+    for (int b = 0; b < 6; ++b) {
+      blk.ptr[b] = src[b];
+      blk.cols[b] = cols[b % 3];
+      blk.cap[b] = (b % 3 == 0) ? h->o.k_max : h->cyc;
+    }
+    rc = block_gram_gh_tc(h, blk, G, H, s);
+  } else {
+    rc = block_gram_gh<T>(h, Z, W, G, H, s);
+  }
   if (rc) return rc;
   pc.lap("gram");
   const int kt = std::min(h->o.k_max, m);
@@ -1237,6 +1314,8 @@ extern "C" int rbicgstab_create(rb_handle* out, const rb_opts* opts) {
   std::memset(h->hst, 0, sizeof(IterState) * kMaxRhs);
   h->dflag = dalloc<int>(1, &err);
   if (!h->dflag) return fail(err);
+  h->tcerr = dalloc<int>(1, &err);
+  if (!h->tcerr) return fail(err);
   h->kcap = o.k_max;
   h->Dinv = dalloc<double>(std::max(1, h->kcap), &err);
   if (!h->Dinv) return fail(err);
@@ -1260,7 +1339,7 @@ extern "C" int rbicgstab_destroy(rb_handle h) {
   for (int i = 0; i < h->nslots; ++i) free_slot(h->sl[i]);
   void* ptrs[] = {h->rp, h->ci, h->cv, h->trp, h->tci, h->tsrc, h->tcv, h->U, h->Ut, h->C, h->Ct,
                   h->Chat, h->T1, h->T2, h->Dinv, h->rt0, h->tmp, h->tmp2, h->frt0, h->fU, h->fC, h->fChat,
-                  h->st, h->partials, h->dflag, h->cstore, h->Yc, h->AYc, h->Yn, h->AYn, h->gwork, h->dG,
+                  h->st, h->partials, h->dflag, h->tcerr, h->cstore, h->Yc, h->AYc, h->Yn, h->AYn, h->gwork, h->dG,
                   h->dR, (void*)h->dptr};
   for (void* p : ptrs) cudaFree(p);
   if (h->hst) cudaFreeHost(h->hst);
@@ -1341,6 +1420,9 @@ extern "C" int rbicgstab_set_matrix(rb_handle h, int64_t n, int64_t nnz, const i
     h->A32.width = h->A.width;
     h->A32.col = h->A.col;
     h->A32.perm = h->A.perm;
+    h->A32.offs = h->A.offs;
+    h->A32.offs_stride = h->A.offs_stride;
+    h->A32.stencil_slices = h->A.stencil_slices;
     h->A32.val = dalloc<float>(h->A.cap, &err);
     if (err) return err;
   }
@@ -1446,6 +1528,92 @@ extern "C" int rbicgstab_pattern_outer(rb_handle h, const double* u, const doubl
   return sync(h);
 }
 
+extern "C" int rbicgstab_update_gram(int64_t n, int64_t ld, int32_t ky, int32_t nit, int32_t ns, int32_t kcap,
+                                     int32_t scap, const float* Y, const float* AY, const float* P,
+                                     const float* AP, const float* S, const float* AS, double* G, double* H,
+                                     int32_t path, void* cuda_stream) {
+  using namespace rb;
+  const int m = ky + nit + ns;
+  if (n <= 0 || ld < n || ld % 4 != 0 || ky < 0 || nit < 0 || ns < 0 || m <= 0 || ky > kcap || nit > scap ||
+      ns > scap || !G || !H || path < RB_GRAM_AUTO || path > RB_GRAM_TENSOR)
+    return RB_EINVAL;
+  if (m > kMaxGram) return RB_EINVAL;
+  const float* src[6] = {AY, AP, AS, Y, P, S};
+  const int cols[3] = {ky, nit, ns};
+  for (int b = 0; b < 6; ++b)
+    if (cols[b % 3] > 0 && !src[b]) return RB_EINVAL;
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  const int cap[6] = {kcap, scap, scap, kcap, scap, scap};
+  const bool tc = path == RB_GRAM_TENSOR || (path == RB_GRAM_AUTO && gram_tc_eligible(cap));
+  if (path == RB_GRAM_TENSOR && !gram_tc_eligible(cap)) return RB_EINVAL;
+  int dev = 0, nsm = 0;
+  RB_CUDA_TRY(cudaGetDevice(&dev));
+  RB_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  int err = 0;
+  double* dGH = dalloc<double>(2 * (int64_t)m * m, &err);
+  if (!dGH) return err;
+  int rc = RB_OK;
+  void* work = nullptr;
+  int* derr = nullptr;
+  const float** dptr = nullptr;
+  if (tc) {
+    GramTcBlocks blk;
+    for (int b = 0; b < 6; ++b) {
+      blk.ptr[b] = src[b];
+      blk.cols[b] = cols[b % 3];
+      blk.cap[b] = cap[b];
+    }
+    const size_t wf = gram_tc_work_floats(cap, nsm);
+    if (cudaMalloc(&work, sizeof(float) * wf) != cudaSuccess || cudaMalloc(&derr, sizeof(int)) != cudaSuccess ||
+        cudaMemsetAsync(derr, 0, sizeof(int), s) != cudaSuccess) {
+      rc = RB_ENOMEM;
+    } else {
+      rc = gram_tc(blk, n, ld, dGH, dGH + (size_t)m * m, (float*)work, derr, nsm, s);
+      int herr = 0;
+      if (rc == RB_OK && (cudaMemcpyAsync(&herr, derr, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+                          cudaStreamSynchronize(s) != cudaSuccess))
+        rc = RB_ECUDA;
+      if (rc == RB_OK && herr) rc = RB_ETIMEOUT;
+    }
+  } else {
+    std::vector<const float*> Z, W;
+    for (int b = 0; b < 3; ++b)
+      for (int j = 0; j < cols[b]; ++j) {
+        Z.push_back(src[b] + (int64_t)j * ld);
+        W.push_back(src[3 + b] + (int64_t)j * ld);
+      }
+    const int grid = 2 * nsm;
+    if (cudaMalloc(&work, sizeof(double) * (size_t)grid * gram_gh_work(m)) != cudaSuccess ||
+        cudaMalloc((void**)&dptr, sizeof(float*) * 2 * m) != cudaSuccess) {
+      rc = RB_ENOMEM;
+    } else if (cudaMemcpyAsync(dptr, Z.data(), sizeof(float*) * m, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+               cudaMemcpyAsync(dptr + m, W.data(), sizeof(float*) * m, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+               gram_gh<float>(dptr, dptr + m, m, ld, dGH, dGH + (size_t)m * m, (double*)work, grid, s) !=
+                   cudaSuccess) {
+      rc = RB_ECUDA;
+    }
+  }
+  if (rc == RB_OK &&
+      (cudaMemcpyAsync(G, dGH, sizeof(double) * m * m, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+       cudaMemcpyAsync(H, dGH + (size_t)m * m, sizeof(double) * m * m, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+       cudaStreamSynchronize(s) != cudaSuccess))
+    rc = RB_ECUDA;
+  cudaStreamSynchronize(s);
+  cudaFree(dGH);
+  cudaFree(work);
+  cudaFree(derr);
+  cudaFree((void*)dptr);
+  return rc;
+}
+
+extern "C" int rbicgstab_sell_stats(rb_handle h, int64_t* nslices, int64_t* stencil_slices) {
+  if (!h || !nslices || !stencil_slices) return RB_EINVAL;
+  if (!h->have_matrix) return RB_EDIM;
+  *nslices = h->A.nslices;
+  *stencil_slices = h->A.stencil_slices;
+  return RB_OK;
+}
+
 extern "C" int rbicgstab_svd_small(int32_t k, const double* M, double* P, double* sigma, double* Q) {
   if (k < 1 || k > 256 || !M || !P || !sigma || !Q) return RB_EINVAL;
   for (int64_t i = 0; i < (int64_t)k * k; ++i)
@@ -1549,8 +1717,9 @@ extern "C" int rbicgstab_solve_block(rb_handle h, int32_t nrhs, const double* B,
 namespace {
 
 // Eq. (3.5) for the dual system: r~_{-1} = b~ - A^T x~_{-1} (x~_{-1} in s.x),
-// x~_0 = x~_{-1} + U~ C-check^T r~_{-1}, r~_0 = r~_{-1} - C~ C-check^T r~_{-1}
-// (C-check^T v = D_c^{-1} C^T v).  Slot 1 holds the dual system.
+// x~_0 = x~_{-1} + U~ C-check^T r~_{-1}, r~_0 = r~_{-1} - C~ C-check^T r~_{-1}.
+// In the basis the setup keeps, C~ C-check^T = C-hat C^T and U~ C-check^T =
+// (U~ Mpt) C^T; T2 holds U~ Mpt.  Slot 1 holds the dual system.
 int bicg_dual_start(rb_ctx* h) {
   Slot& d = h->sl[1];
   const int64_t ld = h->npad;
@@ -1559,8 +1728,8 @@ int bicg_dual_start(rb_ctx* h) {
     DotArgs da{};
     da.M = h->C; da.ld = ld; da.km = h->k; da.v = d.r; da.nd = 0;
     RB_CUDA_TRY(dots(da, h->npad, h->st + 1, h->partials, vec_grid(h), h->us));
-    RB_CUDA_TRY(gemv_update(d.x, h->Ut, ld, h->k, h->st[1].red, h->Dinv, 1.0, h->npad, vec_grid(h), h->us));
-    RB_CUDA_TRY(gemv_update(d.r, h->Ct, ld, h->k, h->st[1].red, h->Dinv, -1.0, h->npad, vec_grid(h), h->us));
+    RB_CUDA_TRY(gemv_update(d.x, h->T2, ld, h->k, h->st[1].red, nullptr, 1.0, h->npad, vec_grid(h), h->us));
+    RB_CUDA_TRY(gemv_update(d.r, h->Chat, ld, h->k, h->st[1].red, nullptr, -1.0, h->npad, vec_grid(h), h->us));
   }
   return RB_OK;
 }
@@ -1579,7 +1748,7 @@ BiArgs bicg_args(rb_ctx* h) {
 // One iteration of Alg. 1 on stream s, composed of the library's kernels:
 //   z = A p, zeta = C-hat^T z        (the FP64 SpMV + projection pass, state st[0])
 //   z~ = A^T p~, C^T z~              (the same pass on A^T and C, state st[1])
-//   q = z - C zeta, q~ = z~ - C~ D_c^{-1} C^T z~   (in place over z, z~) and (p~, q)
+//   q = z - C zeta, q~ = z~ - C-hat C^T z~   (in place over z, z~) and (p~, q)
 //   alpha, zeta_c, zeta~_c; x, x~, r, r~, ||r||, ||r~||, beta; p, p~
 cudaError_t bicg_iteration(rb_ctx* h, const Grids& g13, int grid, cudaStream_t s) {
   Slot &P = h->sl[0], &D = h->sl[1];
@@ -1608,7 +1777,7 @@ cudaError_t bicg_iteration(rb_ctx* h, const Grids& g13, int grid, cudaStream_t s
     ad.st = h->st + 1;
     if ((e = launch_pass<double>(P3, ap, k, g13, s)) != cudaSuccess) return e;
     if ((e = launch_pass<double>(P3, ad, k, g13, s)) != cudaSuccess) return e;
-    if ((e = bicg_project(bicg_args(h), h->C, h->Ct, ld, h->Dinv, grid, s)) != cudaSuccess) return e;
+    if ((e = bicg_project(bicg_args(h), h->C, h->Chat, ld, h->Dinv, grid, s)) != cudaSuccess) return e;
   }
   if (k == 0) {
     DotArgs d{};
@@ -1658,6 +1827,16 @@ extern "C" int rbicg_solve(rb_handle h, const double* b, const double* bt, doubl
     int64_t mv = 0;
     if ((rc = ensure_setup(h, &mv)) < 0) return rc;
     so.mv_setup = mv;
+  }
+  if (h->k > 0) {   // T2 = U~ Mpt: the dual solution's basis (see bicg_dual_start)
+    std::vector<double*> out;
+    std::vector<const double*> src;
+    for (int j = 0; j < h->k; ++j) {
+      out.push_back(colp(h->T2, h->npad, j));
+      src.push_back(colp(h->Ut, h->npad, j));
+    }
+    if ((rc = block_gemm<double>(h, out, src, h->Mpt, h->k))) return rc;
+    if ((rc = sync(h))) return rc;
   }
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   auto done = [&](int code) {
@@ -1767,7 +1946,7 @@ extern "C" int rbicg_solve(rb_handle h, const double* b, const double* bt, doubl
   // the final correction and the true residuals
   if (h->k > 0) {
     RB_CUDA_TRY(gemv_update(P.x, h->U, ld, h->k, h->st[0].xc, nullptr, -1.0, h->npad, vec_grid(h), h->us));
-    RB_CUDA_TRY(gemv_update(D.x, h->Ut, ld, h->k, h->st[1].xc, nullptr, -1.0, h->npad, vec_grid(h), h->us));
+    RB_CUDA_TRY(gemv_update(D.x, h->T2, ld, h->k, h->st[1].xc, nullptr, -1.0, h->npad, vec_grid(h), h->us));
   }
   double tr[2];
   RB_CUDA_TRY(residual_norm(h->A.view(), P.b, P.x, h->tmp, h->npad, h->st, h->partials, h->grids.spmv, h->us));

@@ -93,6 +93,10 @@ def lib():
     L.rbicg_solve.argtypes = [vp, dp, dp, dp, dp, ctypes.c_int, ctypes.POINTER(Stats), ctypes.POINTER(Stats)]
     L.rbicgstab_residual_noalloc.argtypes = [i64, dp, dp, dp, dp, dp, dp, dp, vp]
     L.rbicgstab_residual_noalloc.restype = ctypes.c_int
+    L.rbicgstab_update_gram.argtypes = [i64, i64, i32, i32, i32, i32, i32, dp, dp, dp, dp, dp, dp, dp, dp, i32, vp]
+    L.rbicgstab_update_gram.restype = ctypes.c_int
+    L.rbicgstab_sell_stats.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64)]
+    L.rbicgstab_sell_stats.restype = ctypes.c_int
     L.rbicgstab_kernel_launches.argtypes = []
     L.rbicgstab_kernel_launches.restype = ctypes.c_longlong
     L.rbicgstab_error_string.argtypes = [ctypes.c_int]
@@ -320,6 +324,13 @@ class Solver:
                "rbicg_solve")
         return SolveResult(x=x, stats=st.as_dict()), SolveResult(x=xt, stats=sd.as_dict())
 
+    def sell_stats(self):
+        """(slices, stencil slices) of the current matrix's SELL-32 layout
+        (rbicgstab_sell_stats)."""
+        a, b = ctypes.c_int64(0), ctypes.c_int64(0)
+        _check(lib().rbicgstab_sell_stats(self._h, ctypes.byref(a), ctypes.byref(b)), "rbicgstab_sell_stats")
+        return int(a.value), int(b.value)
+
     def apply(self, v, transpose=False):
         """y = A v (or A^T v) with the library's SpMV."""
         vp, w, keep = _ptr(v, np.float64)
@@ -389,6 +400,45 @@ def residual_noalloc(row_ptr, col, val, x, b, r, rnorm2, stream=None, n=None) ->
     args = [t.data_ptr() for t in tensors]
     sp = None if stream is None else (stream if isinstance(stream, int) else stream.cuda_stream)
     return _check(lib().rbicgstab_residual_noalloc(nn, *args, sp), "rbicgstab_residual_noalloc")
+
+
+GRAM_PATH = {"auto": 0, "cudacore": 1, "tensor": 2}
+
+
+def update_gram(Y, AY, P, AP, S, AS, kcap: int, scap: int, path: str = "auto", stream=None):
+    """Gram step of the recycle update (rbicgstab_update_gram): returns
+    (G, H) = (Z^T Z, Z^T W) as float64 numpy arrays for W = [Y, P, S],
+    Z = [AY, AP, AS].  Each block is a CUDA float32 tensor of shape
+    (columns, ld): the columns stored one after another (column-major with
+    leading dimension ld, shared by all blocks); n = ld."""
+    blocks = (Y, AY, P, AP, S, AS)
+    for t in blocks:
+        if not (_is_torch(t) and t.is_cuda and t.is_contiguous()):
+            raise RbError(C["RB_EINVAL"], "update_gram takes contiguous CUDA tensors")
+    import torch
+    if any(t.dtype != torch.float32 or t.dim() != 2 for t in blocks):
+        raise RbError(C["RB_EINVAL"], "update_gram takes 2-D float32 tensors (columns, ld)")
+    ld = Y.shape[1]
+    if any(t.shape[1] != ld for t in blocks):
+        raise RbError(C["RB_EINVAL"], "update_gram: blocks differ in ld")
+    return update_gram_n(ld, Y, AY, P, AP, S, AS, kcap, scap, path, stream)
+
+
+def update_gram_n(n: int, Y, AY, P, AP, S, AS, kcap: int, scap: int, path: str = "auto", stream=None):
+    """update_gram with the vector length n <= ld given explicitly."""
+    ld = Y.shape[1]
+    ky, nit, ns = Y.shape[0], P.shape[0], S.shape[0]
+    if AY.shape[0] != ky or AP.shape[0] != nit or AS.shape[0] != ns:
+        raise RbError(C["RB_EINVAL"], "update_gram: W and Z blocks differ in columns")
+    m = ky + nit + ns
+    G = np.zeros((m, m), order="F")
+    H = np.zeros((m, m), order="F")
+    sp = None if stream is None else (stream if isinstance(stream, int) else stream.cuda_stream)
+    ptr = lambda t: t.data_ptr() if t.numel() else None
+    _check(lib().rbicgstab_update_gram(int(n), int(ld), ky, nit, ns, int(kcap), int(scap), ptr(Y), ptr(AY),
+                                       ptr(P), ptr(AP), ptr(S), ptr(AS), G.ctypes.data, H.ctypes.data,
+                                       GRAM_PATH[path], sp), "rbicgstab_update_gram")
+    return G, H
 
 
 def kernel_launches() -> int:
