@@ -58,6 +58,16 @@ def parse():
     ap.add_argument("--quick", action="store_true", help="small grid for a smoke run (not a bench line)")
     ap.add_argument("--rbicg", action="store_true",
                     help="time Alg. 1 (RBiCG, primary + dual, FP64) on system 1 instead of the sequence")
+    ap.add_argument("--adjoint", action="store_true",
+                    help="the differentiation workload (100^3, 8 parameters, 6 steps) through the autograd "
+                         "function: forward + backward time per step, with and without checkpointing, and a "
+                         "central-difference check of two parameters")
+    ap.add_argument("--large", action="store_true",
+                    help="the large 27-point sequence (256 x 256 x 128, 10 systems, k = 30): recycled mixed vs "
+                         "plain FP64 and plain mixed, with the dominant pass's roofline")
+    ap.add_argument("--gram-only", action="store_true",
+                    help="time the recycle update's Gram step (tensor-core and CUDA-core kernels) on random FP32 "
+                         "blocks of the benchmark's shapes (n = N^3, k, s = 25) and exit")
     ap.add_argument("--passes-only", action="store_true",
                     help="set up one system and a k-column right-only recycle space, time the five "
                          "fused passes (recycled and plain) and exit; a short program for profilers")
@@ -313,6 +323,234 @@ def run_passes_only(args):
                       "passes_GBs": [round(bb / (m * 1e-3) / 1e9, 1) if m > 0 else 0 for bb, m in zip(pb, ms)],
                       "status": code}
         del s
+    return out
+
+
+def run_adjoint(args):
+    """The differentiation workload: config_param_3d (7-point convection-
+    diffusion on N^3, N = 100, 8 regional coefficients), L = ||C_out x||^2 with
+    a 16 x n Gaussian C_out, 6 parameter steps p <- 1.01 p.  One handle
+    carries the recycle space across the steps (update from each forward
+    solve, U~ = U); every step runs the forward solve and the backward (the
+    dual system A^T lam = dL/dx by Alg. 1 with the handle's space, then
+    dL/dA_ij = -lam_i x_j on the pattern, chained to dL/dp by autograd).
+    Device time per step (CUDA events), with and without checkpointing of x.
+    Check: at the first step, with solver tolerance 1e-12, dL/dp_k for two
+    parameters against central differences (h = 1e-6 max(1, |p_k|)) of tight
+    plain solves."""
+    import numpy as np
+    import torch
+
+    from paper_1406_2831_gb300 import autograd as rag
+    from paper_1406_2831_gb300 import inputs
+    from paper_1406_2831_gb300 import rbicgstab as rb
+    N = 24 if args.quick else 100
+    spec = inputs.config_param_3d(N=N)
+    P = spec.pattern
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream(dev)
+    basis = torch.from_numpy(np.stack(spec.basis)).to(dev)
+    b = torch.from_numpy(spec.b).to(dev)
+    Cout = torch.from_numpy(spec.C_out).to(dev)
+
+    def loss_of(s, p, checkpoint=False):
+        pt = torch.tensor(p, dtype=torch.float64, device=dev, requires_grad=True)
+        vals = (pt[:, None] * basis).sum(0)
+        x = rag.solve(s, vals, b, checkpoint=checkpoint)
+        L = (Cout @ x).square().sum()
+        L.backward()
+        return float(L.item()), pt.grad.detach().cpu().numpy()
+
+    out = {"metric": "adjoint gradient steps/sec", "config": {"workload": f"3d-7pt-param-{N}^3, 8 parameters, "
+                                                               f"{len(spec.steps)} steps, L = ||C_out x||^2",
+                                                               "n": P.n, "nnz": P.nnz, "k": spec.k, "tol": 1e-8}}
+    for ck in (False, True):
+        s = rb.Solver(k_max=spec.k, cycle_s=25, recycle="update_first", tol=1e-8, stream=stream)
+        s.set_matrix(P.row_ptr, P.col, spec.values(spec.p0))
+        loss_of(s, spec.steps[0], ck)     # warm-up (graphs, workspaces)
+        s.set_recycle(None)
+        torch.cuda.synchronize()
+        times, grads = [], []
+        for p in spec.steps:
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            L, g = loss_of(s, p, ck)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+            grads.append(g)
+        out["checkpoint" if ck else "stored_x"] = {"ms_per_step": [round(t, 2) for t in times],
+                                                   "steps_per_s": round(len(times) / (sum(times) * 1e-3), 3)}
+        del s
+    # central differences of two parameters at the first step, tight solves
+    st = rb.Solver(recycle="none", tol=1e-12, stream=stream)
+    st.set_matrix(P.row_ptr, P.col, spec.values(spec.p0))
+    _, g = loss_of(st, spec.p0)
+
+    def L_at(p):
+        st.set_values(torch.from_numpy(spec.values(p)).to(dev))
+        r = st.solve(b)
+        return float((Cout @ r.x).square().sum().item())
+    fd = {}
+    for kk in (0, 4):
+        h = 1e-6 * max(1.0, abs(spec.p0[kk]))
+        e = np.zeros(len(spec.p0))
+        e[kk] = h
+        d = (L_at(spec.p0 + e) - L_at(spec.p0 - e)) / (2 * h)
+        fd[f"p{kk}"] = {"adjoint": float(g[kk]), "central_difference": d,
+                        "rel_err": abs(g[kk] - d) / abs(d)}
+    out["gradient_check"] = fd
+    out["value"] = out["stored_x"]["steps_per_s"]
+    out["unit"] = "steps/s"
+    return out
+
+
+def run_large(args):
+    """The large 27-point sequence: stencil27_noisy on 256 x 256 x 128
+    (n = 8,388,608, ~224M nonzeros), convection c_j = 10 * 1.02^j for 10
+    systems, one fixed noise draw, one Gaussian right-hand side per system,
+    k = 30, s = 25, tol 1e-8.  The values are linear in c, so every system's
+    values are formed on the device as V(0) + c_j (V(1) - V(0)) from two
+    generations.  Arms (each the whole sequence once after one untimed pass):
+    recycled mixed (FP32 inner, FP64 refinement, the update from every
+    system), plain FP64 and plain mixed BiCGSTAB.  Then the five passes on
+    system 1 with the recycled handle's space (CUDA events)."""
+    import numpy as np
+    import torch
+
+    from paper_1406_2831_gb300 import inputs
+    from paper_1406_2831_gb300 import rbicgstab as rb
+    Nx, Ny, Nz = (64, 64, 32) if args.quick else (256, 256, 128)
+    spec = inputs.config_large_27pt(Nx, Ny, Nz)
+    t0 = time.perf_counter()
+    A0 = inputs.stencil27_noisy(Nx, Ny, Nz, 0.0, seed=5)
+    A1 = inputs.stencil27_noisy(Nx, Ny, Nz, 1.0, seed=5)
+    assert np.array_equal(A0.row_ptr, A1.row_ptr) and np.array_equal(A0.col, A1.col)
+    t_gen = time.perf_counter() - t0
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream(dev)
+    n, z = A0.n, A0.nnz
+    rp = torch.from_numpy(A0.row_ptr).to(dev)
+    col = torch.from_numpy(A0.col).to(dev)
+    V0 = torch.from_numpy(A0.val).to(dev)
+    dV = torch.from_numpy(A1.val).to(dev) - V0
+    del A1
+    cs = [10.0 * 1.02 ** j for j in range(len(spec.values))]
+    vals = [V0 + c * dV for c in cs]
+    rhs = [torch.from_numpy(row[0]()).to(dev) for row in spec.rhs]
+    x = torch.zeros(n, dtype=torch.float64, device=dev)
+    torch.cuda.synchronize()
+
+    def arm(recycled, precision):
+        s = rb.Solver(k_max=spec.k if recycled else 0, cycle_s=spec.cycle_s,
+                      recycle="update_first" if recycled else "none", precision=precision, tol=spec.tol,
+                      stream=stream)
+        s.set_matrix(rp, col, vals[0])
+
+        def seq(log):
+            if recycled:
+                s.set_recycle(None)
+            for j, v in enumerate(vals):
+                s.set_values(v)
+                x.zero_()
+                r = s.solve(rhs[j], x)
+                if r.stats["status"] != 0:
+                    raise RuntimeError(f"system {j}: {r.stats}")
+                if log is not None:
+                    log.append(r.stats)
+        seq(None)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        logs = []
+        e0.record(stream)
+        seq(logs)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        its = [l["iters"] for l in logs]
+        out = {"solves_per_s": round(len(logs) / (ms * 1e-3), 3), "ms_per_sequence": round(ms, 1),
+               "iters": its, "iters_mean": round(statistics.mean(its), 1),
+               "matvecs": int(sum(l["matvecs"] for l in logs)),
+               "matvecs_setup": int(sum(l["matvecs_setup"] for l in logs)),
+               "relres_true_max": max(l["relres_true"] for l in logs)}
+        return s, out
+
+    res = {}
+    s_rec, res["recycled_mixed"] = arm(True, "mixed")
+    s_rec.set_values(vals[0])
+    ms_pass, code = rb.time_passes(s_rec, rhs[0], reps=5)
+    k_used = s_rec.get_recycle()[0].shape[1]
+    del s_rec
+    _, res["plain_fp64"] = arm(False, "fp64")
+    _, res["plain_mixed"] = arm(False, "mixed")
+    peaks = measured_peaks()
+    pb = pass_bytes(n, z, k_used, vb=4, ab=4, R=1)
+    dom = int(np.argmax(ms_pass))
+    gbs = pb[dom] / (ms_pass[dom] * 1e-3) / 1e9
+    it_ms = float(sum(ms_pass))
+    rec, pl = res["recycled_mixed"], res["plain_fp64"]
+    return {"metric": "solves/sec at 1e-8 rel. residual, large 27-point sequence", "value": rec["solves_per_s"],
+            "unit": "solves/s", "dtype": "f32-inner/f64-refined", "data": "synthetic",
+            "config": {"workload": f"3d-27pt-noisy-{Nx}x{Ny}x{Nz}-drift", "n": n, "nnz": z, "systems": len(vals),
+                       "k": spec.k, "cycle_s": spec.cycle_s, "tol": spec.tol,
+                       "recycle": "update from every system (harmonic Ritz), in force from the next"},
+            **res,
+            "recycled_over_plain_fp64": round(rec["solves_per_s"] / pl["solves_per_s"], 4),
+            "matvecs_recycled_over_plain_fp64": round((rec["matvecs"] + rec["matvecs_setup"]) / pl["matvecs"], 4),
+            "roofline": {"bound": "hbm", "kernel": f"P{dom + 1}", "achieved": round(gbs, 1), "peak": peaks["hbm_gbs"],
+                         "unit": "GB/s", "frac": round(gbs / peaks["hbm_gbs"], 4), "k_used": k_used,
+                         "passes_ms": [round(v, 5) for v in ms_pass], "passes_bytes": pb,
+                         "iteration": {"ms": round(it_ms, 5),
+                                       "frac": round(sum(pb) / (it_ms * 1e-3) / 1e9 / peaks["hbm_gbs"], 4)}},
+            "generation_s": round(t_gen, 1)}
+
+
+def run_gram_only(args):
+    """The recycle update's Gram step, G = Z^T Z and H = Z^T W for W = [Y, P, S],
+    Z = [AY, AP, AS] (FP32 columns, k + 2 s of each), on seeded random blocks of
+    the benchmark's sizes: device time of each kernel (CUDA events around the
+    kernels, median of 10 after 3 warm-up calls) and its rooflines.  Algorithmic
+    bytes: every column read once.  Useful flops: 2 n (m (m + 1) / 2 + m^2); the
+    tensor-core kernel computes 3 TF32 products of a 128 x R tile per 8 rows."""
+    import numpy as np
+    import torch
+
+    from paper_1406_2831_gb300 import rbicgstab as rb
+    n = args.N ** 3
+    ld = (n + 31) // 32 * 32
+    k, s_ = args.k, 25
+    gen = torch.Generator(device="cuda").manual_seed(0)
+    blocks = [torch.randn((c, ld), device="cuda", generator=gen, dtype=torch.float32) for c in (k, k, s_, s_, s_, s_)]
+    m = k + 2 * s_
+    byt = 2 * m * n * 4
+    useful = 2.0 * n * (m * (m + 1) / 2 + m * m)
+    r8 = lambda c: (c + 7) // 8 * 8
+    R = max(128, 2 * (r8(k) + 2 * r8(s_)))
+    tensor_flops = 3 * 2.0 * 128 * R * ((n + 31) // 32 * 32)
+    peaks = measured_peaks()
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            bf16 = float(json.load(f)["bf16_tflops"])
+        tf32_src = "measured bf16 x 1.1 / 2.25 (nominal TF32 / BF16 dense)"
+    except Exception:
+        bf16, tf32_src = 1900.0, "fallback bf16 x 1.1 / 2.25"
+    tf32 = bf16 * 1.1 / 2.25
+    out = {"metric": "recycle-update Gram device time", "n": n, "m": m, "k": k, "s": s_, "bytes": byt}
+    for path in ("tensor", "cudacore"):
+        for _ in range(3):
+            rb.update_gram_n(n, *blocks, kcap=k, scap=s_, path=path, timing=True)
+        ms = sorted(rb.update_gram_n(n, *blocks, kcap=k, scap=s_, path=path, timing=True)[2] for _ in range(10))
+        t = ms[len(ms) // 2]
+        gbs = byt / (t * 1e-3) / 1e9
+        ent = {"ms": round(t, 4), "GB/s": round(gbs, 1), "hbm_frac": round(gbs / peaks["hbm_gbs"], 4),
+               "useful_TFLOP/s": round(useful / (t * 1e-3) / 1e12, 2)}
+        if path == "tensor":
+            tt = tensor_flops / (t * 1e-3) / 1e12
+            ent.update({"tensor_TFLOP/s": round(tt, 1), "tf32_peak": round(tf32, 1), "tf32_frac": round(tt / tf32, 4),
+                        "tf32_peak_source": tf32_src})
+        out[path] = ent
     return out
 
 
@@ -785,6 +1023,12 @@ def main():
         line = run_rbicg(args)
     elif args.passes_only:
         line = run_passes_only(args)
+    elif args.gram_only:
+        line = run_gram_only(args)
+    elif args.large:
+        line = run_large(args)
+    elif args.adjoint:
+        line = run_adjoint(args)
     else:
         line = run_reference(args) if args.impl == "reference" else run_ours(args)
     if line is not None:

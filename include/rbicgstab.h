@@ -269,17 +269,19 @@ int rbicgstab_residual_noalloc(int64_t n, const int32_t* row_ptr, const int32_t*
  * r8 = round up to 8), else the CUDA-core kernel; RB_GRAM_CUDACORE forces
  * the latter, RB_GRAM_TENSOR the former (RB_EINVAL if it does not fit).
  * This is the kernel the solver runs between cycles; the entry point exists
- * so that it can be checked on its own.  It allocates its own scratch, runs
- * on cuda_stream and synchronises it.  Errors: RB_EINVAL (arguments,
- * m > 90), RB_ENOMEM, RB_ECUDA, RB_ETIMEOUT (a bounded device wait of the
- * tensor-core kernel expired; outputs undefined). */
+ * so that it can be checked and timed on its own.  It allocates its own
+ * scratch, runs on cuda_stream and synchronises it.  ms_kernel (may be NULL)
+ * receives the device time of the Gram kernels alone (CUDA events on
+ * cuda_stream around them, scratch allocation excluded).  Errors: RB_EINVAL
+ * (arguments, m > 90), RB_ENOMEM, RB_ECUDA, RB_ETIMEOUT (a bounded device
+ * wait of the tensor-core kernel expired; outputs undefined). */
 #define RB_GRAM_AUTO     0
 #define RB_GRAM_CUDACORE 1
 #define RB_GRAM_TENSOR   2
 int rbicgstab_update_gram(int64_t n, int64_t ld, int32_t ky, int32_t nit, int32_t ns, int32_t kcap,
                           int32_t scap, const float* Y, const float* AY, const float* P, const float* AP,
                           const float* S, const float* AS, double* G, double* H, int32_t path,
-                          void* cuda_stream);
+                          void* cuda_stream, double* ms_kernel);
 
 /* Layout statistics of the current matrix A on the device (SELL-32, slices of
  * 32 rows): the number of slices and of stencil slices, those whose rows use

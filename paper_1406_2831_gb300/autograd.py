@@ -23,7 +23,7 @@ from . import rbicgstab as rb
 
 class RecycledSolve(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, values, b, solver):
+    def forward(ctx, values, b, solver, checkpoint=False):
         values = values.detach().contiguous()
         b = b.detach().contiguous()
         solver.set_values(values)
@@ -33,12 +33,16 @@ class RecycledSolve(torch.autograd.Function):
         x = res.x
         ctx.solver = solver
         ctx.version = solver.values_version
-        ctx.save_for_backward(values, b, x)
+        ctx.checkpoint = checkpoint
+        # checkpointing: x is not kept; backward solves for it again (one
+        # more forward solve in exchange for n values of memory per step)
+        ctx.save_for_backward(values, b, *(() if checkpoint else (x,)))
         return x
 
     @staticmethod
     def backward(ctx, gx):
-        values, b, x = ctx.saved_tensors
+        saved = ctx.saved_tensors
+        values, b = saved[0], saved[1]
         s = ctx.solver
         if s.values_version != ctx.version:   # the solver moved on: put this step's matrix back
             s.set_values(values)
@@ -46,12 +50,21 @@ class RecycledSolve(torch.autograd.Function):
         if dual.stats["status"] != rb.RB_OK:
             raise RuntimeError(f"dual solve: {rb.error_string(dual.stats['status'])}")
         lam = dual.x
+        if ctx.checkpoint:
+            res = s.solve(b)
+            if res.stats["status"] != rb.RB_OK:
+                raise RuntimeError(f"recomputed forward solve: {rb.error_string(res.stats['status'])}")
+            x = res.x
+        else:
+            x = saved[2]
         gvals = s.pattern_outer(lam, x, -1.0) if ctx.needs_input_grad[0] else None
         gb = lam if ctx.needs_input_grad[1] else None
-        return gvals, gb, None
+        return gvals, gb, None, None
 
 
-def solve(solver: rb.Solver, values: torch.Tensor, b: torch.Tensor) -> torch.Tensor:
+def solve(solver: rb.Solver, values: torch.Tensor, b: torch.Tensor, checkpoint: bool = False) -> torch.Tensor:
     """x with A(values) x = b, differentiable in values and b (CUDA float64
-    tensors; the solver holds the pattern from ``set_matrix``)."""
-    return RecycledSolve.apply(values, b, solver)
+    tensors; the solver holds the pattern from ``set_matrix``).  With
+    ``checkpoint`` the solution is not stored for the backward pass but
+    solved for again there (for long sequences of large systems)."""
+    return RecycledSolve.apply(values, b, solver, checkpoint)

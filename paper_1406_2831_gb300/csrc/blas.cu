@@ -19,12 +19,17 @@ __global__ void __launch_bounds__(kBlock) k_dots(DotArgs d, int64_t npad, IterSt
   double acc[NV];
 #pragma unroll
   for (int v = 0; v < NV; ++v) acc[v] = 0.0;
+  const double* __restrict__ Mp = d.M;
+  const int km = d.km;
   for (int64_t i = gtid(); i < npad; i += gstride()) {
-    if (d.M) {
-      const double vi = d.v[i];
+    if (Mp) {
+      // every column load of the row is issued before the first FMA
+      const double vi = __ldg(d.v + i);
+      double mv[KMAX > 0 ? KMAX : 1];
 #pragma unroll
-      for (int j = 0; j < KMAX; ++j)
-        if (j < d.km) acc[j] = fma(d.M[j * d.ld + i], vi, acc[j]);
+      for (int j = 0; j < KMAX; ++j) mv[j] = j < km ? __ldg(Mp + j * d.ld + i) : 0.0;
+#pragma unroll
+      for (int j = 0; j < KMAX; ++j) acc[j] = fma(mv[j], vi, acc[j]);
     }
 #pragma unroll
     for (int q = 0; q < 4; ++q)
@@ -115,32 +120,48 @@ __global__ void __launch_bounds__(kBlock) k_gemm_cols(T* const* __restrict__ out
   for (int j = threadIdx.x; j < m; j += blockDim.x) sX[j] = X[j];
   __syncthreads();
   constexpr int JB = 8;   // column loads issued together
-  for (int64_t i = gtid(); i < npad; i += gstride()) {
-    if constexpr (std::is_same<T, float>::value) {
-      // pairs of output columns on packed FMAs (each lane rounded as fma_t)
-      using P = Pair<float>;
-      float2 acc[KC / 2];
+  if constexpr (std::is_same<T, float>::value) {
+    // two consecutive rows per thread (8-byte loads); each 16-byte broadcast
+    // of four coefficients serves both rows on packed FMAs (each lane rounded
+    // as fma_t, the columns summed in order j = 0, 1, ..: the products of the
+    // one-row form, bit for bit)
+    static_assert(KC % 4 == 0, "KC must be a multiple of 4");
+    using P = Pair<float>;
+    const int64_t nrow2 = npad / 2;
+    for (int64_t i2 = gtid(); i2 < nrow2; i2 += gstride()) {
+      const int64_t i = 2 * i2;
+      float2 a0[KC / 2], a1[KC / 2];
 #pragma unroll
-      for (int c = 0; c < KC / 2; ++c) acc[c] = make_float2(0.0f, 0.0f);
+      for (int c = 0; c < KC / 2; ++c) a0[c] = a1[c] = make_float2(0.0f, 0.0f);
       for (int j0 = 0; j0 < m; j0 += JB) {
-        float xv[JB];
+        float2 xv[JB];
 #pragma unroll
-        for (int u = 0; u < JB; ++u) xv[u] = (j0 + u < m) ? __ldg(sX[j0 + u] + i) : 0.0f;
+        for (int u = 0; u < JB; ++u)
+          xv[u] = (j0 + u < m) ? __ldg(reinterpret_cast<const float2*>(sX[j0 + u] + i)) : make_float2(0.f, 0.f);
 #pragma unroll
         for (int u = 0; u < JB; ++u) {
           if (j0 + u >= m) break;
-          const float2* rj = reinterpret_cast<const float2*>(sR + (size_t)(j0 + u) * KC);
-          const float2 xx = P::mk(xv[u], xv[u]);
+          const float4* rj = reinterpret_cast<const float4*>(sR + (size_t)(j0 + u) * KC);
+          const float2 x0 = P::mk(xv[u].x, xv[u].x), x1 = P::mk(xv[u].y, xv[u].y);
 #pragma unroll
-          for (int c = 0; c < KC / 2; ++c) acc[c] = P::fma(xx, rj[c], acc[c]);
+          for (int c4 = 0; c4 < KC / 4; ++c4) {
+            const float4 r = rj[c4];
+            const float2 rlo = make_float2(r.x, r.y), rhi = make_float2(r.z, r.w);
+            a0[2 * c4] = P::fma(x0, rlo, a0[2 * c4]);
+            a0[2 * c4 + 1] = P::fma(x0, rhi, a0[2 * c4 + 1]);
+            a1[2 * c4] = P::fma(x1, rlo, a1[2 * c4]);
+            a1[2 * c4 + 1] = P::fma(x1, rhi, a1[2 * c4 + 1]);
+          }
         }
       }
 #pragma unroll
       for (int c = 0; c < KC / 2; ++c) {
-        if (2 * c < kc) out[2 * c][i] = acc[c].x;
-        if (2 * c + 1 < kc) out[2 * c + 1][i] = acc[c].y;
+        if (2 * c < kc) *reinterpret_cast<float2*>(out[2 * c] + i) = make_float2(a0[c].x, a1[c].x);
+        if (2 * c + 1 < kc) *reinterpret_cast<float2*>(out[2 * c + 1] + i) = make_float2(a0[c].y, a1[c].y);
       }
-    } else {
+    }
+  } else {
+    for (int64_t i = gtid(); i < npad; i += gstride()) {
       T acc[KC];
 #pragma unroll
       for (int c = 0; c < KC; ++c) acc[c] = T(0);

@@ -401,6 +401,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 // order.
 __global__ void k_gram_tc_reduce(const float* __restrict__ work, int nblk, int zrows, int R, int m,
                                  const GramTcPos pos, double* __restrict__ G, double* __restrict__ H) {
+  // entries of one output row a (b fastest) are consecutive tile columns
+  // for most b, so a warp's reads of one CTA partial coalesce; the loads of
+  // 8 CTAs are issued before their (in-order) additions
   const int tot = 2 * m * m;
   for (int o = blockIdx.x * blockDim.x + threadIdx.x; o < tot; o += gridDim.x * blockDim.x) {
     const int a = o / (2 * m), b = o % (2 * m);
@@ -414,7 +417,17 @@ __global__ void k_gram_tc_reduce(const float* __restrict__ work, int nblk, int z
       pc = pos.w[b - m];
     }
     double sum = 0.0;
-    for (int c = 0; c < nblk; ++c) sum += (double)work[((size_t)c * zrows + pr) * R + pc];
+    const size_t stride = (size_t)zrows * R;
+    const float* w = work + (size_t)pr * R + pc;
+    int c = 0;
+    for (; c + 8 <= nblk; c += 8) {
+      float v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = __ldg(w + (size_t)(c + u) * stride);
+#pragma unroll
+      for (int u = 0; u < 8; ++u) sum += (double)v[u];
+    }
+    for (; c < nblk; ++c) sum += (double)__ldg(w + (size_t)c * stride);
     if (b < m) {
       G[a + (size_t)b * m] = sum;
       G[b + (size_t)a * m] = sum;

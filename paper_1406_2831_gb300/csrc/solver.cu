@@ -1531,7 +1531,7 @@ extern "C" int rbicgstab_pattern_outer(rb_handle h, const double* u, const doubl
 extern "C" int rbicgstab_update_gram(int64_t n, int64_t ld, int32_t ky, int32_t nit, int32_t ns, int32_t kcap,
                                      int32_t scap, const float* Y, const float* AY, const float* P,
                                      const float* AP, const float* S, const float* AS, double* G, double* H,
-                                     int32_t path, void* cuda_stream) {
+                                     int32_t path, void* cuda_stream, double* ms_kernel) {
   using namespace rb;
   const int m = ky + nit + ns;
   if (n <= 0 || ld < n || ld % 4 != 0 || ky < 0 || nit < 0 || ns < 0 || m <= 0 || ky > kcap || nit > scap ||
@@ -1552,6 +1552,12 @@ extern "C" int rbicgstab_update_gram(int64_t n, int64_t ld, int32_t ky, int32_t 
   int err = 0;
   double* dGH = dalloc<double>(2 * (int64_t)m * m, &err);
   if (!dGH) return err;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  if (ms_kernel && (cudaEventCreate(&ev0) != cudaSuccess || cudaEventCreate(&ev1) != cudaSuccess)) {
+    if (ev0) cudaEventDestroy(ev0);
+    cudaFree(dGH);
+    return RB_ECUDA;
+  }
   int rc = RB_OK;
   void* work = nullptr;
   int* derr = nullptr;
@@ -1568,7 +1574,9 @@ extern "C" int rbicgstab_update_gram(int64_t n, int64_t ld, int32_t ky, int32_t 
         cudaMemsetAsync(derr, 0, sizeof(int), s) != cudaSuccess) {
       rc = RB_ENOMEM;
     } else {
+      if (ev0) cudaEventRecord(ev0, s);
       rc = gram_tc(blk, n, ld, dGH, dGH + (size_t)m * m, (float*)work, derr, nsm, s);
+      if (ev1) cudaEventRecord(ev1, s);
       int herr = 0;
       if (rc == RB_OK && (cudaMemcpyAsync(&herr, derr, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
                           cudaStreamSynchronize(s) != cudaSuccess))
@@ -1587,12 +1595,22 @@ extern "C" int rbicgstab_update_gram(int64_t n, int64_t ld, int32_t ky, int32_t 
         cudaMalloc((void**)&dptr, sizeof(float*) * 2 * m) != cudaSuccess) {
       rc = RB_ENOMEM;
     } else if (cudaMemcpyAsync(dptr, Z.data(), sizeof(float*) * m, cudaMemcpyHostToDevice, s) != cudaSuccess ||
-               cudaMemcpyAsync(dptr + m, W.data(), sizeof(float*) * m, cudaMemcpyHostToDevice, s) != cudaSuccess ||
-               gram_gh<float>(dptr, dptr + m, m, ld, dGH, dGH + (size_t)m * m, (double*)work, grid, s) !=
-                   cudaSuccess) {
+               cudaMemcpyAsync(dptr + m, W.data(), sizeof(float*) * m, cudaMemcpyHostToDevice, s) != cudaSuccess) {
       rc = RB_ECUDA;
+    } else {
+      if (ev0) cudaEventRecord(ev0, s);
+      if (gram_gh<float>(dptr, dptr + m, m, ld, dGH, dGH + (size_t)m * m, (double*)work, grid, s) != cudaSuccess)
+        rc = RB_ECUDA;
+      if (ev1) cudaEventRecord(ev1, s);
     }
   }
+  if (rc == RB_OK && ms_kernel) {
+    float ms = 0.f;
+    if (cudaEventSynchronize(ev1) != cudaSuccess || cudaEventElapsedTime(&ms, ev0, ev1) != cudaSuccess) rc = RB_ECUDA;
+    *ms_kernel = ms;
+  }
+  if (ev0) cudaEventDestroy(ev0);
+  if (ev1) cudaEventDestroy(ev1);
   if (rc == RB_OK &&
       (cudaMemcpyAsync(G, dGH, sizeof(double) * m * m, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
        cudaMemcpyAsync(H, dGH + (size_t)m * m, sizeof(double) * m * m, cudaMemcpyDeviceToHost, s) != cudaSuccess ||

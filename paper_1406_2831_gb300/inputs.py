@@ -153,12 +153,24 @@ def conv_diff_3d(N: int, c, kappa=None) -> CSR:
 
 def stencil27_noisy(Nx: int, Ny: int, Nz: int, c: float, seed: int = 5,
                     noise: float = 0.1) -> CSR:
-    """27-point operator: diffusion centre 26, neighbours -1; upwind convection
-    c on the 6 face neighbours; every nonzero times (1 + noise U[-1, 1]).
+    """27-point convection-diffusion operator with noisy coefficients.
+
+    Couplings: -1 to each of the 26 neighbours (diffusion), and -c h more to
+    the three upwind face neighbours (first-order upwind convection c(1,1,1)
+    with c > 0); every coupling is multiplied by (1 + noise U[-1, 1]), one
+    draw per (row, neighbour), so the operator is non-symmetric.  The
+    diagonal is the sum of the magnitudes of all 26 couplings of its row,
+    those to neighbours outside the grid included (a conservative
+    discretisation with homogeneous Dirichlet boundaries): interior row sums
+    vanish, boundary rows are strictly dominant, so A is an irreducibly
+    diagonally dominant M-matrix for any noise below 1.  Multiplying the
+    diagonal by noise of its own as well would leave random row sums of
+    order noise * 26 against a smallest eigenvalue of order h^2, which makes
+    large grids indefinite.
 
     h = 1/(max(Nx,Ny,Nz)+1); h^2-scaled.  The noise draw is fixed by ``seed``
-    and independent of ``c``, so a drifting ``c`` changes only the convection
-    part.
+    and independent of ``c``, and every entry is linear in ``c``, so a
+    drifting ``c`` changes only the centre and the upwind face entries.
     """
     h = 1.0 / (max(Nx, Ny, Nz) + 1)
     n = Nx * Ny * Nz
@@ -166,27 +178,31 @@ def stencil27_noisy(Nx: int, Ny: int, Nz: int, c: float, seed: int = 5,
     i = idx % Nx
     j = (idx // Nx) % Ny
     l = idx // (Nx * Ny)
+    rng = np.random.default_rng(seed)
+    eta = 1.0 + noise * rng.uniform(-1.0, 1.0, size=(n, 27))
     cols = np.full((n, 27), -1, dtype=np.int64)
     vals = np.zeros((n, 27))
+    diag = np.zeros(n)
+    centre = -1
     slot = 0
     for dz in (-1, 0, 1):
         for dy in (-1, 0, 1):
             for dx in (-1, 0, 1):
+                off = dx + dy * Nx + dz * Nx * Ny
+                if off == 0:
+                    centre = slot
+                    slot += 1
+                    continue
+                face = abs(dx) + abs(dy) + abs(dz) == 1
+                w = (-1.0 - (c * h if (face and off < 0) else 0.0)) * eta[:, slot]
+                diag -= w
                 m = ((i + dx >= 0) & (i + dx < Nx) & (j + dy >= 0) & (j + dy < Ny)
                      & (l + dz >= 0) & (l + dz < Nz))
-                off = dx + dy * Nx + dz * Nx * Ny
                 cols[m, slot] = idx[m] + off
-                if off == 0:
-                    vals[m, slot] = 26.0 + 3.0 * c * h
-                else:
-                    face = abs(dx) + abs(dy) + abs(dz) == 1
-                    w = -1.0
-                    if face and off < 0:
-                        w -= c * h
-                    vals[m, slot] = w
+                vals[m, slot] = w[m]
                 slot += 1
-    rng = np.random.default_rng(seed)
-    vals *= 1.0 + noise * rng.uniform(-1.0, 1.0, size=vals.shape)
+    cols[:, centre] = idx
+    vals[:, centre] = diag
     return _assemble(n, cols, vals)
 
 

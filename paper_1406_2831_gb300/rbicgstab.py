@@ -93,7 +93,8 @@ def lib():
     L.rbicg_solve.argtypes = [vp, dp, dp, dp, dp, ctypes.c_int, ctypes.POINTER(Stats), ctypes.POINTER(Stats)]
     L.rbicgstab_residual_noalloc.argtypes = [i64, dp, dp, dp, dp, dp, dp, dp, vp]
     L.rbicgstab_residual_noalloc.restype = ctypes.c_int
-    L.rbicgstab_update_gram.argtypes = [i64, i64, i32, i32, i32, i32, i32, dp, dp, dp, dp, dp, dp, dp, dp, i32, vp]
+    L.rbicgstab_update_gram.argtypes = [i64, i64, i32, i32, i32, i32, i32, dp, dp, dp, dp, dp, dp, dp, dp, i32, vp,
+                                        ctypes.POINTER(ctypes.c_double)]
     L.rbicgstab_update_gram.restype = ctypes.c_int
     L.rbicgstab_sell_stats.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64)]
     L.rbicgstab_sell_stats.restype = ctypes.c_int
@@ -424,8 +425,10 @@ def update_gram(Y, AY, P, AP, S, AS, kcap: int, scap: int, path: str = "auto", s
     return update_gram_n(ld, Y, AY, P, AP, S, AS, kcap, scap, path, stream)
 
 
-def update_gram_n(n: int, Y, AY, P, AP, S, AS, kcap: int, scap: int, path: str = "auto", stream=None):
-    """update_gram with the vector length n <= ld given explicitly."""
+def update_gram_n(n: int, Y, AY, P, AP, S, AS, kcap: int, scap: int, path: str = "auto", stream=None,
+                  timing: bool = False):
+    """update_gram with the vector length n <= ld given explicitly.  With
+    ``timing`` returns (G, H, ms) where ms is the Gram kernels' device time."""
     ld = Y.shape[1]
     ky, nit, ns = Y.shape[0], P.shape[0], S.shape[0]
     if AY.shape[0] != ky or AP.shape[0] != nit or AS.shape[0] != ns:
@@ -435,10 +438,12 @@ def update_gram_n(n: int, Y, AY, P, AP, S, AS, kcap: int, scap: int, path: str =
     H = np.zeros((m, m), order="F")
     sp = None if stream is None else (stream if isinstance(stream, int) else stream.cuda_stream)
     ptr = lambda t: t.data_ptr() if t.numel() else None
+    ms = ctypes.c_double(0.0)
     _check(lib().rbicgstab_update_gram(int(n), int(ld), ky, nit, ns, int(kcap), int(scap), ptr(Y), ptr(AY),
                                        ptr(P), ptr(AP), ptr(S), ptr(AS), G.ctypes.data, H.ctypes.data,
-                                       GRAM_PATH[path], sp), "rbicgstab_update_gram")
-    return G, H
+                                       GRAM_PATH[path], sp, ctypes.byref(ms) if timing else None),
+           "rbicgstab_update_gram")
+    return (G, H, ms.value) if timing else (G, H)
 
 
 def kernel_launches() -> int:

@@ -76,3 +76,21 @@ def test_backward_restores_the_forward_matrix():
     x = np.linalg.solve(M, b.numpy())
     want = -lam[s.rows] * x[A.col]
     assert np.allclose(v0.grad.numpy(), want, rtol=1e-12, atol=1e-14)
+
+
+def test_checkpointing_recomputes_x_with_the_same_gradient():
+    """With checkpoint=True the forward keeps no solution; backward solves
+    for it again (after the dual solve) and returns the same gradients."""
+    A = inputs.conv_diff_2d(5, 3.0)
+    b0 = torch.from_numpy(inputs.gaussian_rhs(A.n, 1))
+    grads = []
+    for ck in (False, True):
+        s = DenseStandIn(A)
+        vals = torch.from_numpy(A.val.copy()).requires_grad_(True)
+        b = b0.clone().requires_grad_(True)
+        x = rag.solve(s, vals, b, checkpoint=ck)
+        (x.square().sum()).backward()
+        grads.append((vals.grad.clone(), b.grad.clone()))
+        assert s.log.count("solve_dual") == 1
+    assert torch.allclose(grads[0][0], grads[1][0], rtol=1e-12, atol=0)
+    assert torch.allclose(grads[0][1], grads[1][1], rtol=1e-12, atol=0)

@@ -325,3 +325,33 @@ def test_block_mixed_full_size_against_tight_reference():
           f"iters gpu {res.stats[0]['iters']} oracle {io.iters}")
     assert e_gpu <= max(2.0 * e_ora, 1e-7), (e_gpu, e_ora)
     assert 0.9 * io.iters <= res.stats[0]["iters"] <= 1.6 * io.iters, (res.stats[0]["iters"], io.iters)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("nrhs", [1, 4])
+def test_27pt_k30_against_dense_lu(precision, nrhs):
+    """The large workload's kernels at a size dense LU can check: the noisy
+    27-point operator (17 x 15 x 13, n = 3315 = 103 slices + 19 rows), k = 30
+    (the 32-column bucket), one right-hand side and a block of four.  Every
+    solution is as close to the exact one as the FP64 oracle's with the same
+    space (within 2x), or within 1e-7."""
+    import scipy.linalg as sla
+    A = inputs.stencil27_noisy(17, 15, 13, 10.0)
+    S = A.to_scipy()
+    D = S.toarray()
+    U = inputs.random_recycle_basis(A.n, 30, 31)
+    B = _rhs_block(A.n, nrhs, seed0=90)
+    s = _solver(A, precision=precision, recycle="fixed", k_max=30, tol=1e-8)
+    s.set_recycle(U)
+    res = s.solve_block(B) if nrhs > 1 else s.solve(B[0])
+    stats = res.stats if nrhs > 1 else [res.stats]
+    X = res.x if nrhs > 1 else [res.x]
+    rec = orb.recycle_setup(S, U)
+    for i in range(nrhs):
+        assert stats[i]["status"] == rb.RB_OK, stats[i]
+        assert stats[i]["k_used"] == 30
+        xstar = sla.solve(D, B[i])
+        xo, io = orb.rbicgstab(S, B[i], rec, tol=1e-8)
+        assert _rel(X[i], xstar) <= max(2.0 * _rel(xo, xstar), 1e-7), (i, _rel(X[i], xstar), _rel(xo, xstar))
+        if precision == "fp64":
+            assert _iters_close(stats[i]["iters"], io.iters), (i, stats[i]["iters"], io.iters)

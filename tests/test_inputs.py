@@ -58,3 +58,24 @@ def test_large_27pt_sequence_structure():
     Q = inputs.config_large_27pt(5, 4, 3, n_systems=1).pattern()
     assert Q.nnz == (3 * 5 - 2) * (3 * 4 - 2) * (3 * 3 - 2)
 
+
+
+def test_stencil27_noisy_is_a_diagonally_dominant_m_matrix():
+    """Off-diagonal couplings negative, interior row sums zero, boundary rows
+    strictly dominant, non-symmetric; the oracle's BiCGSTAB solves it."""
+    import scipy.sparse as sp
+    from oracle import bicgstab as obs
+    A = inputs.stencil27_noisy(9, 8, 7, 10.0)
+    S = A.to_scipy()
+    d = S.diagonal()
+    off = S - sp.diags(d)
+    assert off.max() <= 0.0 and d.min() > 0
+    rowsum = np.asarray(S.sum(axis=1)).ravel()
+    interior = np.array([(r % 9 not in (0, 8)) and ((r // 9) % 8 not in (0, 7)) and (r // 72 not in (0, 6))
+                         for r in range(A.n)])
+    assert np.abs(rowsum[interior]).max() <= 1e-12 * d.max()
+    assert rowsum[~interior].min() > 0.1
+    assert abs(S - S.T).max() > 0.01
+    b = inputs.gaussian_rhs(A.n, 3)
+    x, info = obs.bicgstab(S, b, tol=1e-10)
+    assert np.linalg.norm(b - S @ x) <= 1e-9 * np.linalg.norm(b)
