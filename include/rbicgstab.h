@@ -255,6 +255,36 @@ int rbicgstab_residual_noalloc(int64_t n, const int32_t* row_ptr, const int32_t*
                                const double* val, const double* x, const double* b, double* r,
                                double* rnorm2, void* cuda_stream);
 
+/* The dual system A^T lam = g (the dual system of Sec. 2, real arithmetic):
+ * Alg. 2 on A^T with the recycle space's roles swapped, right space U~ and
+ * left space U, which reuses the products C~ = A^T U~ and C = A U of the
+ * setup (Sec. 3).  This is the adjoint solve of a gradient: for
+ * L(x(b, A)), lam = A^-T dL/dx gives dL/db = lam and dL/dA_ij = -lam_i x_j.
+ * FP64 and with the space held fixed, whatever the handle's precision and
+ * recycle mode.  g, lam: n doubles on RB_HOST or RB_DEVICE; lam holds the
+ * initial guess on entry and the solution on return; st as for
+ * rbicgstab_solve.  Errors as for rbicgstab_solve. */
+int rbicgstab_solve_adjoint(rb_handle h, const double* g, double* lam, int where, rb_stats* st);
+
+/* Recycled BiCGstab(l) (Sleijpen and Fokkema, 1993): the breakdown-robust
+ * variant of Alg. 2 behind the paper's remark on omega = 0 (Sec. 4) and its
+ * outlook (Sec. 7).  The iteration runs on the projected operator
+ * (I - C C-hat^T) A of Sec. 3 from the start of eq. (3.5) with the handle's
+ * current recycle space held fixed (no update, whatever the recycle mode);
+ * each outer step takes l BiCG steps and then minimises the residual over
+ * l directions, so the stabilising polynomial no longer has to take
+ * BiCGSTAB's degree-1 steps (whose omega collapses on nearly skew
+ * operators).  l = 1 is mathematically Alg. 2.  FP64 throughout, whatever
+ * the handle's precision.  b, x: n doubles on RB_HOST or RB_DEVICE; x holds
+ * x_{-1} on entry and the solution on return.  st (may be NULL): iters =
+ * BiCG steps (l per outer step), outer = outer steps, matvecs, relres of the
+ * recursive and the true residual.  Converged when ||r|| <= tol ||b|| after
+ * an outer step.  Returns RB_OK, RB_ENOTCONV (max_itn BiCG steps),
+ * RB_EBREAKDOWN_RHO ((r~_0, r_j) or (r~_0, u_{j+1}) = 0),
+ * RB_EBREAKDOWN_OMEGA (rank-deficient residual block or omega = 0),
+ * RB_ENONFINITE, RB_EINVAL (l outside 1..8), RB_EDIM, RB_ECUDA. */
+int rbicgstab_solve_l(rb_handle h, int32_t ell, const double* b, double* x, int where, rb_stats* st);
+
 /* Gram step of the recycle update (the harmonic-Ritz update after each cycle,
  * Sec. 6.2; the selection rule is the harmonic-Ritz reading of that update):
  * G = Z^T Z and H = Z^T W for the FP32 column blocks of the mixed path,

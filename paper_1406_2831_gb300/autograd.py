@@ -4,9 +4,9 @@ The values of A (on the pattern given to ``Solver.set_matrix``) and b are the
 differentiable inputs.  Forward: ``set_values`` and one solve (Alg. 2, with
 the handle's recycle space).  Backward, for an upstream gradient g = dL/dx:
 the dual system A^T lam = g (the dual system of Sec. 2, A^* x~ = b~ with
-b~ = g) is solved by ``rbicg_solve`` (Alg. 1 solves a primary system and its
-dual together; the primary is the forward system again), with the recycle
-space's left half U~ serving the dual; then
+b~ = g) is solved by ``rbicgstab_solve_adjoint`` (Alg. 2 on A^T with the
+recycle space's roles swapped: the left space U~ serves as the dual's right
+space, reusing the setup's products); then
 
     dL/db = lam,    dL/dA_ij = -lam_i x_j   (``rbicgstab_pattern_outer``).
 
@@ -46,7 +46,7 @@ class RecycledSolve(torch.autograd.Function):
         s = ctx.solver
         if s.values_version != ctx.version:   # the solver moved on: put this step's matrix back
             s.set_values(values)
-        _, dual = s.solve_dual(b, gx.detach().contiguous())
+        dual = s.solve_adjoint(gx.detach().contiguous())
         if dual.stats["status"] != rb.RB_OK:
             raise RuntimeError(f"dual solve: {rb.error_string(dual.stats['status'])}")
         lam = dual.x

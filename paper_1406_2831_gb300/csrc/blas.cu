@@ -82,6 +82,21 @@ cudaError_t gemv_update(double* y, const double* M, int64_t ld, int k, const dou
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------- y = a y + sum_t c_t x_t
+__global__ void k_lincomb(double* __restrict__ y, double a, LinComb lc, int64_t npad) {
+  for (int64_t i = gtid(); i < npad; i += gstride()) {
+    double acc = a == 0.0 ? 0.0 : a * y[i];
+    for (int t = 0; t < lc.nx; ++t) acc = fma(lc.c[t], lc.x[t][i], acc);
+    y[i] = acc;
+  }
+}
+
+cudaError_t lincomb(double* y, double a, const LinComb& lc, int64_t npad, int grid, cudaStream_t s) {
+  count_launches(1);
+  k_lincomb<<<grid, kBlock, 0, s>>>(y, a, lc, npad);
+  return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------- pattern outer product
 // out[e] = scale * u[i] * v[col[e]] for every entry e of row i of a CSR
 // pattern (one thread per row; rows of stencil operators are short).

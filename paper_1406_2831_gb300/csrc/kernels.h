@@ -132,6 +132,14 @@ struct DotArgs {
 };
 cudaError_t dots(const DotArgs& d, int64_t npad, IterState* st, double* partials, int grid,
                  cudaStream_t s);
+// y = a y + sum_{t < nx} c[t] x[t] (FP64, rows < npad; a = 0 ignores y's
+// old contents).  x[t] may alias y only as x[t] == y.
+struct LinComb {
+  const double* x[4];
+  double c[4];
+  int nx;
+};
+cudaError_t lincomb(double* y, double a, const LinComb& lc, int64_t npad, int grid, cudaStream_t s);
 // out[e] = scale * u[i] * v[ci[e]] over the entries e of each row i of the
 // CSR pattern (rp, ci) with n rows (device arrays; out in CSR order).
 cudaError_t pattern_outer(int64_t n, const int32_t* rp, const int32_t* ci, const double* u, const double* v,

@@ -126,6 +126,8 @@ struct rb_ctx {
   int64_t partials_cap = 0;
   int* dflag = nullptr;
   int* tcerr = nullptr;   // bounded-wait failures of the tensor-core Gram
+  double* lvec = nullptr;   // BiCGstab(l) work vectors (lvec_cnt columns of npad)
+  int lvec_cnt = 0;
   // cycle store for the recycle update, kBanks banks of cyc vectors each for
   // P, S, QR = A P and TR = A S, of the inner precision (double for RB_FP64,
   // float for RB_MIXED), and the candidate Y, A Y
@@ -1339,7 +1341,7 @@ extern "C" int rbicgstab_destroy(rb_handle h) {
   for (int i = 0; i < h->nslots; ++i) free_slot(h->sl[i]);
   void* ptrs[] = {h->rp, h->ci, h->cv, h->trp, h->tci, h->tsrc, h->tcv, h->U, h->Ut, h->C, h->Ct,
                   h->Chat, h->T1, h->T2, h->Dinv, h->rt0, h->tmp, h->tmp2, h->frt0, h->fU, h->fC, h->fChat,
-                  h->st, h->partials, h->dflag, h->tcerr, h->cstore, h->Yc, h->AYc, h->Yn, h->AYn, h->gwork, h->dG,
+                  h->st, h->partials, h->dflag, h->tcerr, h->lvec, h->cstore, h->Yc, h->AYc, h->Yn, h->AYn, h->gwork, h->dG,
                   h->dR, (void*)h->dptr};
   for (void* p : ptrs) cudaFree(p);
   if (h->hst) cudaFreeHost(h->hst);
@@ -1997,6 +1999,332 @@ extern "C" int rbicg_solve(rb_handle h, const double* b, const double* bt, doubl
     o.relres_rec = nb[i] > 0 ? std::sqrt(h->hst[i].rnorm2 / nb[i]) : 0.0;
     o.relres_true = nb[i] > 0 ? std::sqrt(tr[i] / nb[i]) : 0.0;
     o.ms_total = ms;
+  }
+  return done(status);
+}
+
+// ============================================================ adjoint (dual) solve
+// The dual system A^T lam = g of Sec. 2 by Alg. 2 on A^T with the recycle
+// space's roles swapped: right space U~ (A^T U~ = C~, already formed by the
+// setup) and left space U ((A^T)^T U = C).  With M = C~^T C the dual's
+// M' = C^T C~ = M^T, so its C-hat' = C (M^+) (C-hat = C~ (M^+)^T of the
+// primary): one n x k product; no new products with A.  FP64, the space
+// held fixed.  The call swaps A with A^T and the space blocks in the handle,
+// runs the blocked solve of one right-hand side, and swaps them back (the
+// captured graphs of either orientation are dropped).
+extern "C" int rbicgstab_solve_adjoint(rb_handle h, const double* g, double* lam, int where, rb_stats* st) {
+  using namespace rb;
+  if (!h || !g || !lam || (where != RB_HOST && where != RB_DEVICE)) return RB_EINVAL;
+  if (!h->have_matrix) return RB_EDIM;
+  int rc = ensure_slots(h, 1);
+  if (rc) return rc;
+  int64_t mv_setup = 0;
+  if ((rc = ensure_setup(h, &mv_setup)) < 0) return rc;
+  const int k = h->k;
+  if (k > 0) {   // T1 = C Mpt^T = C (M^+)
+    std::vector<double> MptT((size_t)k * k);
+    for (int r = 0; r < k; ++r)
+      for (int c = 0; c < k; ++c) MptT[r + (size_t)c * k] = h->Mpt[c + (size_t)r * k];
+    std::vector<double*> out;
+    std::vector<const double*> src;
+    for (int j = 0; j < k; ++j) {
+      out.push_back(colp(h->T1, h->npad, j));
+      src.push_back(colp(h->C, h->npad, j));
+    }
+    if ((rc = block_gemm<double>(h, out, src, MptT, k))) return rc;
+  }
+  const rb_opts saved = h->o;
+  auto swap_all = [&]() {
+    std::swap(h->A, h->AT);
+    std::swap(h->U, h->Ut);
+    std::swap(h->C, h->Ct);
+    std::swap(h->Chat, h->T1);
+    reset_graphs(h);
+  };
+  h->o.precision = RB_FP64;
+  if (h->o.recycle_mode != RB_RECYCLE_NONE) h->o.recycle_mode = RB_RECYCLE_FIXED;
+  swap_all();
+  rc = rbicgstab_solve_block(h, 1, g, lam, h->n, where, st);
+  swap_all();
+  h->o = saved;
+  if (st) st->matvecs_setup += mv_setup;
+  return rc;
+}
+
+// ============================================================ BiCGstab(l)
+// Recycled BiCGstab(l) (Sleijpen and Fokkema, ETNA 1, 1993) on the projected
+// operator B = (I - C C-hat^T) A of Sec. 3, FP64, with the handle's recycle
+// space held fixed: the breakdown-robust variant behind the omega = 0
+// remark of Sec. 4 and the outlook of Sec. 7.  Each outer step takes l BiCG
+// steps (two products with B each), which keep r_j = B r_{j-1} and
+// u_j = B u_{j-1}, and then minimises ||r_0 - sum_j g_j r_j|| over
+// g in R^l; then x += sum_j g_j r_{j-1}, r_0 -= sum_j g_j r_j,
+// u_0 -= sum_j g_j u_j, omega = g_l.  The minimiser comes from the Gram
+// matrix of the residual block, diagonally scaled, by a Cholesky solve
+// (the same minimiser as modified Gram-Schmidt on the block, up to
+// rounding).  Every product's projection coefficients C-hat^T A v are
+// carried on the host alongside the vectors (x_c of Alg. 2), so the end is
+// x = x_0 + y - U x_c.  Vectors and products run in the library's kernels;
+// the scalars and the k-coefficients are formed on the host between them.
+namespace {
+constexpr int kMaxEll = 8;
+}
+
+extern "C" int rbicgstab_solve_l(rb_handle h, int32_t ell, const double* b, double* x, int where, rb_stats* st) {
+  using namespace rb;
+  if (!h || !b || !x || (where != RB_HOST && where != RB_DEVICE) || ell < 1 || ell > kMaxEll) return RB_EINVAL;
+  if (!h->have_matrix) return RB_EDIM;
+  int rc = ensure_slots(h, 1);
+  if (rc) return rc;
+  int64_t mv_setup = 0;
+  if ((rc = ensure_setup(h, &mv_setup)) < 0) return rc;
+  const int64_t n = h->n, ld = h->npad;
+  const int k = h->k, vg = vec_grid(h);
+  const int nvec = 2 * (ell + 1) + 1;
+  if (h->lvec_cnt < nvec) {
+    cudaFree(h->lvec);
+    h->lvec_cnt = 0;
+    int err = 0;
+    h->lvec = dalloc<double>((int64_t)nvec * ld, &err);
+    if (!h->lvec) return err;
+    h->lvec_cnt = nvec;
+  }
+  auto R = [&](int j) { return h->lvec + (int64_t)j * ld; };
+  auto Uv = [&](int j) { return h->lvec + (int64_t)(ell + 1 + j) * ld; };
+  double* y = h->lvec + (int64_t)(2 * (ell + 1)) * ld;
+  Slot& S0 = h->sl[0];
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  auto done = [&](int code) {
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    return code;
+  };
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return done(RB_ECUDA);
+  cudaEventRecord(e0, h->us);
+  RB_CUDA_TRY(cudaMemsetAsync(h->lvec, 0, sizeof(double) * nvec * ld, h->us));
+  if ((rc = copy_in(S0.b, b, sizeof(double) * n, where, h->us))) return done(rc);
+  if ((rc = copy_in(S0.x, x, sizeof(double) * n, where, h->us))) return done(rc);
+  for (double* v : {S0.b, S0.x}) {
+    int f = 0;
+    RB_CUDA_TRY(check_finite(v, n, h->dflag, h->us));
+    RB_CUDA_TRY(cudaMemcpyAsync(&f, h->dflag, sizeof(int), cudaMemcpyDeviceToHost, h->us));
+    if ((rc = sync(h))) return done(rc);
+    if (f) return done(RB_ENONFINITE);
+  }
+  int64_t mv = 0;
+  auto dot = [&](const double* a, const double* c, double* out) {
+    DotArgs d{};
+    d.nd = 1;
+    d.a[0] = a;
+    d.b[0] = c;
+    return run_dots(h, d, out, 1);
+  };
+  auto lin = [&](double* yv, double a, std::initializer_list<std::pair<const double*, double>> terms) -> int {
+    LinComb lc{};
+    for (auto& t : terms) {
+      lc.x[lc.nx] = t.first;
+      lc.c[lc.nx] = t.second;
+      ++lc.nx;
+    }
+    RB_CUDA_TRY(lincomb(yv, a, lc, ld, vg, h->us));
+    return RB_OK;
+  };
+  // out = B v; z = C-hat^T A v (host)
+  auto Bop = [&](const double* v, double* out, std::vector<double>& z) -> int {
+    RB_CUDA_TRY(spmv<double>(h->A.view(), v, out, 1.0, 0.0, h->grids.spmv, h->us));
+    ++mv;
+    z.assign(k, 0.0);
+    if (k > 0) {
+      DotArgs d{};
+      d.M = h->Chat; d.ld = ld; d.km = k; d.v = out; d.nd = 0;
+      int r2 = run_dots(h, d, z.data(), k);
+      if (r2) return r2;
+      RB_CUDA_TRY(gemv_update(out, h->C, ld, k, h->st[0].red, nullptr, -1.0, h->npad, vg, h->us));
+    }
+    return RB_OK;
+  };
+  double nb = 0.0, nx0 = 0.0;
+  if ((rc = dot(S0.b, S0.b, &nb))) return done(rc);
+  if ((rc = dot(S0.x, S0.x, &nx0))) return done(rc);
+  // eq. (3.5): r_{-1} = b - A x_{-1}; x_0 = x_{-1} + U C-hat^T r_{-1}; r_0 = (I - C C-hat^T) r_{-1}
+  RB_CUDA_TRY(residual_norm(h->A.view(), S0.b, S0.x, R(0), h->npad, h->st, h->partials, h->grids.spmv, h->us));
+  if (nx0 > 0) ++mv;
+  if (k > 0) {
+    DotArgs d{};
+    d.M = h->Chat; d.ld = ld; d.km = k; d.v = R(0); d.nd = 0;
+    RB_CUDA_TRY(dots(d, h->npad, h->st, h->partials, vg, h->us));
+    RB_CUDA_TRY(gemv_update(S0.x, h->U, ld, k, h->st[0].red, nullptr, 1.0, h->npad, vg, h->us));
+    RB_CUDA_TRY(gemv_update(R(0), h->C, ld, k, h->st[0].red, nullptr, -1.0, h->npad, vg, h->us));
+  }
+  // shadow r~_0 = (I - C~ C-check^T) r~_{-1} = r~_{-1} - C-hat (C^T r~_{-1})
+  RB_CUDA_TRY(shadow(h->rt0, n, h->npad, h->o.shadow_seed, h->us));
+  if (k > 0) {
+    DotArgs d{};
+    d.M = h->C; d.ld = ld; d.km = k; d.v = h->rt0; d.nd = 0;
+    RB_CUDA_TRY(dots(d, h->npad, h->st, h->partials, vg, h->us));
+    RB_CUDA_TRY(gemv_update(h->rt0, h->Chat, ld, k, h->st->red, nullptr, -1.0, h->npad, vg, h->us));
+  }
+  const int max_itn = h->o.max_itn > 0 ? h->o.max_itn : (int)std::min<int64_t>(n, 20000);
+  const double thresh2 = h->o.tol * h->o.tol * nb;
+  std::vector<std::vector<double>> zr(ell + 1, std::vector<double>(k, 0.0)), zu(ell + 1, std::vector<double>(k, 0.0));
+  std::vector<double> xc(k, 0.0), z;
+  double rnorm2 = 0.0;
+  if ((rc = dot(R(0), R(0), &rnorm2))) return done(rc);
+  int status = RB_OK, iters = 0, outer = 0;
+  double rho0 = 1.0, alpha = 1.0, omega = 1.0;
+  bool converged = !(rnorm2 > thresh2);
+  while (!converged && status == RB_OK) {
+    if (iters + ell > max_itn) {
+      status = RB_ENOTCONV;
+      break;
+    }
+    rho0 = -omega * rho0;
+    for (int j = 0; j < ell && status == RB_OK; ++j) {
+      double rho1 = 0.0;
+      if ((rc = dot(h->rt0, R(j), &rho1))) return done(rc);
+      if (rho1 == 0.0 || rho0 == 0.0 || !std::isfinite(rho1)) {
+        status = std::isfinite(rho1) ? RB_EBREAKDOWN_RHO : RB_ENONFINITE;
+        break;
+      }
+      const double beta = alpha * rho1 / rho0;
+      rho0 = rho1;
+      for (int i = 0; i <= j; ++i) {
+        if ((rc = lin(Uv(i), -beta, {{R(i), 1.0}}))) return done(rc);
+        if (i >= 1)
+          for (int c = 0; c < k; ++c) zu[i][c] = zr[i][c] - beta * zu[i][c];
+      }
+      if ((rc = Bop(Uv(j), Uv(j + 1), z))) return done(rc);
+      zu[j + 1] = z;
+      double gam = 0.0;
+      if ((rc = dot(h->rt0, Uv(j + 1), &gam))) return done(rc);
+      if (gam == 0.0 || !std::isfinite(gam)) {
+        status = std::isfinite(gam) ? RB_EBREAKDOWN_RHO : RB_ENONFINITE;
+        break;
+      }
+      alpha = rho0 / gam;
+      for (int i = 0; i <= j; ++i) {
+        if ((rc = lin(R(i), 1.0, {{Uv(i + 1), -alpha}}))) return done(rc);
+        if (i >= 1)
+          for (int c = 0; c < k; ++c) zr[i][c] -= alpha * zu[i + 1][c];
+      }
+      if ((rc = Bop(R(j), R(j + 1), z))) return done(rc);
+      zr[j + 1] = z;
+      if ((rc = lin(y, 1.0, {{Uv(0), alpha}}))) return done(rc);
+      for (int c = 0; c < k; ++c) xc[c] += alpha * zu[1][c];
+      ++iters;
+    }
+    if (status != RB_OK) break;
+    // minimal residual over span{r_1..r_l}: Gram matrix G(i, j) = (r_i, r_j)
+    std::vector<double> G((size_t)(ell + 1) * (ell + 1), 0.0);
+    {
+      std::vector<std::pair<int, int>> pairs;
+      for (int i = 0; i <= ell; ++i)
+        for (int j = i; j <= ell; ++j) pairs.push_back({i, j});
+      for (size_t q0 = 0; q0 < pairs.size(); q0 += 4) {
+        DotArgs d{};
+        for (size_t q = q0; q < std::min(pairs.size(), q0 + 4); ++q) {
+          d.a[d.nd] = R(pairs[q].first);
+          d.b[d.nd] = R(pairs[q].second);
+          ++d.nd;
+        }
+        double out4[4];
+        if ((rc = run_dots(h, d, out4, d.nd))) return done(rc);
+        for (int q = 0; q < d.nd; ++q) {
+          const int i = pairs[q0 + q].first, j = pairs[q0 + q].second;
+          G[i + (size_t)j * (ell + 1)] = G[j + (size_t)i * (ell + 1)] = out4[q];
+        }
+      }
+    }
+    // scaled normal equations D G_11 D (D^-1 g) = D G_10, Cholesky
+    std::vector<double> sc(ell + 1, 0.0), L((size_t)ell * ell, 0.0), g(ell + 1, 0.0);
+    bool ok = true;
+    for (int j = 1; j <= ell; ++j) {
+      const double gjj = G[j + (size_t)j * (ell + 1)];
+      if (!(gjj > 0.0) || !std::isfinite(gjj)) ok = false;
+      sc[j] = ok ? 1.0 / std::sqrt(gjj) : 0.0;
+    }
+    for (int j = 0; ok && j < ell; ++j) {
+      for (int i = j; i < ell; ++i) {
+        double v = G[(i + 1) + (size_t)(j + 1) * (ell + 1)] * sc[i + 1] * sc[j + 1];
+        for (int q = 0; q < j; ++q) v -= L[i + (size_t)q * ell] * L[j + (size_t)q * ell];
+        if (i == j) {
+          if (!(v > 1e-28)) {
+            ok = false;
+            break;
+          }
+          L[j + (size_t)j * ell] = std::sqrt(v);
+        } else {
+          L[i + (size_t)j * ell] = v / L[j + (size_t)j * ell];
+        }
+      }
+    }
+    if (!ok) {
+      status = RB_EBREAKDOWN_OMEGA;
+      break;
+    }
+    std::vector<double> w(ell, 0.0);
+    for (int i = 0; i < ell; ++i) {   // L w = D G_10
+      double v = G[(i + 1) + 0] * sc[i + 1];
+      for (int q = 0; q < i; ++q) v -= L[i + (size_t)q * ell] * w[q];
+      w[i] = v / L[i + (size_t)i * ell];
+    }
+    for (int i = ell - 1; i >= 0; --i) {   // L^T (D^-1 g) = w
+      double v = w[i];
+      for (int q = i + 1; q < ell; ++q) v -= L[q + (size_t)i * ell] * w[q];
+      w[i] = v / L[i + (size_t)i * ell];
+    }
+    for (int j = 1; j <= ell; ++j) g[j] = w[j - 1] * sc[j];
+    omega = g[ell];
+    if (omega == 0.0 || !std::isfinite(omega)) {
+      status = std::isfinite(omega) ? RB_EBREAKDOWN_OMEGA : RB_ENONFINITE;
+      break;
+    }
+    // y gains sum_j g_j r_{j-1}; its B-image sum_j g_j r_j has the projection
+    // coefficients sum_j g_j zr[j]
+    for (int j = 1; j <= ell; ++j) {
+      if ((rc = lin(y, 1.0, {{R(j - 1), g[j]}}))) return done(rc);
+      for (int c = 0; c < k; ++c) xc[c] += g[j] * zr[j][c];
+    }
+    for (int j = 1; j <= ell; ++j) {
+      if ((rc = lin(R(0), 1.0, {{R(j), -g[j]}}))) return done(rc);
+      if ((rc = lin(Uv(0), 1.0, {{Uv(j), -g[j]}}))) return done(rc);
+    }
+    ++outer;
+    if ((rc = dot(R(0), R(0), &rnorm2))) return done(rc);
+    if (!std::isfinite(rnorm2)) {
+      status = RB_ENONFINITE;
+      break;
+    }
+    converged = rnorm2 <= thresh2;
+  }
+  // x = x_0 + y - U x_c
+  if ((rc = lin(S0.x, 1.0, {{y, 1.0}}))) return done(rc);
+  if (k > 0) {
+    RB_CUDA_TRY(cudaMemcpyAsync(h->st[0].red, xc.data(), sizeof(double) * k, cudaMemcpyHostToDevice, h->us));
+    RB_CUDA_TRY(gemv_update(S0.x, h->U, ld, k, h->st[0].red, nullptr, -1.0, h->npad, vg, h->us));
+    if ((rc = sync(h))) return done(rc);
+  }
+  RB_CUDA_TRY(residual_norm(h->A.view(), S0.b, S0.x, h->tmp, h->npad, h->st, h->partials, h->grids.spmv, h->us));
+  if ((rc = read_state(h, 1))) return done(rc);
+  const double tr = h->hst[0].red[0];
+  if ((rc = copy_out(x, S0.x, sizeof(double) * n, where, h->us))) return done(rc);
+  cudaEventRecord(e1, h->us);
+  if ((rc = sync(h))) return done(rc);
+  float ms = 0;
+  cudaEventElapsedTime(&ms, e0, e1);
+  if (st) {
+    *st = rb_stats{};
+    st->iters = iters;
+    st->status = status;
+    st->k_used = k;
+    st->seeds_used = 1;
+    st->matvecs = mv;
+    st->matvecs_setup = mv_setup;
+    st->matvecs_check = 1;
+    st->outer = outer;
+    st->relres_rec = nb > 0 ? std::sqrt(rnorm2 / nb) : 0.0;
+    st->relres_true = nb > 0 ? std::sqrt(tr / nb) : 0.0;
+    st->ms_total = ms;
   }
   return done(status);
 }

@@ -97,6 +97,10 @@ def lib():
                                         ctypes.POINTER(ctypes.c_double)]
     L.rbicgstab_update_gram.restype = ctypes.c_int
     L.rbicgstab_sell_stats.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64)]
+    L.rbicgstab_solve_l.argtypes = [vp, i32, dp, dp, ctypes.c_int, ctypes.POINTER(Stats)]
+    L.rbicgstab_solve_adjoint.argtypes = [vp, dp, dp, ctypes.c_int, ctypes.POINTER(Stats)]
+    L.rbicgstab_solve_adjoint.restype = ctypes.c_int
+    L.rbicgstab_solve_l.restype = ctypes.c_int
     L.rbicgstab_sell_stats.restype = ctypes.c_int
     L.rbicgstab_kernel_launches.argtypes = []
     L.rbicgstab_kernel_launches.restype = ctypes.c_longlong
@@ -324,6 +328,54 @@ class Solver:
         _check(lib().rbicg_solve(self._h, bp, btp, xp, xtp, wb, ctypes.byref(st), ctypes.byref(sd)),
                "rbicg_solve")
         return SolveResult(x=x, stats=st.as_dict()), SolveResult(x=xt, stats=sd.as_dict())
+
+    def solve_adjoint(self, g, lam=None) -> SolveResult:
+        """The dual system A^T lam = g by Alg. 2 on A^T with the swapped
+        recycle space (rbicgstab_solve_adjoint); ``lam`` (updated in place when
+        given) is the initial guess."""
+        if lam is None:
+            if _is_torch(g):
+                import torch
+                lam = torch.zeros_like(g)
+            else:
+                lam = np.zeros(len(g))
+        gp, wg, kg = _ptr(g, np.float64)
+        if _is_torch(lam):
+            lp, wl, kl = _ptr(lam, np.float64)
+        else:
+            if not (isinstance(lam, np.ndarray) and lam.dtype == np.float64 and lam.flags.c_contiguous):
+                lam = np.ascontiguousarray(lam, dtype=np.float64)
+            lp, wl, kl = lam.ctypes.data, RB_HOST, lam
+        if wg != wl:
+            raise ValueError("g and lam must live in the same memory space")
+        st = Stats()
+        _check(lib().rbicgstab_solve_adjoint(self._h, gp, lp, wg, ctypes.byref(st)), "rbicgstab_solve_adjoint")
+        return SolveResult(x=lam, stats=st.as_dict())
+
+    def solve_l(self, b, ell: int = 2, x=None) -> SolveResult:
+        """Recycled BiCGstab(ell) with the handle's fixed space
+        (rbicgstab_solve_l); ``x`` (updated in place when given) is x_{-1}.
+        Breakdowns and non-convergence are reported in ``stats['status']``."""
+        if x is None:
+            if _is_torch(b):
+                import torch
+                x = torch.zeros_like(b)
+            else:
+                x = np.zeros(len(b))
+        bp, wb, kb = _ptr(b, np.float64)
+        if _is_torch(x):
+            xp, wx, kx = _ptr(x, np.float64)
+        else:
+            if not (isinstance(x, np.ndarray) and x.dtype == np.float64 and x.flags.c_contiguous):
+                x = np.ascontiguousarray(x, dtype=np.float64)
+            xp, wx, kx = x.ctypes.data, RB_HOST, x
+        if wb != wx:
+            raise ValueError("b and x must live in the same memory space")
+        st = Stats()
+        code = lib().rbicgstab_solve_l(self._h, int(ell), bp, xp, wb, ctypes.byref(st))
+        if code in HARD_ERRORS:
+            raise RbError(code, "rbicgstab_solve_l")
+        return SolveResult(x=x, stats=st.as_dict())
 
     def sell_stats(self):
         """(slices, stencil slices) of the current matrix's SELL-32 layout

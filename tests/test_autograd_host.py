@@ -1,5 +1,5 @@
 """Host logic of the autograd function (``autograd.RecycledSolve``) on CPU:
-its backward wiring (dual solve -> dL/db, pattern product -> dL/dvalues) is
+its backward wiring (adjoint solve -> dL/db, pattern product -> dL/dvalues) is
 checked by torch's numerical gradient check with a dense stand-in for the
 solver handle, and a solver that moved on to another matrix is put back to
 the forward's matrix before the dual solve."""
@@ -41,11 +41,9 @@ class DenseStandIn:
     def solve(self, b):
         return _Res(torch.from_numpy(np.linalg.solve(self._M(), b.numpy())))
 
-    def solve_dual(self, b, bt):
-        self.log.append("solve_dual")
-        M = self._M()
-        return _Res(torch.from_numpy(np.linalg.solve(M, b.numpy()))), \
-            _Res(torch.from_numpy(np.linalg.solve(M.T, bt.numpy())))
+    def solve_adjoint(self, g):
+        self.log.append("solve_adjoint")
+        return _Res(torch.from_numpy(np.linalg.solve(self._M().T, g.numpy())))
 
     def pattern_outer(self, u, v, scale):
         return torch.from_numpy(scale * u.numpy()[self.rows] * v.numpy()[self.col])
@@ -70,7 +68,7 @@ def test_backward_restores_the_forward_matrix():
     rag.solve(s, torch.from_numpy(2.0 * A.val), b)
     s.log.clear()
     x0.sum().backward()
-    assert s.log == ["set_values", "solve_dual"]
+    assert s.log == ["set_values", "solve_adjoint"]
     M = sp.csr_matrix((A.val, A.col, A.row_ptr), shape=(A.n, A.n)).toarray()
     lam = np.linalg.solve(M.T, np.ones(A.n))
     x = np.linalg.solve(M, b.numpy())
@@ -91,6 +89,6 @@ def test_checkpointing_recomputes_x_with_the_same_gradient():
         x = rag.solve(s, vals, b, checkpoint=ck)
         (x.square().sum()).backward()
         grads.append((vals.grad.clone(), b.grad.clone()))
-        assert s.log.count("solve_dual") == 1
+        assert s.log.count("solve_adjoint") == 1
     assert torch.allclose(grads[0][0], grads[1][0], rtol=1e-12, atol=0)
     assert torch.allclose(grads[0][1], grads[1][1], rtol=1e-12, atol=0)

@@ -77,3 +77,31 @@ def test_autograd_gradient_matches_oracle_and_differences(k):
         Lm = oad.loss(spec.C_out, spla.spsolve(_A(spec, spec.p0 - e).tocsc(), spec.b))
         fd[kk] = (Lp - Lm) / (2 * h)
     assert np.max(np.abs(gp - fd)) <= 1e-5 * np.max(np.abs(fd))
+
+
+@pytest.mark.parametrize("two_sided", [False, True])
+def test_adjoint_solve_matches_oracle_dual(two_sided):
+    """rbicgstab_solve_adjoint: Alg. 2 on A^T with the swapped space (right
+    U~, left U) against the oracle's dual solve of the same construction
+    (iterations within 5%, lam within 1e-7), ragged n = 13^3."""
+    spec = inputs.config_param_3d(N=13, m_out=4)
+    P = spec.pattern
+    A = _A(spec, spec.p0)
+    U = inputs.random_recycle_basis(P.n, 8, 17)
+    Ut = inputs.random_recycle_basis(P.n, 8, 18) if two_sided else None
+    from oracle import rbicgstab as orb
+    rec = orb.recycle_setup(A, U, Ut)
+    g = inputs.gaussian_rhs(P.n, 21)
+    lo, io = orb.rbicgstab(sp.csr_matrix(A.T), g, oad.dual_space(A, rec), tol=1e-8)
+    s = rb.Solver(recycle="fixed", k_max=8, tol=1e-8)
+    s.set_matrix(P.row_ptr, P.col, spec.values(spec.p0))
+    s.set_recycle(U, Ut)
+    r = s.solve_adjoint(g)
+    assert r.stats["status"] == rb.RB_OK
+    assert abs(r.stats["iters"] - io.iters) <= max(1, int(0.05 * io.iters)), (r.stats["iters"], io.iters)
+    assert np.linalg.norm(r.x - lo) <= 1e-7 * np.linalg.norm(lo)
+    assert np.linalg.norm(g - A.T @ r.x) <= 1.5e-8 * np.linalg.norm(g)
+    # the handle is back in its primary orientation
+    b = inputs.gaussian_rhs(P.n, 22)
+    xp = s.solve(b).x
+    assert np.linalg.norm(b - A @ xp) <= 1.5e-8 * np.linalg.norm(b)
