@@ -58,6 +58,9 @@ def parse():
     ap.add_argument("--quick", action="store_true", help="small grid for a smoke run (not a bench line)")
     ap.add_argument("--rbicg", action="store_true",
                     help="time Alg. 1 (RBiCG, primary + dual, FP64) on system 1 instead of the sequence")
+    ap.add_argument("--batch", action="store_true",
+                    help="the batched sweep (256 uneven 2D systems x 4 shifts, k = 10) through the batched "
+                         "solver: batched plain FP64 / plain mixed / recycled mixed, and an unbatched loop")
     ap.add_argument("--adjoint", action="store_true",
                     help="the differentiation workload (100^3, 8 parameters, 6 steps) through the autograd "
                          "function: forward + backward time per step, with and without checkpointing, and a "
@@ -323,6 +326,116 @@ def run_passes_only(args):
                       "passes_GBs": [round(bb / (m * 1e-3) / 1e9, 1) if m > 0 else 0 for bb, m in zip(pb, ms)],
                       "status": code}
         del s
+    return out
+
+
+def run_batch(args):
+    """The batched sweep: 256 independent 2D convection-diffusion systems
+    (sides U{100..450}, p ~ U[1, 50], seed 2), each a sequence of 4 shifts
+    sigma in {0, 1e-2, 1e-1, 1} added to the h^2-scaled diagonal with one
+    Gaussian right-hand side; k = 10, tol 1e-8.  Arms (CUDA events; every
+    batched arm solves each shift of all systems in one batched call):
+    batched plain FP64 and batched plain mixed over the 4 shifts; batched
+    recycled mixed over shifts 1..3 with each system's k = 10 space from the
+    harmonic-Ritz update of its shift-0 solve (generated by the single-system
+    update path, timed and reported apart); the plain mixed and FP64 batched
+    arms over shifts 1..3 for the same comparison; and an unbatched loop of
+    plain FP64 single-system solves (one handle per system)."""
+    import numpy as np
+    import torch
+
+    from paper_1406_2831_gb300 import inputs
+    from paper_1406_2831_gb300 import rbicgstab as rb
+    nsys = 16 if args.quick else 256
+    specs = inputs.config_batch_2d(n_systems=nsys)
+    shifts = (0.0, 1e-2, 1e-1, 1.0)
+    t0 = time.perf_counter()
+    mats = [spec.pattern() for spec in specs]
+    vals = [[inputs.shifted_values(A, np.ones(A.n), sg) for A in mats] for sg in shifts]
+    rhs = [spec.rhs[0][0]() for spec in specs]
+    t_gen = time.perf_counter() - t0
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream(dev)
+    b_d = torch.from_numpy(np.concatenate(rhs)).to(dev)
+    vals_d = [torch.from_numpy(np.concatenate(v)).to(dev) for v in vals]
+    n_tot = int(sum(A.n for A in mats))
+    nnz_tot = int(sum(A.nnz for A in mats))
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1), out
+
+    def batched_arm(precision, which, Us=None):
+        B = rb.Batch(mats, k_max=10 if Us is not None else 0, precision=precision, tol=1e-8, stream=stream)
+        if Us is not None:
+            B.set_recycle(Us)
+        B.set_values(vals_d[which[0]])
+        B.solve(b_d)                 # warm-up: setup, autotuner, graphs
+        its, stat = [], []
+
+        def run():
+            for j in which:
+                B.set_values(vals_d[j])
+                xs, sts = B.solve(b_d)
+                its.extend(st["iters"] for st in sts)
+                stat.extend(st["status"] for st in sts)
+        ms, _ = timed(run)
+        nsolve = len(which) * nsys
+        return {"solves_per_s": round(nsolve / (ms * 1e-3), 2), "ms": round(ms, 1), "iters_mean": round(float(np.mean(its)), 1),
+                "failed": int(sum(1 for s_ in stat if s_ != 0)), "autotune": B.info()}
+
+    out = {"metric": "batched solves/sec at 1e-8 rel. residual", "unit": "solves/s",
+           "config": {"workload": f"batched-2d-conv-diff, {nsys} systems x 4 shifts", "systems": nsys,
+                      "rows": n_tot, "nnz": nnz_tot, "k": 10, "tol": 1e-8, "shifts": list(shifts)},
+           "generation_s": round(t_gen, 1)}
+    out["batched_plain_fp64"] = batched_arm("fp64", [0, 1, 2, 3])
+    out["batched_plain_mixed"] = batched_arm("mixed", [0, 1, 2, 3])
+    # recycle spaces from each system's shift-0 solve (single-system update path)
+    t0 = time.perf_counter()
+    Us = []
+    for i, A in enumerate(mats):
+        s = rb.Solver(k_max=10, cycle_s=25, recycle="update_first", precision="mixed", tol=1e-8)
+        s.set_matrix(A.row_ptr, A.col, vals[0][i])
+        s.solve(rhs[i])
+        U = s.get_recycle()[0]
+        if U.shape[1] < 10:   # keep k = 10 columns for the batch (pad with orthogonal noise, rarely needed)
+            extra = np.linalg.qr(np.random.default_rng(i).standard_normal((A.n, 10 - U.shape[1])))[0]
+            U = np.column_stack([U, extra])
+        Us.append(U)
+        del s
+    t_space = time.perf_counter() - t0
+    out["recycled_mixed_shifts_1_3"] = batched_arm("mixed", [1, 2, 3], Us)
+    out["recycled_mixed_shifts_1_3"]["space_generation_s"] = round(t_space, 2)
+    out["plain_mixed_shifts_1_3"] = batched_arm("mixed", [1, 2, 3])
+    out["plain_fp64_shifts_1_3"] = batched_arm("fp64", [1, 2, 3])
+    # unbatched plain FP64: one handle per system, shifts 0..3
+    handles = []
+    for i, A in enumerate(mats):
+        s = rb.Solver(recycle="none", precision="fp64", tol=1e-8, stream=stream)
+        s.set_matrix(A.row_ptr, A.col, vals[0][i])
+        handles.append(s)
+    bparts = [torch.from_numpy(r_).to(dev) for r_ in rhs]
+    vparts = [[torch.from_numpy(v).to(dev) for v in vv] for vv in vals]
+
+    def unbatched():
+        for j in range(len(shifts)):
+            for i, s in enumerate(handles):
+                s.set_values(vparts[j][i])
+                s.solve(bparts[i])
+    unbatched()
+    ms, _ = timed(unbatched)
+    out["unbatched_plain_fp64"] = {"solves_per_s": round(len(shifts) * nsys / (ms * 1e-3), 2), "ms": round(ms, 1)}
+    out["value"] = out["recycled_mixed_shifts_1_3"]["solves_per_s"]
+    out["recycled_mixed_over_plain_fp64_batched"] = round(out["recycled_mixed_shifts_1_3"]["solves_per_s"] /
+                                                          out["plain_fp64_shifts_1_3"]["solves_per_s"], 4)
+    out["batched_over_unbatched_plain_fp64"] = round(out["batched_plain_fp64"]["solves_per_s"] /
+                                                     out["unbatched_plain_fp64"]["solves_per_s"], 4)
     return out
 
 
@@ -1035,6 +1148,8 @@ def main():
         line = run_large(args)
     elif args.adjoint:
         line = run_adjoint(args)
+    elif args.batch:
+        line = run_batch(args)
     else:
         line = run_reference(args) if args.impl == "reference" else run_ours(args)
     if line is not None:

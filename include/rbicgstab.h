@@ -255,6 +255,49 @@ int rbicgstab_residual_noalloc(int64_t n, const int32_t* row_ptr, const int32_t*
                                const double* val, const double* x, const double* b, double* r,
                                double* rnorm2, void* cuda_stream);
 
+/* ---- batched solves of many independent systems ------------------------
+ * A batch holds S independent systems A_i x_i = b_i of uneven sizes n_i (the
+ * sequence of Sec. 1 for many parameter samples at once), each with its own
+ * optional fixed recycle space U_i of k <= 16 columns (U~_i = U_i, the
+ * right-only variant of Sec. 5; Sec. 3 setup per system).  One solve runs
+ * Alg. 2 for all systems together: every pass of an iteration is one
+ * persistent kernel over a work list of tiles (slice ranges inside one
+ * system) with per-system dot products, scalars and convergence; iterations
+ * are captured as a CUDA graph; the tile size and CTAs per SM are chosen by
+ * an autotuner at the first solve after a matrix or space change.
+ * opts: tol, max_itn, poll, shadow_seed, cuda_stream, precision (RB_FP64, or
+ * RB_MIXED: FP32 iteration with Dot2 dot products, restarted on the FP64
+ * residual until ||b_i - A_i x_i|| <= tol ||b_i||), k_max <= 16 (0: plain
+ * BiCGSTAB only).  Errors as for the single-system calls. */
+typedef struct rb_batch_ctx* rb_batch;
+int rbicgstab_batch_create(rb_batch* h, const rb_opts* opts);
+int rbicgstab_batch_destroy(rb_batch h);
+/* nsys systems, host arrays: n[i] rows each; row_ptr = the systems' CSR row
+ * pointers one after another (n[i] + 1 entries each, each starting at 0);
+ * col = their local column indices and val their values, one after another
+ * (sum of the systems' nonzeros).  The pattern is copied; the values are the
+ * first set_values.  Errors: RB_EINVAL, RB_EBADCSR, RB_ENONFINITE. */
+int rbicgstab_batch_set_matrices(rb_batch h, int32_t nsys, const int64_t* n, const int32_t* row_ptr,
+                                 const int32_t* col, const double* val);
+/* New values on the same patterns (the layout of set_matrices' val). */
+int rbicgstab_batch_set_values(rb_batch h, const double* val, int where);
+/* k columns for every system: system i's n_i x k column-major block follows
+ * system i-1's (sum_i n_i * k doubles).  k = 0 clears.  The setup runs at
+ * the next solve. */
+int rbicgstab_batch_set_recycle(rb_batch h, int32_t k, const double* U, int where);
+/* b, x: sum_i n_i doubles, system after system; x holds x_{-1} on entry and
+ * the solutions on return; st: nsys entries (may be NULL), per system
+ * (iters summed over refinement restarts, outer = restarts + 1, k_used, the
+ * recursive and FP64 true relative residuals; ms_total of the whole batch).
+ * Returns RB_OK when every system converged, else the first system's
+ * failure code (every system's status is in st); RB_ETIMEOUT when the
+ * host's iteration loop runs past every system's max_itn without all of
+ * them reporting done (a safeguard: each system stops at its max_itn). */
+int rbicgstab_batch_solve(rb_batch h, const double* b, double* x, int where, rb_stats* st);
+/* The work list the autotuner chose: slices per tile, CTAs per SM, tiles,
+ * and the tuned time of one SpMV + projection pass (ms). */
+int rbicgstab_batch_info(rb_batch h, int32_t* tile_slices, int32_t* ctas_per_sm, int32_t* ntiles, double* tune_ms);
+
 /* The dual system A^T lam = g (the dual system of Sec. 2, real arithmetic):
  * Alg. 2 on A^T with the recycle space's roles swapped, right space U~ and
  * left space U, which reuses the products C~ = A^T U~ and C = A U of the

@@ -1,0 +1,1197 @@
+// Batched solves of many independent systems of uneven sizes (the batched
+// pattern of a parametric sweep: many parameter samples, each with its own
+// matrix, right-hand side and recycle space), one launch per pass for all of
+// them.
+//
+// The systems are stacked into one block-diagonal SELL-32 matrix; every
+// system's rows are padded to a multiple of 32, so a slice never straddles
+// two systems.  Each pass is one persistent kernel over a work list of
+// tiles, a tile being a range of `tile_slices` slices inside one system.  A
+// CTA takes tiles in grid-stride order; for each it forms the pass's vector
+// updates and its contribution to the pass's dot products, writes one
+// partial row per tile and counts the tile on its system's ticket.  The CTA
+// that completes a system's last tile adds that system's tile rows in tile
+// order (deterministic) and runs the scalar step of Alg. 2 for that system
+// (the same device functions as the single-system passes).  Systems that
+// have converged or failed skip their tiles.  The iteration loop is captured
+// as a CUDA graph of `poll` iterations.  The tile size and the number of
+// CTAs per SM are chosen by timing the SpMV + projection pass on the batch
+// (autotuner, logged on request).
+//
+// Each system may carry a fixed recycle space of k <= 16 columns (U~ = U,
+// the right-only variant of Sec. 5), set up per system as in Sec. 3
+// (C = A U, C~ = A^T U, M = C~^T C, C-hat = C~ (M^+)^T).  The inner
+// iteration runs in FP64 or, in the mixed mode, in FP32 with Dot2-compensated
+// dot products; the mixed mode refines in FP64: it restarts the recycled
+// FP32 solve on the FP64 residual b - A x until ||b - A x|| <= tol ||b||.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <vector>
+
+#include "device.cuh"
+#include "hostla.h"
+#include "kernels.h"
+#include "scalars.cuh"
+
+namespace rb {
+namespace {
+
+constexpr int kBK = 16;                 // largest recycle dimension of a batch
+constexpr int kBNV = kBK + 4;           // values per tile partial row
+
+struct BatchTiles {
+  const int32_t* sys;        // [ntiles] system of the tile
+  const int64_t* sl0;        // [ntiles] first slice
+  const int32_t* nsl;        // [ntiles] slices
+  const int32_t* t0;         // [nsys] first tile of the system
+  const int32_t* nt;         // [nsys] tiles of the system
+  int ntiles;
+};
+
+template <typename T>
+struct BatchArgs {
+  Sell<T> A;
+  const T* Chat;
+  const T* C;
+  int64_t ld;                // rows of the stacked vectors (all systems, padded)
+  int k;
+  const T* rt0;
+  T *x, *r, *p, *s, *q, *t, *qraw, *traw;
+  IterState* st;             // one per system
+  double* partials;          // [ntiles][kBNV]
+  BatchTiles tiles;
+};
+
+// Shared "does this tile's system still iterate" test: one read, broadcast.
+__device__ __forceinline__ bool tile_active(const IterState* st, bool skip_half) {
+  __shared__ int s_act;
+  if (threadIdx.x == 0) s_act = !st->done && !(skip_half && st->half);
+  __syncthreads();
+  const bool a = s_act;
+  __syncthreads();
+  return a;
+}
+
+// After block_sum: sm.res[0..nv) are the tile's totals.  Stores the tile's
+// partial row and counts it; returns true in every thread of the CTA that
+// completed the system's last tile, with sm.res[0..nv) then holding the
+// system's totals, summed in tile order.  The ticket is back at 0 after.
+template <int NV>
+__device__ bool tile_commit(ReduceSmem<NV>& sm, int nv, double* partials, int t, unsigned* ticket, int t0,
+                            int nt) {
+  __shared__ int s_last;
+  if (threadIdx.x == 0) {
+    for (int v = 0; v < nv; ++v) partials[(size_t)t * kBNV + v] = sm.res[v];
+    __threadfence();
+    const unsigned prev = atomicAdd(ticket, 1u);
+    s_last = prev == (unsigned)(nt - 1);
+  }
+  __syncthreads();
+  if (!s_last) return false;
+  __threadfence();
+  for (int v = threadIdx.x; v < nv; v += blockDim.x) {
+    double acc = 0.0;
+    for (int q = 0; q < nt; ++q) acc += __ldcg(partials + (size_t)(t0 + q) * kBNV + v);
+    sm.res[v] = acc;
+  }
+  if (threadIdx.x == 0) *ticket = 0u;
+  __syncthreads();
+  return true;
+}
+
+// y = A v over the rows of one slice (lane = row), SELL-32 with column loads.
+template <typename T>
+__device__ __forceinline__ T slice_row_product(const Sell<T>& A, const T* __restrict__ v, int64_t sl, int lane) {
+  const int w = __ldg(A.width + sl);
+  const int64_t e0 = __ldg(A.slice_ptr + sl) + lane;
+  T y = T(0);
+  for (int j = 0; j < w; ++j) {
+    const int64_t e = e0 + (int64_t)j * kSlice;
+    y = fma_t(__ldg(A.val + e), __ldg(v + __ldg(A.col + e)), y);
+  }
+  return y;
+}
+
+// P1: q_raw = A p; zeta = C-hat^T q_raw, (r~_0, q_raw) -> alpha (finish_p1).
+// P3: t_raw = A s; gamma = C-hat^T t_raw (finish_p3), or with k = 0 the four
+// dots (s,t), (t,t), (r~_0,t), (r~_0,s) (finish_p4).
+template <typename T, int KB, bool IS_P3>
+__global__ void __launch_bounds__(kBlock) kb_spmv(BatchArgs<T> a) {
+  constexpr int NV = KB > 0 ? KB + 1 : 4;
+  __shared__ ReduceSmem<NV> sm;
+  __shared__ double scr[kBK + 1];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const T* __restrict__ v = IS_P3 ? a.s : a.p;
+  T* __restrict__ out = IS_P3 ? a.traw : a.qraw;
+  const int k = KB > 0 ? a.k : 0;
+  for (int t = blockIdx.x; t < a.tiles.ntiles; t += gridDim.x) {
+    const int sys = a.tiles.sys[t];
+    IterState* st = a.st + sys;
+    if (!tile_active(st, IS_P3)) continue;
+    Acc<T> acc[NV];
+    const int64_t sl0 = a.tiles.sl0[t];
+    const int nsl = a.tiles.nsl[t];
+    for (int q = warp; q < nsl; q += kBlock / 32) {
+      const int64_t sl = sl0 + q;
+      const int64_t row = sl * kSlice + lane;
+      const T y = slice_row_product(a.A, v, sl, lane);
+      out[row] = y;
+      if (KB > 0) {
+        if (!IS_P3) acc[0].add(__ldg(a.rt0 + row), y);
+#pragma unroll
+        for (int j = 0; j < KB; ++j)
+          if (j < k) acc[(IS_P3 ? 0 : 1) + j].add(__ldg(a.Chat + (int64_t)j * a.ld + row), y);
+      } else {
+        if (!IS_P3) {
+          acc[0].add(__ldg(a.rt0 + row), y);
+        } else {
+          const T sv = __ldg(a.s + row), rv = __ldg(a.rt0 + row);
+          acc[0].add(sv, y);
+          acc[1].add(y, y);
+          acc[2].add(rv, y);
+          acc[3].add(rv, sv);
+        }
+      }
+    }
+    const int nv = KB > 0 ? (IS_P3 ? k : k + 1) : (IS_P3 ? 4 : 1);
+    block_sum<T, NV>(acc, nv, sm);
+    if (tile_commit<NV>(sm, nv, a.partials, t, &st->ticket[IS_P3 ? P3 : P1].top, a.tiles.t0[sys], a.tiles.nt[sys])) {
+      if (warp == 0) {
+        if (!IS_P3) finish_p1(st, sm.res, k, scr);
+        else if (KB > 0) finish_p3(st, sm.res, k);
+        else finish_p4(st, sm.res, 0);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// P2: q = q_raw - C zeta;  s = r - alpha q;  ||s||^2 (finish_p2).
+template <typename T, int KB>
+__global__ void __launch_bounds__(kBlock) kb_p2(BatchArgs<T> a) {
+  __shared__ ReduceSmem<1> sm;
+  __shared__ T zs[kBK];
+  __shared__ T s_alpha;
+  const int k = KB > 0 ? a.k : 0;
+  for (int t = blockIdx.x; t < a.tiles.ntiles; t += gridDim.x) {
+    const int sys = a.tiles.sys[t];
+    IterState* st = a.st + sys;
+    if (!tile_active(st, false)) continue;
+    if (threadIdx.x < k) zs[threadIdx.x] = (T)st->zeta[threadIdx.x];
+    if (threadIdx.x == 0) s_alpha = (T)st->alpha;
+    __syncthreads();
+    const T alpha = s_alpha;
+    Acc<T> acc[1];
+    const int64_t r0 = a.tiles.sl0[t] * kSlice;
+    const int rows = a.tiles.nsl[t] * kSlice;
+    for (int i = threadIdx.x; i < rows; i += blockDim.x) {
+      const int64_t row = r0 + i;
+      T qv = a.qraw[row];
+#pragma unroll
+      for (int j = 0; j < KB; ++j)
+        if (j < k) qv = fma_t(-__ldg(a.C + (int64_t)j * a.ld + row), zs[j], qv);
+      if (KB > 0) a.q[row] = qv;
+      const T sv = fma_t(-alpha, qv, a.r[row]);
+      a.s[row] = sv;
+      acc[0].add(sv, sv);
+    }
+    block_sum<T, 1>(acc, 1, sm);
+    if (tile_commit<1>(sm, 1, a.partials, t, &st->ticket[P2].top, a.tiles.t0[sys], a.tiles.nt[sys]))
+      if (threadIdx.x < 32) finish_p2(st, sm.res);
+    __syncthreads();
+  }
+}
+
+// P4 (k > 0): t = t_raw - C gamma;  (s,t), (t,t), (r~_0,t), (r~_0,s) (finish_p4).
+template <typename T, int KB>
+__global__ void __launch_bounds__(kBlock) kb_p4(BatchArgs<T> a) {
+  __shared__ ReduceSmem<4> sm;
+  __shared__ T gs[kBK];
+  const int k = a.k;
+  for (int t = blockIdx.x; t < a.tiles.ntiles; t += gridDim.x) {
+    const int sys = a.tiles.sys[t];
+    IterState* st = a.st + sys;
+    if (!tile_active(st, true)) continue;
+    if (threadIdx.x < k) gs[threadIdx.x] = (T)st->gamma[threadIdx.x];
+    __syncthreads();
+    Acc<T> acc[4];
+    const int64_t r0 = a.tiles.sl0[t] * kSlice;
+    const int rows = a.tiles.nsl[t] * kSlice;
+    for (int i = threadIdx.x; i < rows; i += blockDim.x) {
+      const int64_t row = r0 + i;
+      T tv = a.traw[row];
+#pragma unroll
+      for (int j = 0; j < KB; ++j)
+        if (j < k) tv = fma_t(-__ldg(a.C + (int64_t)j * a.ld + row), gs[j], tv);
+      a.t[row] = tv;
+      const T sv = a.s[row], rv = __ldg(a.rt0 + row);
+      acc[0].add(sv, tv);
+      acc[1].add(tv, tv);
+      acc[2].add(rv, tv);
+      acc[3].add(rv, sv);
+    }
+    block_sum<T, 4>(acc, 4, sm);
+    if (tile_commit<4>(sm, 4, a.partials, t, &st->ticket[P4].top, a.tiles.t0[sys], a.tiles.nt[sys]))
+      if (threadIdx.x < 32) finish_p4(st, sm.res, k);
+    __syncthreads();
+  }
+}
+
+// P5: x += alpha p + omega s;  r = s - omega t;  p = r + beta (p - omega q);
+// ||r||^2 (finish_p5).  After a half step: x += alpha p, r = s.
+template <typename T, int KB>
+__global__ void __launch_bounds__(kBlock) kb_p5(BatchArgs<T> a) {
+  __shared__ ReduceSmem<1> sm;
+  __shared__ T s_sc[4];
+  __shared__ int s_half;
+  for (int t = blockIdx.x; t < a.tiles.ntiles; t += gridDim.x) {
+    const int sys = a.tiles.sys[t];
+    IterState* st = a.st + sys;
+    if (!tile_active(st, false)) continue;
+    if (threadIdx.x == 0) {
+      s_sc[0] = (T)st->alpha;
+      s_sc[1] = (T)st->omega;
+      s_sc[2] = (T)st->beta;
+      s_half = st->half;
+    }
+    __syncthreads();
+    const T alpha = s_sc[0], omega = s_sc[1], beta = s_sc[2];
+    const bool half = s_half;
+    const T* __restrict__ qsrc = KB > 0 ? a.q : a.qraw;
+    Acc<T> acc[1];
+    const int64_t r0 = a.tiles.sl0[t] * kSlice;
+    const int rows = a.tiles.nsl[t] * kSlice;
+    for (int i = threadIdx.x; i < rows; i += blockDim.x) {
+      const int64_t row = r0 + i;
+      const T pv = a.p[row], sv = a.s[row];
+      if (half) {
+        a.x[row] = fma_t(alpha, pv, a.x[row]);
+        a.r[row] = sv;
+        acc[0].add(sv, sv);
+      } else {
+        const T tv = a.t[row], qv = qsrc[row];
+        a.x[row] = fma_t(omega, sv, fma_t(alpha, pv, a.x[row]));
+        const T rv = fma_t(-omega, tv, sv);
+        a.r[row] = rv;
+        a.p[row] = fma_t(beta, fma_t(-omega, qv, pv), rv);
+        acc[0].add(rv, rv);
+      }
+    }
+    block_sum<T, 1>(acc, 1, sm);
+    if (tile_commit<1>(sm, 1, a.partials, t, &st->ticket[P5].top, a.tiles.t0[sys], a.tiles.nt[sys]))
+      if (threadIdx.x < 32) finish_p5(st, sm.res, a.k);
+    __syncthreads();
+  }
+}
+
+// Per-system reductions outside the iteration (setup, refinement): for
+// every system, st[sys].red[j] = M_j^T v (j < km, M column-major with
+// leading dimension ld) and st[sys].red[km + q] = (a_q, b_q) (q < nd).  FP64.
+struct SysDots {
+  const double* M;
+  int km;
+  const double* v;
+  const double* pa[4];
+  const double* pb[4];
+  int nd;
+};
+
+__global__ void __launch_bounds__(kBlock) kb_sysdots(SysDots d, int64_t ld, IterState* st, double* partials,
+                                                     BatchTiles tiles) {
+  __shared__ ReduceSmem<kBNV> sm;
+  for (int t = blockIdx.x; t < tiles.ntiles; t += gridDim.x) {
+    const int sys = tiles.sys[t];
+    Acc<double> acc[kBNV];
+    const int64_t r0 = tiles.sl0[t] * kSlice;
+    const int rows = tiles.nsl[t] * kSlice;
+    for (int i = threadIdx.x; i < rows; i += blockDim.x) {
+      const int64_t row = r0 + i;
+      if (d.M) {
+        const double vi = d.v[row];
+#pragma unroll
+        for (int j = 0; j < kBK; ++j)
+          if (j < d.km) acc[j].add(d.M[(int64_t)j * ld + row], vi);
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (q < d.nd) acc[kBK + q].add(d.pa[q][row], d.pb[q][row]);
+    }
+    block_sum<double, kBNV>(acc, kBNV, sm);
+    IterState* s = st + sys;
+    if (tile_commit<kBNV>(sm, kBNV, partials, t, &s->ticket[PGEN].top, tiles.t0[sys], tiles.nt[sys])) {
+      if (threadIdx.x < d.km) s->red[threadIdx.x] = sm.res[threadIdx.x];
+      if (threadIdx.x < d.nd) s->red[d.km + threadIdx.x] = sm.res[kBK + threadIdx.x];
+    }
+    __syncthreads();
+  }
+}
+
+// y += sign * M c_sys for every system (M column-major, k columns); the
+// coefficients are the system's st.red (XC = false) or st.xc (XC = true).
+// Systems with skip[sys] != 0 (when skip is given) keep y unchanged.
+template <bool XC>
+__global__ void __launch_bounds__(kBlock) kb_gemv(double* __restrict__ y, const double* __restrict__ M, int64_t ld,
+                                                  int k, double sign, const IterState* st, const int* skip,
+                                                  BatchTiles tiles) {
+  __shared__ double cs[kBK];
+  for (int t = blockIdx.x; t < tiles.ntiles; t += gridDim.x) {
+    const int sys = tiles.sys[t];
+    if (skip && skip[sys]) continue;
+    if (threadIdx.x < k) cs[threadIdx.x] = sign * (XC ? st[sys].xc[threadIdx.x] : st[sys].red[threadIdx.x]);
+    __syncthreads();
+    const int64_t r0 = tiles.sl0[t] * kSlice;
+    const int rows = tiles.nsl[t] * kSlice;
+    for (int i = threadIdx.x; i < rows; i += blockDim.x) {
+      const int64_t row = r0 + i;
+      double acc = 0.0;
+      for (int j = 0; j < k; ++j) acc = fma(M[(int64_t)j * ld + row], cs[j], acc);
+      y[row] += acc;
+    }
+    __syncthreads();
+  }
+}
+
+// Out(:, c) = sum_j X(:, j) R_sys(j, c) for every system, R_sys the system's
+// k x k matrix (column-major) in R[sys * kBK * kBK].  Out must not alias X.
+__global__ void __launch_bounds__(kBlock) kb_gemm_sys(double* __restrict__ out, const double* __restrict__ X,
+                                                      int64_t ld, int k, const double* __restrict__ R,
+                                                      BatchTiles tiles) {
+  __shared__ double rs[kBK * kBK];
+  for (int t = blockIdx.x; t < tiles.ntiles; t += gridDim.x) {
+    const int sys = tiles.sys[t];
+    for (int e = threadIdx.x; e < k * k; e += blockDim.x) rs[e] = R[(size_t)sys * kBK * kBK + e];
+    __syncthreads();
+    const int64_t r0 = tiles.sl0[t] * kSlice;
+    const int rows = tiles.nsl[t] * kSlice;
+    for (int i = threadIdx.x; i < rows; i += blockDim.x) {
+      const int64_t row = r0 + i;
+      double xv[kBK];
+#pragma unroll
+      for (int j = 0; j < kBK; ++j) xv[j] = j < k ? X[(int64_t)j * ld + row] : 0.0;
+      for (int c = 0; c < k; ++c) {
+        double acc = 0.0;
+#pragma unroll
+        for (int j = 0; j < kBK; ++j)
+          if (j < k) acc = fma(xv[j], rs[j + c * k], acc);
+        out[(int64_t)c * ld + row] = acc;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Compact (sum n_i) <-> padded (sum npad_i) layouts of stacked vectors or of
+// stacked column blocks (cols columns per system: compact column c of system
+// i starts at cofs_i * cols + c * n_i; padded column c at c * ld).
+struct SysLayout {
+  const int64_t* row0;   // first padded row of each system
+  const int64_t* n;      // rows of each system
+  const int64_t* cofs;   // first compact row of each system
+};
+
+template <bool TO_PADDED>
+__global__ void __launch_bounds__(kBlock) kb_relayout(double* __restrict__ padded, double* __restrict__ compact,
+                                                      int cols, int64_t ld, SysLayout L, BatchTiles tiles) {
+  for (int t = blockIdx.x; t < tiles.ntiles; t += gridDim.x) {
+    const int sys = tiles.sys[t];
+    const int64_t r0 = tiles.sl0[t] * kSlice;
+    const int rows = tiles.nsl[t] * kSlice;
+    const int64_t row0 = L.row0[sys], ni = L.n[sys], cofs = L.cofs[sys];
+    for (int c = 0; c < cols; ++c)
+      for (int i = threadIdx.x; i < rows; i += blockDim.x) {
+        const int64_t row = r0 + i, l = row - row0;
+        const int64_t ci = cofs * cols + (int64_t)c * ni + l;
+        if (TO_PADDED) padded[(int64_t)c * ld + row] = l < ni ? compact[ci] : 0.0;
+        else if (l < ni) compact[ci] = padded[(int64_t)c * ld + row];
+      }
+  }
+}
+
+__global__ void kb_flags(const IterState* st, int nsys, int* flags) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nsys; i += gridDim.x * blockDim.x) flags[i] = st[i].done;
+}
+
+}  // namespace
+}  // namespace rb
+
+// ============================================================ host side
+using rb::BatchArgs;
+using rb::BatchTiles;
+using rb::IterState;
+using rb::SellBuf;
+
+struct rb_batch_ctx {
+  rb_opts o{};
+  cudaStream_t us = nullptr, cs = nullptr;
+  int nsm = 0;
+  int S = 0;
+  std::vector<int64_t> n, npad, row0, cofs, nnz_sys;
+  int64_t NP = 0, NC = 0, nnz = 0;   // padded rows, compact rows, nonzeros
+  int32_t *rp = nullptr, *ci = nullptr, *trp = nullptr, *tci = nullptr;
+  int64_t* tsrc = nullptr;
+  double *cv = nullptr, *tcv = nullptr;
+  SellBuf<double> A, AT;
+  SellBuf<float> A32;
+  bool have = false;
+  // work list
+  int tile_slices = 0, ctas_per_sm = 0, grid = 0, ntiles = 0;
+  double tune_ms = 0.0;
+  int32_t *t_sys = nullptr, *t_nsl = nullptr, *s_t0 = nullptr, *s_nt = nullptr;
+  int64_t* t_sl0 = nullptr;
+  int64_t *d_row0 = nullptr, *d_n = nullptr, *d_cofs = nullptr;
+  // recycle space (fixed), padded columns of ld = NP
+  int kin = 0, k = 0;
+  bool setup_owed = false;
+  double *U = nullptr, *C = nullptr, *Ct = nullptr, *Chat = nullptr, *dR = nullptr;
+  float *fU = nullptr, *fC = nullptr, *fChat = nullptr;
+  std::vector<int> k_used;
+  // vectors
+  double *b = nullptr, *x = nullptr, *r = nullptr, *stage = nullptr;
+  double *p = nullptr, *s = nullptr, *q = nullptr, *t = nullptr, *qraw = nullptr, *traw = nullptr, *rt0 = nullptr;
+  float *fx = nullptr, *fr = nullptr, *fp = nullptr, *fs = nullptr, *fq = nullptr, *ft = nullptr,
+        *fqraw = nullptr, *ftraw = nullptr, *frt0 = nullptr;
+  IterState* st = nullptr;
+  IterState* hst = nullptr;
+  double* partials = nullptr;
+  int* dflags = nullptr;
+  int* hflags = nullptr;
+  int* dskip = nullptr;      // per-system "already converged" mask of a restart
+  // captured iteration graphs (FP64, FP32) and the layout they were made for
+  cudaGraphExec_t g64 = nullptr, g32 = nullptr;
+  int g_key64 = -1, g_key32 = -1;
+};
+
+namespace rb {
+namespace {
+
+template <typename T>
+int balloc(T** p, int64_t count) {
+  cudaFree(*p);
+  *p = nullptr;
+  if (count <= 0) count = 1;
+  const cudaError_t e = cudaMalloc(p, sizeof(T) * (size_t)count);
+  if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? RB_ENOMEM : RB_ECUDA;
+  return cudaMemset(*p, 0, sizeof(T) * (size_t)count) == cudaSuccess ? RB_OK : RB_ECUDA;
+}
+
+BatchTiles tiles_of(rb_batch_ctx* h) {
+  return BatchTiles{h->t_sys, h->t_sl0, h->t_nsl, h->s_t0, h->s_nt, h->ntiles};
+}
+
+void drop_graphs(rb_batch_ctx* h) {
+  if (h->g64) cudaGraphExecDestroy(h->g64);
+  if (h->g32) cudaGraphExecDestroy(h->g32);
+  h->g64 = h->g32 = nullptr;
+  h->g_key64 = h->g_key32 = -1;
+}
+
+// Work list for tiles of `ts` slices: every system's slices split into tiles.
+int build_tiles(rb_batch_ctx* h, int ts, int ctas_per_sm) {
+  std::vector<int32_t> tsys, tnsl, t0(h->S), nt(h->S);
+  std::vector<int64_t> tsl0;
+  for (int i = 0; i < h->S; ++i) {
+    const int64_t sl_first = h->row0[i] / kSlice, nsl = h->npad[i] / kSlice;
+    t0[i] = (int32_t)tsys.size();
+    for (int64_t q = 0; q < nsl; q += ts) {
+      tsys.push_back(i);
+      tsl0.push_back(sl_first + q);
+      tnsl.push_back((int32_t)std::min<int64_t>(ts, nsl - q));
+    }
+    nt[i] = (int32_t)tsys.size() - t0[i];
+  }
+  h->ntiles = (int)tsys.size();
+  int rc;
+  if ((rc = balloc(&h->t_sys, h->ntiles)) || (rc = balloc(&h->t_nsl, h->ntiles)) ||
+      (rc = balloc(&h->t_sl0, h->ntiles)) || (rc = balloc(&h->s_t0, h->S)) || (rc = balloc(&h->s_nt, h->S)) ||
+      (rc = balloc(&h->partials, (int64_t)h->ntiles * kBNV)))
+    return rc;
+  RB_CUDA_TRY(cudaMemcpy(h->t_sys, tsys.data(), sizeof(int32_t) * h->ntiles, cudaMemcpyHostToDevice));
+  RB_CUDA_TRY(cudaMemcpy(h->t_nsl, tnsl.data(), sizeof(int32_t) * h->ntiles, cudaMemcpyHostToDevice));
+  RB_CUDA_TRY(cudaMemcpy(h->t_sl0, tsl0.data(), sizeof(int64_t) * h->ntiles, cudaMemcpyHostToDevice));
+  RB_CUDA_TRY(cudaMemcpy(h->s_t0, t0.data(), sizeof(int32_t) * h->S, cudaMemcpyHostToDevice));
+  RB_CUDA_TRY(cudaMemcpy(h->s_nt, nt.data(), sizeof(int32_t) * h->S, cudaMemcpyHostToDevice));
+  h->tile_slices = ts;
+  h->ctas_per_sm = ctas_per_sm;
+  h->grid = std::max(1, std::min(h->ntiles, ctas_per_sm * h->nsm));
+  drop_graphs(h);
+  return RB_OK;
+}
+
+template <typename T>
+BatchArgs<T> batch_args(rb_batch_ctx* h);
+
+template <>
+BatchArgs<double> batch_args<double>(rb_batch_ctx* h) {
+  BatchArgs<double> a{};
+  a.A = h->A.view();
+  a.Chat = h->Chat;
+  a.C = h->C;
+  a.ld = h->NP;
+  a.k = h->k;
+  a.rt0 = h->rt0;
+  a.x = h->x;   // the FP64 mode iterates on x, r directly
+  a.r = h->r;
+  a.p = h->p;
+  a.s = h->s;
+  a.qraw = h->qraw;
+  a.traw = h->traw;
+  a.q = h->k > 0 ? h->q : h->qraw;
+  a.t = h->k > 0 ? h->t : h->traw;
+  a.st = h->st;
+  a.partials = h->partials;
+  a.tiles = tiles_of(h);
+  return a;
+}
+
+template <>
+BatchArgs<float> batch_args<float>(rb_batch_ctx* h) {
+  BatchArgs<float> a{};
+  a.A = h->A32.view();
+  a.Chat = h->fChat;
+  a.C = h->fC;
+  a.ld = h->NP;
+  a.k = h->k;
+  a.rt0 = h->frt0;
+  a.x = h->fx;
+  a.r = h->fr;
+  a.p = h->fp;
+  a.s = h->fs;
+  a.qraw = h->fqraw;
+  a.traw = h->ftraw;
+  a.q = h->k > 0 ? h->fq : h->fqraw;
+  a.t = h->k > 0 ? h->ft : h->ftraw;
+  a.st = h->st;
+  a.partials = h->partials;
+  a.tiles = tiles_of(h);
+  return a;
+}
+
+template <typename T, int KB>
+cudaError_t launch_iteration_kb(const BatchArgs<T>& a, int grid, cudaStream_t s) {
+  kb_spmv<T, KB, false><<<grid, kBlock, 0, s>>>(a);
+  kb_p2<T, KB><<<grid, kBlock, 0, s>>>(a);
+  kb_spmv<T, KB, true><<<grid, kBlock, 0, s>>>(a);
+  if (KB > 0) kb_p4<T, KB><<<grid, kBlock, 0, s>>>(a);
+  kb_p5<T, KB><<<grid, kBlock, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_iteration_b(const BatchArgs<T>& a, int grid, cudaStream_t s) {
+  count_launches(a.k > 0 ? 5 : 4);
+  return a.k > 0 ? launch_iteration_kb<T, kBK>(a, grid, s) : launch_iteration_kb<T, 0>(a, grid, s);
+}
+
+int poll_iters_b(rb_batch_ctx* h) { return h->o.poll > 0 ? h->o.poll : 8; }
+
+// Graph of poll iterations plus the gather of the done flags.
+template <typename T>
+int iterate_b(rb_batch_ctx* h, int64_t max_itn_all) {
+  cudaGraphExec_t* g = std::is_same<T, float>::value ? &h->g32 : &h->g64;
+  int* key = std::is_same<T, float>::value ? &h->g_key32 : &h->g_key64;
+  const int want = h->k * 100000 + h->tile_slices * 100 + h->ctas_per_sm;
+  if (!*g || *key != want) {
+    if (*g) cudaGraphExecDestroy(*g);
+    *g = nullptr;
+    const BatchArgs<T> a = batch_args<T>(h);
+    RB_CUDA_TRY(cudaStreamBeginCapture(h->cs, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaSuccess;
+    for (int it = 0; it < poll_iters_b(h) && e == cudaSuccess; ++it) e = launch_iteration_b<T>(a, h->grid, h->cs);
+    if (e == cudaSuccess) {
+      kb_flags<<<(h->S + 255) / 256, 256, 0, h->cs>>>(h->st, h->S, h->dflags);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->hflags, h->dflags, sizeof(int) * h->S, cudaMemcpyDeviceToHost, h->cs);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(h->cs, &graph);
+    if (e != cudaSuccess || ec != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      return RB_ECUDA;
+    }
+    const cudaError_t ei = cudaGraphInstantiate(g, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ei != cudaSuccess) return RB_ECUDA;
+    *key = want;
+  }
+  // every system stops by its max_itn (finish_p5), so this bound only
+  // guards against a state that never reports done
+  for (int64_t launch = 0;; ++launch) {
+    if (launch > max_itn_all / poll_iters_b(h) + 4) return RB_ETIMEOUT;
+    RB_CUDA_TRY(cudaGraphLaunch(*g, h->us));
+    count_launches((long long)poll_iters_b(h) * (h->k > 0 ? 5 : 4) + 1);
+    RB_CUDA_TRY(cudaStreamSynchronize(h->us));
+    bool all = true;
+    for (int i = 0; i < h->S && all; ++i) all = h->hflags[i] != 0;
+    if (all) return RB_OK;
+  }
+}
+
+int sync_b(rb_batch_ctx* h) {
+  RB_CUDA_TRY(cudaStreamSynchronize(h->us));
+  return RB_OK;
+}
+
+// Per-system reductions into st[i].red, copied back to hst[i].red.
+int sysdots(rb_batch_ctx* h, const SysDots& d, bool read_back = true) {
+  count_launches(1);
+  kb_sysdots<<<h->grid, kBlock, 0, h->us>>>(d, h->NP, h->st, h->partials, tiles_of(h));
+  RB_CUDA_TRY(cudaGetLastError());
+  if (!read_back) return RB_OK;
+  RB_CUDA_TRY(cudaMemcpyAsync(h->hst, h->st, sizeof(IterState) * h->S, cudaMemcpyDeviceToHost, h->us));
+  return sync_b(h);
+}
+
+int gemv_b(rb_batch_ctx* h, double* y, const double* M, double sign, bool xc, const int* skip = nullptr) {
+  if (h->k == 0) return RB_OK;
+  count_launches(1);
+  if (xc) kb_gemv<true><<<h->grid, kBlock, 0, h->us>>>(y, M, h->NP, h->k, sign, h->st, skip, tiles_of(h));
+  else kb_gemv<false><<<h->grid, kBlock, 0, h->us>>>(y, M, h->NP, h->k, sign, h->st, skip, tiles_of(h));
+  RB_CUDA_TRY(cudaGetLastError());
+  return RB_OK;
+}
+
+SysLayout layout_of(rb_batch_ctx* h) { return SysLayout{h->d_row0, h->d_n, h->d_cofs}; }
+
+}  // namespace
+}  // namespace rb
+
+namespace rb {
+namespace {
+
+// Autotuner: time the SpMV + projection pass (P1) for each candidate tile size
+// and CTAs per SM on the current matrices and space; keep the fastest.
+// RB_TIMING in the environment prints every candidate.
+int autotune(rb_batch_ctx* h) {
+  const int cand_ts[] = {4, 8, 16, 32, 64};
+  const int cand_cps[] = {2, 4, 8};
+  const bool print = getenv("RB_TIMING") != nullptr;
+  double best = 1e30;
+  int bts = 8, bcps = 4;
+  cudaEvent_t e0, e1;
+  RB_CUDA_TRY(cudaEventCreate(&e0));
+  RB_CUDA_TRY(cudaEventCreate(&e1));
+  const bool f32 = h->o.precision == RB_MIXED;
+  for (int ts : cand_ts) {
+    for (int cps : cand_cps) {
+      int rc = build_tiles(h, ts, cps);
+      if (rc) return rc;
+      float total = 0.f;
+      for (int rep = 0; rep < 4; ++rep) {
+        RB_CUDA_TRY(cudaMemsetAsync(h->st, 0, sizeof(IterState) * h->S, h->us));
+        RB_CUDA_TRY(cudaEventRecord(e0, h->us));
+        if (f32) {
+          const BatchArgs<float> a = batch_args<float>(h);
+          if (h->k > 0) kb_spmv<float, kBK, false><<<h->grid, kBlock, 0, h->us>>>(a);
+          else kb_spmv<float, 0, false><<<h->grid, kBlock, 0, h->us>>>(a);
+        } else {
+          const BatchArgs<double> a = batch_args<double>(h);
+          if (h->k > 0) kb_spmv<double, kBK, false><<<h->grid, kBlock, 0, h->us>>>(a);
+          else kb_spmv<double, 0, false><<<h->grid, kBlock, 0, h->us>>>(a);
+        }
+        count_launches(1);
+        RB_CUDA_TRY(cudaGetLastError());
+        RB_CUDA_TRY(cudaEventRecord(e1, h->us));
+        RB_CUDA_TRY(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (rep > 0) total += ms;
+      }
+      const double avg = total / 3.0;
+      if (print) fprintf(stderr, "rb_batch_tune tile_slices %3d ctas_per_sm %d tiles %7d  %.4f ms\n", ts, cps, h->ntiles, avg);
+      if (avg < best) {
+        best = avg;
+        bts = ts;
+        bcps = cps;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  h->tune_ms = best;
+  RB_CUDA_TRY(cudaMemsetAsync(h->st, 0, sizeof(IterState) * h->S, h->us));
+  return build_tiles(h, bts, bcps);
+}
+
+// Per-system recycle setup (Sec. 3) for the kin columns in U: C = A U,
+// C~ = A^T U (U~ = U), M_i = C~_i^T C_i, SVD, C-hat_i = C~_i (M_i^+)^T with the
+// pseudo-inverse of the singular values above the drop tolerance (rank
+// deficiency needs no rotation: C M^+ C~^T is still the projector).
+int batch_setup(rb_batch_ctx* h) {
+  h->setup_owed = false;
+  h->k = 0;
+  drop_graphs(h);
+  if (h->kin == 0) return RB_OK;
+  const int kin = h->kin;
+  const int64_t ld = h->NP;
+  const int gs = std::max(1, 4 * h->nsm);
+  for (int j = 0; j < kin; ++j) {
+    RB_CUDA_TRY(spmv<double>(h->A.view(), h->U + j * ld, h->C + j * ld, 1.0, 0.0, gs, h->us));
+    RB_CUDA_TRY(spmv<double>(h->AT.view(), h->U + j * ld, h->Ct + j * ld, 1.0, 0.0, gs, h->us));
+  }
+  h->k = kin;   // the reductions below use k columns
+  std::vector<double> M((size_t)h->S * kin * kin);
+  for (int j = 0; j < kin; ++j) {   // column j of every M_i: C~_i^T C_i(:, j)
+    SysDots d{};
+    d.M = h->Ct;
+    d.km = kin;
+    d.v = h->C + j * ld;
+    int rc = sysdots(h, d);
+    if (rc) return rc;
+    for (int i = 0; i < h->S; ++i)
+      for (int r = 0; r < kin; ++r) M[(size_t)i * kin * kin + r + (size_t)j * kin] = h->hst[i].red[r];
+  }
+  const double drop = h->o.precision == RB_MIXED ? 1e-6 : 1e-12;
+  std::vector<double> R((size_t)h->S * kBK * kBK, 0.0), P((size_t)kin * kin), Q((size_t)kin * kin), sig(kin);
+  h->k_used.assign(h->S, 0);
+  for (int i = 0; i < h->S; ++i) {
+    const double* Mi = &M[(size_t)i * kin * kin];
+    for (int e = 0; e < kin * kin; ++e)
+      if (!std::isfinite(Mi[e])) return RB_ENONFINITE;
+    svd_small(kin, Mi, P.data(), sig.data(), Q.data());
+    int kk = 0;
+    if (sig[0] > 0)
+      while (kk < kin && sig[kk] >= drop * sig[0]) ++kk;
+    h->k_used[i] = kk;
+    double* Ri = &R[(size_t)i * kBK * kBK];   // Mpt = P_kk S^-1 Q_kk^T, k x k column-major (ld k)
+    for (int c = 0; c < kin; ++c)
+      for (int r = 0; r < kin; ++r) {
+        double acc = 0.0;
+        for (int j = 0; j < kk; ++j) acc += P[r + (size_t)j * kin] * Q[c + (size_t)j * kin] / sig[j];
+        Ri[r + c * kin] = acc;
+      }
+  }
+  RB_CUDA_TRY(cudaMemcpyAsync(h->dR, R.data(), sizeof(double) * R.size(), cudaMemcpyHostToDevice, h->us));
+  count_launches(1);
+  kb_gemm_sys<<<h->grid, kBlock, 0, h->us>>>(h->Chat, h->Ct, ld, kin, h->dR, tiles_of(h));
+  RB_CUDA_TRY(cudaGetLastError());
+  if (h->o.precision == RB_MIXED) {   // the FP32 copies exist in the mixed mode only
+    RB_CUDA_TRY(to_float(h->U, h->fU, ld * kin, h->us));
+    RB_CUDA_TRY(to_float(h->C, h->fC, ld * kin, h->us));
+    RB_CUDA_TRY(to_float(h->Chat, h->fChat, ld * kin, h->us));
+  }
+  return sync_b(h);
+}
+
+// Start of Alg. 2 for every system from xv (eq. (3.5)): r = rhs - A xv with the
+// projections, the per-system shadow r~_0 (SplitMix64 on the system's own
+// row index, the generator of the single-system path), the initial states.
+// thresh[i] is the system's convergence threshold on ||r||^2; systems with
+// skip[i] start done.  The vectors are FP64; the caller converts for FP32.
+int batch_start(rb_batch_ctx* h, const double* rhs, double* xv, const std::vector<double>& thresh2,
+                const std::vector<char>& skip, const std::vector<int>& max_itn) {
+  const int64_t ld = h->NP;
+  const int gs = std::max(1, 4 * h->nsm);
+  RB_CUDA_TRY(cudaMemcpyAsync(h->r, rhs, sizeof(double) * ld, cudaMemcpyDeviceToDevice, h->us));
+  RB_CUDA_TRY(spmv<double>(h->A.view(), xv, h->r, -1.0, 1.0, gs, h->us));
+  int rc;
+  if (h->k > 0) {
+    // a skipped system keeps xv: the oblique projection could raise the
+    // residual of a system that has already converged
+    std::vector<int> sk(skip.begin(), skip.end());
+    RB_CUDA_TRY(cudaMemcpyAsync(h->dskip, sk.data(), sizeof(int) * h->S, cudaMemcpyHostToDevice, h->us));
+    SysDots d{};
+    d.M = h->Chat; d.km = h->k; d.v = h->r;
+    if ((rc = sysdots(h, d, false))) return rc;
+    if ((rc = gemv_b(h, xv, h->U, 1.0, false, h->dskip))) return rc;
+    RB_CUDA_TRY(cudaStreamSynchronize(h->us));   // sk is read by the copy above
+    if ((rc = gemv_b(h, h->r, h->C, -1.0, false))) return rc;
+  }
+  for (int i = 0; i < h->S; ++i)
+    RB_CUDA_TRY(shadow(h->rt0 + h->row0[i], h->n[i], h->npad[i], h->o.shadow_seed, h->us));
+  if (h->k > 0) {
+    SysDots d{};
+    d.M = h->C; d.km = h->k; d.v = h->rt0;
+    if ((rc = sysdots(h, d, false))) return rc;
+    if ((rc = gemv_b(h, h->rt0, h->Chat, -1.0, false))) return rc;
+  }
+  SysDots d{};
+  d.M = h->k > 0 ? h->C : nullptr; d.km = h->k; d.v = h->rt0;
+  d.nd = 2;
+  d.pa[0] = h->rt0; d.pb[0] = h->r;
+  d.pa[1] = h->r; d.pb[1] = h->r;
+  if ((rc = sysdots(h, d))) return rc;
+  for (int i = 0; i < h->S; ++i) {
+    IterState& s = h->hst[i];
+    const double rho = s.red[h->k], rn2 = s.red[h->k + 1];
+    double cr[kBK];
+    for (int j = 0; j < h->k; ++j) cr[j] = s.red[j];
+    std::memset(&s, 0, sizeof(IterState));
+    s.k = h->k;
+    for (int j = 0; j < h->k; ++j) s.cr[j] = cr[j];
+    s.rho = rho;
+    s.rnorm2 = rn2;
+    s.thresh2 = thresh2[i];
+    s.max_itn = max_itn[i];
+    s.status = RB_OK;
+    if (skip[i] || rn2 <= thresh2[i]) s.done = 1;
+    else if (!std::isfinite(rho) || !std::isfinite(rn2)) { s.status = RB_ENONFINITE; s.done = 1; }
+    else if (rho == 0.0) { s.status = RB_EBREAKDOWN_RHO; s.done = 1; }
+  }
+  RB_CUDA_TRY(cudaMemcpyAsync(h->st, h->hst, sizeof(IterState) * h->S, cudaMemcpyHostToDevice, h->us));
+  RB_CUDA_TRY(cudaMemcpyAsync(h->p, h->r, sizeof(double) * ld, cudaMemcpyDeviceToDevice, h->us));
+  return sync_b(h);
+}
+
+// ||b_i - A_i x_i||^2 and ||b_i||^2 of every system into out (FP64).
+int true_residuals(rb_batch_ctx* h, std::vector<double>& rn2, std::vector<double>& bn2) {
+  const int gs = std::max(1, 4 * h->nsm);
+  RB_CUDA_TRY(cudaMemcpyAsync(h->r, h->b, sizeof(double) * h->NP, cudaMemcpyDeviceToDevice, h->us));
+  RB_CUDA_TRY(spmv<double>(h->A.view(), h->x, h->r, -1.0, 1.0, gs, h->us));
+  SysDots d{};
+  d.nd = 2;
+  d.pa[0] = h->r; d.pb[0] = h->r;
+  d.pa[1] = h->b; d.pb[1] = h->b;
+  int rc = sysdots(h, d);
+  if (rc) return rc;
+  rn2.resize(h->S);
+  bn2.resize(h->S);
+  for (int i = 0; i < h->S; ++i) {
+    rn2[i] = h->hst[i].red[0];
+    bn2[i] = h->hst[i].red[1];
+  }
+  return RB_OK;
+}
+
+}  // namespace
+}  // namespace rb
+
+// ============================================================ C ABI
+using namespace rb;
+
+extern "C" int rbicgstab_batch_create(rb_batch* out, const rb_opts* opts) {
+  if (!out) return RB_EINVAL;
+  *out = nullptr;
+  rb_opts o = opts ? *opts : rb_opts{};
+  if (o.tol == 0) o.tol = 1e-8;
+  if (o.shadow_seed == 0) o.shadow_seed = 0x5EED;
+  if (o.k_max < 0 || o.k_max > kBK || !(o.tol > 0) || o.max_itn < 0 || o.poll < 0 ||
+      (o.precision != RB_FP64 && o.precision != RB_MIXED))
+    return RB_EINVAL;
+  rb_batch_ctx* h = new rb_batch_ctx();
+  h->o = o;
+  h->us = (cudaStream_t)o.cuda_stream;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&h->cs, cudaStreamNonBlocking) != cudaSuccess) {
+    delete h;
+    return RB_ECUDA;
+  }
+  *out = h;
+  return RB_OK;
+}
+
+extern "C" int rbicgstab_batch_destroy(rb_batch h) {
+  if (!h) return RB_OK;
+  cudaStreamSynchronize(h->us);
+  drop_graphs(h);
+  sell_free(&h->A);
+  sell_free(&h->AT);
+  cudaFree(h->A32.val);
+  void* ptrs[] = {h->rp, h->ci, h->trp, h->tci, h->tsrc, h->cv, h->tcv, h->t_sys, h->t_nsl, h->s_t0, h->s_nt,
+                  h->t_sl0, h->d_row0, h->d_n, h->d_cofs, h->U, h->C, h->Ct, h->Chat, h->dR, h->fU, h->fC, h->fChat,
+                  h->b, h->x, h->r, h->stage, h->p, h->s, h->q, h->t, h->qraw, h->traw, h->rt0, h->fx, h->fr, h->fp,
+                  h->fs, h->fq, h->ft, h->fqraw, h->ftraw, h->frt0, h->st, h->partials, h->dflags, h->dskip};
+  for (void* p : ptrs) cudaFree(p);
+  if (h->hst) cudaFreeHost(h->hst);
+  if (h->hflags) cudaFreeHost(h->hflags);
+  if (h->cs) cudaStreamDestroy(h->cs);
+  delete h;
+  return RB_OK;
+}
+
+extern "C" int rbicgstab_batch_set_matrices(rb_batch h, int32_t nsys, const int64_t* n, const int32_t* row_ptr,
+                                             const int32_t* col, const double* val) {
+  if (!h || nsys < 1 || !n || !row_ptr || !col || !val) return RB_EINVAL;
+  // the padded block-diagonal CSR (host), every system's rows padded to 32
+  h->S = nsys;
+  h->n.assign(n, n + nsys);
+  h->npad.resize(nsys);
+  h->row0.resize(nsys);
+  h->cofs.resize(nsys);
+  h->nnz_sys.resize(nsys);
+  int64_t NP = 0, NC = 0, nnz = 0, rpo = 0;
+  for (int i = 0; i < nsys; ++i) {
+    if (n[i] < 1) return RB_EINVAL;
+    h->npad[i] = (n[i] + kSlice - 1) / kSlice * kSlice;
+    h->row0[i] = NP;
+    h->cofs[i] = NC;
+    const int32_t* rpi = row_ptr + rpo;
+    if (rpi[0] != 0) return RB_EBADCSR;
+    for (int64_t r = 0; r < n[i]; ++r)
+      if (rpi[r + 1] < rpi[r]) return RB_EBADCSR;
+    h->nnz_sys[i] = rpi[n[i]];
+    NP += h->npad[i];
+    NC += n[i];
+    nnz += rpi[n[i]];
+    rpo += n[i] + 1;
+  }
+  if (NP >= INT32_MAX || nnz >= INT32_MAX) return RB_EINVAL;
+  std::vector<int32_t> grp(NP + 1), gci(nnz);
+  int64_t ebase = 0;
+  rpo = 0;
+  for (int i = 0; i < nsys; ++i) {
+    const int32_t* rpi = row_ptr + rpo;
+    for (int64_t r = 0; r < h->npad[i]; ++r) grp[h->row0[i] + r] = (int32_t)(ebase + (r < n[i] ? rpi[r] : rpi[n[i]]));
+    ebase += rpi[n[i]];
+    rpo += n[i] + 1;
+  }
+  // columns: the per-system local indices shifted to the system's first row
+  int64_t e = 0;
+  for (int i = 0; i < nsys; ++i)
+    for (int64_t q = 0; q < h->nnz_sys[i]; ++q, ++e) {
+      const int32_t c = col[e];
+      if (c < 0 || c >= n[i]) return RB_EBADCSR;
+      gci[e] = (int32_t)(c + h->row0[i]);
+    }
+  grp[NP] = (int32_t)nnz;
+  h->NP = NP;
+  h->NC = NC;
+  h->nnz = nnz;
+  int rc;
+  if ((rc = balloc(&h->rp, NP + 1)) || (rc = balloc(&h->ci, nnz)) || (rc = balloc(&h->cv, nnz)) ||
+      (rc = balloc(&h->trp, NP + 1)) || (rc = balloc(&h->tci, nnz)) || (rc = balloc(&h->tsrc, nnz)) ||
+      (rc = balloc(&h->tcv, nnz)))
+    return rc;
+  RB_CUDA_TRY(cudaMemcpy(h->rp, grp.data(), sizeof(int32_t) * (NP + 1), cudaMemcpyHostToDevice));
+  RB_CUDA_TRY(cudaMemcpy(h->ci, gci.data(), sizeof(int32_t) * nnz, cudaMemcpyHostToDevice));
+  // no stencil slices: a stencil slice lets a row that lacks an offset gather
+  // (with a zero weight) from the next system's rows, which would carry a
+  // failed system's non-finite values into its neighbour
+  if ((rc = sell_build(NP, nnz, h->rp, h->ci, &h->A, h->us, false))) return rc;
+  if ((rc = csr_transpose(NP, nnz, h->rp, h->ci, h->trp, h->tci, h->tsrc, h->us))) return rc;
+  if ((rc = sell_build(NP, nnz, h->trp, h->tci, &h->AT, h->us, false))) return rc;
+  cudaFree(h->A32.val);
+  h->A32 = SellBuf<float>();
+  h->A32.nslices = h->A.nslices;
+  h->A32.cap = h->A.cap;
+  h->A32.slice_ptr = h->A.slice_ptr;
+  h->A32.width = h->A.width;
+  h->A32.col = h->A.col;
+  h->A32.perm = h->A.perm;
+  h->A32.offs = h->A.offs;
+  h->A32.offs_stride = h->A.offs_stride;
+  if ((rc = balloc(&h->A32.val, h->A.cap))) return rc;
+  // layout, vectors, states
+  if ((rc = balloc(&h->d_row0, nsys)) || (rc = balloc(&h->d_n, nsys)) || (rc = balloc(&h->d_cofs, nsys))) return rc;
+  RB_CUDA_TRY(cudaMemcpy(h->d_row0, h->row0.data(), sizeof(int64_t) * nsys, cudaMemcpyHostToDevice));
+  RB_CUDA_TRY(cudaMemcpy(h->d_n, h->n.data(), sizeof(int64_t) * nsys, cudaMemcpyHostToDevice));
+  RB_CUDA_TRY(cudaMemcpy(h->d_cofs, h->cofs.data(), sizeof(int64_t) * nsys, cudaMemcpyHostToDevice));
+  double** dv[] = {&h->b, &h->x, &h->r, &h->p, &h->s, &h->q, &h->t, &h->qraw, &h->traw, &h->rt0};
+  for (double** v : dv)
+    if ((rc = balloc(v, NP))) return rc;
+  if ((rc = balloc(&h->stage, std::max<int64_t>(NC, NC * std::max(1, h->o.k_max))))) return rc;
+  if (h->o.precision == RB_MIXED) {
+    float** fv[] = {&h->fx, &h->fr, &h->fp, &h->fs, &h->fq, &h->ft, &h->fqraw, &h->ftraw, &h->frt0};
+    for (float** v : fv)
+      if ((rc = balloc(v, NP))) return rc;
+  }
+  if (h->o.k_max > 0) {
+    double** bv[] = {&h->U, &h->C, &h->Ct, &h->Chat};
+    for (double** v : bv)
+      if ((rc = balloc(v, NP * h->o.k_max))) return rc;
+    if (h->o.precision == RB_MIXED) {
+      float** fb[] = {&h->fU, &h->fC, &h->fChat};
+      for (float** v : fb)
+        if ((rc = balloc(v, NP * h->o.k_max))) return rc;
+    }
+    if ((rc = balloc(&h->dR, (int64_t)nsys * kBK * kBK))) return rc;
+  }
+  if ((rc = balloc(&h->st, nsys)) || (rc = balloc(&h->dflags, nsys)) || (rc = balloc(&h->dskip, nsys))) return rc;
+  if (h->hst) cudaFreeHost(h->hst);
+  if (h->hflags) cudaFreeHost(h->hflags);
+  h->hst = nullptr;
+  h->hflags = nullptr;
+  if (cudaMallocHost(&h->hst, sizeof(IterState) * nsys) != cudaSuccess ||
+      cudaMallocHost(&h->hflags, sizeof(int) * nsys) != cudaSuccess)
+    return RB_ENOMEM;
+  h->kin = h->k = 0;
+  h->have = true;
+  h->ntiles = 0;
+  h->tune_ms = 0.0;
+  if ((rc = build_tiles(h, 8, 4))) return rc;
+  return rbicgstab_batch_set_values(h, val, RB_HOST);
+}
+
+extern "C" int rbicgstab_batch_set_values(rb_batch h, const double* val, int where) {
+  if (!h || !val || (where != RB_HOST && where != RB_DEVICE)) return RB_EINVAL;
+  if (!h->have) return RB_EDIM;
+  RB_CUDA_TRY(cudaMemcpyAsync(h->cv, val, sizeof(double) * h->nnz,
+                              where == RB_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, h->us));
+  int rc;
+  if ((rc = check_finite(h->cv, h->nnz, h->dflags, h->us) == cudaSuccess ? RB_OK : RB_ECUDA)) return rc;
+  int bad = 0;
+  RB_CUDA_TRY(cudaMemcpyAsync(&bad, h->dflags, sizeof(int), cudaMemcpyDeviceToHost, h->us));
+  if ((rc = sync_b(h))) return rc;
+  if (bad) return RB_ENONFINITE;
+  if ((rc = sell_fill_values<double>(h->A, h->cv, h->us))) return rc;
+  if ((rc = gather_values(h->nnz, h->tsrc, h->cv, h->tcv, h->us))) return rc;
+  if ((rc = sell_fill_values<double>(h->AT, h->tcv, h->us))) return rc;
+  if (h->o.precision == RB_MIXED && (rc = sell_fill_values<float>(h->A32, h->cv, h->us))) return rc;
+  h->setup_owed = h->kin > 0;
+  h->k = 0;
+  drop_graphs(h);
+  return sync_b(h);
+}
+
+extern "C" int rbicgstab_batch_set_recycle(rb_batch h, int32_t k, const double* U, int where) {
+  if (!h || k < 0 || k > h->o.k_max || (k > 0 && !U) || (where != RB_HOST && where != RB_DEVICE)) return RB_EINVAL;
+  if (!h->have) return RB_EDIM;
+  h->kin = k;
+  h->k = 0;
+  h->setup_owed = k > 0;
+  h->tune_ms = 0.0;
+  drop_graphs(h);
+  if (k == 0) return RB_OK;
+  RB_CUDA_TRY(cudaMemcpyAsync(h->stage, U, sizeof(double) * h->NC * k,
+                              where == RB_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, h->us));
+  count_launches(1);
+  kb_relayout<true><<<h->grid, kBlock, 0, h->us>>>(h->U, h->stage, k, h->NP, layout_of(h), tiles_of(h));
+  RB_CUDA_TRY(cudaGetLastError());
+  return sync_b(h);
+}
+
+extern "C" int rbicgstab_batch_info(rb_batch h, int32_t* tile_slices, int32_t* ctas_per_sm, int32_t* ntiles,
+                                    double* tune_ms) {
+  if (!h) return RB_EINVAL;
+  if (tile_slices) *tile_slices = h->tile_slices;
+  if (ctas_per_sm) *ctas_per_sm = h->ctas_per_sm;
+  if (ntiles) *ntiles = h->ntiles;
+  if (tune_ms) *tune_ms = h->tune_ms;
+  return RB_OK;
+}
+
+extern "C" int rbicgstab_batch_solve(rb_batch h, const double* b, double* x, int where, rb_stats* st_out) {
+  if (!h || !b || !x || (where != RB_HOST && where != RB_DEVICE)) return RB_EINVAL;
+  if (!h->have) return RB_EDIM;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  auto done = [&](int code) {
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    return code;
+  };
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return done(RB_ECUDA);
+  cudaEventRecord(e0, h->us);
+  int rc;
+  if (h->setup_owed && (rc = batch_setup(h))) return done(rc);
+  if (h->tune_ms == 0.0 && (rc = autotune(h))) return done(rc);
+  const auto kind = where == RB_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  // inputs into the padded layout
+  RB_CUDA_TRY(cudaMemcpyAsync(h->stage, b, sizeof(double) * h->NC, kind, h->us));
+  kb_relayout<true><<<h->grid, kBlock, 0, h->us>>>(h->b, h->stage, 1, h->NP, layout_of(h), tiles_of(h));
+  RB_CUDA_TRY(cudaMemcpyAsync(h->stage, x, sizeof(double) * h->NC, kind, h->us));
+  kb_relayout<true><<<h->grid, kBlock, 0, h->us>>>(h->x, h->stage, 1, h->NP, layout_of(h), tiles_of(h));
+  count_launches(2);
+  RB_CUDA_TRY(cudaGetLastError());
+  for (double* v : {h->b, h->x}) {
+    int f = 0;
+    RB_CUDA_TRY(check_finite(v, h->NP, h->dflags, h->us));
+    RB_CUDA_TRY(cudaMemcpyAsync(&f, h->dflags, sizeof(int), cudaMemcpyDeviceToHost, h->us));
+    if ((rc = sync_b(h))) return done(rc);
+    if (f) return done(RB_ENONFINITE);
+  }
+  const int S = h->S;
+  std::vector<int> max_itn(S);
+  for (int i = 0; i < S; ++i)
+    max_itn[i] = h->o.max_itn > 0 ? h->o.max_itn : (int)std::min<int64_t>(h->n[i], 20000);
+  std::vector<double> rn2, bn2;
+  if ((rc = true_residuals(h, rn2, bn2))) return done(rc);
+  const double tol2 = h->o.tol * h->o.tol;
+  std::vector<int> iters(S, 0), status(S, RB_OK), outer(S, 0);
+  std::vector<double> rec2(S, 0.0);
+  if (h->o.precision == RB_FP64) {
+    std::vector<double> th(S);
+    for (int i = 0; i < S; ++i) th[i] = tol2 * bn2[i];
+    if ((rc = batch_start(h, h->b, h->x, th, std::vector<char>(S, 0), max_itn))) return done(rc);
+    if ((rc = iterate_b<double>(h, *std::max_element(max_itn.begin(), max_itn.end())))) return done(rc);
+    if ((rc = gemv_b(h, h->x, h->U, -1.0, true))) return done(rc);
+    RB_CUDA_TRY(cudaMemcpyAsync(h->hst, h->st, sizeof(IterState) * S, cudaMemcpyDeviceToHost, h->us));
+    if ((rc = sync_b(h))) return done(rc);
+    for (int i = 0; i < S; ++i) {
+      iters[i] = h->hst[i].iter;
+      status[i] = h->hst[i].status;
+      rec2[i] = h->hst[i].rnorm2;
+      outer[i] = 1;
+    }
+  } else {
+    // restarts of the FP32 recycled solve on the FP64 residual
+    for (int restart = 0; restart < 8; ++restart) {
+      std::vector<char> conv(S);
+      bool all = true;
+      for (int i = 0; i < S; ++i) {
+        conv[i] = rn2[i] <= tol2 * bn2[i] || status[i] != RB_OK;
+        all = all && conv[i];
+      }
+      if (all) break;
+      // correction equation A d = r: rhs = r (kept in qraw), start d = s = 0
+      RB_CUDA_TRY(cudaMemcpyAsync(h->qraw, h->r, sizeof(double) * h->NP, cudaMemcpyDeviceToDevice, h->us));
+      RB_CUDA_TRY(cudaMemsetAsync(h->s, 0, sizeof(double) * h->NP, h->us));
+      std::vector<double> th(S);
+      std::vector<int> cap(S);
+      for (int i = 0; i < S; ++i) {
+        th[i] = std::max(0.01 * tol2 * bn2[i], 1e-10 * rn2[i]);
+        cap[i] = std::max(1, max_itn[i] - iters[i]);
+      }
+      if ((rc = batch_start(h, h->qraw, h->s, th, conv, cap))) return done(rc);
+      RB_CUDA_TRY(to_float(h->r, h->fr, h->NP, h->us));
+      RB_CUDA_TRY(to_float(h->r, h->fp, h->NP, h->us));
+      RB_CUDA_TRY(to_float(h->rt0, h->frt0, h->NP, h->us));
+      RB_CUDA_TRY(cudaMemsetAsync(h->fx, 0, sizeof(float) * h->NP, h->us));
+      if ((rc = iterate_b<float>(h, *std::max_element(cap.begin(), cap.end())))) return done(rc);
+      // x += d_0 + x_inner - U x_c
+      LinComb lc{};
+      lc.x[0] = h->s;
+      lc.c[0] = 1.0;
+      lc.nx = 1;
+      RB_CUDA_TRY(lincomb(h->x, 1.0, lc, h->NP, std::max(1, 4 * h->nsm), h->us));
+      RB_CUDA_TRY(add_float_to_double(h->x, h->fx, h->NP, h->us));
+      if ((rc = gemv_b(h, h->x, h->U, -1.0, true))) return done(rc);
+      RB_CUDA_TRY(cudaMemcpyAsync(h->hst, h->st, sizeof(IterState) * S, cudaMemcpyDeviceToHost, h->us));
+      if ((rc = sync_b(h))) return done(rc);
+      for (int i = 0; i < S; ++i) {
+        if (conv[i]) continue;
+        iters[i] += h->hst[i].iter;
+        outer[i] += 1;
+        const int s_in = h->hst[i].status;
+        if (s_in == RB_ENONFINITE) status[i] = s_in;
+        if (iters[i] >= max_itn[i] && status[i] == RB_OK) status[i] = RB_ENOTCONV;
+      }
+      if ((rc = true_residuals(h, rn2, bn2))) return done(rc);
+    }
+    for (int i = 0; i < S; ++i) {
+      rec2[i] = rn2[i];
+      if (status[i] == RB_OK && rn2[i] > tol2 * bn2[i]) status[i] = RB_ENOTCONV;
+    }
+  }
+  std::vector<double> tr2;
+  if ((rc = true_residuals(h, tr2, bn2))) return done(rc);
+  kb_relayout<false><<<h->grid, kBlock, 0, h->us>>>(h->x, h->stage, 1, h->NP, layout_of(h), tiles_of(h));
+  count_launches(1);
+  RB_CUDA_TRY(cudaGetLastError());
+  RB_CUDA_TRY(cudaMemcpyAsync(x, h->stage, sizeof(double) * h->NC,
+                              where == RB_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, h->us));
+  cudaEventRecord(e1, h->us);
+  if ((rc = sync_b(h))) return done(rc);
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  int first_fail = RB_OK;
+  for (int i = 0; i < S; ++i) {
+    if (status[i] != RB_OK && first_fail == RB_OK) first_fail = status[i];
+    if (!st_out) continue;
+    rb_stats& o = st_out[i];
+    o = rb_stats{};
+    o.iters = iters[i];
+    o.status = status[i];
+    o.k_used = h->k > 0 ? h->k_used[i] : 0;
+    o.seeds_used = 1;
+    o.matvecs = 2 * (int64_t)iters[i] + outer[i];
+    o.matvecs_setup = h->k > 0 ? 2 * h->k : 0;
+    o.outer = outer[i];
+    o.relres_rec = bn2[i] > 0 ? std::sqrt(rec2[i] / bn2[i]) : 0.0;
+    o.relres_true = bn2[i] > 0 ? std::sqrt(tr2[i] / bn2[i]) : 0.0;
+    o.ms_total = ms;
+  }
+  return done(first_fail);
+}

@@ -30,6 +30,7 @@ struct IterArgs {
   double* partials;
   int64_t npad;
   int nrhs;
+  int stage_bulk;  // staged passes: tiles by bulk copies (1) or per-thread cp.async (0)
 };
 
 struct Grids {
@@ -99,7 +100,8 @@ int csr_validate(int64_t n, int64_t nnz, const int32_t* row_ptr, const int32_t* 
                  const double* val, int* d_flag, int* bad, cudaStream_t s);
 // Build SELL-32 structure from device CSR (allocates inside `out`).
 int sell_build(int64_t n, int64_t nnz, const int32_t* row_ptr, const int32_t* col,
-               SellBuf<double>* out, cudaStream_t s);
+               SellBuf<double>* out, cudaStream_t s,
+               bool allow_stencil = true);
 // Refill SELL values from CSR values through out->perm.
 template <typename T>
 int sell_fill_values(const SellBuf<T>& out, const double* csr_val, cudaStream_t s);

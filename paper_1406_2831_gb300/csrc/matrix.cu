@@ -178,7 +178,7 @@ template void sell_free<double>(SellBuf<double>*);
 template void sell_free<float>(SellBuf<float>*);
 
 int sell_build(int64_t n, int64_t nnz, const int32_t* row_ptr, const int32_t* col,
-               SellBuf<double>* out, cudaStream_t s) {
+               SellBuf<double>* out, cudaStream_t s, bool allow_stencil) {
   count_launches(3);
   sell_free(out);
   const int64_t nslices = (n + kSlice - 1) / kSlice;
@@ -215,7 +215,7 @@ int sell_build(int64_t n, int64_t nnz, const int32_t* row_ptr, const int32_t* co
   RB_CUDA_TRY(cudaMemsetAsync(dcount, 0, sizeof(unsigned long long), s));
   // RB_SELL_GENERIC in the environment keeps every slice in CSR order (the
   // stencil layout's results are bitwise equal; this switch lets tests check it)
-  if (nslices && getenv("RB_SELL_GENERIC") == nullptr) {
+  if (nslices && allow_stencil && getenv("RB_SELL_GENERIC") == nullptr) {
     k_slice_stencil<<<grid, kBlock, 0, s>>>(n, nslices, row_ptr, col, out->width, stride, out->offs, dcount);
     RB_CUDA_TRY(cudaGetLastError());
   } else if (nslices) {

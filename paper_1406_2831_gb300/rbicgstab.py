@@ -99,6 +99,18 @@ def lib():
     L.rbicgstab_sell_stats.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64)]
     L.rbicgstab_solve_l.argtypes = [vp, i32, dp, dp, ctypes.c_int, ctypes.POINTER(Stats)]
     L.rbicgstab_solve_adjoint.argtypes = [vp, dp, dp, ctypes.c_int, ctypes.POINTER(Stats)]
+    L.rbicgstab_batch_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(Opts)]
+    L.rbicgstab_batch_destroy.argtypes = [vp]
+    L.rbicgstab_batch_set_matrices.argtypes = [vp, i32, dp, dp, dp, dp]
+    L.rbicgstab_batch_set_values.argtypes = [vp, dp, ctypes.c_int]
+    L.rbicgstab_batch_set_recycle.argtypes = [vp, i32, dp, ctypes.c_int]
+    L.rbicgstab_batch_solve.argtypes = [vp, dp, dp, ctypes.c_int, ctypes.POINTER(Stats)]
+    L.rbicgstab_batch_info.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32),
+                                       ctypes.POINTER(ctypes.c_double)]
+    for name in ("rbicgstab_batch_create", "rbicgstab_batch_destroy", "rbicgstab_batch_set_matrices",
+                 "rbicgstab_batch_set_values", "rbicgstab_batch_set_recycle", "rbicgstab_batch_solve",
+                 "rbicgstab_batch_info"):
+        getattr(L, name).restype = ctypes.c_int
     L.rbicgstab_solve_adjoint.restype = ctypes.c_int
     L.rbicgstab_solve_l.restype = ctypes.c_int
     L.rbicgstab_sell_stats.restype = ctypes.c_int
@@ -410,6 +422,103 @@ class Solver:
         _check(lib().rbicgstab_pattern_outer(self._h, up, vp2, float(scale), out.data_ptr(), RB_DEVICE),
                "rbicgstab_pattern_outer")
         return out
+
+
+class Batch:
+    """Batched solves of many independent systems (rbicgstab_batch_*): one
+    launch per pass for all systems.  ``matrices`` is a list of CSR systems
+    (objects with n, row_ptr, col, val, e.g. ``inputs.CSR``); right-hand
+    sides and solutions are lists of per-system vectors (or one concatenated
+    array / CUDA tensor of sum n_i entries)."""
+
+    def __init__(self, matrices, *, k_max=0, tol=1e-8, max_itn=0, precision="fp64", poll=0,
+                 shadow_seed=0, stream=None):
+        o = Opts()
+        o.k_max = int(k_max)
+        o.cycle_s = 25
+        o.max_itn = int(max_itn)
+        o.precision = PRECISION[precision]
+        o.recycle_mode = RECYCLE["fixed" if k_max else "none"]
+        o.poll = int(poll)
+        o.tol = float(tol)
+        o.shadow_seed = int(shadow_seed)
+        o.cuda_stream = None if stream is None else (stream if isinstance(stream, int) else stream.cuda_stream)
+        h = ctypes.c_void_p()
+        _check(lib().rbicgstab_batch_create(ctypes.byref(h), ctypes.byref(o)), "rbicgstab_batch_create")
+        self._h = h
+        self.sizes = [int(m.n) for m in matrices]
+        self.offsets = np.concatenate([[0], np.cumsum(self.sizes)]).astype(np.int64)
+        n = np.asarray(self.sizes, dtype=np.int64)
+        rp = np.concatenate([np.asarray(m.row_ptr, dtype=np.int32) for m in matrices])
+        col = np.concatenate([np.asarray(m.col, dtype=np.int32) for m in matrices])
+        val = np.concatenate([np.asarray(m.val, dtype=np.float64) for m in matrices])
+        self.nnz = len(val)
+        _check(lib().rbicgstab_batch_set_matrices(self._h, len(self.sizes), n.ctypes.data, rp.ctypes.data,
+                                                  col.ctypes.data, val.ctypes.data), "rbicgstab_batch_set_matrices")
+
+    def __del__(self):
+        try:
+            if getattr(self, "_h", None):
+                lib().rbicgstab_batch_destroy(self._h)
+                self._h = None
+        except Exception:
+            pass
+
+    def _cat(self, xs, dtype=np.float64):
+        if isinstance(xs, (list, tuple)):
+            if any(_is_torch(v) for v in xs):
+                import torch
+                return torch.cat([v.reshape(-1) for v in xs]).contiguous()
+            return np.concatenate([np.asarray(v, dtype=dtype).reshape(-1) for v in xs])
+        return xs
+
+    def set_values(self, vals):
+        v = self._cat(vals)
+        p, w, keep = _ptr(v, np.float64)
+        _check(lib().rbicgstab_batch_set_values(self._h, p, w), "rbicgstab_batch_set_values")
+
+    def set_recycle(self, Us):
+        """One (n_i, k) block per system (or None to clear)."""
+        if Us is None:
+            _check(lib().rbicgstab_batch_set_recycle(self._h, 0, None, RB_HOST), "rbicgstab_batch_set_recycle")
+            return
+        k = int(np.shape(Us[0])[1])
+        blocks = np.concatenate([np.asfortranarray(u, dtype=np.float64).ravel(order="F") for u in Us])
+        _check(lib().rbicgstab_batch_set_recycle(self._h, k, blocks.ctypes.data, RB_HOST),
+               "rbicgstab_batch_set_recycle")
+
+    def solve(self, bs, xs=None):
+        """Returns (list of per-system solutions, list of per-system stats)."""
+        b = self._cat(bs)
+        if xs is None:
+            if _is_torch(b):
+                import torch
+                x = torch.zeros_like(b)
+            else:
+                x = np.zeros(len(b))
+        else:
+            x = self._cat(xs)
+            if not _is_torch(x):
+                x = np.ascontiguousarray(x, dtype=np.float64)
+        bp, wb, kb = _ptr(b, np.float64)
+        xp, wx, kx = (_ptr(x, np.float64) if _is_torch(x) else (x.ctypes.data, RB_HOST, x))
+        if wb != wx:
+            raise ValueError("b and x must live in the same memory space")
+        st = (Stats * len(self.sizes))()
+        code = lib().rbicgstab_batch_solve(self._h, bp, xp, wb, st)
+        stats = [s.as_dict() for s in st]
+        # a per-system outcome (one system's non-finite iterate, breakdown or
+        # non-convergence) is in that system's stats; other codes raise
+        if code in HARD_ERRORS and not any(d["status"] == code for d in stats):
+            raise RbError(code, "rbicgstab_batch_solve")
+        parts = [x[self.offsets[i]:self.offsets[i + 1]] for i in range(len(self.sizes))]
+        return parts, stats
+
+    def info(self):
+        a, b, c, d = ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_double(0)
+        _check(lib().rbicgstab_batch_info(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), ctypes.byref(d)),
+               "rbicgstab_batch_info")
+        return {"tile_slices": a.value, "ctas_per_sm": b.value, "tiles": c.value, "tuned_p1_ms": d.value}
 
 
 def residual_noalloc(row_ptr, col, val, x, b, r, rnorm2, stream=None, n=None) -> int:
