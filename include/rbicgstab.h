@@ -364,6 +364,19 @@ int rbicgstab_update_gram(int64_t n, int64_t ld, int32_t ky, int32_t nit, int32_
  * Errors: RB_EINVAL (NULL argument), RB_EDIM (no matrix). */
 int rbicgstab_sell_stats(rb_handle h, int64_t* nslices, int64_t* stencil_slices);
 
+/* Self-test of the bounded device wait (failure detection without a GPU
+ * fault).  The kernels that wait on the copy engine or the tensor cores
+ * through mbarriers give up after a time limit instead of hanging, leave
+ * normally and report RB_ETIMEOUT.  This call runs that same wait in one
+ * block on an mbarrier of one arrival: complete != 0 makes a thread arrive
+ * first (returns RB_OK); complete == 0 leaves the barrier incomplete, so the
+ * wait gives up after limit_ms (0 < limit_ms <= 1000, converted to SM clock
+ * cycles at the rated clock) and the call returns RB_ETIMEOUT with the
+ * context usable.  *waited_ms (may be NULL) receives the kernel's duration.
+ * Current device, legacy default stream, synchronous.  Errors: RB_EINVAL,
+ * RB_ENOMEM, RB_ECUDA. */
+int rbicgstab_wait_selftest(int32_t complete, double limit_ms, double* waited_ms);
+
 /* Number of CUDA kernels this library has launched in the process so far
  * (each graph replay adds the kernels its graph holds).  Thread-safe. */
 long long rbicgstab_kernel_launches(void);

@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "librbicgstab.so")
 
-SOURCES = ["iter.cu", "blas.cu", "matrix.cu", "solver.cu", "noalloc.cu", "gram_tc.cu", "batch.cu", "hostla.cpp"]
+SOURCES = ["iter.cu", "blas.cu", "matrix.cu", "solver.cu", "noalloc.cu", "gram_tc.cu", "batch.cu", "selftest.cu", "hostla.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -29,6 +29,7 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <functional>
 #include <vector>
 
 #include "device.cuh"
@@ -80,7 +81,7 @@ __device__ __forceinline__ bool tile_active(const IterState* st, bool skip_half)
 // completed the system's last tile, with sm.res[0..nv) then holding the
 // system's totals, summed in tile order.  The ticket is back at 0 after.
 template <int NV>
-__device__ bool tile_commit(ReduceSmem<NV>& sm, int nv, double* partials, int t, unsigned* ticket, int t0,
+__device__ bool tile_commit(ReduceCore<NV>& sm, int nv, double* partials, int t, unsigned* ticket, int t0,
                             int nt) {
   __shared__ int s_last;
   if (threadIdx.x == 0) {
@@ -115,18 +116,18 @@ __device__ __forceinline__ T slice_row_product(const Sell<T>& A, const T* __rest
   return y;
 }
 
-// P1: q_raw = A p; zeta = C-hat^T q_raw, (r~_0, q_raw) -> alpha (finish_p1).
-// P3: t_raw = A s; gamma = C-hat^T t_raw (finish_p3), or with k = 0 the four
-// dots (s,t), (t,t), (r~_0,t), (r~_0,s) (finish_p4).
-template <typename T, int KB, bool IS_P3>
-__global__ void __launch_bounds__(kBlock) kb_spmv(BatchArgs<T> a) {
-  constexpr int NV = KB > 0 ? KB + 1 : 4;
+// P1 / P3 without a recycle space: q_raw = A p and (r~_0, q_raw) -> alpha
+// (finish_p1); t_raw = A s and the four dots (s,t), (t,t), (r~_0,t),
+// (r~_0,s) -> omega, rho, beta (finish_p4: P4 folds into P3).  One warp per
+// SELL slice, row per lane, Dot2 (FP32) or FP64 accumulators.
+template <typename T, bool IS_P3>
+__global__ void __launch_bounds__(kBlock) kb_spmv_plain(BatchArgs<T> a) {
+  constexpr int NV = 4;
   __shared__ ReduceSmem<NV> sm;
   __shared__ double scr[kBK + 1];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const T* __restrict__ v = IS_P3 ? a.s : a.p;
   T* __restrict__ out = IS_P3 ? a.traw : a.qraw;
-  const int k = KB > 0 ? a.k : 0;
   for (int t = blockIdx.x; t < a.tiles.ntiles; t += gridDim.x) {
     const int sys = a.tiles.sys[t];
     IterState* st = a.st + sys;
@@ -137,32 +138,141 @@ __global__ void __launch_bounds__(kBlock) kb_spmv(BatchArgs<T> a) {
     for (int q = warp; q < nsl; q += kBlock / 32) {
       const int64_t sl = sl0 + q;
       const int64_t row = sl * kSlice + lane;
+      const T rv = __ldg(a.rt0 + row);
+      const T sv = IS_P3 ? __ldg(a.s + row) : T(0);
       const T y = slice_row_product(a.A, v, sl, lane);
       out[row] = y;
-      if (KB > 0) {
-        if (!IS_P3) acc[0].add(__ldg(a.rt0 + row), y);
-#pragma unroll
-        for (int j = 0; j < KB; ++j)
-          if (j < k) acc[(IS_P3 ? 0 : 1) + j].add(__ldg(a.Chat + (int64_t)j * a.ld + row), y);
+      if (!IS_P3) {
+        acc[0].add(rv, y);
       } else {
-        if (!IS_P3) {
-          acc[0].add(__ldg(a.rt0 + row), y);
-        } else {
-          const T sv = __ldg(a.s + row), rv = __ldg(a.rt0 + row);
-          acc[0].add(sv, y);
-          acc[1].add(y, y);
-          acc[2].add(rv, y);
-          acc[3].add(rv, sv);
-        }
+        acc[0].add(sv, y);
+        acc[1].add(y, y);
+        acc[2].add(rv, y);
+        acc[3].add(rv, sv);
       }
     }
-    const int nv = KB > 0 ? (IS_P3 ? k : k + 1) : (IS_P3 ? 4 : 1);
+    const int nv = IS_P3 ? 4 : 1;
     block_sum<T, NV>(acc, nv, sm);
     if (tile_commit<NV>(sm, nv, a.partials, t, &st->ticket[IS_P3 ? P3 : P1].top, a.tiles.t0[sys], a.tiles.nt[sys])) {
       if (warp == 0) {
-        if (!IS_P3) finish_p1(st, sm.res, k, scr);
-        else if (KB > 0) finish_p3(st, sm.res, k);
+        if (!IS_P3) finish_p1(st, sm.res, 0, scr);
         else finish_p4(st, sm.res, 0);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Warp total of a per-lane accumulator (valid in lane 0): FP32 Dot2 pairs
+// combined by TwoSum along a fixed shuffle tree, FP64 by plain adds.
+template <typename T>
+__device__ __forceinline__ double warp_total(const Acc<T>& a);
+template <>
+__device__ __forceinline__ double warp_total<float>(const Acc<float>& a) {
+  float hi = a.hi, lo = a.lo;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float h2 = __shfl_down_sync(0xffffffffu, hi, o);
+    const float l2 = __shfl_down_sync(0xffffffffu, lo, o);
+    const float s = __fadd_rn(hi, h2);
+    const float bb = __fsub_rn(s, hi);
+    const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(h2, bb));
+    hi = s;
+    lo = __fadd_rn(__fadd_rn(lo, l2), e);
+  }
+  return (double)hi + (double)lo;
+}
+template <>
+__device__ __forceinline__ double warp_total<double>(const Acc<double>& a) {
+  double x = a.v;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+  return x;
+}
+
+// sum_l c[l] ys[l] over the 32 rows of a slice, in row order (c 16-byte
+// aligned: a column of C-hat from the slice's first row).
+__device__ __forceinline__ float slice_col_dot(const float* __restrict__ c, const float* ys) {
+  const float4* c4 = reinterpret_cast<const float4*>(c);
+  float s = 0.f;
+#pragma unroll
+  for (int i = 0; i < kSlice / 4; ++i) {
+    const float4 v = __ldg(c4 + i);
+    s = __fmaf_rn(v.x, ys[4 * i], s);
+    s = __fmaf_rn(v.y, ys[4 * i + 1], s);
+    s = __fmaf_rn(v.z, ys[4 * i + 2], s);
+    s = __fmaf_rn(v.w, ys[4 * i + 3], s);
+  }
+  return s;
+}
+__device__ __forceinline__ double slice_col_dot(const double* __restrict__ c, const double* ys) {
+  const double2* c2 = reinterpret_cast<const double2*>(c);
+  double s = 0.0;
+#pragma unroll
+  for (int i = 0; i < kSlice / 2; ++i) {
+    const double2 v = __ldg(c2 + i);
+    s = __fma_rn(v.x, ys[2 * i], s);
+    s = __fma_rn(v.y, ys[2 * i + 1], s);
+  }
+  return s;
+}
+
+// P1 / P3 with a recycle space (k > 0): the SpMV of kb_spmv_plain, and the
+// projection C-hat^T y with lane j owning column j: the warp puts the
+// slice's 32 products in shared memory, lane j < k sums column j's 32 rows
+// against them in FP32 (row order) and carries the slice sums across slices
+// in a Dot2 pair (FP64 data: FP64 throughout).  One accumulator per lane
+// instead of k per thread keeps the kernel at full occupancy.  P1 also forms
+// (r~_0, q_raw) row per lane.
+template <typename T, bool IS_P3>
+__global__ void __launch_bounds__(kBlock) kb_spmv_proj(BatchArgs<T> a) {
+  constexpr int NW = kBlock / 32;
+  __shared__ ReduceCore<kBK + 1> sm;
+  __shared__ double scr[kBK + 1];
+  __shared__ __align__(16) T ys[NW][kSlice];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const T* __restrict__ v = IS_P3 ? a.s : a.p;
+  T* __restrict__ out = IS_P3 ? a.traw : a.qraw;
+  const int k = a.k;
+  const int off = IS_P3 ? 0 : 1;   // P1: res[0] = (r~_0, q_raw), res[1 + j] = zeta_j; P3: res[j] = gamma_j
+  const int nv = k + off;
+  for (int t = blockIdx.x; t < a.tiles.ntiles; t += gridDim.x) {
+    const int sys = a.tiles.sys[t];
+    IterState* st = a.st + sys;
+    if (!tile_active(st, IS_P3)) continue;
+    Acc<T> col, rq;
+    const int64_t sl0 = a.tiles.sl0[t];
+    const int nsl = a.tiles.nsl[t];
+    for (int q = warp; q < nsl; q += NW) {
+      const int64_t sl = sl0 + q;
+      const int64_t row = sl * kSlice + lane;
+      const T rv = IS_P3 ? T(0) : __ldg(a.rt0 + row);
+      const T y = slice_row_product(a.A, v, sl, lane);
+      out[row] = y;
+      if (!IS_P3) rq.add(rv, y);
+      ys[warp][lane] = y;
+      __syncwarp();
+      if (lane < k) col.add1(slice_col_dot(a.Chat + (int64_t)lane * a.ld + sl * kSlice, ys[warp]));
+      __syncwarp();
+    }
+    if (!IS_P3) {
+      const double w = warp_total(rq);
+      if (lane == 0) sm.w[warp][0] = w;
+    }
+    if (lane < k) sm.w[warp][off + lane] = col.get();
+    __syncthreads();
+    for (int vv = threadIdx.x; vv < nv; vv += blockDim.x) {
+      double sum = 0.0;
+#pragma unroll
+      for (int w = 0; w < NW; ++w) sum += sm.w[w][vv];
+      sm.res[vv] = sum;
+    }
+    __syncthreads();
+    if (tile_commit<kBK + 1>(sm, nv, a.partials, t, &st->ticket[IS_P3 ? P3 : P1].top, a.tiles.t0[sys],
+                             a.tiles.nt[sys])) {
+      if (warp == 0) {
+        if (!IS_P3) finish_p1(st, sm.res, k, scr);
+        else finish_p3(st, sm.res, k);
       }
     }
     __syncthreads();
@@ -180,7 +290,7 @@ __global__ void __launch_bounds__(kBlock) kb_p2(BatchArgs<T> a) {
     const int sys = a.tiles.sys[t];
     IterState* st = a.st + sys;
     if (!tile_active(st, false)) continue;
-    if (threadIdx.x < k) zs[threadIdx.x] = (T)st->zeta[threadIdx.x];
+    if ((int)threadIdx.x < k) zs[threadIdx.x] = (T)st->zeta[threadIdx.x];
     if (threadIdx.x == 0) s_alpha = (T)st->alpha;
     __syncthreads();
     const T alpha = s_alpha;
@@ -410,8 +520,73 @@ __global__ void __launch_bounds__(kBlock) kb_relayout(double* __restrict__ padde
   }
 }
 
-__global__ void kb_flags(const IterState* st, int nsys, int* flags) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nsys; i += gridDim.x * blockDim.x) flags[i] = st[i].done;
+// What the host reads of every system after a graph replay.
+struct SysFlag {
+  int32_t done, status, iter, half;
+  double rnorm2;
+};
+
+__global__ void kb_flags(const IterState* st, int nsys, SysFlag* flags) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nsys; i += gridDim.x * blockDim.x)
+    flags[i] = SysFlag{st[i].done, st[i].status, st[i].iter, st[i].half, st[i].rnorm2};
+}
+
+// Per-system commands of the mixed mode's residual replacement.
+enum SysCmd { kCmdNone = 0, kCmdFold = 1, kCmdDrop = 2 };
+
+// cmd[sys] == kCmdFold: x += fx - U x_c (the inner increment of the FP32
+// solve since the last fold, eq. (3.5)'s final correction); kCmdDrop: the
+// increment is discarded (a non-finite inner iterate).  Both zero fx.
+__global__ void __launch_bounds__(kBlock) kb_fold(double* __restrict__ x, float* __restrict__ fx,
+                                                  const double* __restrict__ U, int64_t ld, int k,
+                                                  const IterState* st, const int* cmd, BatchTiles tiles) {
+  __shared__ double cs[kBK];
+  for (int t = blockIdx.x; t < tiles.ntiles; t += gridDim.x) {
+    const int sys = tiles.sys[t];
+    const int c = cmd[sys];
+    if (c == kCmdNone) continue;
+    if (threadIdx.x < k) cs[threadIdx.x] = st[sys].xc[threadIdx.x];
+    __syncthreads();
+    const int64_t r0 = tiles.sl0[t] * kSlice;
+    const int rows = tiles.nsl[t] * kSlice;
+    for (int i = threadIdx.x; i < rows; i += blockDim.x) {
+      const int64_t row = r0 + i;
+      if (c == kCmdFold) {
+        double d = (double)fx[row];
+        for (int j = 0; j < k; ++j) d = fma(-U[(int64_t)j * ld + row], cs[j], d);
+        x[row] += d;
+      }
+      fx[row] = 0.f;
+    }
+    __syncthreads();
+  }
+}
+
+// For every system with cmd[sys] != kCmdNone (cmd may be null): x_c = 0.
+// run[sys] (run may be null): 1 = iterate again (done = half = 0), 2 = stop
+// (done = 1).
+__global__ void kb_state_cmd(IterState* st, int nsys, int k, const int* cmd, const int* run) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nsys; i += gridDim.x * blockDim.x) {
+    if (cmd && cmd[i] != kCmdNone)
+      for (int j = 0; j < k; ++j) st[i].xc[j] = 0.0;
+    if (run && run[i] == 1) {
+      st[i].done = 0;
+      st[i].half = 0;
+    } else if (run && run[i] == 2) {
+      st[i].done = 1;
+    }
+  }
+}
+
+// out = (float) in over the rows of the systems with mask[sys] != 0.
+__global__ void __launch_bounds__(kBlock) kb_to_float(float* __restrict__ out, const double* __restrict__ in,
+                                                      const int* mask, BatchTiles tiles) {
+  for (int t = blockIdx.x; t < tiles.ntiles; t += gridDim.x) {
+    if (!mask[tiles.sys[t]]) continue;
+    const int64_t r0 = tiles.sl0[t] * kSlice;
+    const int rows = tiles.nsl[t] * kSlice;
+    for (int i = threadIdx.x; i < rows; i += blockDim.x) out[r0 + i] = (float)in[r0 + i];
+  }
 }
 
 }  // namespace
@@ -456,9 +631,11 @@ struct rb_batch_ctx {
   IterState* st = nullptr;
   IterState* hst = nullptr;
   double* partials = nullptr;
-  int* dflags = nullptr;
-  int* hflags = nullptr;
+  int* dflags = nullptr;     // device validation flag
   int* dskip = nullptr;      // per-system "already converged" mask of a restart
+  int *dcmd = nullptr, *dres = nullptr;   // per-system fold / resume commands
+  rb::SysFlag* dsf = nullptr;             // flags gathered after each graph replay
+  rb::SysFlag* hsf = nullptr;
   // captured iteration graphs (FP64, FP32) and the layout they were made for
   cudaGraphExec_t g64 = nullptr, g32 = nullptr;
   int g_key64 = -1, g_key32 = -1;
@@ -571,9 +748,11 @@ BatchArgs<float> batch_args<float>(rb_batch_ctx* h) {
 
 template <typename T, int KB>
 cudaError_t launch_iteration_kb(const BatchArgs<T>& a, int grid, cudaStream_t s) {
-  kb_spmv<T, KB, false><<<grid, kBlock, 0, s>>>(a);
+  if (KB > 0) kb_spmv_proj<T, false><<<grid, kBlock, 0, s>>>(a);
+  else kb_spmv_plain<T, false><<<grid, kBlock, 0, s>>>(a);
   kb_p2<T, KB><<<grid, kBlock, 0, s>>>(a);
-  kb_spmv<T, KB, true><<<grid, kBlock, 0, s>>>(a);
+  if (KB > 0) kb_spmv_proj<T, true><<<grid, kBlock, 0, s>>>(a);
+  else kb_spmv_plain<T, true><<<grid, kBlock, 0, s>>>(a);
   if (KB > 0) kb_p4<T, KB><<<grid, kBlock, 0, s>>>(a);
   kb_p5<T, KB><<<grid, kBlock, 0, s>>>(a);
   return cudaGetLastError();
@@ -587,9 +766,11 @@ cudaError_t launch_iteration_b(const BatchArgs<T>& a, int grid, cudaStream_t s) 
 
 int poll_iters_b(rb_batch_ctx* h) { return h->o.poll > 0 ? h->o.poll : 8; }
 
-// Graph of poll iterations plus the gather of the done flags.
+// Graph of poll iterations plus the gather of the systems' flags.  After
+// each replay `hook` (if given) may act on the flags (fold, replace, resume
+// systems); the loop ends once every system reports done.
 template <typename T>
-int iterate_b(rb_batch_ctx* h, int64_t max_itn_all) {
+int iterate_b(rb_batch_ctx* h, int64_t max_itn_all, const std::function<int()>& hook = nullptr) {
   cudaGraphExec_t* g = std::is_same<T, float>::value ? &h->g32 : &h->g64;
   int* key = std::is_same<T, float>::value ? &h->g_key32 : &h->g_key64;
   const int want = h->k * 100000 + h->tile_slices * 100 + h->ctas_per_sm;
@@ -601,10 +782,11 @@ int iterate_b(rb_batch_ctx* h, int64_t max_itn_all) {
     cudaError_t e = cudaSuccess;
     for (int it = 0; it < poll_iters_b(h) && e == cudaSuccess; ++it) e = launch_iteration_b<T>(a, h->grid, h->cs);
     if (e == cudaSuccess) {
-      kb_flags<<<(h->S + 255) / 256, 256, 0, h->cs>>>(h->st, h->S, h->dflags);
+      kb_flags<<<(h->S + 255) / 256, 256, 0, h->cs>>>(h->st, h->S, h->dsf);
       e = cudaGetLastError();
     }
-    if (e == cudaSuccess) e = cudaMemcpyAsync(h->hflags, h->dflags, sizeof(int) * h->S, cudaMemcpyDeviceToHost, h->cs);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(h->hsf, h->dsf, sizeof(SysFlag) * h->S, cudaMemcpyDeviceToHost, h->cs);
     cudaGraph_t graph = nullptr;
     const cudaError_t ec = cudaStreamEndCapture(h->cs, &graph);
     if (e != cudaSuccess || ec != cudaSuccess) {
@@ -623,8 +805,12 @@ int iterate_b(rb_batch_ctx* h, int64_t max_itn_all) {
     RB_CUDA_TRY(cudaGraphLaunch(*g, h->us));
     count_launches((long long)poll_iters_b(h) * (h->k > 0 ? 5 : 4) + 1);
     RB_CUDA_TRY(cudaStreamSynchronize(h->us));
+    if (hook) {
+      const int rc = hook();
+      if (rc) return rc;
+    }
     bool all = true;
-    for (int i = 0; i < h->S && all; ++i) all = h->hflags[i] != 0;
+    for (int i = 0; i < h->S && all; ++i) all = h->hsf[i].done != 0;
     if (all) return RB_OK;
   }
 }
@@ -684,12 +870,12 @@ int autotune(rb_batch_ctx* h) {
         RB_CUDA_TRY(cudaEventRecord(e0, h->us));
         if (f32) {
           const BatchArgs<float> a = batch_args<float>(h);
-          if (h->k > 0) kb_spmv<float, kBK, false><<<h->grid, kBlock, 0, h->us>>>(a);
-          else kb_spmv<float, 0, false><<<h->grid, kBlock, 0, h->us>>>(a);
+          if (h->k > 0) kb_spmv_proj<float, false><<<h->grid, kBlock, 0, h->us>>>(a);
+          else kb_spmv_plain<float, false><<<h->grid, kBlock, 0, h->us>>>(a);
         } else {
           const BatchArgs<double> a = batch_args<double>(h);
-          if (h->k > 0) kb_spmv<double, kBK, false><<<h->grid, kBlock, 0, h->us>>>(a);
-          else kb_spmv<double, 0, false><<<h->grid, kBlock, 0, h->us>>>(a);
+          if (h->k > 0) kb_spmv_proj<double, false><<<h->grid, kBlock, 0, h->us>>>(a);
+          else kb_spmv_plain<double, false><<<h->grid, kBlock, 0, h->us>>>(a);
         }
         count_launches(1);
         RB_CUDA_TRY(cudaGetLastError());
@@ -781,7 +967,7 @@ int batch_setup(rb_batch_ctx* h) {
 // thresh[i] is the system's convergence threshold on ||r||^2; systems with
 // skip[i] start done.  The vectors are FP64; the caller converts for FP32.
 int batch_start(rb_batch_ctx* h, const double* rhs, double* xv, const std::vector<double>& thresh2,
-                const std::vector<char>& skip, const std::vector<int>& max_itn) {
+                const std::vector<char>& skip, const std::vector<int>& max_itn, uint64_t seed) {
   const int64_t ld = h->NP;
   const int gs = std::max(1, 4 * h->nsm);
   RB_CUDA_TRY(cudaMemcpyAsync(h->r, rhs, sizeof(double) * ld, cudaMemcpyDeviceToDevice, h->us));
@@ -800,7 +986,7 @@ int batch_start(rb_batch_ctx* h, const double* rhs, double* xv, const std::vecto
     if ((rc = gemv_b(h, h->r, h->C, -1.0, false))) return rc;
   }
   for (int i = 0; i < h->S; ++i)
-    RB_CUDA_TRY(shadow(h->rt0 + h->row0[i], h->n[i], h->npad[i], h->o.shadow_seed, h->us));
+    RB_CUDA_TRY(shadow(h->rt0 + h->row0[i], h->n[i], h->npad[i], seed, h->us));
   if (h->k > 0) {
     SysDots d{};
     d.M = h->C; d.km = h->k; d.v = h->rt0;
@@ -893,10 +1079,10 @@ extern "C" int rbicgstab_batch_destroy(rb_batch h) {
   void* ptrs[] = {h->rp, h->ci, h->trp, h->tci, h->tsrc, h->cv, h->tcv, h->t_sys, h->t_nsl, h->s_t0, h->s_nt,
                   h->t_sl0, h->d_row0, h->d_n, h->d_cofs, h->U, h->C, h->Ct, h->Chat, h->dR, h->fU, h->fC, h->fChat,
                   h->b, h->x, h->r, h->stage, h->p, h->s, h->q, h->t, h->qraw, h->traw, h->rt0, h->fx, h->fr, h->fp,
-                  h->fs, h->fq, h->ft, h->fqraw, h->ftraw, h->frt0, h->st, h->partials, h->dflags, h->dskip};
+                  h->fs, h->fq, h->ft, h->fqraw, h->ftraw, h->frt0, h->st, h->partials, h->dflags, h->dskip, h->dcmd, h->dres, h->dsf};
   for (void* p : ptrs) cudaFree(p);
   if (h->hst) cudaFreeHost(h->hst);
-  if (h->hflags) cudaFreeHost(h->hflags);
+  if (h->hsf) cudaFreeHost(h->hsf);
   if (h->cs) cudaStreamDestroy(h->cs);
   delete h;
   return RB_OK;
@@ -999,13 +1185,15 @@ extern "C" int rbicgstab_batch_set_matrices(rb_batch h, int32_t nsys, const int6
     }
     if ((rc = balloc(&h->dR, (int64_t)nsys * kBK * kBK))) return rc;
   }
-  if ((rc = balloc(&h->st, nsys)) || (rc = balloc(&h->dflags, nsys)) || (rc = balloc(&h->dskip, nsys))) return rc;
+  if ((rc = balloc(&h->st, nsys)) || (rc = balloc(&h->dflags, nsys)) || (rc = balloc(&h->dskip, nsys)) ||
+      (rc = balloc(&h->dcmd, nsys)) || (rc = balloc(&h->dres, nsys)) || (rc = balloc(&h->dsf, nsys)))
+    return rc;
   if (h->hst) cudaFreeHost(h->hst);
-  if (h->hflags) cudaFreeHost(h->hflags);
+  if (h->hsf) cudaFreeHost(h->hsf);
   h->hst = nullptr;
-  h->hflags = nullptr;
+  h->hsf = nullptr;
   if (cudaMallocHost(&h->hst, sizeof(IterState) * nsys) != cudaSuccess ||
-      cudaMallocHost(&h->hflags, sizeof(int) * nsys) != cudaSuccess)
+      cudaMallocHost(&h->hsf, sizeof(rb::SysFlag) * nsys) != cudaSuccess)
     return RB_ENOMEM;
   h->kin = h->k = 0;
   h->have = true;
@@ -1104,7 +1292,7 @@ extern "C" int rbicgstab_batch_solve(rb_batch h, const double* b, double* x, int
   if (h->o.precision == RB_FP64) {
     std::vector<double> th(S);
     for (int i = 0; i < S; ++i) th[i] = tol2 * bn2[i];
-    if ((rc = batch_start(h, h->b, h->x, th, std::vector<char>(S, 0), max_itn))) return done(rc);
+    if ((rc = batch_start(h, h->b, h->x, th, std::vector<char>(S, 0), max_itn, h->o.shadow_seed))) return done(rc);
     if ((rc = iterate_b<double>(h, *std::max_element(max_itn.begin(), max_itn.end())))) return done(rc);
     if ((rc = gemv_b(h, h->x, h->U, -1.0, true))) return done(rc);
     RB_CUDA_TRY(cudaMemcpyAsync(h->hst, h->st, sizeof(IterState) * S, cudaMemcpyDeviceToHost, h->us));
@@ -1116,53 +1304,140 @@ extern "C" int rbicgstab_batch_solve(rb_batch h, const double* b, double* x, int
       outer[i] = 1;
     }
   } else {
-    // restarts of the FP32 recycled solve on the FP64 residual
-    for (int restart = 0; restart < 8; ++restart) {
-      std::vector<char> conv(S);
-      bool all = true;
+    // FP32 inner iteration with FP64 residual replacement per system, the
+    // single-system mixed scheme (reliable updates): a system folds its FP32
+    // increment into the FP64 x whenever its recursive residual has fallen
+    // by kReplaceB since the last replacement or it reports convergence; the
+    // true residual then either meets the target (a tenth of the tolerance)
+    // or, projected as in eq. (3.5), replaces the FP32 residual while the
+    // search direction and scalars carry on.  A breakdown, a non-finite
+    // inner iterate (its increment is dropped) or a half-step exit above the
+    // target restarts that system in the next round with a new shadow.
+    constexpr double kReplaceB = 1e-2;
+    constexpr int kRounds = 6;
+    std::vector<double> target(S), rlast(S, 0.0);
+    for (int i = 0; i < S; ++i) target[i] = 0.1 * h->o.tol * std::sqrt(bn2[i]);
+    std::vector<char> fin(S, 0), skip(S, 1), ended(S, 0);
+    std::vector<int> cmd(S), res(S), last_status(S, RB_OK);
+    for (int round = 0; round < kRounds; ++round) {
+      bool any = false;
       for (int i = 0; i < S; ++i) {
-        conv[i] = rn2[i] <= tol2 * bn2[i] || status[i] != RB_OK;
-        all = all && conv[i];
+        skip[i] = 1;
+        ended[i] = 0;
+        if (fin[i]) continue;
+        if (!std::isfinite(rn2[i])) {
+          status[i] = RB_ENONFINITE;
+          fin[i] = 1;
+        } else if (std::sqrt(rn2[i]) <= target[i] || bn2[i] == 0.0) {
+          status[i] = RB_OK;
+          fin[i] = 1;
+        } else if (iters[i] >= max_itn[i]) {
+          status[i] = last_status[i] != RB_OK ? last_status[i] : RB_ENOTCONV;
+          fin[i] = 1;
+        } else {
+          skip[i] = 0;
+          any = true;
+        }
       }
-      if (all) break;
-      // correction equation A d = r: rhs = r (kept in qraw), start d = s = 0
-      RB_CUDA_TRY(cudaMemcpyAsync(h->qraw, h->r, sizeof(double) * h->NP, cudaMemcpyDeviceToDevice, h->us));
-      RB_CUDA_TRY(cudaMemsetAsync(h->s, 0, sizeof(double) * h->NP, h->us));
+      if (!any) break;
       std::vector<double> th(S);
       std::vector<int> cap(S);
       for (int i = 0; i < S; ++i) {
-        th[i] = std::max(0.01 * tol2 * bn2[i], 1e-10 * rn2[i]);
+        th[i] = target[i] * target[i];
         cap[i] = std::max(1, max_itn[i] - iters[i]);
+        rlast[i] = std::sqrt(rn2[i]);
       }
-      if ((rc = batch_start(h, h->qraw, h->s, th, conv, cap))) return done(rc);
+      if ((rc = batch_start(h, h->b, h->x, th, skip, cap, h->o.shadow_seed + (uint64_t)round))) return done(rc);
       RB_CUDA_TRY(to_float(h->r, h->fr, h->NP, h->us));
       RB_CUDA_TRY(to_float(h->r, h->fp, h->NP, h->us));
       RB_CUDA_TRY(to_float(h->rt0, h->frt0, h->NP, h->us));
       RB_CUDA_TRY(cudaMemsetAsync(h->fx, 0, sizeof(float) * h->NP, h->us));
-      if ((rc = iterate_b<float>(h, *std::max_element(cap.begin(), cap.end())))) return done(rc);
-      // x += d_0 + x_inner - U x_c
-      LinComb lc{};
-      lc.x[0] = h->s;
-      lc.c[0] = 1.0;
-      lc.nx = 1;
-      RB_CUDA_TRY(lincomb(h->x, 1.0, lc, h->NP, std::max(1, 4 * h->nsm), h->us));
-      RB_CUDA_TRY(add_float_to_double(h->x, h->fx, h->NP, h->us));
-      if ((rc = gemv_b(h, h->x, h->U, -1.0, true))) return done(rc);
+      for (int i = 0; i < S; ++i)
+        if (!skip[i]) outer[i] += 1;
+      auto hook = [&]() -> int {
+        bool anyc = false;
+        for (int i = 0; i < S; ++i) {
+          cmd[i] = kCmdNone;
+          res[i] = 0;
+          if (skip[i] || ended[i]) continue;
+          const SysFlag& f = h->hsf[i];
+          if (f.done) cmd[i] = f.status == RB_ENONFINITE ? kCmdDrop : kCmdFold;
+          else if (f.rnorm2 <= kReplaceB * kReplaceB * rlast[i] * rlast[i]) cmd[i] = kCmdFold;
+          anyc = anyc || cmd[i] != kCmdNone;
+        }
+        if (!anyc) return RB_OK;
+        RB_CUDA_TRY(cudaMemcpyAsync(h->dcmd, cmd.data(), sizeof(int) * S, cudaMemcpyHostToDevice, h->us));
+        count_launches(2);
+        kb_fold<<<h->grid, kBlock, 0, h->us>>>(h->x, h->fx, h->U, h->NP, h->k, h->st, h->dcmd, tiles_of(h));
+        kb_state_cmd<<<(S + 255) / 256, 256, 0, h->us>>>(h->st, S, h->k, h->dcmd, nullptr);
+        RB_CUDA_TRY(cudaGetLastError());
+        int rc2 = true_residuals(h, rn2, bn2);   // synchronises: cmd is free again after it
+        if (rc2) return rc2;
+        bool anyr = false;   // systems whose FP32 residual is replaced
+        std::vector<int> rep(S, 0);
+        for (int i = 0; i < S; ++i) {
+          if (cmd[i] == kCmdNone) continue;
+          const SysFlag& f = h->hsf[i];
+          const bool met = std::isfinite(rn2[i]) && std::sqrt(rn2[i]) <= target[i];
+          if (met) {   // converged: stop it
+            if (!f.done) res[i] = 2;
+            h->hsf[i].done = 1;
+            ended[i] = 1;
+            fin[i] = 1;
+            status[i] = RB_OK;
+          } else if (!f.done || (f.status == RB_OK && !f.half)) {   // replace and carry on
+            rep[i] = 1;
+            anyr = true;
+            if (f.done) res[i] = 1;
+            h->hsf[i].done = 0;
+            rlast[i] = std::sqrt(rn2[i]);
+            outer[i] += 1;
+          } else {   // a failure or a half-step exit: this round ends for it
+            ended[i] = 1;
+            last_status[i] = f.status;
+            if (f.status == RB_ENOTCONV || (f.status == RB_ENONFINITE && !std::isfinite(rn2[i]))) {
+              fin[i] = 1;
+              status[i] = std::isfinite(rn2[i]) ? RB_ENOTCONV : RB_ENONFINITE;
+            }
+          }
+        }
+        if (anyr) {
+          if (h->k > 0) {
+            RB_CUDA_TRY(cudaMemcpyAsync(h->dskip, rep.data(), sizeof(int) * S, cudaMemcpyHostToDevice, h->us));
+            // skip mask = not replaced: invert on the host into cmd (free after the sync above)
+            for (int i = 0; i < S; ++i) cmd[i] = rep[i] ? 0 : 1;
+            RB_CUDA_TRY(cudaMemcpyAsync(h->dcmd, cmd.data(), sizeof(int) * S, cudaMemcpyHostToDevice, h->us));
+            SysDots d{};
+            d.M = h->Chat; d.km = h->k; d.v = h->r;
+            if ((rc2 = sysdots(h, d, false))) return rc2;
+            if ((rc2 = gemv_b(h, h->x, h->U, 1.0, false, h->dcmd))) return rc2;
+            if ((rc2 = gemv_b(h, h->r, h->C, -1.0, false, h->dcmd))) return rc2;
+          } else {
+            RB_CUDA_TRY(cudaMemcpyAsync(h->dskip, rep.data(), sizeof(int) * S, cudaMemcpyHostToDevice, h->us));
+          }
+          count_launches(1);
+          kb_to_float<<<h->grid, kBlock, 0, h->us>>>(h->fr, h->r, h->dskip, tiles_of(h));
+          RB_CUDA_TRY(cudaGetLastError());
+        }
+        bool anys = false;
+        for (int i = 0; i < S; ++i) anys = anys || res[i] != 0;
+        if (anys) {
+          RB_CUDA_TRY(cudaMemcpyAsync(h->dres, res.data(), sizeof(int) * S, cudaMemcpyHostToDevice, h->us));
+          count_launches(1);
+          kb_state_cmd<<<(S + 255) / 256, 256, 0, h->us>>>(h->st, S, h->k, nullptr, h->dres);
+          RB_CUDA_TRY(cudaGetLastError());
+        }
+        return sync_b(h);   // the host vectors above are read by the copies
+      };
+      if ((rc = iterate_b<float>(h, *std::max_element(cap.begin(), cap.end()), hook))) return done(rc);
       RB_CUDA_TRY(cudaMemcpyAsync(h->hst, h->st, sizeof(IterState) * S, cudaMemcpyDeviceToHost, h->us));
       if ((rc = sync_b(h))) return done(rc);
-      for (int i = 0; i < S; ++i) {
-        if (conv[i]) continue;
-        iters[i] += h->hst[i].iter;
-        outer[i] += 1;
-        const int s_in = h->hst[i].status;
-        if (s_in == RB_ENONFINITE) status[i] = s_in;
-        if (iters[i] >= max_itn[i] && status[i] == RB_OK) status[i] = RB_ENOTCONV;
-      }
-      if ((rc = true_residuals(h, rn2, bn2))) return done(rc);
+      for (int i = 0; i < S; ++i)
+        if (!skip[i]) iters[i] += h->hst[i].iter;
     }
     for (int i = 0; i < S; ++i) {
       rec2[i] = rn2[i];
-      if (status[i] == RB_OK && rn2[i] > tol2 * bn2[i]) status[i] = RB_ENOTCONV;
+      if (!fin[i] && status[i] == RB_OK) status[i] = last_status[i] != RB_OK ? last_status[i] : RB_ENOTCONV;
     }
   }
   std::vector<double> tr2;

@@ -49,6 +49,7 @@
 
 #include "common.cuh"
 #include "kernels.h"
+#include "mbar.cuh"
 
 namespace rb {
 namespace {
@@ -56,54 +57,7 @@ namespace {
 constexpr int kTcThreads = 448;              // 14 warps
 constexpr int kSplitWarp0 = 2, kEpiWarp0 = 6;
 constexpr int kChunkTiles = 4;               // tiles (32 rows) per accumulator buffer
-constexpr long long kWaitCycles = 2000000000LL;
 constexpr int kTmemCols = 512;               // two accumulator buffers of up to 256 columns
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
-__device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(bar), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// Wait for the phase of parity `parity` to complete.  Gives up when the
-// shared abort flag is raised (if abort != nullptr) or after kWaitCycles,
-// raising the flag itself; returns whether the phase completed.
-__device__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort) {
-  const long long t0 = clock64();
-  for (uint32_t it = 0;; ++it) {
-    if (mbar_test(bar, parity)) return true;
-    if ((it & 31) == 31) {
-      if (abort && *abort) return false;
-      if (clock64() - t0 > kWaitCycles) {
-        if (abort) *abort = 1;
-        return false;
-      }
-    }
-  }
-}
-
-__device__ __forceinline__ void fence_barrier_init() {
-  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-// Generic-proxy writes to shared memory become visible to the async proxy
-// (TMA, tensor cores).
-__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int c0, int c1, uint32_t bar) {
   asm volatile(

@@ -34,6 +34,7 @@
 
 #include "device.cuh"
 #include "kernels.h"
+#include "mbar.cuh"
 #include "scalars.cuh"
 
 namespace rb {
@@ -1023,6 +1024,96 @@ __device__ __forceinline__ void staged_rows(const T* __restrict__ C, int64_t ld,
   cp_async_wait<0>();
 }
 
+// The same stream through bulk copies: one 1D cp.async.bulk per stream and
+// tile (kBlock rows, 16-byte aligned as every array here is), issued by the
+// lanes of warp 0 and completing as transaction bytes on the stage's
+// mbarrier, so the block's threads spend no instructions on addresses and
+// copies and only wait (bounded, mbar.cuh) for the stage to land.  Returns
+// false when a wait expired; the copies still in flight are then waited for
+// (bounded) before the CTA leaves.
+template <typename T, int NSTG, typename F>
+__device__ __forceinline__ bool staged_rows_bulk(const T* __restrict__ C, int64_t ld, int kc, const T* const* vsrc,
+                                                 int nv, int64_t npad, T* buf, F&& f) {
+  __shared__ __align__(8) uint64_t bars[NSTG];
+  __shared__ int s_abort;
+  const int ns = kc + nv;
+  const int64_t ntiles = (npad + kBlock - 1) / kBlock;
+  const int64_t stage = (int64_t)ns * kBlock;
+  const int64_t step = gridDim.x;
+  const int lane = threadIdx.x & 31;
+  const bool producer = threadIdx.x < 32;
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < NSTG; ++q) mbar_init(smem_u32(&bars[q]), 1);
+    s_abort = 0;
+    fence_barrier_init();
+  }
+  __syncthreads();
+  uint32_t pending = 0;   // warp 0: stages issued and not yet consumed
+  auto issue = [&](int64_t tile, int stg) {
+    if (tile >= ntiles) return;
+    const int64_t row0 = tile * kBlock;
+    const uint32_t bytes = (uint32_t)(npad - row0 < kBlock ? npad - row0 : kBlock) * (uint32_t)sizeof(T);
+    const uint32_t bar = smem_u32(&bars[stg]);
+    if (lane == 0) {
+      fence_proxy_async();   // the block's reads of this stage come first
+      mbar_expect_tx(bar, bytes * (uint32_t)ns);
+    }
+    __syncwarp();
+    T* b = buf + stg * stage;
+    for (int sidx = lane; sidx < ns; sidx += 32) {
+      const T* src = sidx < kc ? C + (int64_t)sidx * ld : vsrc[sidx - kc];
+      bulk_load_1d(smem_u32(b + (int64_t)sidx * kBlock), src + row0, bytes, bar);
+    }
+    pending |= 1u << stg;
+  };
+  int64_t tile = blockIdx.x;
+  if (producer)
+#pragma unroll
+    for (int q = 0; q < NSTG - 1; ++q) issue(tile + q * step, q);
+  int stg = 0;
+  uint32_t phase = 0;     // parity bit per stage
+  bool ok = true;
+  for (; tile < ntiles; tile += step) {
+    if (producer) issue(tile + (NSTG - 1) * step, stg == 0 ? NSTG - 1 : stg - 1);
+    const uint32_t bar = smem_u32(&bars[stg]);
+    const uint32_t par = (phase >> stg) & 1u;
+    const bool landed = mbar_test(bar, par) || mbar_wait(bar, par, &s_abort);
+    phase ^= 1u << stg;
+    pending &= ~(1u << stg);
+    const int64_t row = tile * kBlock + threadIdx.x;
+    if (landed && row < npad) f(row, buf + stg * stage + threadIdx.x);
+    __syncthreads();
+    if (s_abort) {
+      ok = false;
+      break;
+    }
+    stg = stg == NSTG - 1 ? 0 : stg + 1;
+  }
+  if (!ok && lane == 0 && producer) {
+    for (int q = 0; q < NSTG; ++q)
+      if (pending & (1u << q)) mbar_wait(smem_u32(&bars[q]), (phase >> q) & 1u, nullptr);
+  }
+  __syncthreads();
+  return ok;
+}
+
+// Stage rows by bulk copies (bulk != 0) or by per-thread cp.async.
+template <typename T, int NSTG, typename F>
+__device__ __forceinline__ bool stage_rows(int bulk, const T* __restrict__ C, int64_t ld, int kc, const T* const* vsrc,
+                                           int nv, int64_t npad, T* buf, F&& f) {
+  if (bulk) return staged_rows_bulk<T, NSTG>(C, ld, kc, vsrc, nv, npad, buf, f);
+  staged_rows<T, NSTG>(C, ld, kc, vsrc, nv, npad, buf, f);
+  return true;
+}
+
+// A staged pass whose copies did not land marks its right-hand sides failed.
+#define RB_STAGE_TIMEOUT(R, ACT)                                      \
+  do {                                                                \
+    if (threadIdx.x == 0)                                             \
+      for (int r_ = 0; r_ < (R); ++r_)                                \
+        if (ACT[r_]) fail(&st[r_], RB_ETIMEOUT);                      \
+  } while (0)
+
 // Warp sums of the pair accumulators acc[h][d] (right-hand sides 2h, 2h+1)
 // into the slots slot(r, d); inactive right-hand sides give zeros.
 template <typename T, int R, int ND, int NV, typename SlotF>
@@ -1085,7 +1176,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_p2_staged(IterArgs<T> a) {
 #pragma unroll
   for (int r = 0; r < R; ++r) vi[r] = vix[r];
   AccP<T> acc[H][1];
-  staged_rows<T, SC::nstg>(a.C, a.ld, k, src, nsrc, a.npad, reinterpret_cast<T*>(dsm), [&](int64_t row, const T* sb) {
+  auto row_fn = [&](int64_t row, const T* sb) {
     V corr[H];
 #pragma unroll
     for (int h = 0; h < H; ++h) corr[h] = P::mk(T(0), T(0));
@@ -1114,7 +1205,9 @@ __global__ void __launch_bounds__(kBlock, 1) k_p2_staged(IterArgs<T> a) {
         a.s[r1][row] = sv.y;
       }
     }
-  });
+  };
+  if (!stage_rows<T, SC::nstg>(a.stage_bulk & 1, a.C, a.ld, k, src, nsrc, a.npad, reinterpret_cast<T*>(dsm), row_fn))
+    RB_STAGE_TIMEOUT(R, act);
   pair_slots<T, R, 1>(acc, act, sm, [](int r, int) { return r; });
   if (grid_finish<R>(R, sm, a.partials, &st[0].ticket[P2])) RB_FINISH_WARPS(R, act, finish_p2(&st[r], sm.res + r));
 }
@@ -1162,7 +1255,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_p4_staged(IterArgs<T> a) {
 #pragma unroll
   for (int r = 0; r < R; ++r) vi[r] = vix[r];
   AccP<T> acc[H][4];
-  staged_rows<T, SC::nstg>(a.C, a.ld, k, src, nsrc, a.npad, reinterpret_cast<T*>(dsm), [&](int64_t row, const T* sb) {
+  auto row_fn = [&](int64_t row, const T* sb) {
     V corr[H];
 #pragma unroll
     for (int h = 0; h < H; ++h) corr[h] = P::mk(T(0), T(0));
@@ -1188,7 +1281,9 @@ __global__ void __launch_bounds__(kBlock, 1) k_p4_staged(IterArgs<T> a) {
       if (act[r0]) a.t[r0][row] = t.x;
       if (act[r1]) a.t[r1][row] = t.y;
     }
-  });
+  };
+  if (!stage_rows<T, SC::nstg>(a.stage_bulk & 2, a.C, a.ld, k, src, nsrc, a.npad, reinterpret_cast<T*>(dsm), row_fn))
+    RB_STAGE_TIMEOUT(R, act);
   pair_slots<T, R, 4>(acc, act, sm, [](int r, int d) { return 4 * r + d; });
   if (grid_finish<4 * R>(4 * R, sm, a.partials, &st[0].ticket[P4]))
     RB_FINISH_WARPS(R, act, finish_p4(&st[r], sm.res + 4 * r, k));
@@ -1246,7 +1341,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_p5_staged(IterArgs<T> a) {
 #pragma unroll
   for (int r = 0; r < R; ++r) vi[r] = vix[r];
   AccP<T> acc[H][1];
-  staged_rows<T, SC::nstg>(a.C, a.ld, 0, src, nsrc, a.npad, reinterpret_cast<T*>(dsm), [&](int64_t row, const T* sb) {
+  auto row_fn = [&](int64_t row, const T* sb) {
     if (!anyhalf) {
 #pragma unroll
       for (int h = 0; h < H; ++h) {
@@ -1294,7 +1389,9 @@ __global__ void __launch_bounds__(kBlock, 1) k_p5_staged(IterArgs<T> a) {
       a.r[r][row] = rr;
       a.p_out[r][row] = pn;
     }
-  });
+  };
+  if (!stage_rows<T, SC::nstg>(a.stage_bulk & 4, a.C, a.ld, 0, src, nsrc, a.npad, reinterpret_cast<T*>(dsm), row_fn))
+    RB_STAGE_TIMEOUT(R, act);
   pair_slots<T, R, 1>(acc, act, sm, [](int r, int) { return r; });
   if (grid_finish<R>(R, sm, a.partials, &st[0].ticket[P5])) RB_FINISH_WARPS(R, act, finish_p5(&st[r], sm.res + r, k));
 }

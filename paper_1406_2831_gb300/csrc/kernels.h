@@ -30,7 +30,7 @@ struct IterArgs {
   double* partials;
   int64_t npad;
   int nrhs;
-  int stage_bulk;  // staged passes: tiles by bulk copies (1) or per-thread cp.async (0)
+  int stage_bulk;  // staged passes taking tiles by bulk copies: bit 0 P2, bit 1 P4, bit 2 P5
 };
 
 struct Grids {

@@ -91,6 +91,7 @@ struct rb_ctx {
   int dev = 0, nsm = 0;
   // matrix
   int64_t n = 0, nnz = 0, npad = 0;
+  uint64_t seed_bump = 0;   // added to the shadow seed by a mixed solve's retry after a failure
   int32_t *rp = nullptr, *ci = nullptr;
   double* cv = nullptr;
   int32_t *trp = nullptr, *tci = nullptr;
@@ -580,6 +581,19 @@ int ensure_setup(rb_ctx* h, int64_t* setup_mv) {
 }
 
 // ------------------------------------------------------------ iteration args
+// Which staged passes move their tiles by bulk copies (bit 0: P2, bit 1:
+// P4, bit 2: P5; the others use per-thread cp.async; same arithmetic,
+// bitwise-equal results).  Measured at 128^3, k = 20, four right-hand sides
+// (microseconds, bulk / cp.async): P2 63 / 67-73, P4 76 / 71-72, P5 53 /
+// 50-52, so only P2 takes bulk copies.  RB_STAGE_BULK=<mask> overrides.
+int stage_bulk() {
+  static const int v = [] {
+    const char* e = getenv("RB_STAGE_BULK");
+    return e ? atoi(e) & 7 : 1;
+  }();
+  return v;
+}
+
 template <typename T>
 IterArgs<T> base_args(rb_ctx* h, int nrhs);
 
@@ -607,6 +621,7 @@ IterArgs<double> base_args<double>(rb_ctx* h, int nrhs) {
   a.partials = h->partials;
   a.npad = h->npad;
   a.nrhs = nrhs;
+  a.stage_bulk = stage_bulk();
   return a;
 }
 
@@ -634,6 +649,7 @@ IterArgs<float> base_args<float>(rb_ctx* h, int nrhs) {
   a.partials = h->partials;
   a.npad = h->npad;
   a.nrhs = nrhs;
+  a.stage_bulk = stage_bulk();
   return a;
 }
 
@@ -754,7 +770,7 @@ int setup_block(rb_ctx* h, int nrhs, double* const* rhs, double* const* xb, cons
     }
   }
   for (int attempt = 0; attempt < 4; ++attempt) {
-    RB_CUDA_TRY(shadow(h->rt0, h->n, h->npad, h->o.shadow_seed + (uint64_t)attempt, h->us));
+    RB_CUDA_TRY(shadow(h->rt0, h->n, h->npad, h->o.shadow_seed + h->seed_bump + (uint64_t)attempt, h->us));
     if (k > 0) {
       DotArgs d{};
       d.M = h->C; d.ld = ld; d.km = k; d.v = h->rt0; d.nd = 0;
@@ -1100,6 +1116,12 @@ int solve_mixed(rb_ctx* h, int nrhs, SolveOut* so) {
     RB_CUDA_TRY(cudaMemsetAsync(h->sl[i].fx, 0, sizeof(float) * ld, h->us));
     return RB_OK;
   };
+  // Drop slot i's inner increment (fx = 0, x_c = 0): x keeps its last fold.
+  auto drop = [&](int i) -> int {
+    if (h->k > 0) RB_CUDA_TRY(cudaMemsetAsync(h->st[i].xc, 0, sizeof(double) * h->k, h->us));
+    RB_CUDA_TRY(cudaMemsetAsync(h->sl[i].fx, 0, sizeof(float) * ld, h->us));
+    return RB_OK;
+  };
   // True residual of slot i into sl[i].rin and rn[i].
   auto true_residual = [&](int i) -> int {
     RB_CUDA_TRY(residual_norm(h->A.view(), h->sl[i].b, h->sl[i].x, h->sl[i].rin, h->npad, h->st + i, h->partials,
@@ -1165,8 +1187,14 @@ int solve_mixed(rb_ctx* h, int nrhs, SolveOut* so) {
   };
 
   PhaseClock pcs;
+  struct SeedReset {   // every other solve draws the shadow from the handle's seed
+    rb_ctx* h;
+    ~SeedReset() { h->seed_bump = 0; }
+  } seed_reset{h};
+  h->seed_bump = 0;
   for (int round = 0;; ++round) {
     bool any = false;
+    bool failed_round = false;
     bool skip[kMaxRhs] = {true, true, true, true};
     bool xnz[kMaxRhs] = {false, false, false, false};
     double* rhs[kMaxRhs];
@@ -1237,13 +1265,19 @@ int solve_mixed(rb_ctx* h, int nrhs, SolveOut* so) {
       if (stop[i]) continue;   // converged at a replacement (x already folded)
       running[i] = false;
       // a breakdown, max_itn, or a half-step exit: fold the correction and
-      // let the next outer (refinement) step restart from x
-      if ((rc = fold(i))) return rc;
-      if (hs.status != RB_OK && hs.status != RB_ENOTCONV) {
-        so[i].status = hs.status;
-        stop[i] = true;
+      // let the next outer (refinement) step restart from x.  A non-finite
+      // inner iterate (an FP32 overflow) is dropped instead: x keeps its
+      // last fold.  After a failure the next round draws another shadow, so
+      // the restarted iteration is not the same one again.
+      if (hs.status == RB_ENONFINITE) {
+        if ((rc = drop(i))) return rc;
+        failed_round = true;
+      } else {
+        if ((rc = fold(i))) return rc;
+        if (hs.status != RB_OK && hs.status != RB_ENOTCONV) failed_round = true;
       }
     }
+    if (failed_round) h->seed_bump += 16;
     rc = sync(h);
     if (rc) return rc;
   }

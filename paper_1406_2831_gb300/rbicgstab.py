@@ -114,6 +114,8 @@ def lib():
     L.rbicgstab_solve_adjoint.restype = ctypes.c_int
     L.rbicgstab_solve_l.restype = ctypes.c_int
     L.rbicgstab_sell_stats.restype = ctypes.c_int
+    L.rbicgstab_wait_selftest.argtypes = [i32, ctypes.c_double, ctypes.POINTER(ctypes.c_double)]
+    L.rbicgstab_wait_selftest.restype = ctypes.c_int
     L.rbicgstab_kernel_launches.argtypes = []
     L.rbicgstab_kernel_launches.restype = ctypes.c_longlong
     L.rbicgstab_error_string.argtypes = [ctypes.c_int]
@@ -519,6 +521,17 @@ class Batch:
         _check(lib().rbicgstab_batch_info(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), ctypes.byref(d)),
                "rbicgstab_batch_info")
         return {"tile_slices": a.value, "ctas_per_sm": b.value, "tiles": c.value, "tuned_p1_ms": d.value}
+
+
+def wait_selftest(complete: bool, limit_ms: float):
+    """Run the library's bounded device wait once (rbicgstab_wait_selftest):
+    returns (status, kernel milliseconds); RB_ETIMEOUT when nothing completes
+    the barrier, RB_OK when it is completed first."""
+    ms = ctypes.c_double(0.0)
+    code = lib().rbicgstab_wait_selftest(int(bool(complete)), float(limit_ms), ctypes.byref(ms))
+    if code not in (RB_OK, C["RB_ETIMEOUT"]):
+        raise RbError(code, "rbicgstab_wait_selftest")
+    return code, ms.value
 
 
 def residual_noalloc(row_ptr, col, val, x, b, r, rnorm2, stream=None, n=None) -> int:
