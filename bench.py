@@ -61,6 +61,12 @@ def parse():
     ap.add_argument("--batch", action="store_true",
                     help="the batched sweep (256 uneven 2D systems x 4 shifts, k = 10) through the batched "
                          "solver: batched plain FP64 / plain mixed / recycled mixed, and an unbatched loop")
+    ap.add_argument("--arms", default="",
+                    help="--batch: comma-separated arms to run (batched_plain_fp64, batched_plain_mixed, "
+                         "recycled_mixed_shifts_1_3, plain_mixed_shifts_1_3, plain_fp64_shifts_1_3, "
+                         "unbatched_plain_fp64); default all")
+    ap.add_argument("--systems", type=int, default=0,
+                    help="--batch: number of systems (default 256; 16 with --quick)")
     ap.add_argument("--adjoint", action="store_true",
                     help="the differentiation workload (100^3, 8 parameters, 6 steps) through the autograd "
                          "function: forward + backward time per step, with and without checkpointing, and a "
@@ -346,7 +352,7 @@ def run_batch(args):
 
     from paper_1406_2831_gb300 import inputs
     from paper_1406_2831_gb300 import rbicgstab as rb
-    nsys = 16 if args.quick else 256
+    nsys = args.systems if args.systems else (16 if args.quick else 256)
     specs = inputs.config_batch_2d(n_systems=nsys)
     shifts = (0.0, 1e-2, 1e-1, 1.0)
     t0 = time.perf_counter()
@@ -403,8 +409,18 @@ def run_batch(args):
            "config": {"workload": f"batched-2d-conv-diff, {nsys} systems x 4 shifts", "systems": nsys,
                       "rows": n_tot, "nnz": nnz_tot, "k": 10, "tol": 1e-8, "shifts": list(shifts)},
            "generation_s": round(t_gen, 1)}
-    out["batched_plain_fp64"] = batched_arm("fp64", [0, 1, 2, 3])
-    out["batched_plain_mixed"] = batched_arm("mixed", [0, 1, 2, 3])
+    arms = set(args.arms.split(",")) if args.arms else None
+
+    def want(name):
+        return arms is None or name in arms
+    if want("batched_plain_fp64"):
+        out["batched_plain_fp64"] = batched_arm("fp64", [0, 1, 2, 3])
+    if want("batched_plain_mixed"):
+        out["batched_plain_mixed"] = batched_arm("mixed", [0, 1, 2, 3])
+    if not (want("recycled_mixed_shifts_1_3") or want("plain_mixed_shifts_1_3") or want("plain_fp64_shifts_1_3")
+            or want("unbatched_plain_fp64")):
+        out["value"] = None
+        return out
     # recycle spaces from each system's shift-0 solve (single-system update path)
     t0 = time.perf_counter()
     Us = []
@@ -424,11 +440,13 @@ def run_batch(args):
         Us.append(U)
         del s
     t_space = time.perf_counter() - t0
-    out["recycled_mixed_shifts_1_3"] = batched_arm("mixed", [1, 2, 3], Us)
+    out["recycled_mixed_shifts_1_3"] = batched_arm("mixed", [1, 2, 3], Us) if want("recycled_mixed_shifts_1_3") else {}
     out["recycled_mixed_shifts_1_3"]["space_generation_s"] = round(t_space, 2)
     out["recycled_mixed_shifts_1_3"]["space_generation_failures"] = space_fail
-    out["plain_mixed_shifts_1_3"] = batched_arm("mixed", [1, 2, 3])
-    out["plain_fp64_shifts_1_3"] = batched_arm("fp64", [1, 2, 3])
+    if want("plain_mixed_shifts_1_3"):
+        out["plain_mixed_shifts_1_3"] = batched_arm("mixed", [1, 2, 3])
+    if want("plain_fp64_shifts_1_3"):
+        out["plain_fp64_shifts_1_3"] = batched_arm("fp64", [1, 2, 3])
     # unbatched plain FP64: one handle per system, shifts 0..3
     handles = []
     for i, A in enumerate(mats):
@@ -439,6 +457,8 @@ def run_batch(args):
     vparts = [[torch.from_numpy(v).to(dev) for v in vv] for vv in vals]
 
     ub_fail = []
+    if not want("unbatched_plain_fp64"):
+        handles = []
 
     def unbatched():
         ub_fail.clear()
@@ -451,8 +471,10 @@ def run_batch(args):
                     ub_fail.append(f"shift {j} system {i}: {e}")
     unbatched()
     ms, _ = timed(unbatched)
-    out["unbatched_plain_fp64"] = {"solves_per_s": round(len(shifts) * nsys / (ms * 1e-3), 2), "ms": round(ms, 1),
-                                   "failed": len(ub_fail), "failures": ub_fail[:8]}
+    if want("unbatched_plain_fp64"):
+        out["unbatched_plain_fp64"] = {"solves_per_s": round(len(shifts) * nsys / (ms * 1e-3), 2), "ms": round(ms, 1),
+                                       "failed": len(ub_fail), "failures": ub_fail[:8]}
+
     def ratio(a, b):
         try:
             return round(out[a]["solves_per_s"] / out[b]["solves_per_s"], 4)
@@ -471,8 +493,9 @@ def run_adjoint(args):
     a 16 x n Gaussian C_out, 6 parameter steps p <- 1.01 p.  One handle
     carries the recycle space across the steps (update from each forward
     solve, U~ = U); every step runs the forward solve and the backward (the
-    dual system A^T lam = dL/dx by Alg. 1 with the handle's space, then
-    dL/dA_ij = -lam_i x_j on the pattern, chained to dL/dp by autograd).
+    dual system A^T lam = dL/dx by Alg. 2 on A^T with the space's roles
+    swapped, then dL/dA_ij = -lam_i x_j on the pattern, chained to dL/dp by
+    autograd).
     Device time per step (CUDA events), with and without checkpointing of x.
     Check: at the first step, with solver tolerance 1e-12, dL/dp_k for two
     parameters against central differences (h = 1e-6 max(1, |p_k|)) of tight

@@ -43,6 +43,10 @@ namespace {
 constexpr int kBK = 16;                 // largest recycle dimension of a batch
 constexpr int kBNV = kBK + 4;           // values per tile partial row
 
+struct PassGrids {
+  int g[5];   // P1..P5
+};
+
 struct BatchTiles {
   const int32_t* sys;        // [ntiles] system of the tile
   const int64_t* sl0;        // [ntiles] first slice
@@ -103,13 +107,37 @@ __device__ bool tile_commit(ReduceCore<NV>& sm, int nv, double* partials, int t,
   return true;
 }
 
-// y = A v over the rows of one slice (lane = row), SELL-32 with column loads.
+// y = A v over the rows of one slice (lane = row), SELL-32 with column
+// loads; w and sp are the slice's width and first entry.  The first kHead
+// entries of every row are loaded together (values and columns), then their
+// gathers, then the products: two memory latencies per slice instead of two
+// per entry (a warp issues in order, so a product waiting for its gather
+// would hold back the next entry's loads).  Longer rows continue entry by
+// entry; the sum runs in entry order either way.
+constexpr int kHead = 8;
 template <typename T>
-__device__ __forceinline__ T slice_row_product(const Sell<T>& A, const T* __restrict__ v, int64_t sl, int lane) {
-  const int w = __ldg(A.width + sl);
-  const int64_t e0 = __ldg(A.slice_ptr + sl) + lane;
+__device__ __forceinline__ T slice_row_product(const Sell<T>& A, const T* __restrict__ v, int w, int64_t sp,
+                                               int lane) {
+  const int64_t e0 = sp + lane;
+  T val[kHead];
+  int32_t col[kHead];
+#pragma unroll
+  for (int j = 0; j < kHead; ++j) {
+    val[j] = T(0);
+    col[j] = 0;
+    if (j < w) {
+      val[j] = __ldg(A.val + e0 + (int64_t)j * kSlice);
+      col[j] = __ldg(A.col + e0 + (int64_t)j * kSlice);
+    }
+  }
+  T g[kHead];
+#pragma unroll
+  for (int j = 0; j < kHead; ++j) g[j] = j < w ? __ldg(v + col[j]) : T(0);
   T y = T(0);
-  for (int j = 0; j < w; ++j) {
+#pragma unroll
+  for (int j = 0; j < kHead; ++j)
+    if (j < w) y = fma_t(val[j], g[j], y);
+  for (int j = kHead; j < w; ++j) {
     const int64_t e = e0 + (int64_t)j * kSlice;
     y = fma_t(__ldg(A.val + e), __ldg(v + __ldg(A.col + e)), y);
   }
@@ -135,12 +163,25 @@ __global__ void __launch_bounds__(kBlock) kb_spmv_plain(BatchArgs<T> a) {
     Acc<T> acc[NV];
     const int64_t sl0 = a.tiles.sl0[t];
     const int nsl = a.tiles.nsl[t];
+    // the next slice's width and start are loaded one step ahead
+    int w_nx = 0;
+    int64_t sp_nx = 0;
+    if (warp < nsl) {
+      w_nx = __ldg(a.A.width + sl0 + warp);
+      sp_nx = __ldg(a.A.slice_ptr + sl0 + warp);
+    }
     for (int q = warp; q < nsl; q += kBlock / 32) {
       const int64_t sl = sl0 + q;
+      const int w = w_nx;
+      const int64_t sp = sp_nx;
+      if (q + kBlock / 32 < nsl) {
+        w_nx = __ldg(a.A.width + sl + kBlock / 32);
+        sp_nx = __ldg(a.A.slice_ptr + sl + kBlock / 32);
+      }
       const int64_t row = sl * kSlice + lane;
       const T rv = __ldg(a.rt0 + row);
       const T sv = IS_P3 ? __ldg(a.s + row) : T(0);
-      const T y = slice_row_product(a.A, v, sl, lane);
+      const T y = slice_row_product(a.A, v, w, sp, lane);
       out[row] = y;
       if (!IS_P3) {
         acc[0].add(rv, y);
@@ -243,11 +284,23 @@ __global__ void __launch_bounds__(kBlock) kb_spmv_proj(BatchArgs<T> a) {
     Acc<T> col, rq;
     const int64_t sl0 = a.tiles.sl0[t];
     const int nsl = a.tiles.nsl[t];
+    int w_nx = 0;
+    int64_t sp_nx = 0;
+    if (warp < nsl) {
+      w_nx = __ldg(a.A.width + sl0 + warp);
+      sp_nx = __ldg(a.A.slice_ptr + sl0 + warp);
+    }
     for (int q = warp; q < nsl; q += NW) {
       const int64_t sl = sl0 + q;
+      const int w = w_nx;
+      const int64_t sp = sp_nx;
+      if (q + NW < nsl) {
+        w_nx = __ldg(a.A.width + sl + NW);
+        sp_nx = __ldg(a.A.slice_ptr + sl + NW);
+      }
       const int64_t row = sl * kSlice + lane;
       const T rv = IS_P3 ? T(0) : __ldg(a.rt0 + row);
-      const T y = slice_row_product(a.A, v, sl, lane);
+      const T y = slice_row_product(a.A, v, w, sp, lane);
       out[row] = y;
       if (!IS_P3) rq.add(rv, y);
       ys[warp][lane] = y;
@@ -523,12 +576,12 @@ __global__ void __launch_bounds__(kBlock) kb_relayout(double* __restrict__ padde
 // What the host reads of every system after a graph replay.
 struct SysFlag {
   int32_t done, status, iter, half;
-  double rnorm2;
+  double rnorm2, rmax2;
 };
 
 __global__ void kb_flags(const IterState* st, int nsys, SysFlag* flags) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nsys; i += gridDim.x * blockDim.x)
-    flags[i] = SysFlag{st[i].done, st[i].status, st[i].iter, st[i].half, st[i].rnorm2};
+    flags[i] = SysFlag{st[i].done, st[i].status, st[i].iter, st[i].half, st[i].rnorm2, st[i].rmax2};
 }
 
 // Per-system commands of the mixed mode's residual replacement.
@@ -563,18 +616,32 @@ __global__ void __launch_bounds__(kBlock) kb_fold(double* __restrict__ x, float*
 }
 
 // For every system with cmd[sys] != kCmdNone (cmd may be null): x_c = 0.
-// run[sys] (run may be null): 1 = iterate again (done = half = 0), 2 = stop
-// (done = 1).
-__global__ void kb_state_cmd(IterState* st, int nsys, int k, const int* cmd, const int* run) {
+// run[sys] (run may be null): 1 = iterate again (done = half = 0) with the
+// residual peak restarted at rmax2[sys], 2 = stop (done = 1), 3 = carry on
+// with the peak restarted at rmax2[sys].
+__global__ void kb_state_cmd(IterState* st, int nsys, int k, const int* cmd, const int* run, const double* rmax2) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nsys; i += gridDim.x * blockDim.x) {
     if (cmd && cmd[i] != kCmdNone)
       for (int j = 0; j < k; ++j) st[i].xc[j] = 0.0;
-    if (run && run[i] == 1) {
+    const int c = run ? run[i] : 0;
+    if (c == 1) {
       st[i].done = 0;
       st[i].half = 0;
-    } else if (run && run[i] == 2) {
+    } else if (c == 2) {
       st[i].done = 1;
     }
+    if ((c == 1 || c == 3) && rmax2) st[i].rmax2 = rmax2[i];
+  }
+}
+
+// dst = src over the rows of the systems with mask[sys] != 0.
+__global__ void __launch_bounds__(kBlock) kb_copy_rows(double* __restrict__ dst, const double* __restrict__ src,
+                                                       const int* mask, BatchTiles tiles) {
+  for (int t = blockIdx.x; t < tiles.ntiles; t += gridDim.x) {
+    if (!mask[tiles.sys[t]]) continue;
+    const int64_t r0 = tiles.sl0[t] * kSlice;
+    const int rows = tiles.nsl[t] * kSlice;
+    for (int i = threadIdx.x; i < rows; i += blockDim.x) dst[r0 + i] = src[r0 + i];
   }
 }
 
@@ -613,6 +680,7 @@ struct rb_batch_ctx {
   bool have = false;
   // work list
   int tile_slices = 0, ctas_per_sm = 0, grid = 0, ntiles = 0;
+  rb::PassGrids pg64[2]{}, pg32[2]{};   // per-pass grids: [plain, recycled]
   double tune_ms = 0.0;
   int32_t *t_sys = nullptr, *t_nsl = nullptr, *s_t0 = nullptr, *s_nt = nullptr;
   int64_t* t_sl0 = nullptr;
@@ -634,6 +702,7 @@ struct rb_batch_ctx {
   int* dflags = nullptr;     // device validation flag
   int* dskip = nullptr;      // per-system "already converged" mask of a restart
   int *dcmd = nullptr, *dres = nullptr;   // per-system fold / resume commands
+  double* drm = nullptr;                  // per-system residual peaks after a replacement
   rb::SysFlag* dsf = nullptr;             // flags gathered after each graph replay
   rb::SysFlag* hsf = nullptr;
   // captured iteration graphs (FP64, FP32) and the layout they were made for
@@ -665,6 +734,35 @@ void drop_graphs(rb_batch_ctx* h) {
   h->g_key64 = h->g_key32 = -1;
 }
 
+// Grids of the five pass kernels of one precision: each takes
+// min(ctas_per_sm, its own resident blocks per SM) blocks per SM, so that a
+// grid-stride work list never starts a second wave of blocks that wait for
+// the first to finish all their tiles, and a light kernel is not held to a
+// heavier one's occupancy.
+template <typename T>
+PassGrids pass_grids(int ctas_per_sm, int nsm, int ntiles, bool recycled) {
+  auto grid = [&](const void* f) {
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, f, kBlock, 0) != cudaSuccess || b < 1) b = 1;
+    return std::max(1, std::min(ntiles, std::min(ctas_per_sm, b) * nsm));
+  };
+  PassGrids g{};
+  if (recycled) {
+    g.g[0] = grid((const void*)kb_spmv_proj<T, false>);
+    g.g[1] = grid((const void*)kb_p2<T, kBK>);
+    g.g[2] = grid((const void*)kb_spmv_proj<T, true>);
+    g.g[3] = grid((const void*)kb_p4<T, kBK>);
+    g.g[4] = grid((const void*)kb_p5<T, kBK>);
+  } else {
+    g.g[0] = grid((const void*)kb_spmv_plain<T, false>);
+    g.g[1] = grid((const void*)kb_p2<T, 0>);
+    g.g[2] = grid((const void*)kb_spmv_plain<T, true>);
+    g.g[3] = g.g[2];
+    g.g[4] = grid((const void*)kb_p5<T, 0>);
+  }
+  return g;
+}
+
 // Work list for tiles of `ts` slices: every system's slices split into tiles.
 int build_tiles(rb_batch_ctx* h, int ts, int ctas_per_sm) {
   std::vector<int32_t> tsys, tnsl, t0(h->S), nt(h->S);
@@ -693,6 +791,10 @@ int build_tiles(rb_batch_ctx* h, int ts, int ctas_per_sm) {
   h->tile_slices = ts;
   h->ctas_per_sm = ctas_per_sm;
   h->grid = std::max(1, std::min(h->ntiles, ctas_per_sm * h->nsm));
+  for (int rec = 0; rec < 2; ++rec) {
+    h->pg64[rec] = pass_grids<double>(ctas_per_sm, h->nsm, h->ntiles, rec != 0);
+    h->pg32[rec] = pass_grids<float>(ctas_per_sm, h->nsm, h->ntiles, rec != 0);
+  }
   drop_graphs(h);
   return RB_OK;
 }
@@ -747,21 +849,27 @@ BatchArgs<float> batch_args<float>(rb_batch_ctx* h) {
 }
 
 template <typename T, int KB>
-cudaError_t launch_iteration_kb(const BatchArgs<T>& a, int grid, cudaStream_t s) {
-  if (KB > 0) kb_spmv_proj<T, false><<<grid, kBlock, 0, s>>>(a);
-  else kb_spmv_plain<T, false><<<grid, kBlock, 0, s>>>(a);
-  kb_p2<T, KB><<<grid, kBlock, 0, s>>>(a);
-  if (KB > 0) kb_spmv_proj<T, true><<<grid, kBlock, 0, s>>>(a);
-  else kb_spmv_plain<T, true><<<grid, kBlock, 0, s>>>(a);
-  if (KB > 0) kb_p4<T, KB><<<grid, kBlock, 0, s>>>(a);
-  kb_p5<T, KB><<<grid, kBlock, 0, s>>>(a);
+cudaError_t launch_iteration_kb(const BatchArgs<T>& a, const PassGrids& g, cudaStream_t s) {
+  if (KB > 0) kb_spmv_proj<T, false><<<g.g[0], kBlock, 0, s>>>(a);
+  else kb_spmv_plain<T, false><<<g.g[0], kBlock, 0, s>>>(a);
+  kb_p2<T, KB><<<g.g[1], kBlock, 0, s>>>(a);
+  if (KB > 0) kb_spmv_proj<T, true><<<g.g[2], kBlock, 0, s>>>(a);
+  else kb_spmv_plain<T, true><<<g.g[2], kBlock, 0, s>>>(a);
+  if (KB > 0) kb_p4<T, KB><<<g.g[3], kBlock, 0, s>>>(a);
+  kb_p5<T, KB><<<g.g[4], kBlock, 0, s>>>(a);
   return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t launch_iteration_b(const BatchArgs<T>& a, int grid, cudaStream_t s) {
+const PassGrids& grids_of(rb_batch_ctx* h) {
+  const int rec = h->k > 0 ? 1 : 0;
+  return std::is_same<T, float>::value ? h->pg32[rec] : h->pg64[rec];
+}
+
+template <typename T>
+cudaError_t launch_iteration_b(const BatchArgs<T>& a, const PassGrids& g, cudaStream_t s) {
   count_launches(a.k > 0 ? 5 : 4);
-  return a.k > 0 ? launch_iteration_kb<T, kBK>(a, grid, s) : launch_iteration_kb<T, 0>(a, grid, s);
+  return a.k > 0 ? launch_iteration_kb<T, kBK>(a, g, s) : launch_iteration_kb<T, 0>(a, g, s);
 }
 
 int poll_iters_b(rb_batch_ctx* h) { return h->o.poll > 0 ? h->o.poll : 8; }
@@ -780,7 +888,7 @@ int iterate_b(rb_batch_ctx* h, int64_t max_itn_all, const std::function<int()>& 
     const BatchArgs<T> a = batch_args<T>(h);
     RB_CUDA_TRY(cudaStreamBeginCapture(h->cs, cudaStreamCaptureModeThreadLocal));
     cudaError_t e = cudaSuccess;
-    for (int it = 0; it < poll_iters_b(h) && e == cudaSuccess; ++it) e = launch_iteration_b<T>(a, h->grid, h->cs);
+    for (int it = 0; it < poll_iters_b(h) && e == cudaSuccess; ++it) e = launch_iteration_b<T>(a, grids_of<T>(h), h->cs);
     if (e == cudaSuccess) {
       kb_flags<<<(h->S + 255) / 256, 256, 0, h->cs>>>(h->st, h->S, h->dsf);
       e = cudaGetLastError();
@@ -870,12 +978,14 @@ int autotune(rb_batch_ctx* h) {
         RB_CUDA_TRY(cudaEventRecord(e0, h->us));
         if (f32) {
           const BatchArgs<float> a = batch_args<float>(h);
-          if (h->k > 0) kb_spmv_proj<float, false><<<h->grid, kBlock, 0, h->us>>>(a);
-          else kb_spmv_plain<float, false><<<h->grid, kBlock, 0, h->us>>>(a);
+          const int g = grids_of<float>(h).g[0];
+          if (h->k > 0) kb_spmv_proj<float, false><<<g, kBlock, 0, h->us>>>(a);
+          else kb_spmv_plain<float, false><<<g, kBlock, 0, h->us>>>(a);
         } else {
           const BatchArgs<double> a = batch_args<double>(h);
-          if (h->k > 0) kb_spmv_proj<double, false><<<h->grid, kBlock, 0, h->us>>>(a);
-          else kb_spmv_plain<double, false><<<h->grid, kBlock, 0, h->us>>>(a);
+          const int g = grids_of<double>(h).g[0];
+          if (h->k > 0) kb_spmv_proj<double, false><<<g, kBlock, 0, h->us>>>(a);
+          else kb_spmv_plain<double, false><<<g, kBlock, 0, h->us>>>(a);
         }
         count_launches(1);
         RB_CUDA_TRY(cudaGetLastError());
@@ -1009,6 +1119,7 @@ int batch_start(rb_batch_ctx* h, const double* rhs, double* xv, const std::vecto
     for (int j = 0; j < h->k; ++j) s.cr[j] = cr[j];
     s.rho = rho;
     s.rnorm2 = rn2;
+    s.rmax2 = rn2;
     s.thresh2 = thresh2[i];
     s.max_itn = max_itn[i];
     s.status = RB_OK;
@@ -1079,7 +1190,7 @@ extern "C" int rbicgstab_batch_destroy(rb_batch h) {
   void* ptrs[] = {h->rp, h->ci, h->trp, h->tci, h->tsrc, h->cv, h->tcv, h->t_sys, h->t_nsl, h->s_t0, h->s_nt,
                   h->t_sl0, h->d_row0, h->d_n, h->d_cofs, h->U, h->C, h->Ct, h->Chat, h->dR, h->fU, h->fC, h->fChat,
                   h->b, h->x, h->r, h->stage, h->p, h->s, h->q, h->t, h->qraw, h->traw, h->rt0, h->fx, h->fr, h->fp,
-                  h->fs, h->fq, h->ft, h->fqraw, h->ftraw, h->frt0, h->st, h->partials, h->dflags, h->dskip, h->dcmd, h->dres, h->dsf};
+                  h->fs, h->fq, h->ft, h->fqraw, h->ftraw, h->frt0, h->st, h->partials, h->dflags, h->dskip, h->dcmd, h->dres, h->dsf, h->drm};
   for (void* p : ptrs) cudaFree(p);
   if (h->hst) cudaFreeHost(h->hst);
   if (h->hsf) cudaFreeHost(h->hsf);
@@ -1186,7 +1297,8 @@ extern "C" int rbicgstab_batch_set_matrices(rb_batch h, int32_t nsys, const int6
     if ((rc = balloc(&h->dR, (int64_t)nsys * kBK * kBK))) return rc;
   }
   if ((rc = balloc(&h->st, nsys)) || (rc = balloc(&h->dflags, nsys)) || (rc = balloc(&h->dskip, nsys)) ||
-      (rc = balloc(&h->dcmd, nsys)) || (rc = balloc(&h->dres, nsys)) || (rc = balloc(&h->dsf, nsys)))
+      (rc = balloc(&h->dcmd, nsys)) || (rc = balloc(&h->dres, nsys)) || (rc = balloc(&h->dsf, nsys)) ||
+      (rc = balloc(&h->drm, nsys)))
     return rc;
   if (h->hst) cudaFreeHost(h->hst);
   if (h->hsf) cudaFreeHost(h->hsf);
@@ -1307,24 +1419,29 @@ extern "C" int rbicgstab_batch_solve(rb_batch h, const double* b, double* x, int
     // FP32 inner iteration with FP64 residual replacement per system, the
     // single-system mixed scheme (reliable updates): a system folds its FP32
     // increment into the FP64 x whenever its recursive residual has fallen
-    // by kReplaceB since the last replacement or it reports convergence; the
-    // true residual then either meets the target (a tenth of the tolerance)
-    // or, projected as in eq. (3.5), replaces the FP32 residual while the
-    // search direction and scalars carry on.  A breakdown, a non-finite
-    // inner iterate (its increment is dropped) or a half-step exit above the
-    // target restarts that system in the next round with a new shadow.
+    // by kReplaceB below the larger of its last true residual and its peak
+    // since then, or it reports convergence; the true residual then either
+    // meets the target (a tenth of the tolerance) or, projected as in eq.
+    // (3.5), replaces the FP32 residual while the search direction and the
+    // scalars carry on.  A half-step exit above the target, and a fold that
+    // would raise the true residual (the FP32 process diverged: an
+    // ill-conditioned system at the FP32 accuracy floor; the fold is undone),
+    // restart the system in the next round.  Two undone folds in a row, a
+    // breakdown or a non-finite inner iterate (its increment dropped) hand
+    // the system to FP64 rounds from its current x at the end.
     constexpr double kReplaceB = 1e-2;
+    constexpr int kStallSwitchB = 2;   // folds undone in a row before the FP64 rounds
     constexpr int kRounds = 6;
-    std::vector<double> target(S), rlast(S, 0.0);
+    std::vector<double> target(S), rlast(S, 0.0), rmx(S, 0.0);
     for (int i = 0; i < S; ++i) target[i] = 0.1 * h->o.tol * std::sqrt(bn2[i]);
-    std::vector<char> fin(S, 0), skip(S, 1), ended(S, 0);
-    std::vector<int> cmd(S), res(S), last_status(S, RB_OK);
+    std::vector<char> fin(S, 0), skip(S, 1), ended(S, 0), to64(S, 0);
+    std::vector<int> cmd(S), res(S), last_status(S, RB_OK), stalls(S, 0);
     for (int round = 0; round < kRounds; ++round) {
       bool any = false;
       for (int i = 0; i < S; ++i) {
         skip[i] = 1;
         ended[i] = 0;
-        if (fin[i]) continue;
+        if (fin[i] || to64[i]) continue;
         if (!std::isfinite(rn2[i])) {
           status[i] = RB_ENONFINITE;
           fin[i] = 1;
@@ -1347,7 +1464,7 @@ extern "C" int rbicgstab_batch_solve(rb_batch h, const double* b, double* x, int
         cap[i] = std::max(1, max_itn[i] - iters[i]);
         rlast[i] = std::sqrt(rn2[i]);
       }
-      if ((rc = batch_start(h, h->b, h->x, th, skip, cap, h->o.shadow_seed + (uint64_t)round))) return done(rc);
+      if ((rc = batch_start(h, h->b, h->x, th, skip, cap, h->o.shadow_seed))) return done(rc);
       RB_CUDA_TRY(to_float(h->r, h->fr, h->NP, h->us));
       RB_CUDA_TRY(to_float(h->r, h->fp, h->NP, h->us));
       RB_CUDA_TRY(to_float(h->rt0, h->frt0, h->NP, h->us));
@@ -1361,50 +1478,76 @@ extern "C" int rbicgstab_batch_solve(rb_batch h, const double* b, double* x, int
           res[i] = 0;
           if (skip[i] || ended[i]) continue;
           const SysFlag& f = h->hsf[i];
+          const double peak2 = std::max(f.rmax2, rlast[i] * rlast[i]);
           if (f.done) cmd[i] = f.status == RB_ENONFINITE ? kCmdDrop : kCmdFold;
-          else if (f.rnorm2 <= kReplaceB * kReplaceB * rlast[i] * rlast[i]) cmd[i] = kCmdFold;
+          else if (f.rnorm2 <= kReplaceB * kReplaceB * peak2) cmd[i] = kCmdFold;
           anyc = anyc || cmd[i] != kCmdNone;
         }
         if (!anyc) return RB_OK;
         RB_CUDA_TRY(cudaMemcpyAsync(h->dcmd, cmd.data(), sizeof(int) * S, cudaMemcpyHostToDevice, h->us));
-        count_launches(2);
+        count_launches(3);
+        // the folded systems' previous x waits in s (idle in the FP32 rounds)
+        kb_copy_rows<<<h->grid, kBlock, 0, h->us>>>(h->s, h->x, h->dcmd, tiles_of(h));
         kb_fold<<<h->grid, kBlock, 0, h->us>>>(h->x, h->fx, h->U, h->NP, h->k, h->st, h->dcmd, tiles_of(h));
-        kb_state_cmd<<<(S + 255) / 256, 256, 0, h->us>>>(h->st, S, h->k, h->dcmd, nullptr);
+        kb_state_cmd<<<(S + 255) / 256, 256, 0, h->us>>>(h->st, S, h->k, h->dcmd, nullptr, nullptr);
         RB_CUDA_TRY(cudaGetLastError());
         int rc2 = true_residuals(h, rn2, bn2);   // synchronises: cmd is free again after it
         if (rc2) return rc2;
-        bool anyr = false;   // systems whose FP32 residual is replaced
-        std::vector<int> rep(S, 0);
+        bool anyr = false, anyu = false;   // systems whose FP32 residual is replaced / whose fold is undone
+        std::vector<int> rep(S, 0), undo(S, 0);
         for (int i = 0; i < S; ++i) {
           if (cmd[i] == kCmdNone) continue;
           const SysFlag& f = h->hsf[i];
-          const bool met = std::isfinite(rn2[i]) && std::sqrt(rn2[i]) <= target[i];
-          if (met) {   // converged: stop it
+          const double rn = std::sqrt(rn2[i]);
+          const bool finite = std::isfinite(rn);
+          if (!finite || rn > rlast[i]) {    // the fold made x worse: undo it, restart next round
+            undo[i] = 1;
+            anyu = true;
+            rn2[i] = rlast[i] * rlast[i];
+            if (!f.done) res[i] = 2;
+            h->hsf[i].done = 1;
+            ended[i] = 1;
+            if (++stalls[i] >= kStallSwitchB) to64[i] = 1;
+            continue;
+          }
+          stalls[i] = 0;
+          if (rn <= target[i]) {             // converged: stop it
             if (!f.done) res[i] = 2;
             h->hsf[i].done = 1;
             ended[i] = 1;
             fin[i] = 1;
             status[i] = RB_OK;
-          } else if (!f.done || (f.status == RB_OK && !f.half)) {   // replace and carry on
+          } else if (f.done && f.status != RB_OK && f.status != RB_ENOTCONV) {   // breakdown / overflow
+            ended[i] = 1;
+            to64[i] = 1;
+            last_status[i] = f.status;
+          } else if (f.done && f.status == RB_ENOTCONV) {
+            ended[i] = 1;
+            fin[i] = 1;
+            status[i] = RB_ENOTCONV;
+          } else if (!f.done || !f.half) {   // replace and carry on
             rep[i] = 1;
             anyr = true;
-            if (f.done) res[i] = 1;
+            res[i] = f.done ? 1 : 3;
             h->hsf[i].done = 0;
-            rlast[i] = std::sqrt(rn2[i]);
+            rlast[i] = rn;
+            rmx[i] = rn2[i];
             outer[i] += 1;
-          } else {   // a failure or a half-step exit: this round ends for it
+          } else {   // a half-step exit above the target: the next round restarts it
             ended[i] = 1;
-            last_status[i] = f.status;
-            if (f.status == RB_ENOTCONV || (f.status == RB_ENONFINITE && !std::isfinite(rn2[i]))) {
-              fin[i] = 1;
-              status[i] = std::isfinite(rn2[i]) ? RB_ENOTCONV : RB_ENONFINITE;
-            }
           }
         }
+        if (anyu) {
+          RB_CUDA_TRY(cudaMemcpyAsync(h->dres, undo.data(), sizeof(int) * S, cudaMemcpyHostToDevice, h->us));
+          count_launches(1);
+          kb_copy_rows<<<h->grid, kBlock, 0, h->us>>>(h->x, h->s, h->dres, tiles_of(h));
+          RB_CUDA_TRY(cudaGetLastError());
+          RB_CUDA_TRY(cudaStreamSynchronize(h->us));   // dres is written again below
+        }
         if (anyr) {
+          RB_CUDA_TRY(cudaMemcpyAsync(h->dskip, rep.data(), sizeof(int) * S, cudaMemcpyHostToDevice, h->us));
           if (h->k > 0) {
-            RB_CUDA_TRY(cudaMemcpyAsync(h->dskip, rep.data(), sizeof(int) * S, cudaMemcpyHostToDevice, h->us));
-            // skip mask = not replaced: invert on the host into cmd (free after the sync above)
+            // gemv skip mask = not replaced (cmd is free after the sync above)
             for (int i = 0; i < S; ++i) cmd[i] = rep[i] ? 0 : 1;
             RB_CUDA_TRY(cudaMemcpyAsync(h->dcmd, cmd.data(), sizeof(int) * S, cudaMemcpyHostToDevice, h->us));
             SysDots d{};
@@ -1412,8 +1555,6 @@ extern "C" int rbicgstab_batch_solve(rb_batch h, const double* b, double* x, int
             if ((rc2 = sysdots(h, d, false))) return rc2;
             if ((rc2 = gemv_b(h, h->x, h->U, 1.0, false, h->dcmd))) return rc2;
             if ((rc2 = gemv_b(h, h->r, h->C, -1.0, false, h->dcmd))) return rc2;
-          } else {
-            RB_CUDA_TRY(cudaMemcpyAsync(h->dskip, rep.data(), sizeof(int) * S, cudaMemcpyHostToDevice, h->us));
           }
           count_launches(1);
           kb_to_float<<<h->grid, kBlock, 0, h->us>>>(h->fr, h->r, h->dskip, tiles_of(h));
@@ -1423,8 +1564,9 @@ extern "C" int rbicgstab_batch_solve(rb_batch h, const double* b, double* x, int
         for (int i = 0; i < S; ++i) anys = anys || res[i] != 0;
         if (anys) {
           RB_CUDA_TRY(cudaMemcpyAsync(h->dres, res.data(), sizeof(int) * S, cudaMemcpyHostToDevice, h->us));
+          RB_CUDA_TRY(cudaMemcpyAsync(h->drm, rmx.data(), sizeof(double) * S, cudaMemcpyHostToDevice, h->us));
           count_launches(1);
-          kb_state_cmd<<<(S + 255) / 256, 256, 0, h->us>>>(h->st, S, h->k, nullptr, h->dres);
+          kb_state_cmd<<<(S + 255) / 256, 256, 0, h->us>>>(h->st, S, h->k, nullptr, h->dres, h->drm);
           RB_CUDA_TRY(cudaGetLastError());
         }
         return sync_b(h);   // the host vectors above are read by the copies
@@ -1434,6 +1576,46 @@ extern "C" int rbicgstab_batch_solve(rb_batch h, const double* b, double* x, int
       if ((rc = sync_b(h))) return done(rc);
       for (int i = 0; i < S; ++i)
         if (!skip[i]) iters[i] += h->hst[i].iter;
+    }
+    for (int i = 0; i < S; ++i)   // FP32 rounds used up: those systems finish in FP64
+      if (!fin[i] && !to64[i] && iters[i] < max_itn[i]) to64[i] = 1;
+    // FP64 rounds for the systems the FP32 iteration could not finish: Alg. 2
+    // in FP64 from the current x to the mixed target on the recursive
+    // residual; a true residual still above the tolerance after a round (the
+    // recursive residual drifts from the true one over a long run) takes
+    // another round, at most three.
+    for (int round64 = 0; round64 < 3; ++round64) {
+      bool any64 = false;
+      std::vector<char> skip64(S, 1);
+      for (int i = 0; i < S; ++i)
+        if (to64[i] && !fin[i]) {
+          skip64[i] = 0;
+          any64 = true;
+        }
+      if (!any64) break;
+      if ((rc = true_residuals(h, rn2, bn2))) return done(rc);
+      std::vector<double> th(S);
+      std::vector<int> cap(S);
+      for (int i = 0; i < S; ++i) {
+        th[i] = target[i] * target[i];
+        cap[i] = std::max(1, max_itn[i] - iters[i]);
+      }
+      if ((rc = batch_start(h, h->b, h->x, th, skip64, cap, h->o.shadow_seed))) return done(rc);
+      if ((rc = iterate_b<double>(h, *std::max_element(cap.begin(), cap.end())))) return done(rc);
+      if ((rc = gemv_b(h, h->x, h->U, -1.0, true))) return done(rc);
+      RB_CUDA_TRY(cudaMemcpyAsync(h->hst, h->st, sizeof(IterState) * S, cudaMemcpyDeviceToHost, h->us));
+      if ((rc = sync_b(h))) return done(rc);
+      if ((rc = true_residuals(h, rn2, bn2))) return done(rc);
+      for (int i = 0; i < S; ++i) {
+        if (skip64[i]) continue;
+        iters[i] += h->hst[i].iter;
+        outer[i] += 1;
+        status[i] = h->hst[i].status;
+        const bool more = status[i] == RB_OK && std::sqrt(rn2[i]) > h->o.tol * std::sqrt(bn2[i]) &&
+                          iters[i] < max_itn[i] && round64 < 2;
+        if (!more) fin[i] = 1;
+        if (status[i] == RB_OK && std::sqrt(rn2[i]) > h->o.tol * std::sqrt(bn2[i]) && !more) status[i] = RB_ENOTCONV;
+      }
     }
     for (int i = 0; i < S; ++i) {
       rec2[i] = rn2[i];

@@ -694,6 +694,7 @@ __global__ void k_init_state(IterState* st, int k, double tol, int max_itn) {
   st->k = k;
   st->rho = st->red[k];
   st->rnorm2 = st->red[k + 1];
+  st->rmax2 = st->rnorm2;
   st->thresh2 = tol * tol * st->bnorm2;
   st->alpha = st->omega = st->beta = 0.0;
   st->iter = 0;

@@ -76,6 +76,7 @@ struct IterState {
   double thresh2;  // (tol ||b||)^2
   double st, tt, rts, rtt;
   double bnorm2;
+  double rmax2;     // largest recursive ||r||^2 since the last reset (residual replacement)
   int32_t iter;     // completed iterations
   int32_t done;     // 1 once converged / failed: every later pass returns at once
   int32_t half;     // the current iteration ended after its half step

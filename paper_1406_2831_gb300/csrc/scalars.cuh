@@ -86,6 +86,7 @@ static __device__ void finish_p5(IterState* st, const double* res, int k) {
     if (lane == 0) {
       st->iter += 1;
       st->rnorm2 = st->snorm2;
+      st->rmax2 = fmax(st->rmax2, st->snorm2);
       st->done = 1;
     }
     return;
@@ -94,6 +95,7 @@ static __device__ void finish_p5(IterState* st, const double* res, int k) {
   st->iter += 1;
   const double rn2 = res[0];
   st->rnorm2 = rn2;
+  st->rmax2 = fmax(st->rmax2, rn2);   // fmax ignores a NaN: the finiteness test below catches it
   if (!isfinite(rn2)) fail(st, RB_ENONFINITE);
   else if (rn2 <= st->thresh2) st->done = 1;
   else if (st->rho == 0.0) fail(st, RB_EBREAKDOWN_RHO);

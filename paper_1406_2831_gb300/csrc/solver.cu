@@ -66,6 +66,7 @@ T* dalloc(int64_t count, int* err) {
 struct GraphSlot {
   cudaGraphExec_t exec = nullptr;
   bool valid = false;
+  int k = -1, nrhs = -1;   // the recycle dimension and block size it was captured for
 };
 
 // Vectors of one right-hand side.  FP64: b, x and the iteration vectors;
@@ -91,7 +92,6 @@ struct rb_ctx {
   int dev = 0, nsm = 0;
   // matrix
   int64_t n = 0, nnz = 0, npad = 0;
-  uint64_t seed_bump = 0;   // added to the shadow seed by a mixed solve's retry after a failure
   int32_t *rp = nullptr, *ci = nullptr;
   double* cv = nullptr;
   int32_t *trp = nullptr, *tci = nullptr;
@@ -141,10 +141,10 @@ struct rb_ctx {
   double *dG = nullptr, *dR = nullptr;
   const double** dptr = nullptr;   // device pointer lists (4 * 128)
   Grids grids{};
-  GraphSlot g_plain, g_cycle[kBanks];
+  GraphSlot g_plain[2], g_cycle[kBanks];   // plain iterations: [0] FP32, [1] FP64
   GraphSlot g_bicg;       // Alg. 1 iterations (primary + dual)
   int g_bicg_k = -1;
-  int g_k = -1, g_nrhs = -1;
+  int g_cycle_ts = 0;     // element size the cycle graphs were captured for
 };
 
 // ============================================================ helpers
@@ -168,13 +168,13 @@ int sync(rb_ctx* h) {
 }
 
 void reset_graphs(rb_ctx* h) {
-  for (GraphSlot* g : {&h->g_plain, &h->g_cycle[0], &h->g_cycle[1], &h->g_cycle[2], &h->g_bicg}) {
+  for (GraphSlot* g : {&h->g_plain[0], &h->g_plain[1], &h->g_cycle[0], &h->g_cycle[1], &h->g_cycle[2], &h->g_bicg}) {
     if (g->exec) cudaGraphExecDestroy(g->exec);
     g->exec = nullptr;
     g->valid = false;
+    g->k = g->nrhs = -1;
   }
-  h->g_k = -1;
-  h->g_nrhs = -1;
+  h->g_cycle_ts = 0;
   h->g_bicg_k = -1;
 }
 
@@ -770,7 +770,7 @@ int setup_block(rb_ctx* h, int nrhs, double* const* rhs, double* const* xb, cons
     }
   }
   for (int attempt = 0; attempt < 4; ++attempt) {
-    RB_CUDA_TRY(shadow(h->rt0, h->n, h->npad, h->o.shadow_seed + h->seed_bump + (uint64_t)attempt, h->us));
+    RB_CUDA_TRY(shadow(h->rt0, h->n, h->npad, h->o.shadow_seed + (uint64_t)attempt, h->us));
     if (k > 0) {
       DotArgs d{};
       d.M = h->C; d.ld = ld; d.km = k; d.v = h->rt0; d.nd = 0;
@@ -834,15 +834,15 @@ using PollHook = std::function<int()>;
 // Launch graphs until every slot reports done.  Non-update mode.
 template <typename T>
 int iterate_plain(rb_ctx* h, int nrhs, const PollHook& hook = nullptr) {
-  if (!h->g_plain.valid || h->g_k != h->k || h->g_nrhs != nrhs) {
-    reset_graphs(h);
-    int rc = capture<T>(h, &h->g_plain, poll_iters(h), 0, false, nrhs);
+  GraphSlot& g = h->g_plain[sizeof(T) == sizeof(double) ? 1 : 0];
+  if (!g.valid || g.k != h->k || g.nrhs != nrhs) {   // only this graph is captured again
+    int rc = capture<T>(h, &g, poll_iters(h), 0, false, nrhs);
     if (rc) return rc;
-    h->g_k = h->k;
-    h->g_nrhs = nrhs;
+    g.k = h->k;
+    g.nrhs = nrhs;
   }
   for (;;) {
-    RB_CUDA_TRY(cudaGraphLaunch(h->g_plain.exec, h->us));
+    RB_CUDA_TRY(cudaGraphLaunch(g.exec, h->us));
     count_launches((long long)poll_iters(h) * passes_per_iter(h));
     int rc = read_state(h, nrhs);
     if (rc) return rc;
@@ -940,16 +940,17 @@ int iterate_cycles(rb_ctx* h, int nrhs, SolveOut* so, const PollHook& hook = nul
     RB_CUDA_TRY(cudaMemcpyAsync(h->AYc, f32 ? (const void*)h->fC : (const void*)h->C, sizeof(T) * ld * h->k,
                                 cudaMemcpyDeviceToDevice, h->us));
   }
-  bool have_graphs = h->g_k == h->k && h->g_nrhs == nrhs;
-  for (int b = 0; b < kBanks; ++b) have_graphs = have_graphs && h->g_cycle[b].valid;
-  if (!have_graphs) {
-    reset_graphs(h);
+  bool have_graphs = h->g_cycle_ts == (int)sizeof(T);
+  for (int b = 0; b < kBanks; ++b)
+    have_graphs = have_graphs && h->g_cycle[b].valid && h->g_cycle[b].k == h->k && h->g_cycle[b].nrhs == nrhs;
+  if (!have_graphs) {   // only the cycle graphs are captured again
     for (int b = 0; b < kBanks; ++b) {
       int rc = capture<T>(h, &h->g_cycle[b], h->cyc, b, true, nrhs);
       if (rc) return rc;
+      h->g_cycle[b].k = h->k;
+      h->g_cycle[b].nrhs = nrhs;
     }
-    h->g_k = h->k;
-    h->g_nrhs = nrhs;
+    h->g_cycle_ts = (int)sizeof(T);
   }
   int rc = sync(h);   // the update stream reads the candidate set up above
   if (rc) return rc;
@@ -1077,23 +1078,31 @@ int solve_fp64(rb_ctx* h, int nrhs, const bool* x_nonzero, SolveOut* so) {
 // residual replacement ("reliable updates", Sleijpen and van der Vorst,
 // Computing 56, 1996).  The FP64 iterate x takes the FP32 correction
 // d = x_inner - U x_c (the final correction of the inner solve) whenever the
-// recursive FP32 residual has fallen by kReplace since the last replacement
-// or reports convergence; the true residual b - A x is then formed in FP64
-// and, unless it meets the tolerance, replaces the recursive one while the
-// search direction and the scalars carry on.  So one Krylov process serves
-// the whole solve.  A breakdown, or a half-step exit whose true residual
-// misses the tolerance, restarts the inner solve from the current x (a
-// refinement step).  The target is a tenth of the tolerance, so the FP64
-// answer carries a forward error comparable to the FP64 solver's.
+// recursive FP32 residual has fallen by kReplace below the larger of the last
+// true residual and its own peak since then (the rounding of the increment
+// grows with the peak), or reports convergence; the true residual b - A x is
+// then formed in FP64 and, unless it meets the target, replaces the recursive
+// one while the search direction and the scalars carry on.  So one Krylov
+// process serves the whole solve.  A half-step exit whose true residual misses
+// the target, and a fold that would raise the true residual (the FP32 process
+// diverged: an ill-conditioned system at the FP32 accuracy floor), restart the
+// inner solve from the current x (a refinement step; the latter fold is
+// undone).  After kStallSwitch undone folds in a row, a breakdown or an FP32
+// overflow the slot is finished in FP64 from x.  The target is a tenth of the
+// tolerance, so the answer carries a forward error comparable to the FP64
+// solver's.
 constexpr double kReplace = 1e-2;
+constexpr int kStallSwitch = 2;   // folds undone in a row before the FP64 finish
 
 int solve_mixed(rb_ctx* h, int nrhs, SolveOut* so) {
   const int64_t ld = h->npad;
   const int max_rounds = 12;
   const int max_itn = h->o.max_itn > 0 ? h->o.max_itn : (int)std::min<int64_t>(h->n, 20000);
   double bn2[kMaxRhs], target[kMaxRhs], rn[kMaxRhs], rlast[kMaxRhs];
-  bool stop[kMaxRhs], running[kMaxRhs];
+  bool stop[kMaxRhs], running[kMaxRhs], to64[kMaxRhs] = {false, false, false, false};
+  int stalls[kMaxRhs] = {0, 0, 0, 0};
   int total_it[kMaxRhs], last_status[kMaxRhs];
+  double rmax_reset[kMaxRhs];   // host source of the device peak's reset after a replacement
   for (int i = 0; i < nrhs; ++i) {
     bn2[i] = h->hst[i].red[0];
     target[i] = 0.1 * h->o.tol * std::sqrt(bn2[i]);
@@ -1149,20 +1158,44 @@ int solve_mixed(rb_ctx* h, int nrhs, SolveOut* so) {
         fprintf(stderr, "rb_trace slot %d iter %d rn2 %.3e rlast %.3e done %d half %d status %d\n", i, hs.iter,
                 hs.rnorm2, rlast[i], hs.done, hs.half, hs.status);
       const bool conv_rec = hs.done && hs.status == RB_OK && !hs.half && !(cycles_running && i == 0);
-      const bool due = !hs.done && hs.rnorm2 <= kReplace * kReplace * rlast[i] * rlast[i];
+      const double peak2 = std::max(hs.rmax2, rlast[i] * rlast[i]);
+      const bool due = !hs.done && hs.rnorm2 <= kReplace * kReplace * peak2;
       if (!conv_rec && !due) continue;
       PhaseClock pr;
+      // the previous x waits in xin (unused while the inner solve runs)
+      // until the fold is accepted
+      RB_CUDA_TRY(cudaMemcpyAsync(h->sl[i].xin, h->sl[i].x, sizeof(double) * ld, cudaMemcpyDeviceToDevice, h->us));
       int rc = fold(i);
       if (!rc) rc = true_residual(i);
       if (rc) return rc;
       so[i].outer += 1;
       if (trace) fprintf(stderr, "rb_trace slot %d replace: true residual %.6e target %.3e\n", i, rn[i], target[i]);
-      if (!std::isfinite(rn[i]) || rn[i] <= target[i]) {
+      // A fold that raised the true residual (or made it non-finite): the
+      // FP32 process diverged after an earlier replacement, which is where
+      // an ill-conditioned system meets the FP32 accuracy floor (about u_32
+      // times its condition number).  The fold is undone, the slot restarts
+      // from x in the next round, and after kStallSwitch such folds in a row
+      // it is finished in FP64 instead.
+      if (!std::isfinite(rn[i]) || rn[i] > rlast[i]) {
+        RB_CUDA_TRY(cudaMemcpyAsync(h->sl[i].x, h->sl[i].xin, sizeof(double) * ld, cudaMemcpyDeviceToDevice, h->us));
+        rn[i] = rlast[i];
+        if (!hs.done) RB_CUDA_TRY(cudaMemcpyAsync(&h->st[i].done, &kOne, sizeof(int), cudaMemcpyHostToDevice, h->us));
+        h->hst[i].done = 1;
+        running[i] = false;
+        if (++stalls[i] >= kStallSwitch) {
+          stop[i] = true;
+          to64[i] = true;
+        }
+        if (trace) fprintf(stderr, "rb_trace slot %d fold undone (%d in a row)\n", i, stalls[i]);
+        continue;
+      }
+      stalls[i] = 0;
+      if (rn[i] <= target[i]) {
         if (!hs.done) RB_CUDA_TRY(cudaMemcpyAsync(&h->st[i].done, &kOne, sizeof(int), cudaMemcpyHostToDevice, h->us));
         h->hst[i].done = 1;
         running[i] = false;
         stop[i] = true;
-        so[i].status = std::isfinite(rn[i]) ? RB_OK : RB_ENONFINITE;
+        so[i].status = RB_OK;
         continue;
       }
       // replace the recursive residual and carry on.  The true residual is
@@ -1181,20 +1214,16 @@ int solve_mixed(rb_ctx* h, int nrhs, SolveOut* so) {
       if (hs.done) RB_CUDA_TRY(cudaMemcpyAsync(&h->st[i].done, &kZero, sizeof(int), cudaMemcpyHostToDevice, h->us));
       h->hst[i].done = 0;
       rlast[i] = rn[i];
+      rmax_reset[i] = rn[i] * rn[i];   // the peak restarts from the replaced residual
+      RB_CUDA_TRY(cudaMemcpyAsync(&h->st[i].rmax2, &rmax_reset[i], sizeof(double), cudaMemcpyHostToDevice, h->us));
       pr.lap("replace");
     }
     return sync(h);
   };
 
   PhaseClock pcs;
-  struct SeedReset {   // every other solve draws the shadow from the handle's seed
-    rb_ctx* h;
-    ~SeedReset() { h->seed_bump = 0; }
-  } seed_reset{h};
-  h->seed_bump = 0;
   for (int round = 0;; ++round) {
     bool any = false;
-    bool failed_round = false;
     bool skip[kMaxRhs] = {true, true, true, true};
     bool xnz[kMaxRhs] = {false, false, false, false};
     double* rhs[kMaxRhs];
@@ -1213,9 +1242,12 @@ int solve_mixed(rb_ctx* h, int nrhs, SolveOut* so) {
       } else if (rn[i] <= target[i] || bn2[i] == 0.0) {
         so[i].status = RB_OK;
         stop[i] = true;
-      } else if (round >= max_rounds || total_it[i] >= max_itn) {
+      } else if (total_it[i] >= max_itn) {
         so[i].status = last_status[i] != RB_OK ? last_status[i] : RB_ENOTCONV;
         stop[i] = true;
+      } else if (round >= max_rounds) {   // FP32 rounds used up: finish in FP64
+        stop[i] = true;
+        to64[i] = true;
       } else {
         // inner system A d = r, converged when ||r - A d|| <= target
         skip[i] = false;
@@ -1264,23 +1296,77 @@ int solve_mixed(rb_ctx* h, int nrhs, SolveOut* so) {
       last_status[i] = hs.status;
       if (stop[i]) continue;   // converged at a replacement (x already folded)
       running[i] = false;
-      // a breakdown, max_itn, or a half-step exit: fold the correction and
-      // let the next outer (refinement) step restart from x.  A non-finite
-      // inner iterate (an FP32 overflow) is dropped instead: x keeps its
-      // last fold.  After a failure the next round draws another shadow, so
-      // the restarted iteration is not the same one again.
+      // max_itn or a half-step exit: fold the correction and let the next
+      // outer (refinement) step restart from x.  A breakdown folds too and
+      // a non-finite inner iterate (an FP32 overflow) is dropped (x keeps
+      // its last fold); either hands the slot to the FP64 finish.
       if (hs.status == RB_ENONFINITE) {
         if ((rc = drop(i))) return rc;
-        failed_round = true;
       } else {
         if ((rc = fold(i))) return rc;
-        if (hs.status != RB_OK && hs.status != RB_ENOTCONV) failed_round = true;
+      }
+      if (hs.status != RB_OK && hs.status != RB_ENOTCONV) {
+        to64[i] = true;
+        stop[i] = true;
       }
     }
-    if (failed_round) h->seed_bump += 16;
     rc = sync(h);
     if (rc) return rc;
   }
+  // FP64 finish of the slots whose FP32 iteration stalled, broke down or
+  // overflowed: Alg. 2 in FP64 from the current x, with the same recycle
+  // space, to the mixed target on the recursive residual; a true residual
+  // still above the tolerance after it (the recursive residual drifts from
+  // the true one over a long run) takes another FP64 round from x.
+  for (int round64 = 0; round64 < 3; ++round64) {
+    bool any64 = false;
+    for (int i = 0; i < nrhs; ++i) any64 = any64 || to64[i];
+    if (!any64) break;
+    bool skip64[kMaxRhs] = {true, true, true, true};
+    bool xnz64[kMaxRhs] = {false, false, false, false};
+    double* rhs64[kMaxRhs];
+    double* xb64[kMaxRhs];
+    double tol64[kMaxRhs];
+    for (int i = 0; i < nrhs; ++i) {
+      rhs64[i] = h->sl[i].b;
+      xb64[i] = h->sl[i].x;
+      tol64[i] = 0.1 * h->o.tol;
+      if (!to64[i]) continue;
+      skip64[i] = false;
+      xnz64[i] = true;
+      RB_CUDA_TRY(cudaMemcpyAsync(&h->st[i].bnorm2, &bn2[i], sizeof(double), cudaMemcpyHostToDevice, h->us));
+    }
+    int rc = sync(h);
+    if (!rc) rc = setup_block(h, nrhs, rhs64, xb64, xnz64, skip64, tol64, so);
+    if (rc) return rc;
+    if (!all_done(h, nrhs)) {
+      if ((rc = init_p<double>(h, nrhs, false))) return rc;
+      if ((rc = iterate_plain<double>(h, nrhs))) return rc;
+    }
+    for (int i = 0; i < nrhs; ++i) {
+      if (!to64[i]) continue;
+      if (h->k > 0)
+        RB_CUDA_TRY(gemv_update(h->sl[i].x, h->U, ld, h->k, h->st[i].xc, nullptr, -1.0, h->npad, vec_grid(h), h->us));
+      RB_CUDA_TRY(residual_norm(h->A.view(), h->sl[i].b, h->sl[i].x, h->tmp, h->npad, h->st + i, h->partials,
+                                h->grids.spmv, h->us));
+      so[i].mv_check += 1;
+    }
+    if ((rc = read_state(h, nrhs))) return rc;
+    for (int i = 0; i < nrhs; ++i) {
+      if (!to64[i]) continue;
+      const IterState& hs = h->hst[i];
+      total_it[i] += hs.iter;
+      so[i].mv += 2 * (int64_t)hs.iter - (hs.half ? 1 : 0);
+      so[i].outer += 1;
+      so[i].status = hs.status;
+      rn[i] = std::sqrt(hs.red[0]);
+      // done unless the true residual misses the tolerance with iterations left
+      to64[i] = hs.status == RB_OK && rn[i] > h->o.tol * std::sqrt(bn2[i]) && total_it[i] < max_itn;
+    }
+    pcs.lap("blk_fp64_finish");
+  }
+  for (int i = 0; i < nrhs; ++i)
+    if (to64[i]) so[i].status = RB_ENOTCONV;   // three FP64 rounds did not meet the tolerance
   for (int i = 0; i < nrhs; ++i) {
     so[i].iters = total_it[i];
     so[i].relres_true = bn2[i] > 0 ? rn[i] / std::sqrt(bn2[i]) : 0.0;
