@@ -475,6 +475,27 @@ def run_batch(args):
         out["unbatched_plain_fp64"] = {"solves_per_s": round(len(shifts) * nsys / (ms * 1e-3), 2), "ms": round(ms, 1),
                                        "failed": len(ub_fail), "failures": ub_fail[:8]}
 
+    # P1 (SpMV + projection, all systems active) against the copy roofline:
+    # the CSR byte model of pass_bytes over the whole batch, timed by the
+    # autotuner (CUDA events, the chosen tile configuration)
+    peaks = measured_peaks()
+    roof = {}
+    for arm, vb, k in (("batched_plain_fp64", 8, 0), ("plain_mixed_shifts_1_3", 4, 0),
+                       ("recycled_mixed_shifts_1_3", 4, 10)):
+        tms = (out.get(arm) or {}).get("autotune", {}).get("tuned_p1_ms")
+        if not tms:
+            continue
+        byts = pass_bytes(n_tot, nnz_tot, k, vb=vb, ab=vb, R=1)[0]
+        gbs = byts / (tms * 1e-3) / 1e9
+        roof[arm] = {"bytes": int(byts), "ms": round(tms, 4), "GB/s": round(gbs, 1),
+                     "frac": round(gbs / peaks["hbm_gbs"], 4)}
+    if roof:
+        first = next(iter(roof.values()))
+        out["roofline"] = {"bound": "hbm", "kernel": "batched P1, " + next(iter(roof)), "achieved": first["GB/s"],
+                           "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": first["frac"], "traffic": None,
+                           "peak_source": peaks["source"], "arms": roof,
+                           "timing": "autotuner CUDA events, chosen tile size and CTAs/SM, every system active"}
+
     def ratio(a, b):
         try:
             return round(out[a]["solves_per_s"] / out[b]["solves_per_s"], 4)
