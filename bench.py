@@ -65,6 +65,9 @@ def parse():
                     help="--batch: comma-separated arms to run (batched_plain_fp64, batched_plain_mixed, "
                          "recycled_mixed_shifts_1_3, plain_mixed_shifts_1_3, plain_fp64_shifts_1_3, "
                          "unbatched_plain_fp64); default all")
+    ap.add_argument("--max-itn", type=int, default=0,
+                    help="--batch: iteration cap per system (0: the solver's default); a small cap "
+                         "makes a short run for a profiler")
     ap.add_argument("--systems", type=int, default=0,
                     help="--batch: number of systems (default 256; 16 with --quick)")
     ap.add_argument("--adjoint", action="store_true",
@@ -379,7 +382,8 @@ def run_batch(args):
 
     def batched_arm(precision, which, Us=None):
         try:
-            B = rb.Batch(mats, k_max=10 if Us is not None else 0, precision=precision, tol=1e-8, stream=stream)
+            B = rb.Batch(mats, k_max=10 if Us is not None else 0, precision=precision, tol=1e-8, stream=stream,
+                         max_itn=args.max_itn)
             if Us is not None:
                 B.set_recycle(Us)
             B.set_values(vals_d[which[0]])

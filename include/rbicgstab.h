@@ -51,7 +51,9 @@ extern "C" {
 #define RB_DEVICE  1
 
 #define RB_FP64    0   /* FP64 storage and arithmetic throughout */
-#define RB_MIXED   1   /* FP32 inner RBiCGSTAB + FP64 iterative refinement */
+#define RB_MIXED   1   /* FP32 inner RBiCGSTAB with FP64 residual replacement; a solve
+                         whose FP32 iteration stalls, breaks down or overflows is
+                         finished in FP64 from its current x */
 
 #define RB_RECYCLE_NONE          0  /* plain BiCGSTAB (U ignored) */
 #define RB_RECYCLE_FIXED         1  /* use U, U~ as given; never change them */
@@ -266,9 +268,11 @@ int rbicgstab_residual_noalloc(int64_t n, const int32_t* row_ptr, const int32_t*
  * are captured as a CUDA graph; the tile size and CTAs per SM are chosen by
  * an autotuner at the first solve after a matrix or space change.
  * opts: tol, max_itn, poll, shadow_seed, cuda_stream, precision (RB_FP64, or
- * RB_MIXED: FP32 iteration with Dot2 dot products, restarted on the FP64
- * residual until ||b_i - A_i x_i|| <= tol ||b_i||), k_max <= 16 (0: plain
- * BiCGSTAB only).  Errors as for the single-system calls. */
+ * RB_MIXED: FP32 iteration with Dot2 dot products and FP64 residual
+ * replacement per system, as rbicgstab_solve's mixed mode: a system whose
+ * FP32 iteration stalls, breaks down or overflows is finished in FP64 from
+ * its current x; converged when ||b_i - A_i x_i|| <= tol ||b_i||), k_max <=
+ * 16 (0: plain BiCGSTAB only).  Errors as for the single-system calls. */
 typedef struct rb_batch_ctx* rb_batch;
 int rbicgstab_batch_create(rb_batch* h, const rb_opts* opts);
 int rbicgstab_batch_destroy(rb_batch h);

@@ -959,7 +959,7 @@ namespace {
 // and CTAs per SM on the current matrices and space; keep the fastest.
 // RB_TIMING in the environment prints every candidate.
 int autotune(rb_batch_ctx* h) {
-  const int cand_ts[] = {4, 8, 16, 32, 64};
+  const int cand_ts[] = {4, 8, 16, 32, 64, 128, 256};
   const int cand_cps[] = {2, 4, 8};
   const bool print = getenv("RB_TIMING") != nullptr;
   double best = 1e30;

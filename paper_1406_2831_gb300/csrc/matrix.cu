@@ -263,33 +263,84 @@ __global__ void k_scatter_t(int64_t n, const int32_t* __restrict__ rp, const int
   }
 }
 
-// Exclusive scan of cnt[0..n) into out[0..n] by one block: each thread sums a
-// contiguous chunk, the block scans the chunk sums in shared memory (Hillis-
-// Steele), and each thread writes its chunk's prefix sums.  The transpose is
-// built once per matrix pattern, so one SM's bandwidth is enough.
+// Exclusive prefix sums of the column counts (the row pointers of A^T),
+// out[0..n]: three passes so that every load is coalesced.  The counts are
+// cut into kScanSeg segments; each block sums one segment in tiles of
+// kScanThreads consecutive entries (k_scan_sums), one block scans the
+// segment sums (k_scan_offsets), and each block then scans its segment tile
+// by tile (warp shuffles, then the warp totals), adding the segment's offset
+// and the running tile carry (k_scan_write).  Integer adds: exact, any order.
 constexpr int kScanThreads = 1024;
-__global__ void __launch_bounds__(kScanThreads) k_scan_counts(int64_t n, const int32_t* __restrict__ cnt,
-                                                              int32_t* __restrict__ out) {
-  __shared__ int64_t part[kScanThreads];
-  const int t = threadIdx.x;
-  const int64_t chunk = (n + kScanThreads - 1) / kScanThreads;
-  const int64_t lo = std::min<int64_t>(n, (int64_t)t * chunk), hi = std::min<int64_t>(n, lo + chunk);
-  int64_t sum = 0;
-  for (int64_t i = lo; i < hi; ++i) sum += cnt[i];
-  part[t] = sum;
+constexpr int kScanSeg = 512;
+
+__device__ __forceinline__ int64_t block_incl_scan(int64_t v, int64_t* warp_tot) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int64_t y = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += y;
+  }
+  if (lane == 31) warp_tot[warp] = v;
   __syncthreads();
-  for (int off = 1; off < kScanThreads; off <<= 1) {
-    const int64_t v = t >= off ? part[t - off] : 0;
+  if (warp == 0) {
+    int64_t w = lane < kScanThreads / 32 ? warp_tot[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int64_t y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += y;
+    }
+    if (lane < kScanThreads / 32) warp_tot[lane] = w;   // inclusive over warps
+  }
+  __syncthreads();
+  const int64_t r = v + (warp > 0 ? warp_tot[warp - 1] : 0);
+  __syncthreads();   // warp_tot is reused by the next call
+  return r;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_sums(int64_t n, const int32_t* __restrict__ cnt,
+                                                            int64_t* __restrict__ seg_sum) {
+  __shared__ int64_t red[kScanThreads / 32];
+  const int64_t per = (n + kScanSeg - 1) / kScanSeg;
+  const int64_t lo = std::min<int64_t>(n, (int64_t)blockIdx.x * per), hi = std::min<int64_t>(n, lo + per);
+  int64_t s = 0;
+  for (int64_t i = lo + threadIdx.x; i < hi; i += kScanThreads) s += cnt[i];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int64_t t = 0;
+    for (int w = 0; w < kScanThreads / 32; ++w) t += red[w];
+    seg_sum[blockIdx.x] = t;
+  }
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_offsets(int64_t* seg_sum) {
+  __shared__ int64_t wt[kScanThreads / 32];
+  const int64_t v = threadIdx.x < kScanSeg ? seg_sum[threadIdx.x] : 0;
+  const int64_t incl = block_incl_scan(v, wt);
+  if (threadIdx.x < kScanSeg) seg_sum[threadIdx.x] = incl - v;   // exclusive
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_write(int64_t n, const int32_t* __restrict__ cnt,
+                                                             const int64_t* __restrict__ seg_off,
+                                                             int32_t* __restrict__ out) {
+  __shared__ int64_t wt[kScanThreads / 32];
+  __shared__ int64_t carry;
+  const int64_t per = (n + kScanSeg - 1) / kScanSeg;
+  const int64_t lo = std::min<int64_t>(n, (int64_t)blockIdx.x * per), hi = std::min<int64_t>(n, lo + per);
+  if (threadIdx.x == 0) carry = seg_off[blockIdx.x];
+  __syncthreads();
+  for (int64_t base = lo; base < hi; base += kScanThreads) {
+    const int64_t i = base + threadIdx.x;
+    const int64_t v = i < hi ? cnt[i] : 0;
+    const int64_t incl = block_incl_scan(v, wt);
+    const int64_t c = carry;
+    if (i < hi) out[i] = (int32_t)(c + incl - v);
     __syncthreads();
-    part[t] += v;
+    if (threadIdx.x == kScanThreads - 1) carry = c + incl;
     __syncthreads();
   }
-  int64_t run = part[t] - sum;   // exclusive prefix of this chunk
-  for (int64_t i = lo; i < hi; ++i) {
-    out[i] = (int32_t)run;
-    run += cnt[i];
-  }
-  if (t == kScanThreads - 1) out[n] = (int32_t)part[t];
+  if (blockIdx.x == kScanSeg - 1 && threadIdx.x == 0) out[n] = (int32_t)carry;
 }
 
 // Entries of one row of A^T arrive in arbitrary order; sort each row by its
@@ -356,8 +407,17 @@ int csr_transpose(int64_t n, int64_t nnz, const int32_t* row_ptr, const int32_t*
     k_col_count<<<g, kBlock, 0, s>>>(nnz, col, cnt);
     RB_CUDA_TRY(cudaGetLastError());
   }
-  k_scan_counts<<<1, kScanThreads, 0, s>>>(n, cnt, t_row_ptr);
-  RB_CUDA_TRY(cudaGetLastError());
+  {
+    DeviceScratch segs;
+    RB_CUDA_TRY(cudaMalloc(&segs.p, sizeof(int64_t) * kScanSeg));
+    int64_t* seg = static_cast<int64_t*>(segs.p);
+    count_launches(3);
+    k_scan_sums<<<kScanSeg, kScanThreads, 0, s>>>(n, cnt, seg);
+    k_scan_offsets<<<1, kScanThreads, 0, s>>>(seg);
+    k_scan_write<<<kScanSeg, kScanThreads, 0, s>>>(n, cnt, seg, t_row_ptr);
+    RB_CUDA_TRY(cudaGetLastError());
+    RB_CUDA_TRY(cudaStreamSynchronize(s));   // the scratch is freed at the end of this scope
+  }
   RB_CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (n + 1), s));
   int g = (int)std::min<int64_t>((n + kBlock - 1) / kBlock + 1, 16384);
   k_scatter_t<<<g, kBlock, 0, s>>>(n, row_ptr, col, t_row_ptr, cnt, t_col, t_src);
