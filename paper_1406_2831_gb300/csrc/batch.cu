@@ -83,7 +83,11 @@ __device__ __forceinline__ bool tile_active(const IterState* st, bool skip_half)
 // After block_sum: sm.res[0..nv) are the tile's totals.  Stores the tile's
 // partial row and counts it; returns true in every thread of the CTA that
 // completed the system's last tile, with sm.res[0..nv) then holding the
-// system's totals, summed in tile order.  The ticket is back at 0 after.
+// system's totals.  That CTA sums the system's nt partial rows with all its
+// threads: thread i takes tiles i, i + blockDim, ... in order, a fixed
+// shuffle tree adds the threads of a warp and the warps are added in order
+// (deterministic; a system split into many tiles no longer holds one thread
+// for nt dependent loads).  The ticket is back at 0 after.
 template <int NV>
 __device__ bool tile_commit(ReduceCore<NV>& sm, int nv, double* partials, int t, unsigned* ticket, int t0,
                             int nt) {
@@ -97,9 +101,18 @@ __device__ bool tile_commit(ReduceCore<NV>& sm, int nv, double* partials, int t,
   __syncthreads();
   if (!s_last) return false;
   __threadfence();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int v = 0; v < nv; ++v) {
+    double acc = 0.0;
+    for (int q = threadIdx.x; q < nt; q += blockDim.x) acc += __ldcg(partials + (size_t)(t0 + q) * kBNV + v);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if (lane == 0) sm.w[warp][v] = acc;
+  }
+  __syncthreads();
   for (int v = threadIdx.x; v < nv; v += blockDim.x) {
     double acc = 0.0;
-    for (int q = 0; q < nt; ++q) acc += __ldcg(partials + (size_t)(t0 + q) * kBNV + v);
+    for (int w = 0; w < kBlock / 32; ++w) acc += sm.w[w][v];
     sm.res[v] = acc;
   }
   if (threadIdx.x == 0) *ticket = 0u;
@@ -956,14 +969,26 @@ namespace rb {
 namespace {
 
 // Autotuner: time the SpMV + projection pass (P1) for each candidate tile size
-// and CTAs per SM on the current matrices and space; keep the fastest.
-// RB_TIMING in the environment prints every candidate.
+// and CTAs per SM on the current matrices and space, every system active,
+// and keeps the fastest configuration that gives every block of P1 at least
+// kTilesPerBlock tiles (the fastest overall when none does): systems converge
+// at different times, and the tiles of those still iterating must stay
+// spread over many blocks, which the all-active timing does not see (256
+// systems of the 2D sweep: 512-slice tiles, 1.2 per block, timed 2% faster
+// than 128-slice tiles, 4.6 per block, but solved 6-16% slower).  RB_TIMING
+// in the environment prints every candidate.
 int autotune(rb_batch_ctx* h) {
-  const int cand_ts[] = {4, 8, 16, 32, 64, 128, 256};
+  const int cand_ts[] = {16, 32, 64, 128, 256, 512, 1024};
   const int cand_cps[] = {2, 4, 8};
   const bool print = getenv("RB_TIMING") != nullptr;
+  constexpr int kTilesPerBlock = 4;
+  struct Cand {
+    int ts, cps;
+    double ms;
+    bool spread;
+  };
+  std::vector<Cand> cands;
   double best = 1e30;
-  int bts = 8, bcps = 4;
   cudaEvent_t e0, e1;
   RB_CUDA_TRY(cudaEventCreate(&e0));
   RB_CUDA_TRY(cudaEventCreate(&e1));
@@ -997,16 +1022,24 @@ int autotune(rb_batch_ctx* h) {
       }
       const double avg = total / 3.0;
       if (print) fprintf(stderr, "rb_batch_tune tile_slices %3d ctas_per_sm %d tiles %7d  %.4f ms\n", ts, cps, h->ntiles, avg);
-      if (avg < best) {
-        best = avg;
-        bts = ts;
-        bcps = cps;
-      }
+      const int g1 = f32 ? grids_of<float>(h).g[0] : grids_of<double>(h).g[0];
+      const bool spread = h->ntiles >= kTilesPerBlock * g1;
+      cands.push_back({ts, cps, avg, spread});
+      if (spread) best = std::min(best, avg);
     }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  h->tune_ms = best;
+  const bool any_spread = best < 1e30;
+  int bts = cands[0].ts, bcps = cands[0].cps;
+  double bms = 1e30;
+  for (const Cand& c : cands)
+    if ((c.spread || !any_spread) && c.ms < bms) {
+      bms = c.ms;
+      bts = c.ts;
+      bcps = c.cps;
+    }
+  h->tune_ms = bms;
   RB_CUDA_TRY(cudaMemsetAsync(h->st, 0, sizeof(IterState) * h->S, h->us));
   return build_tiles(h, bts, bcps);
 }
