@@ -345,9 +345,12 @@ __device__ __forceinline__ void spmv_multi(const IterArgs<T>& a, const T* const*
   Acc<T> accr1[R], accd1[R][4], accp1[R][CPL];   // R = 1
   AccP<T> accr[H], accd[H][4], accp[H][CPL];      // pairs
   // width, first entry and column offset `lane` of the warp's next slice.
-  // Stencil slices take the offset path for FP32 data only: the FP64
-  // instantiations measured slower with it (more register spills).
-  constexpr bool kOffsets = sizeof(T) == 4;
+  // Stencil slices take the offset path for FP32 data and for one FP64
+  // right-hand side; FP64 blocks measured slower with it (more register
+  // spills: 7-point 128^3, four RHS, 29.2 -> 26.8 solves/s), while one FP64
+  // RHS has no spills either way and needs it on wide stencils (27-point:
+  // plain FP64 sequence 2.95 s with it, 3.82 s without).
+  constexpr bool kOffsets = sizeof(T) == 4 || R == 1;
   const int ostride = a.A.offs_stride;
   int wn = 0;
   int64_t en = 0;
