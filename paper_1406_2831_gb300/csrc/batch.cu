@@ -10,20 +10,21 @@
 // CTA takes tiles in grid-stride order; for each it forms the pass's vector
 // updates and its contribution to the pass's dot products, writes one
 // partial row per tile and counts the tile on its system's ticket.  The CTA
-// that completes a system's last tile adds that system's tile rows in tile
-// order (deterministic) and runs the scalar step of Alg. 2 for that system
-// (the same device functions as the single-system passes).  Systems that
-// have converged or failed skip their tiles.  The iteration loop is captured
-// as a CUDA graph of `poll` iterations.  The tile size and the number of
-// CTAs per SM are chosen by timing the SpMV + projection pass on the batch
-// (autotuner, logged on request).
+// that completes a system's last tile adds that system's tile rows with all
+// its threads in a fixed order (deterministic) and runs the scalar step of
+// Alg. 2 for that system (the same device functions as the single-system
+// passes).  Systems that have converged or failed skip their tiles.  The
+// iteration loop is captured as a CUDA graph of `poll` iterations.  The tile
+// size and the number of CTAs per SM are chosen by timing the SpMV +
+// projection pass on the batch (autotuner, logged on request).
 //
 // Each system may carry a fixed recycle space of k <= 16 columns (U~ = U,
 // the right-only variant of Sec. 5), set up per system as in Sec. 3
 // (C = A U, C~ = A^T U, M = C~^T C, C-hat = C~ (M^+)^T).  The inner
 // iteration runs in FP64 or, in the mixed mode, in FP32 with Dot2-compensated
-// dot products; the mixed mode refines in FP64: it restarts the recycled
-// FP32 solve on the FP64 residual b - A x until ||b - A x|| <= tol ||b||.
+// dot products and FP64 residual replacement per system (folds of the FP32
+// increment into the FP64 x, masked per system); a system whose FP32
+// iteration stalls, breaks down or overflows is finished in FP64 rounds.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
